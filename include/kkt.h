@@ -1,0 +1,181 @@
+/*
+ * kkt.h -- C ABI of the GPU-resident refactorization + FGMRES KKT solver
+ * (B300, sm_103a).  Method: arXiv 2401.13926.
+ *
+ * The solver targets a sequence of linear systems K_k x_k = r_k that share
+ * one sparsity pattern (Section 1.2, Eq. (kktlinear) and its Summary).  The
+ * four solver steps of Section 1.3 map to this interface as follows:
+ *   1. symbolic decomposition  -> kkt_analyze (host, once per pattern)
+ *   2. numeric decomposition   -> kkt_analyze (first matrix, with pivoting,
+ *                                 host) and kkt_refactor (every later matrix,
+ *                                 fixed pivots, GPU)
+ *   3. triangular solve        -> kkt_solve (GPU), kkt_lu_solve (GPU)
+ *   4. iterative refinement    -> kkt_solve: FGMRES with the LU factors as
+ *                                 right preconditioner, CGS2, estimated
+ *                                 residual, solution formed at restart or
+ *                                 convergence (Section 2.1), refine-or-not
+ *                                 test of Section 2.3, stopping rules of
+ *                                 Section 2.2.
+ *
+ * Conventions
+ *   - Matrices: CSR, 0-based, int32 indices, FP64 values, square n x n, the
+ *     full matrix (both triangles).  Rows need not be sorted; duplicates and
+ *     out-of-range indices are rejected with KKT_ERR_PATTERN.
+ *   - Permutations: B = K(P, Q), B[i][j] = K[P[i]][Q[j]]; B = L U with L unit
+ *     lower and U upper triangular.  P is the pivot sequence, Q the column
+ *     (fill-reducing) order.
+ *   - Ownership: the caller owns every buffer it passes; no pointer is kept
+ *     after a call returns.  The context owns all device memory; it is
+ *     allocated in kkt_analyze only, never in kkt_refactor or kkt_solve
+ *     (buffer reuse across the sequence, Section 2.1).
+ *   - Streams: every device operation of a context is ordered on its stream
+ *     (kkt_opts.stream, or a stream the context creates).  Calls return after
+ *     their results are complete (host-visible scalars are read back).
+ *   - Errors: every call returns KKT_OK (0) or a negative KKT_ERR_* code.
+ *     kkt_strerror gives a message; kkt_last_error_detail gives detail for
+ *     the context's last failure (for example the offending row).
+ *   - Thread safety: one context must not be used from two threads at once.
+ */
+#ifndef KKT_B300_H
+#define KKT_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KKT_OK 0
+#define KKT_ERR_INVALID (-1)        /* bad argument or option */
+#define KKT_ERR_PATTERN (-2)        /* malformed or mismatched sparsity pattern */
+#define KKT_ERR_OOM (-3)            /* device or host allocation failed */
+#define KKT_ERR_ZERO_PIVOT (-4)     /* exact zero (or structurally missing) pivot */
+#define KKT_ERR_NONFINITE (-5)      /* NaN/Inf in values or factors */
+#define KKT_ERR_NOT_CONVERGED (-6)  /* refinement hit max_cycles; x, iters, nrbe still valid */
+#define KKT_ERR_TIMEOUT (-7)        /* a bounded device wait ran out */
+#define KKT_ERR_CUDA (-8)           /* CUDA runtime error */
+#define KKT_ERR_STATE (-9)          /* call out of order (e.g. solve before refactor) */
+
+#define KKT_STOP_NRBE 0   /* Eq. (nbre) <= tol, checked on the true residual */
+#define KKT_STOP_RR 1     /* estimated ||rho_i|| < tol ||rho_0|| (the paper's rule) */
+
+typedef struct kkt_ctx kkt_ctx;
+
+typedef struct {
+    int restart;          /* FGMRES restart length m (default 20, 1..64) */
+    int max_cycles;       /* restart cycles before KKT_ERR_NOT_CONVERGED (default 50) */
+    int stop_mode;        /* KKT_STOP_NRBE (default) or KKT_STOP_RR */
+    int precision;        /* 0 = FP64 (default); others reserved */
+    double refine_delta;  /* Section 2.3: skip refinement if ||r - K x0|| < delta ||r||; 0 = off */
+    double pivot_tol;     /* threshold partial pivoting in kkt_analyze (default 1e-3) */
+    double boost_eps;     /* static-pivot boost: |u_jj| < boost_eps ||K||_inf becomes
+                             sign(u_jj) boost_eps ||K||_inf (sign(0)=+1); 0 = off (default),
+                             then an exact zero pivot is KKT_ERR_ZERO_PIVOT */
+    int device;           /* CUDA device ordinal (default 0) */
+    void* stream;         /* cudaStream_t to use; NULL = the context creates its own */
+    int64_t spin_limit;   /* polls before a device wait gives up (KKT_ERR_TIMEOUT); 0 = default */
+} kkt_opts;
+
+typedef struct {
+    int32_t n;
+    int64_t nnz_a;         /* stored entries of K */
+    int64_t nnz_l;         /* strictly lower entries of L */
+    int64_t nnz_u;         /* entries of U including the diagonal */
+    int32_t levels_l;      /* depth of the L-solve dependency DAG */
+    int32_t levels_u;      /* depth of the U-solve dependency DAG */
+    double refactor_updates; /* multiply-adds of one refactorization */
+    int64_t device_bytes;  /* device memory held by the context */
+    int32_t nboost;        /* pivots boosted by the last kkt_refactor */
+    int32_t last_iters;    /* FGMRES iterations of the last kkt_solve */
+    int32_t last_cycles;   /* restart cycles of the last kkt_solve */
+    double last_nrbe;      /* NRBE of the last kkt_solve's x */
+    double last_rnorm0;    /* ||r - K x0|| of the last kkt_solve */
+    double norm_a_inf;     /* ||K||_inf of the last refactored matrix */
+    double analyze_ms;     /* host time of kkt_analyze */
+} kkt_info;
+
+/* Fill *o with the defaults above. */
+void kkt_default_opts(kkt_opts* o);
+
+/* Create a context on o->device (o may be NULL for defaults). */
+int kkt_create(kkt_ctx** out, const kkt_opts* o);
+
+/*
+ * One-time analysis of the pattern (Section 1.3 steps 1-2 for the first
+ * system; Section 3.1.1: the first factorization runs on the CPU).
+ *   n, rowptr[n+1], colind[nnz]: host CSR pattern of K.
+ *   values0[nnz] (host): the matrix whose numeric factorization picks the
+ *     pivots; may be NULL only when P is given.
+ *   Q[n] (host, optional): column order; NULL = computed on the host
+ *     (approximate minimum degree on the pattern of K^T K).
+ *   P[n] (host, optional): pivot sequence; NULL = threshold partial pivoting
+ *     on values0 with opts.pivot_tol.
+ * Allocates every device buffer the context will use.  Can be called again
+ * on the same context for a new pattern (buffers are re-made).
+ */
+int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* colind,
+                const double* values0, const int32_t* Q, const int32_t* P);
+
+/*
+ * Numeric refactorization on the fixed pattern, P and Q (Section 1.3
+ * definition of refactorization; Section 2.1).  values[nnz] in the caller's
+ * order of kkt_analyze; host memory if values_on_device == 0, else a device
+ * pointer on the context's device.  Also computes ||K||_inf for the NRBE.
+ * Errors: KKT_ERR_ZERO_PIVOT, KKT_ERR_NONFINITE, KKT_ERR_TIMEOUT.
+ */
+int kkt_refactor(kkt_ctx* c, const double* values, int values_on_device);
+
+/*
+ * Solve K x = b with the current factors (Sections 2.1-2.3):
+ * x0 = Q U^{-1} L^{-1} P b; if refinement is needed, FGMRES(m) with M = LU
+ * as right preconditioner until the stopping rule holds.
+ *   b[n], x[n]: host arrays if on_device == 0, else device pointers.
+ *   tol: NRBE tolerance (KKT_STOP_NRBE) or RR tolerance (KKT_STOP_RR).
+ *   iters (out, may be NULL): Arnoldi steps taken (preconditioner applies
+ *     after x0); nrbe (out, may be NULL): Eq. (nbre) of the returned x.
+ * On KKT_ERR_NOT_CONVERGED x, iters and nrbe are still written.
+ */
+int kkt_solve(kkt_ctx* c, const double* b, double* x, int on_device, double tol,
+              int* iters, double* nrbe);
+
+/* x = Q U^{-1} L^{-1} P b only (Section 1.3 step 3), no refinement. */
+int kkt_lu_solve(kkt_ctx* c, const double* b, double* x, int on_device);
+
+/* y = K x with the values of the last kkt_refactor. */
+int kkt_matvec(kkt_ctx* c, const double* x, double* y, int on_device);
+
+/* Copy the permutations (host arrays of n). */
+int kkt_get_perm(kkt_ctx* c, int32_t* P, int32_t* Q);
+
+/* Sizes of the factors: nnz of strict L and of U (with diagonal). */
+int kkt_get_factor_sizes(kkt_ctx* c, int64_t* nnz_l, int64_t* nnz_u);
+
+/*
+ * Host copies of the current factors in CSC, permuted space, rows sorted:
+ * L strictly lower (Lp[n+1], Li/Lx[nnz_l]), U with diagonal (Up[n+1],
+ * Ui/Ux[nnz_u]).  For tests and inspection.
+ */
+int kkt_get_factors(kkt_ctx* c, int64_t* Lp, int32_t* Li, double* Lx,
+                    int64_t* Up, int32_t* Ui, double* Ux);
+
+int kkt_query(kkt_ctx* c, kkt_info* info);
+void kkt_destroy(kkt_ctx* c);
+const char* kkt_strerror(int code);
+const char* kkt_last_error_detail(kkt_ctx* c);
+
+/* ---- host-only helpers (no GPU needed) ---- */
+
+/* Column order of kkt_analyze (approximate minimum degree on K^T K). */
+int kkt_order(int32_t n, const int32_t* rowptr, const int32_t* colind, int32_t* Q);
+
+/*
+ * First factorization with threshold partial pivoting on the host, as
+ * kkt_analyze does it: returns the pivot sequence P and the factor sizes.
+ */
+int kkt_pivot(int32_t n, const int32_t* rowptr, const int32_t* colind, const double* values,
+              const int32_t* Q, double pivot_tol, int32_t* P, int64_t* nnz_l, int64_t* nnz_u);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KKT_B300_H */
