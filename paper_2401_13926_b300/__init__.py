@@ -1,0 +1,255 @@
+"""GPU-resident refactorization + FGMRES solver for same-pattern KKT sequences
+on B300 (sm_103a), after arXiv 2401.13926.
+
+Thin ctypes binding over the C ABI of ``libkkt_b300.so`` (include/kkt.h):
+argument marshalling only -- every numeric step runs in the library's CUDA
+kernels.  Arrays may be numpy arrays (host memory) or CUDA tensors
+(device memory, passed by ``data_ptr()``); PyTorch is only plumbing.
+
+There is no CPU fallback: if the library is missing or cannot load, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+__all__ = ["KKTSolver", "KKTError", "order", "pivot", "lib", "LIB_PATH", "EXPORTS"]
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libkkt_b300.so")
+
+OK = 0
+ERR = {
+    -1: "INVALID", -2: "PATTERN", -3: "OOM", -4: "ZERO_PIVOT", -5: "NONFINITE",
+    -6: "NOT_CONVERGED", -7: "TIMEOUT", -8: "CUDA", -9: "STATE",
+}
+ERR_NOT_CONVERGED = -6
+STOP = {"nrbe": 0, "rr": 1}
+
+# every entry point declared in include/kkt.h
+EXPORTS = [
+    "kkt_default_opts", "kkt_create", "kkt_analyze", "kkt_refactor", "kkt_solve", "kkt_lu_solve",
+    "kkt_matvec", "kkt_get_perm", "kkt_get_factor_sizes", "kkt_get_factors", "kkt_query",
+    "kkt_destroy", "kkt_strerror", "kkt_last_error_detail", "kkt_order", "kkt_pivot",
+]
+
+
+class _Opts(C.Structure):
+    _fields_ = [
+        ("restart", C.c_int), ("max_cycles", C.c_int), ("stop_mode", C.c_int), ("precision", C.c_int),
+        ("refine_delta", C.c_double), ("pivot_tol", C.c_double), ("boost_eps", C.c_double),
+        ("device", C.c_int), ("stream", C.c_void_p), ("spin_limit", C.c_int64),
+    ]
+
+
+class _Info(C.Structure):
+    _fields_ = [
+        ("n", C.c_int32), ("nnz_a", C.c_int64), ("nnz_l", C.c_int64), ("nnz_u", C.c_int64),
+        ("levels_l", C.c_int32), ("levels_u", C.c_int32), ("refactor_updates", C.c_double),
+        ("device_bytes", C.c_int64), ("nboost", C.c_int32), ("last_iters", C.c_int32),
+        ("last_cycles", C.c_int32), ("last_nrbe", C.c_double), ("last_rnorm0", C.c_double),
+        ("norm_a_inf", C.c_double), ("analyze_ms", C.c_double),
+    ]
+
+
+class KKTError(RuntimeError):
+    def __init__(self, code, where, detail=""):
+        super().__init__(f"{where}: KKT_ERR_{ERR.get(code, code)} ({code}) {detail}".strip())
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libkkt_b300.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing; build it with `python -m paper_2401_13926_b300.build`")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, d, ip = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_int
+    L.kkt_default_opts.argtypes = [C.POINTER(_Opts)]
+    L.kkt_default_opts.restype = None
+    L.kkt_create.argtypes = [C.POINTER(vp), C.POINTER(_Opts)]
+    L.kkt_analyze.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    L.kkt_refactor.argtypes = [vp, vp, ip]
+    L.kkt_solve.argtypes = [vp, vp, vp, ip, d, C.POINTER(C.c_int), C.POINTER(d)]
+    L.kkt_lu_solve.argtypes = [vp, vp, vp, ip]
+    L.kkt_matvec.argtypes = [vp, vp, vp, ip]
+    L.kkt_get_perm.argtypes = [vp, vp, vp]
+    L.kkt_get_factor_sizes.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+    L.kkt_get_factors.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.kkt_query.argtypes = [vp, C.POINTER(_Info)]
+    L.kkt_destroy.argtypes = [vp]
+    L.kkt_destroy.restype = None
+    L.kkt_strerror.argtypes = [ip]
+    L.kkt_strerror.restype = C.c_char_p
+    L.kkt_last_error_detail.argtypes = [vp]
+    L.kkt_last_error_detail.restype = C.c_char_p
+    L.kkt_order.argtypes = [i32, vp, vp, vp]
+    L.kkt_pivot.argtypes = [i32, vp, vp, vp, vp, d, vp, C.POINTER(i64), C.POINTER(i64)]
+    for name in EXPORTS:
+        if name not in ("kkt_default_opts", "kkt_destroy", "kkt_strerror", "kkt_last_error_detail"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data
+
+
+def _is_device(a):
+    return hasattr(a, "data_ptr") and getattr(a, "is_cuda", False)
+
+
+def _ptr(a, dtype):
+    """(keepalive, pointer, on_device) for a numpy array or a CUDA tensor."""
+    if _is_device(a):
+        if not a.is_contiguous():
+            raise ValueError("device arrays must be contiguous")
+        return a, a.data_ptr(), 1
+    h, p = _host(a, dtype)
+    return h, p, 0
+
+
+def order(rowptr, colind):
+    """Column order Q of kkt_analyze (approximate minimum degree on K^T K)."""
+    L = lib()
+    rp, prp = _host(rowptr, np.int32)
+    ci, pci = _host(colind, np.int32)
+    n = len(rp) - 1
+    Q = np.zeros(n, np.int32)
+    rc = L.kkt_order(n, prp, pci, Q.ctypes.data)
+    if rc:
+        raise KKTError(rc, "kkt_order")
+    return Q
+
+
+def pivot(rowptr, colind, values, Q=None, tol=1e-3):
+    """Host threshold-pivoting factorization: (P, nnz_l, nnz_u)."""
+    L = lib()
+    rp, prp = _host(rowptr, np.int32)
+    ci, pci = _host(colind, np.int32)
+    v, pv = _host(values, np.float64)
+    n = len(rp) - 1
+    q = None if Q is None else np.ascontiguousarray(Q, np.int32)
+    P = np.zeros(n, np.int32)
+    nl, nu = C.c_int64(), C.c_int64()
+    rc = L.kkt_pivot(n, prp, pci, pv, None if q is None else q.ctypes.data, float(tol), P.ctypes.data,
+                     C.byref(nl), C.byref(nu))
+    if rc:
+        raise KKTError(rc, "kkt_pivot")
+    return P, nl.value, nu.value
+
+
+class KKTSolver:
+    """One solver context: analyze once per pattern, then refactor + solve for
+    every matrix of the sequence (Sections 1.3 and 2.1)."""
+
+    def __init__(self, restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3,
+                 boost_eps=0.0, device=0, stream=None, spin_limit=0):
+        L = lib()
+        o = _Opts()
+        L.kkt_default_opts(C.byref(o))
+        o.restart, o.max_cycles, o.stop_mode = int(restart), int(max_cycles), STOP[stop_mode]
+        o.refine_delta, o.pivot_tol, o.boost_eps = float(refine_delta), float(pivot_tol), float(boost_eps)
+        o.device, o.spin_limit = int(device), int(spin_limit)
+        o.stream = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        h = C.c_void_p()
+        rc = L.kkt_create(C.byref(h), C.byref(o))
+        if rc:
+            raise KKTError(rc, "kkt_create")
+        self._h = h
+        self.n = 0
+        self.nnz = 0
+
+    def _check(self, rc, where, ok=(OK,)):
+        if rc not in ok:
+            raise KKTError(rc, where, lib().kkt_last_error_detail(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().kkt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def analyze(self, rowptr, colind, values0=None, Q=None, P=None):
+        rp, prp = _host(rowptr, np.int32)
+        ci, pci = _host(colind, np.int32)
+        v = None if values0 is None else _host(values0, np.float64)
+        q = None if Q is None else _host(Q, np.int32)
+        p = None if P is None else _host(P, np.int32)
+        n = len(rp) - 1
+        self._check(lib().kkt_analyze(self._h, n, prp, pci, v[1] if v else None, q[1] if q else None,
+                                      p[1] if p else None), "kkt_analyze")
+        self.n, self.nnz = n, int(rp[-1])
+        return self
+
+    def refactor(self, values):
+        keep, p, dev = _ptr(values, np.float64)
+        self._check(lib().kkt_refactor(self._h, p, dev), "kkt_refactor")
+
+    def solve(self, b, x=None, tol=1e-12, allow_not_converged=False):
+        """Returns (x, iters, nrbe).  x is written in place when given."""
+        kb, pb, dev = _ptr(b, np.float64)
+        if x is None:
+            x = b.new_empty(self.n) if dev else np.zeros(self.n)
+        kx, px, devx = _ptr(x, np.float64)
+        if devx != dev:
+            raise ValueError("b and x must both be host or both be device arrays")
+        it, nr = C.c_int(), C.c_double()
+        ok = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
+        rc = self._check(lib().kkt_solve(self._h, pb, px, dev, float(tol), C.byref(it), C.byref(nr)), "kkt_solve", ok)
+        self.last_status = rc
+        return x, it.value, nr.value
+
+    def lu_solve(self, b, x=None):
+        kb, pb, dev = _ptr(b, np.float64)
+        if x is None:
+            x = b.new_empty(self.n) if dev else np.zeros(self.n)
+        kx, px, _ = _ptr(x, np.float64)
+        self._check(lib().kkt_lu_solve(self._h, pb, px, dev), "kkt_lu_solve")
+        return x
+
+    def matvec(self, x, y=None):
+        kx, px, dev = _ptr(x, np.float64)
+        if y is None:
+            y = x.new_empty(self.n) if dev else np.zeros(self.n)
+        ky, py, _ = _ptr(y, np.float64)
+        self._check(lib().kkt_matvec(self._h, px, py, dev), "kkt_matvec")
+        return y
+
+    def perm(self):
+        P = np.zeros(self.n, np.int32)
+        Q = np.zeros(self.n, np.int32)
+        self._check(lib().kkt_get_perm(self._h, P.ctypes.data, Q.ctypes.data), "kkt_get_perm")
+        return P, Q
+
+    def factors(self):
+        """Host CSC copies: (Lp, Li, Lx) strictly lower, (Up, Ui, Ux) with diagonal."""
+        nl, nu = C.c_int64(), C.c_int64()
+        self._check(lib().kkt_get_factor_sizes(self._h, C.byref(nl), C.byref(nu)), "kkt_get_factor_sizes")
+        n = self.n
+        Lp, Up = np.zeros(n + 1, np.int64), np.zeros(n + 1, np.int64)
+        Li, Lx = np.zeros(max(nl.value, 1), np.int32), np.zeros(max(nl.value, 1))
+        Ui, Ux = np.zeros(max(nu.value, 1), np.int32), np.zeros(max(nu.value, 1))
+        self._check(lib().kkt_get_factors(self._h, Lp.ctypes.data, Li.ctypes.data, Lx.ctypes.data,
+                                          Up.ctypes.data, Ui.ctypes.data, Ux.ctypes.data), "kkt_get_factors")
+        return dict(Lp=Lp, Li=Li[:nl.value], Lx=Lx[:nl.value], Up=Up, Ui=Ui[:nu.value], Ux=Ux[:nu.value])
+
+    def info(self):
+        inf = _Info()
+        self._check(lib().kkt_query(self._h, C.byref(inf)), "kkt_query")
+        return {k: getattr(inf, k) for k, _ in _Info._fields_}

@@ -1,0 +1,549 @@
+// Device kernels of the refactor + triangular solve + FGMRES hot path.
+//
+// Layout in device memory (permuted space, B = K(P,Q) = L U):
+//   F  -- combined factor L + U - I, row-major: row i holds its columns in
+//         ascending order, L(i,k<i) first, then U(i,i) at Fdiag[i], then
+//         U(i,j>i).  Fp (int64, n+1), Fj (int32), Fx (double).
+//   A  -- K in canonical CSR (original space) for the residual and the
+//         products with K: Arp (int32, n+1), Aci (int32), Ax (double).
+//   V  -- Krylov basis, column-major n x (m+1), leading dimension ld;
+//   Z  -- preconditioned directions, n x m (flexible GMRES keeps them).
+//
+// Dependency waits (refactor and both triangular solves) are sync-free:
+// each warp takes the next row from an atomic ticket counter in dependency
+// order, so every row it waits on belongs to a warp that is already
+// running; completion flags hold a generation number so they never need
+// clearing.  Every wait is bounded: after `spin_limit` polls, or once any
+// warp has raised the abort flag, the warp records KKT_ERR_TIMEOUT and
+// returns.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "kkt.h"
+
+namespace kkt {
+
+constexpr int MAXM = 32;          // largest restart length
+constexpr int RED_SLOTS = MAXM + 2;
+constexpr int RED_BLOCKS = 296;   // blocks of the reduction kernels (2 per SM)
+constexpr int RED_THREADS = 256;
+
+struct DevScal {
+    // matrix and right-hand side
+    double normA;          // ||K||_inf of the last refactor
+    double normb;          // ||b||_2
+    // current iterate
+    double rnorm;          // ||b - K x||_2
+    double xnorm;          // ||x||_2
+    double rnorm0;         // ||b - K x0||_2 (rho^(0))
+    double nrbe;
+    double thresh;         // inner stopping threshold of the cycle
+    double hn;             // h_{j+1,j}
+    double g[MAXM + 1], cs[MAXM], sn[MAXM], y[MAXM];
+    double H[(MAXM + 1) * MAXM];   // column-major, leading dimension MAXM+1
+    double h[MAXM + 1], h2[MAXM + 1];
+    int j;                 // current Arnoldi column
+    int iters;             // Arnoldi steps of this solve
+    int met;               // inner criterion met in this cycle
+    int done;              // solve finished (converged or nothing to do)
+    // sync-free scheduling
+    unsigned gen_fact, gen_l, gen_u;
+    unsigned ticket_fact, ticket_l, ticket_u;
+    unsigned red_count;
+    // errors
+    int err;               // first error code (0 = none)
+    int err_row;
+    int abort;
+    int nboost;
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_int(const int* p) { return *(volatile const int*)p; }
+
+__device__ __forceinline__ void raise_error(DevScal* s, int code, int row) {
+    if (atomicCAS(&s->err, 0, code) == 0) s->err_row = row;
+    atomicExch(&s->abort, 1);
+}
+
+// Wait until flag == gen.  Returns false if the wait was abandoned.
+__device__ __forceinline__ bool wait_flag(const unsigned* flag, unsigned gen, DevScal* s, long long limit, int row) {
+    if (ld_acquire(flag) == gen) return true;
+    for (long long it = 0;; it++) {
+        if (ld_acquire(flag) == gen) return true;
+        if (ld_volatile_int(&s->abort)) return false;
+        if (it >= limit) { raise_error(s, KKT_ERR_TIMEOUT, row); return false; }
+        __nanosleep(64);
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum (all threads get the result); blockDim.x multiple of 32, <= 1024.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0) t = warp_sum(t);
+    if (threadIdx.x == 0) sh[32] = t;
+    __syncthreads();
+    return sh[32];
+}
+
+// The last block to arrive (deterministic fixed-order sum of the partials)
+// returns true in every thread of that block.
+__device__ __forceinline__ bool last_block(DevScal* s) {
+    __shared__ int is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(&s->red_count, 1u);
+        is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        if (threadIdx.x == 0) s->red_count = 0;
+    }
+    return is_last;
+}
+
+// Sum partials part[b * RED_SLOTS + slot] over blocks b, in block order.
+__device__ __forceinline__ double reduce_partials(const double* part, int slot, double* sh) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(&part[b * RED_SLOTS + slot]);
+    return block_sum(v, sh);
+}
+
+// ---------------------------------------------------------------- K0: gather
+// Start of a refactorization: new generation, tickets and error words.
+__global__ void k_refactor_prep(DevScal* s) {
+    s->gen_fact += 1;
+    s->ticket_fact = 0;
+    s->err = 0;
+    s->err_row = -1;
+    s->abort = 0;
+    s->nboost = 0;
+    s->normA = 0.0;
+}
+
+// Fx[t] = caller value of the entry of A that lands in factor slot t (0 for
+// fill); Ax[e] = caller value of canonical entry e; ||K||_inf from row sums.
+__global__ void k_gather(const double* __restrict__ vals, const int64_t* __restrict__ fsrc, int64_t nnzF,
+                         double* __restrict__ Fx, const int32_t* __restrict__ Arp,
+                         const int64_t* __restrict__ asrc, double* __restrict__ Ax, int n, DevScal* s) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = tid; t < nnzF; t += stride) {
+        int64_t q = fsrc[t];
+        Fx[t] = (q >= 0) ? vals[q] : 0.0;
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = tid >> 5, nwarps = stride >> 5;
+    double rmax = 0.0;
+    bool bad = false;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        double acc = 0.0;
+        for (int64_t e = Arp[i] + lane; e < Arp[i + 1]; e += 32) {
+            double v = vals[asrc ? asrc[e] : e];
+            Ax[e] = v;
+            if (!isfinite(v)) bad = true;
+            acc += fabs(v);
+        }
+        acc = warp_sum(acc);
+        rmax = fmax(rmax, acc);
+    }
+    if (bad) raise_error(s, KKT_ERR_NONFINITE, -1);
+    if (lane == 0 && rmax > 0.0)   // non-negative doubles order like their bit patterns
+        atomicMax((unsigned long long*)&s->normA, (unsigned long long)__double_as_longlong(rmax));
+}
+
+// ---------------------------------------------------------------- K1: refactor
+// Up-looking (row-by-row Doolittle) numeric LU on the fixed pattern: for row
+// i, in ascending k over L(i,:), l_ik = w_k / u_kk and w -= l_ik U(k,:).
+// One warp per row; lanes split the update of U(k,:) and find each target
+// column in row i by binary search.
+__device__ __forceinline__ int64_t find_col(const int32_t* __restrict__ Fj, int64_t lo, int64_t hi, int32_t c) {
+    // first position in [lo, hi) with Fj >= c
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldg(&Fj[mid]) < c) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
+                           const int64_t* __restrict__ Fdiag, double* Fx, unsigned* done, DevScal* s,
+                           double boost_eps, long long limit) {
+    const int lane = threadIdx.x & 31;
+    const unsigned gen = *(volatile unsigned*)&s->gen_fact;
+    const double boost = boost_eps * *(volatile double*)&s->normA;
+    for (;;) {
+        int row = 0;
+        if (lane == 0) row = (int)atomicAdd(&s->ticket_fact, 1u);
+        row = __shfl_sync(0xffffffffu, row, 0);
+        if (row >= n) return;
+        if (ld_volatile_int(&s->abort)) return;
+        const int64_t b = Fp[row], d = Fdiag[row], e = Fp[row + 1];
+        for (int64_t p = b; p < d; p++) {
+            const int32_t k = __ldg(&Fj[p]);
+            int ok = 1;
+            if (lane == 0) ok = wait_flag(&done[k], gen, s, limit, row);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) return;
+            __threadfence();
+            const int64_t dk = __ldg(&Fdiag[k]), ek = __ldg(&Fp[k + 1]);
+            const double lik = __ldcg(&Fx[p]) / __ldcg(&Fx[dk]);
+            __syncwarp();
+            if (lane == 0) __stcg(&Fx[p], lik);
+            for (int64_t q = dk + 1 + lane; q < ek; q += 32) {
+                const int32_t c = __ldg(&Fj[q]);
+                const int64_t pos = find_col(Fj, p + 1, e, c);
+                __stcg(&Fx[pos], __ldcg(&Fx[pos]) - lik * __ldcg(&Fx[q]));
+            }
+            __threadfence();
+            __syncwarp();
+        }
+        if (lane == 0) {
+            double u = __ldcg(&Fx[d]);
+            bool fail = false;
+            if (!isfinite(u)) { raise_error(s, KKT_ERR_NONFINITE, row); fail = true; }
+            else if (boost > 0.0) {
+                if (fabs(u) < boost) { u = (u < 0.0) ? -boost : boost; atomicAdd(&s->nboost, 1); __stcg(&Fx[d], u); }
+            } else if (u == 0.0) { raise_error(s, KKT_ERR_ZERO_PIVOT, row); fail = true; }
+            if (!fail) {
+                __threadfence();
+                st_release(&done[row], gen);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- K2/K3: triangular solves
+__global__ void k_trsv_prep(DevScal* s) {
+    s->gen_l += 1;
+    s->gen_u += 1;
+    s->ticket_l = 0;
+    s->ticket_u = 0;
+}
+
+// y = L^{-1} (P rhs): y_i = rhs[P[i]] - sum_{k<i} L_ik y_k, unit L.
+__global__ void k_lsolve(int n, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
+                         const int64_t* __restrict__ Fdiag, const double* __restrict__ Fx,
+                         const int32_t* __restrict__ P, const double* __restrict__ rhs, double* y,
+                         unsigned* done, DevScal* s, long long limit) {
+    const int lane = threadIdx.x & 31;
+    const unsigned gen = *(volatile unsigned*)&s->gen_l;
+    for (;;) {
+        int row = 0;
+        if (lane == 0) row = (int)atomicAdd(&s->ticket_l, 1u);
+        row = __shfl_sync(0xffffffffu, row, 0);
+        if (row >= n) return;
+        const int64_t b = Fp[row], d = Fdiag[row];
+        double acc = 0.0;
+        int ok = 1;
+        for (int64_t p = b + lane; p < d; p += 32) {
+            const int32_t k = __ldg(&Fj[p]);
+            if (!wait_flag(&done[k], gen, s, limit, row)) { ok = 0; break; }
+            acc += __ldg(&Fx[p]) * __ldcg(&y[k]);
+        }
+        if (!__all_sync(0xffffffffu, ok)) return;
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            __stcg(&y[row], rhs[P[row]] - acc);
+            __threadfence();
+            st_release(&done[row], gen);
+        }
+    }
+}
+
+// x' = U^{-1} y (rows descending), out[Q[i]] = x'_i.
+__global__ void k_usolve(int n, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
+                         const int64_t* __restrict__ Fdiag, const double* __restrict__ Fx,
+                         const int32_t* __restrict__ Q, const double* __restrict__ y, double* xp,
+                         double* __restrict__ out, unsigned* done, DevScal* s, long long limit) {
+    const int lane = threadIdx.x & 31;
+    const unsigned gen = *(volatile unsigned*)&s->gen_u;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = (int)atomicAdd(&s->ticket_u, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= n) return;
+        const int row = n - 1 - t;
+        const int64_t d = Fdiag[row], e = Fp[row + 1];
+        double acc = 0.0;
+        int ok = 1;
+        for (int64_t p = d + 1 + lane; p < e; p += 32) {
+            const int32_t j = __ldg(&Fj[p]);
+            if (!wait_flag(&done[j], gen, s, limit, row)) { ok = 0; break; }
+            acc += __ldg(&Fx[p]) * __ldcg(&xp[j]);
+        }
+        if (!__all_sync(0xffffffffu, ok)) return;
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            const double xi = (__ldcg(&y[row]) - acc) / __ldg(&Fx[d]);
+            __stcg(&xp[row], xi);
+            out[Q[row]] = xi;
+            __threadfence();
+            st_release(&done[row], gen);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- K4: products with K
+// 8 lanes per row; all 8 lanes of a group share `row` and `active`.
+__device__ __forceinline__ double row_dot8(const int32_t* __restrict__ Arp, const int32_t* __restrict__ Aci,
+                                           const double* __restrict__ Ax, const double* __restrict__ x, int row,
+                                           int sub, bool active) {
+    double acc = 0.0;
+    if (active)
+        for (int e = Arp[row] + sub; e < Arp[row + 1]; e += 8) acc += Ax[e] * __ldcg(&x[Aci[e]]);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+// w = K z
+__global__ void k_spmv(int n, const int32_t* __restrict__ Arp, const int32_t* __restrict__ Aci,
+                       const double* __restrict__ Ax, const double* __restrict__ z, double* __restrict__ w) {
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    const int sub = threadIdx.x & 7;
+    const int64_t rows_per_pass = ((int64_t)gridDim.x * blockDim.x) >> 3;
+    const int64_t trips = (n + rows_per_pass - 1) / rows_per_pass;
+    for (int64_t t = 0; t < trips; t++) {
+        const int64_t base = (g >> 3) + t * rows_per_pass;
+        const bool active = base < n;
+        const int row = active ? (int)base : 0;
+        const double v = row_dot8(Arp, Aci, Ax, z, row, sub, active);
+        if (active && sub == 0) w[row] = v;
+    }
+}
+
+// r = b - K x, with ||r||^2, ||x||^2 and ||b||^2 reduced into s (rnorm,
+// xnorm, normb).  mode 0: also sets rnorm0 and the refine decision of the
+// initial solve; mode 1: cycle end (true residual of the formed x).
+__global__ void k_residual(int n, const int32_t* __restrict__ Arp, const int32_t* __restrict__ Aci,
+                           const double* __restrict__ Ax, const double* __restrict__ b,
+                           const double* __restrict__ x, double* __restrict__ r, double* part, DevScal* s) {
+    __shared__ double sh[33];
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    const int sub = threadIdx.x & 7;
+    const int64_t rows_per_pass = ((int64_t)gridDim.x * blockDim.x) >> 3;
+    double rr = 0.0, xx = 0.0, bb = 0.0;
+    const int64_t first = g >> 3;
+    const int64_t trips = (n + rows_per_pass - 1) / rows_per_pass;
+    for (int64_t t = 0; t < trips; t++) {
+        const int64_t base = first + t * rows_per_pass;
+        const bool active = base < n;
+        const int row = active ? (int)base : 0;
+        double v = row_dot8(Arp, Aci, Ax, x, row, sub, active);
+        if (active && sub == 0) {
+            const double ri = b[row] - v;
+            r[row] = ri;
+            rr += ri * ri;
+            const double xi = __ldcg(&x[row]);
+            xx += xi * xi;
+            bb += b[row] * b[row];
+        }
+    }
+    rr = block_sum(rr, sh);
+    xx = block_sum(xx, sh);
+    bb = block_sum(bb, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x * RED_SLOTS + 0] = rr;
+        part[blockIdx.x * RED_SLOTS + 1] = xx;
+        part[blockIdx.x * RED_SLOTS + 2] = bb;
+    }
+    if (!last_block(s)) return;
+    rr = reduce_partials(part, 0, sh);
+    xx = reduce_partials(part, 1, sh);
+    bb = reduce_partials(part, 2, sh);
+    if (threadIdx.x == 0) {
+        s->rnorm = sqrt(rr);
+        s->xnorm = sqrt(xx);
+        s->normb = sqrt(bb);
+    }
+}
+
+// ---------------------------------------------------------------- K5-K7: FGMRES
+// Decision after a residual: NRBE of the current x, refine-or-not (initial
+// solve, Section 2.3) or accept/restart (cycle end).
+// mode 0: after x0; mode 1: after a cycle.  tol, stop_mode, refine_delta.
+__global__ void k_decide(DevScal* s, int mode, double tol, int stop_mode, double refine_delta) {
+    const double rn = s->rnorm, xn = s->xnorm, bn = s->normb;
+    const double nrbe = (rn == 0.0) ? 0.0 : rn / (s->normA * xn + bn);
+    s->nrbe = nrbe;
+    if (!isfinite(rn) || !isfinite(xn)) { s->err = KKT_ERR_NONFINITE; s->done = 1; return; }
+    if (mode == 0) {
+        s->rnorm0 = rn;
+        s->iters = 0;
+        s->done = 0;
+        if (rn == 0.0) s->done = 1;
+        else if (refine_delta > 0.0 && rn < refine_delta * bn) s->done = 1;
+        else if (stop_mode == KKT_STOP_NRBE && nrbe <= tol) s->done = 1;
+    } else {
+        if (rn == 0.0) s->done = 1;
+        else if (stop_mode == KKT_STOP_NRBE && nrbe <= tol) s->done = 1;
+        else if (stop_mode == KKT_STOP_RR && s->met) s->done = 1;
+    }
+}
+
+// v_0 = r / ||r||, g = (||r||, 0, ...), threshold of the inner test.
+__global__ void k_cycle_init(int n, const double* __restrict__ r, double* __restrict__ v0, DevScal* s,
+                             double tol, int stop_mode) {
+    const double beta = *(volatile double*)&s->rnorm;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = tid; t < n; t += stride) v0[t] = r[t] / beta;
+    if (tid == 0) {
+        s->g[0] = beta;
+        for (int i = 1; i <= MAXM; i++) s->g[i] = 0.0;
+        s->thresh = (stop_mode == KKT_STOP_NRBE) ? tol * (s->normA * s->xnorm + s->normb) : tol * s->rnorm0;
+        s->j = 0;
+        s->met = 0;
+    }
+}
+
+// Classical Gram-Schmidt, first projection: h_i = v_i . w for i <= j.
+__global__ void k_cgs_dots(int n, const double* __restrict__ V, int64_t ld, const double* __restrict__ w,
+                           double* part, DevScal* s) {
+    __shared__ double sh[33];
+    const int j = *(volatile int*)&s->j;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int i = 0; i <= j; i++) {
+        const double* vi = V + (int64_t)i * ld;
+        double acc = 0.0;
+        for (int64_t t = tid; t < n; t += stride) acc += vi[t] * w[t];
+        acc = block_sum(acc, sh);
+        if (threadIdx.x == 0) part[blockIdx.x * RED_SLOTS + i] = acc;
+    }
+    if (!last_block(s)) return;
+    for (int i = 0; i <= j; i++) {
+        double v = reduce_partials(part, i, sh);
+        if (threadIdx.x == 0) s->h[i] = v;
+    }
+}
+
+// w -= V h (pass 0: h, then h2_i = v_i . w) or (pass 1: h2, then ||w||^2);
+// the last block of pass 1 finishes the Arnoldi step: H(:,j) = h + h2 and
+// h_{j+1,j} = ||w||, previous Givens rotations applied, new rotation
+// formed, g updated; the inner stopping test sets s->met.
+__global__ void k_cgs_update(int n, const double* __restrict__ V, int64_t ld, double* __restrict__ w, int pass,
+                             double* part, DevScal* s, int m, int stop_mode) {
+    __shared__ double sh[33];
+    __shared__ double hc[MAXM + 1];
+    const int j = *(volatile int*)&s->j;
+    const double* hsrc = pass == 0 ? s->h : s->h2;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) hc[i] = ((volatile double*)hsrc)[i];
+    __syncthreads();
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = tid; t < n; t += stride) {
+        double wt = w[t];
+        for (int i = 0; i <= j; i++) wt -= hc[i] * V[(int64_t)i * ld + t];
+        w[t] = wt;
+    }
+    __syncthreads();
+    if (pass == 0) {
+        for (int i = 0; i <= j; i++) {
+            const double* vi = V + (int64_t)i * ld;
+            double acc = 0.0;
+            for (int64_t t = tid; t < n; t += stride) acc += vi[t] * w[t];
+            acc = block_sum(acc, sh);
+            if (threadIdx.x == 0) part[blockIdx.x * RED_SLOTS + i] = acc;
+        }
+    } else {
+        double acc = 0.0;
+        for (int64_t t = tid; t < n; t += stride) acc += w[t] * w[t];
+        acc = block_sum(acc, sh);
+        if (threadIdx.x == 0) part[blockIdx.x * RED_SLOTS + 0] = acc;
+    }
+    if (!last_block(s)) return;
+    if (pass == 0) {
+        for (int i = 0; i <= j; i++) {
+            double v = reduce_partials(part, i, sh);
+            if (threadIdx.x == 0) s->h2[i] = v;
+        }
+        return;
+    }
+    double nn = reduce_partials(part, 0, sh);
+    if (threadIdx.x != 0) return;
+    const double hn = sqrt(nn);
+    s->hn = hn;
+    double* Hj = s->H + j * (MAXM + 1);
+    for (int i = 0; i <= j; i++) Hj[i] = s->h[i] + s->h2[i];
+    Hj[j + 1] = hn;
+    for (int i = 0; i < j; i++) {
+        const double a = Hj[i], bb = Hj[i + 1];
+        Hj[i] = s->cs[i] * a + s->sn[i] * bb;
+        Hj[i + 1] = -s->sn[i] * a + s->cs[i] * bb;
+    }
+    const double a = Hj[j], bb = Hj[j + 1];
+    const double rr = hypot(a, bb);
+    if (rr == 0.0) { s->cs[j] = 1.0; s->sn[j] = 0.0; }
+    else { s->cs[j] = a / rr; s->sn[j] = bb / rr; }
+    Hj[j] = rr;
+    Hj[j + 1] = 0.0;
+    s->g[j + 1] = -s->sn[j] * s->g[j];
+    s->g[j] = s->cs[j] * s->g[j];
+    s->iters += 1;
+    const double est = fabs(s->g[j + 1]);
+    const int met = (stop_mode == KKT_STOP_NRBE) ? (est <= s->thresh) : (est < s->thresh);
+    s->met = met;
+    s->j = j + 1;
+}
+
+// v_{j+1} = w / h_{j+1,j} (zero on breakdown); j was already advanced.
+__global__ void k_normalize(int n, const double* __restrict__ w, double* __restrict__ V, int64_t ld, DevScal* s) {
+    const int j = *(volatile int*)&s->j;
+    const double hn = *(volatile double*)&s->hn;
+    double* vn = V + (int64_t)j * ld;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = tid; t < n; t += stride) vn[t] = hn > 0.0 ? w[t] / hn : 0.0;
+}
+
+// Cycle end: y = R^{-1} g (R the rotated Hessenberg, jend = s->j columns).
+__global__ void k_hess_solve(DevScal* s) {
+    if (threadIdx.x != 0) return;
+    const int jend = s->j;
+    for (int i = jend - 1; i >= 0; i--) {
+        double v = s->g[i];
+        for (int k = i + 1; k < jend; k++) v -= s->H[k * (MAXM + 1) + i] * s->y[k];
+        s->y[i] = v / s->H[i * (MAXM + 1) + i];
+    }
+}
+
+// x += Z y
+__global__ void k_update_x(int n, const double* __restrict__ Z, int64_t ld, double* __restrict__ x, DevScal* s) {
+    __shared__ double yc[MAXM];
+    const int jend = *(volatile int*)&s->j;
+    for (int i = threadIdx.x; i < jend; i += blockDim.x) yc[i] = ((volatile double*)s->y)[i];
+    __syncthreads();
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = tid; t < n; t += stride) {
+        double v = x[t];
+        for (int k = 0; k < jend; k++) v += yc[k] * Z[(int64_t)k * ld + t];
+        x[t] = v;
+    }
+}
+
+}  // namespace kkt

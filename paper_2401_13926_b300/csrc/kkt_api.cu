@@ -1,0 +1,523 @@
+// C ABI of the GPU-resident KKT solver: context, one-time analysis, and the
+// host sequencing of the device kernels in kernels.cuh.  Declarations and
+// the contract of every entry point are in include/kkt.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "analysis.h"
+#include "kernels.cuh"
+#include "kkt.h"
+
+using kkt::DevScal;
+
+struct kkt_ctx {
+    kkt_opts o{};
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    // host analysis
+    kkt::Csr A;
+    std::vector<int32_t> P, Q;
+    kkt::Layout lay;
+    bool analyzed = false, factored = false;
+    int64_t nnz_a = 0;
+    // device memory (all made in kkt_analyze)
+    std::vector<void*> allocs;
+    int64_t dev_bytes = 0;
+    int64_t *d_Fp = nullptr, *d_Fdiag = nullptr, *d_fsrc = nullptr, *d_asrc = nullptr;
+    int32_t *d_Fj = nullptr, *d_Arp = nullptr, *d_Aci = nullptr, *d_P = nullptr, *d_Q = nullptr;
+    double *d_Fx = nullptr, *d_Ax = nullptr, *d_vals = nullptr;
+    double *d_b = nullptr, *d_x = nullptr, *d_y = nullptr, *d_xp = nullptr, *d_r = nullptr, *d_w = nullptr;
+    double *d_V = nullptr, *d_Z = nullptr, *d_part = nullptr;
+    unsigned *d_done_f = nullptr, *d_done_l = nullptr, *d_done_u = nullptr;
+    DevScal* d_s = nullptr;
+    DevScal* h_s = nullptr;   // pinned mirror
+    int64_t ld = 0;
+    int m = 20;
+    int persist_blocks = 0;
+    // results
+    std::string detail;
+    int nboost = 0, last_iters = 0, last_cycles = 0;
+    double last_nrbe = 0, last_rnorm0 = 0, norm_a = 0, analyze_ms = 0;
+};
+
+namespace {
+
+constexpr int PERSIST_THREADS = 256;
+constexpr long long DEFAULT_SPIN = 1ll << 25;
+
+int cuda_fail(kkt_ctx* c, cudaError_t e, const char* what) {
+    if (c) c->detail = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? KKT_ERR_OOM : KKT_ERR_CUDA;
+}
+#define CK(call)                                             \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+void free_device(kkt_ctx* c) {
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    if (c->h_s) { cudaFreeHost(c->h_s); c->h_s = nullptr; }
+    c->dev_bytes = 0;
+    c->analyzed = c->factored = false;
+}
+
+template <class T>
+int dalloc(kkt_ctx* c, T** p, size_t count) {
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
+    c->allocs.push_back(q);
+    c->dev_bytes += (int64_t)bytes;
+    *p = (T*)q;
+    return KKT_OK;
+}
+
+template <class T>
+int upload(kkt_ctx* c, T** p, const std::vector<T>& v) {
+    int rc = dalloc(c, p, v.size());
+    if (rc) return rc;
+    if (!v.empty()) CK(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    return KKT_OK;
+}
+
+int read_scalars(kkt_ctx* c) {
+    CK(cudaMemcpyAsync(c->h_s, c->d_s, sizeof(DevScal), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return KKT_OK;
+}
+
+int device_error(kkt_ctx* c) {
+    int e = c->h_s->err;
+    if (e) {
+        c->detail = std::string(kkt_strerror(e)) + " at row " + std::to_string(c->h_s->err_row);
+        return e;
+    }
+    return KKT_OK;
+}
+
+long long spin(const kkt_ctx* c) { return c->o.spin_limit > 0 ? (long long)c->o.spin_limit : DEFAULT_SPIN; }
+
+int red_blocks(const kkt_ctx* c) {
+    int64_t need = (c->A.n + kkt::RED_THREADS - 1) / kkt::RED_THREADS;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(kkt::RED_BLOCKS, need));
+}
+
+int persist_grid(const kkt_ctx* c) {
+    int64_t need = (c->A.n + (PERSIST_THREADS / 32) - 1) / (PERSIST_THREADS / 32);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(c->persist_blocks, need));
+}
+
+// x = Q U^{-1} L^{-1} P rhs  (three launches: prep, L-solve, U-solve)
+void lu_apply(kkt_ctx* c, const double* rhs, double* out) {
+    const int n = c->A.n;
+    const int g = persist_grid(c);
+    kkt::k_trsv_prep<<<1, 1, 0, c->stream>>>(c->d_s);
+    kkt::k_lsolve<<<g, PERSIST_THREADS, 0, c->stream>>>(n, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_P, rhs,
+                                                       c->d_y, c->d_done_l, c->d_s, spin(c));
+    kkt::k_usolve<<<g, PERSIST_THREADS, 0, c->stream>>>(n, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_Q,
+                                                       c->d_y, c->d_xp, out, c->d_done_u, c->d_s, spin(c));
+}
+
+int check_ctx(kkt_ctx* c, bool need_factors) {
+    if (!c) return KKT_ERR_INVALID;
+    if (!c->analyzed) { c->detail = "kkt_analyze has not run"; return KKT_ERR_STATE; }
+    if (need_factors && !c->factored) { c->detail = "kkt_refactor has not succeeded"; return KKT_ERR_STATE; }
+    cudaError_t e = cudaSetDevice(c->dev);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return KKT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void kkt_default_opts(kkt_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->restart = 20;
+    o->max_cycles = 50;
+    o->stop_mode = KKT_STOP_NRBE;
+    o->precision = 0;
+    o->refine_delta = 0.0;
+    o->pivot_tol = 1e-3;
+    o->boost_eps = 0.0;
+    o->device = 0;
+    o->stream = nullptr;
+    o->spin_limit = 0;
+}
+
+const char* kkt_strerror(int code) {
+    switch (code) {
+        case KKT_OK: return "ok";
+        case KKT_ERR_INVALID: return "invalid argument";
+        case KKT_ERR_PATTERN: return "invalid or mismatched sparsity pattern";
+        case KKT_ERR_OOM: return "out of memory";
+        case KKT_ERR_ZERO_PIVOT: return "zero pivot";
+        case KKT_ERR_NONFINITE: return "non-finite value";
+        case KKT_ERR_NOT_CONVERGED: return "refinement did not converge";
+        case KKT_ERR_TIMEOUT: return "bounded device wait timed out";
+        case KKT_ERR_CUDA: return "CUDA error";
+        case KKT_ERR_STATE: return "call out of order";
+        default: return "unknown error";
+    }
+}
+
+const char* kkt_last_error_detail(kkt_ctx* c) { return c ? c->detail.c_str() : ""; }
+
+int kkt_create(kkt_ctx** out, const kkt_opts* o) {
+    if (!out) return KKT_ERR_INVALID;
+    *out = nullptr;
+    kkt_ctx* c = new kkt_ctx();
+    if (o) c->o = *o; else kkt_default_opts(&c->o);
+    if (c->o.restart < 1 || c->o.restart > kkt::MAXM || c->o.max_cycles < 0 || c->o.precision != 0 ||
+        (c->o.stop_mode != KKT_STOP_NRBE && c->o.stop_mode != KKT_STOP_RR) || c->o.pivot_tol <= 0 ||
+        c->o.pivot_tol > 1 || c->o.boost_eps < 0) {
+        delete c;
+        return KKT_ERR_INVALID;
+    }
+    c->dev = c->o.device;
+    c->m = c->o.restart;
+    cudaError_t e = cudaSetDevice(c->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev);
+    if (e == cudaSuccess) {
+        if (c->o.stream) c->stream = (cudaStream_t)c->o.stream;
+        else { e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking); c->own_stream = true; }
+    }
+    if (e != cudaSuccess) { delete c; return KKT_ERR_CUDA; }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kkt::k_lsolve, PERSIST_THREADS, 0);
+    int per_sm2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kkt::k_refactor, PERSIST_THREADS, 0);
+    int per_sm3 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, kkt::k_usolve, PERSIST_THREADS, 0);
+    per_sm = std::max(1, std::min(per_sm, std::min(per_sm2, per_sm3)));
+    c->persist_blocks = c->num_sms * per_sm;
+    *out = c;
+    return KKT_OK;
+}
+
+void kkt_destroy(kkt_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->dev);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_device(c);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int kkt_order(int32_t n, const int32_t* rowptr, const int32_t* colind, int32_t* Q) {
+    if (!Q) return KKT_ERR_INVALID;
+    kkt::Csr A;
+    std::string why;
+    int rc = kkt::canonicalize(n, rowptr, colind, &A, &why);
+    if (rc) return rc;
+    std::vector<int32_t> q;
+    rc = kkt::order_colamd_like(A, &q);
+    if (rc) return rc;
+    std::copy(q.begin(), q.end(), Q);
+    return KKT_OK;
+}
+
+int kkt_pivot(int32_t n, const int32_t* rowptr, const int32_t* colind, const double* values, const int32_t* Q,
+              double pivot_tol, int32_t* P, int64_t* nnz_l, int64_t* nnz_u) {
+    if (!P || !values || pivot_tol <= 0 || pivot_tol > 1) return KKT_ERR_INVALID;
+    kkt::Csr A;
+    std::string why;
+    int rc = kkt::canonicalize(n, rowptr, colind, &A, &why);
+    if (rc) return rc;
+    std::vector<int32_t> q;
+    if (Q) q.assign(Q, Q + n); else { rc = kkt::order_colamd_like(A, &q); if (rc) return rc; }
+    std::vector<double> v(A.colind.size());
+    for (size_t e = 0; e < v.size(); e++) v[e] = values[A.src[e]];
+    std::vector<int32_t> p;
+    kkt::ColStructure S;
+    int32_t bad = -1;
+    rc = kkt::pivot_lu(A, v.data(), q, pivot_tol, &p, &S, &bad);
+    if (rc) return rc;
+    std::copy(p.begin(), p.end(), P);
+    if (nnz_l) *nnz_l = S.Lp[n];
+    if (nnz_u) *nnz_u = S.Up[n];
+    return KKT_OK;
+}
+
+int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* colind, const double* values0,
+                const int32_t* Qin, const int32_t* Pin) {
+    if (!c) return KKT_ERR_INVALID;
+    auto t0 = std::chrono::steady_clock::now();
+    CK(cudaSetDevice(c->dev));
+    CK(cudaStreamSynchronize(c->stream));
+    free_device(c);
+    c->detail.clear();
+    std::string why;
+    int rc = kkt::canonicalize(n, rowptr, colind, &c->A, &why);
+    if (rc) { c->detail = why; return rc; }
+    if (n < 1) { c->detail = "n must be positive"; return KKT_ERR_INVALID; }
+    c->nnz_a = (int64_t)c->A.colind.size();
+    if (Qin) {
+        c->Q.assign(Qin, Qin + n);
+        std::vector<char> seen(n, 0);
+        for (int32_t j = 0; j < n; j++) {
+            if (c->Q[j] < 0 || c->Q[j] >= n || seen[c->Q[j]]) { c->detail = "Q is not a permutation"; return KKT_ERR_INVALID; }
+            seen[c->Q[j]] = 1;
+        }
+    } else {
+        rc = kkt::order_colamd_like(c->A, &c->Q);
+        if (rc) { c->detail = "ordering failed"; return rc; }
+    }
+    kkt::ColStructure S;
+    int32_t bad = -1;
+    if (Pin) {
+        c->P.assign(Pin, Pin + n);
+        rc = kkt::symbolic(c->A, c->P, c->Q, &S, &bad);
+        if (rc) { c->detail = "symbolic analysis failed at column " + std::to_string(bad); return rc; }
+    } else {
+        if (!values0) { c->detail = "values0 is required when P is not given"; return KKT_ERR_INVALID; }
+        std::vector<double> v(c->nnz_a);
+        for (int64_t e = 0; e < c->nnz_a; e++) v[e] = values0[c->A.src[e]];
+        rc = kkt::pivot_lu(c->A, v.data(), c->Q, c->o.pivot_tol, &c->P, &S, &bad);
+        if (rc) { c->detail = "pivoting factorization failed at column " + std::to_string(bad); return rc; }
+    }
+    rc = kkt::build_layout(c->A, c->P, c->Q, S, &c->lay);
+    if (rc) { c->detail = "factor layout failed"; return rc; }
+    // composite gather map: factor slot -> caller value index
+    std::vector<int64_t> fsrc(c->lay.Fsrc.size());
+    for (size_t t = 0; t < fsrc.size(); t++) fsrc[t] = c->lay.Fsrc[t] >= 0 ? c->A.src[c->lay.Fsrc[t]] : -1;
+    const int64_t nnzF = (int64_t)c->lay.Fj.size();
+    // ---- device buffers, made once for the whole sequence
+    c->ld = ((int64_t)n + 31) / 32 * 32;
+    if ((rc = upload(c, &c->d_Fp, c->lay.Fp))) return rc;
+    if ((rc = upload(c, &c->d_Fdiag, c->lay.Fdiag))) return rc;
+    if ((rc = upload(c, &c->d_Fj, c->lay.Fj))) return rc;
+    if ((rc = upload(c, &c->d_fsrc, fsrc))) return rc;
+    if (!c->A.identity_src) { if ((rc = upload(c, &c->d_asrc, c->A.src))) return rc; }
+    else c->d_asrc = nullptr;
+    if ((rc = upload(c, &c->d_Arp, c->A.rowptr))) return rc;
+    if ((rc = upload(c, &c->d_Aci, c->A.colind))) return rc;
+    if ((rc = upload(c, &c->d_P, c->P))) return rc;
+    if ((rc = upload(c, &c->d_Q, c->Q))) return rc;
+    if ((rc = dalloc(c, &c->d_Fx, nnzF))) return rc;
+    if ((rc = dalloc(c, &c->d_Ax, c->nnz_a))) return rc;
+    if ((rc = dalloc(c, &c->d_vals, c->nnz_a))) return rc;
+    for (double** p : {&c->d_b, &c->d_x, &c->d_y, &c->d_xp, &c->d_r, &c->d_w})
+        if ((rc = dalloc(c, p, c->ld))) return rc;
+    if ((rc = dalloc(c, &c->d_V, (size_t)c->ld * (c->m + 1)))) return rc;
+    if ((rc = dalloc(c, &c->d_Z, (size_t)c->ld * c->m))) return rc;
+    if ((rc = dalloc(c, &c->d_part, (size_t)kkt::RED_BLOCKS * kkt::RED_SLOTS))) return rc;
+    for (unsigned** p : {&c->d_done_f, &c->d_done_l, &c->d_done_u}) {
+        if ((rc = dalloc(c, p, (size_t)n))) return rc;
+        CK(cudaMemsetAsync(*p, 0, sizeof(unsigned) * (size_t)n, c->stream));
+    }
+    if ((rc = dalloc(c, &c->d_s, 1))) return rc;
+    CK(cudaMemsetAsync(c->d_s, 0, sizeof(DevScal), c->stream));
+    CK(cudaMallocHost(&c->h_s, sizeof(DevScal)));
+    CK(cudaStreamSynchronize(c->stream));
+    c->analyzed = true;
+    c->factored = false;
+    c->analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return KKT_OK;
+}
+
+int kkt_refactor(kkt_ctx* c, const double* values, int values_on_device) {
+    int rc = check_ctx(c, false);
+    if (rc) return rc;
+    if (!values) return KKT_ERR_INVALID;
+    c->factored = false;
+    const double* vals = values;
+    if (!values_on_device) {
+        CK(cudaMemcpyAsync(c->d_vals, values, sizeof(double) * (size_t)c->nnz_a, cudaMemcpyHostToDevice, c->stream));
+        vals = c->d_vals;
+    }
+    const int n = c->A.n;
+    const int64_t nnzF = (int64_t)c->lay.Fj.size();
+    kkt::k_refactor_prep<<<1, 1, 0, c->stream>>>(c->d_s);
+    kkt::k_gather<<<2 * c->num_sms, 256, 0, c->stream>>>(vals, c->d_fsrc, nnzF, c->d_Fx, c->d_Arp, c->d_asrc,
+                                                         c->d_Ax, n, c->d_s);
+    kkt::k_refactor<<<persist_grid(c), PERSIST_THREADS, 0, c->stream>>>(
+        n, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_done_f, c->d_s, c->o.boost_eps, spin(c));
+    CK(cudaGetLastError());
+    if ((rc = read_scalars(c))) return rc;
+    c->nboost = c->h_s->nboost;
+    c->norm_a = c->h_s->normA;
+    if ((rc = device_error(c))) return rc;
+    c->factored = true;
+    return KKT_OK;
+}
+
+int kkt_lu_solve(kkt_ctx* c, const double* b, double* x, int on_device) {
+    int rc = check_ctx(c, true);
+    if (rc) return rc;
+    if (!b || !x) return KKT_ERR_INVALID;
+    const int n = c->A.n;
+    const double* bd = b;
+    double* xd = x;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(c->d_b, b, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        bd = c->d_b;
+        xd = c->d_x;
+    }
+    CK(cudaMemsetAsync(&c->d_s->err, 0, sizeof(int) * 3, c->stream));
+    lu_apply(c, bd, xd);
+    CK(cudaGetLastError());
+    if (!on_device) CK(cudaMemcpyAsync(x, c->d_x, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    if ((rc = read_scalars(c))) return rc;
+    return device_error(c);
+}
+
+int kkt_matvec(kkt_ctx* c, const double* x, double* y, int on_device) {
+    int rc = check_ctx(c, true);
+    if (rc) return rc;
+    if (!x || !y) return KKT_ERR_INVALID;
+    const int n = c->A.n;
+    const double* xd = x;
+    double* yd = y;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(c->d_b, x, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        xd = c->d_b;
+        yd = c->d_w;
+    }
+    kkt::k_spmv<<<red_blocks(c), kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, xd, yd);
+    CK(cudaGetLastError());
+    if (!on_device) CK(cudaMemcpyAsync(y, c->d_w, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return KKT_OK;
+}
+
+int kkt_solve(kkt_ctx* c, const double* b, double* x, int on_device, double tol, int* iters, double* nrbe) {
+    int rc = check_ctx(c, true);
+    if (rc) return rc;
+    if (!b || !x || !(tol > 0)) return KKT_ERR_INVALID;
+    const int n = c->A.n;
+    const int m = c->m;
+    const double* bd = b;
+    double* xd = x;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(c->d_b, b, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        bd = c->d_b;
+        xd = c->d_x;
+    }
+    const int rb = red_blocks(c);
+    const int stop = c->o.stop_mode;
+    CK(cudaMemsetAsync(&c->d_s->err, 0, sizeof(int) * 3, c->stream));
+    // x0 = (LU)^{-1} b, its residual and the refine-or-not decision
+    lu_apply(c, bd, xd);
+    kkt::k_residual<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, bd, xd, c->d_r,
+                                                            c->d_part, c->d_s);
+    kkt::k_decide<<<1, 1, 0, c->stream>>>(c->d_s, 0, tol, stop, c->o.refine_delta);
+    CK(cudaGetLastError());
+    if ((rc = read_scalars(c))) return rc;
+    if ((rc = device_error(c))) return rc;
+    int cycles = 0;
+    int status = KKT_OK;
+    while (!c->h_s->done) {
+        if (cycles >= c->o.max_cycles) { status = KKT_ERR_NOT_CONVERGED; break; }
+        cycles++;
+        kkt::k_cycle_init<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_r, c->d_V, c->d_s, tol, stop);
+        for (int j = 0; j < m; j++) {
+            double* vj = c->d_V + (int64_t)j * c->ld;
+            double* zj = c->d_Z + (int64_t)j * c->ld;
+            lu_apply(c, vj, zj);
+            kkt::k_spmv<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, zj, c->d_w);
+            kkt::k_cgs_dots<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_V, c->ld, c->d_w, c->d_part, c->d_s);
+            kkt::k_cgs_update<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_V, c->ld, c->d_w, 0, c->d_part,
+                                                                      c->d_s, m, stop);
+            kkt::k_cgs_update<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_V, c->ld, c->d_w, 1, c->d_part,
+                                                                      c->d_s, m, stop);
+            kkt::k_normalize<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_w, c->d_V, c->ld, c->d_s);
+            CK(cudaGetLastError());
+            if ((rc = read_scalars(c))) return rc;
+            if ((rc = device_error(c))) return rc;
+            if (c->h_s->met || c->h_s->hn == 0.0) break;
+        }
+        kkt::k_hess_solve<<<1, 32, 0, c->stream>>>(c->d_s);
+        kkt::k_update_x<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Z, c->ld, xd, c->d_s);
+        kkt::k_residual<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, bd, xd, c->d_r,
+                                                                c->d_part, c->d_s);
+        kkt::k_decide<<<1, 1, 0, c->stream>>>(c->d_s, 1, tol, stop, c->o.refine_delta);
+        CK(cudaGetLastError());
+        if ((rc = read_scalars(c))) return rc;
+        if ((rc = device_error(c))) return rc;
+    }
+    if (!on_device) CK(cudaMemcpyAsync(x, c->d_x, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->last_iters = c->h_s->iters;
+    c->last_cycles = cycles;
+    c->last_nrbe = c->h_s->nrbe;
+    c->last_rnorm0 = c->h_s->rnorm0;
+    if (iters) *iters = c->h_s->iters;
+    if (nrbe) *nrbe = c->h_s->nrbe;
+    if (status) c->detail = "max_cycles reached";
+    return status;
+}
+
+int kkt_get_perm(kkt_ctx* c, int32_t* P, int32_t* Q) {
+    if (!c || !c->analyzed) return c ? KKT_ERR_STATE : KKT_ERR_INVALID;
+    if (P) std::copy(c->P.begin(), c->P.end(), P);
+    if (Q) std::copy(c->Q.begin(), c->Q.end(), Q);
+    return KKT_OK;
+}
+
+int kkt_get_factor_sizes(kkt_ctx* c, int64_t* nnz_l, int64_t* nnz_u) {
+    if (!c || !c->analyzed) return c ? KKT_ERR_STATE : KKT_ERR_INVALID;
+    if (nnz_l) *nnz_l = c->lay.nnzL;
+    if (nnz_u) *nnz_u = c->lay.nnzU;
+    return KKT_OK;
+}
+
+int kkt_get_factors(kkt_ctx* c, int64_t* Lp, int32_t* Li, double* Lx, int64_t* Up, int32_t* Ui, double* Ux) {
+    int rc = check_ctx(c, true);
+    if (rc) return rc;
+    if (!Lp || !Li || !Lx || !Up || !Ui || !Ux) return KKT_ERR_INVALID;
+    const int n = c->A.n;
+    const auto& L = c->lay;
+    std::vector<double> fx(L.Fj.size());
+    CK(cudaMemcpyAsync(fx.data(), c->d_Fx, sizeof(double) * fx.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::fill(Lp, Lp + n + 1, 0);
+    std::fill(Up, Up + n + 1, 0);
+    for (int32_t i = 0; i < n; i++) {
+        for (int64_t p = L.Fp[i]; p < L.Fdiag[i]; p++) Lp[L.Fj[p] + 1]++;
+        for (int64_t p = L.Fdiag[i]; p < L.Fp[i + 1]; p++) Up[L.Fj[p] + 1]++;
+    }
+    for (int32_t j = 0; j < n; j++) { Lp[j + 1] += Lp[j]; Up[j + 1] += Up[j]; }
+    std::vector<int64_t> nl(Lp, Lp + n), nu(Up, Up + n);
+    for (int32_t i = 0; i < n; i++) {   // rows ascending -> sorted row indices per column
+        for (int64_t p = L.Fp[i]; p < L.Fdiag[i]; p++) { int64_t t = nl[L.Fj[p]]++; Li[t] = i; Lx[t] = fx[p]; }
+        for (int64_t p = L.Fdiag[i]; p < L.Fp[i + 1]; p++) { int64_t t = nu[L.Fj[p]]++; Ui[t] = i; Ux[t] = fx[p]; }
+    }
+    return KKT_OK;
+}
+
+int kkt_query(kkt_ctx* c, kkt_info* info) {
+    if (!c || !info) return KKT_ERR_INVALID;
+    std::memset(info, 0, sizeof(*info));
+    if (!c->analyzed) return KKT_ERR_STATE;
+    info->n = c->A.n;
+    info->nnz_a = c->nnz_a;
+    info->nnz_l = c->lay.nnzL;
+    info->nnz_u = c->lay.nnzU;
+    info->levels_l = c->lay.levelsL;
+    info->levels_u = c->lay.levelsU;
+    info->refactor_updates = c->lay.updates;
+    info->device_bytes = c->dev_bytes;
+    info->nboost = c->nboost;
+    info->last_iters = c->last_iters;
+    info->last_cycles = c->last_cycles;
+    info->last_nrbe = c->last_nrbe;
+    info->last_rnorm0 = c->last_rnorm0;
+    info->norm_a_inf = c->norm_a;
+    info->analyze_ms = c->analyze_ms;
+    return KKT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+"""CPU checks of the C ABI library: it loads, exports every entry point
+declared in include/kkt.h, and its host-only analysis (ordering, pivoting)
+behaves.  No GPU calls."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2401_13926_b300 as K
+from paper_2401_13926_b300.workload import KKTSequence
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2401_13926_b300 import build
+    build.build()
+    return K.lib()
+
+
+def declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(kkt_[a-z_0-9]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol(L):
+    names = declared()
+    assert names, "no declarations found"
+    for nm in sorted(names):
+        assert hasattr(L, nm), nm
+    assert set(K.EXPORTS) <= names
+
+
+def test_strerror_covers_codes(L):
+    for code in range(0, -10, -1):
+        assert L.kkt_strerror(code).decode() != "unknown error"
+
+
+def test_order_is_a_permutation_with_fill_close_to_oracle(L, oracle_mod):
+    seq = KKTSequence("kkt200")
+    Q = K.order(seq.rowptr, seq.colind)
+    assert sorted(Q) == list(range(seq.n))
+    v = seq.values(0)
+    _, _, Fl = oracle_mod.lu(seq.n, seq.rowptr, seq.colind, v, Q=Q)
+    _, _, Fo = oracle_mod.lu(seq.n, seq.rowptr, seq.colind, v)
+    fill_lib = len(Fl.Li) + len(Fl.Ui)
+    fill_or = len(Fo.Li) + len(Fo.Ui)
+    assert fill_lib <= 1.5 * fill_or
+
+
+def test_pivot_matches_oracle_pivot_rule(L, oracle_mod):
+    """Same order, same threshold rule -> same pivot sequence and sizes."""
+    seq = KKTSequence("kkt200", buses=60, steps=1)
+    v = seq.values(0)
+    Po, Qo, Fo = oracle_mod.lu(seq.n, seq.rowptr, seq.colind, v)
+    P, nl, nu = K.pivot(seq.rowptr, seq.colind, v, Q=Qo, tol=1e-3)
+    assert np.array_equal(P, Po)
+    assert nl == len(Fo.Li) and nu == len(Fo.Ui)
+
+
+def test_pattern_errors(L):
+    rp = np.array([0, 2, 3], np.int32)
+    with pytest.raises(K.KKTError) as e:
+        K.order(rp, np.array([0, 0, 1], np.int32))       # duplicate in row 0
+    assert e.value.code == -2
+    with pytest.raises(K.KKTError) as e:
+        K.order(rp, np.array([0, 5, 1], np.int32))       # out of range
+    assert e.value.code == -2
+    with pytest.raises(K.KKTError) as e:
+        K.pivot(np.array([0, 1, 2], np.int32), np.array([0, 0], np.int32), np.array([1.0, 1.0]))
+    assert e.value.code == -4                              # column 1 is empty: no pivot
