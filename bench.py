@@ -1,0 +1,329 @@
+"""Benchmark: KKT solves/sec on a same-pattern synthetic power-grid KKT sequence.
+
+One step = one pass of the hot path over one matrix of the sequence:
+kkt_refactor (value gather, numeric LU on the fixed pattern and pivots) then
+kkt_solve (triangular solves, residual, FGMRES(20) with CGS2 until
+NRBE <= 1e-12).  Matrices cycle k = 0..M-1 over the sequence.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own
+instance of the workload (independent replicas, weak scaling; one KKT
+system does not shard, so there is no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "kkt2000"
+TOL = 1e-12
+RESTART = 20
+L2_FLUSH_BYTES = 256 << 20   # larger than the 126 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=30)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate(units: float, seconds: float, world: int):
+    """Whole-job throughput: units summed over ranks / slowest rank's time."""
+    if world == 1:
+        return units, seconds
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([units, seconds], dtype=torch.float64, device=dev)
+    u = t[:1].clone()
+    s = t[1:].clone()
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(s.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# -------------------------------------------------------------------- oracle
+def oracle_sample(seq, seconds, steps=None):
+    """The CPU oracle as it stands: analysis once (not timed), then refactor +
+    FGMRES per matrix until `seconds` (or `steps`) are used."""
+    from oracle import oracle as O
+    v0 = seq.values(0)
+    t0 = time.perf_counter()
+    P, Q, _ = O.lu(seq.n, seq.rowptr, seq.colind, v0)
+    t_an = time.perf_counter() - t0
+    done, t_solve, k = 0, 0.0, 0
+    nrbe = []
+    while True:
+        v = seq.values(k % seq.M)
+        b, _ = seq.rhs(k % seq.M, v)
+        t = time.perf_counter()
+        _, res = O.solve_sequence_step(seq.n, seq.rowptr, seq.colind, v, P, Q, b, tol=TOL, restart=RESTART)
+        t_solve += time.perf_counter() - t
+        nrbe.append(res.nrbe)
+        done += 1
+        k += 1
+        if (steps is not None and done >= steps) or (steps is None and t_solve >= seconds):
+            break
+    return done, t_solve, t_an, max(nrbe)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2401_13926_b300.workload import KKTSequence
+    seq = KKTSequence(args.workload)
+    # warmup steps, then the timed ones
+    oracle_sample(seq, 0, steps=max(args.warmup, 0) or 1)
+    done, t, t_an, worst = oracle_sample(seq, 0, steps=args.steps)
+    v = done / t
+    line = {
+        "impl": "reference", "metric": "KKT solves/sec (refactor+FGMRES to NRBE<=1e-12)", "value": v,
+        "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * t / done, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": workload_config(seq),
+        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{done} matrices of the {args.workload} sequence, oracle analysis "
+                                   f"({t_an:.1f} s) excluded, single thread"},
+        "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "max_nrbe": worst,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(seq):
+    return {
+        "workload": f"{seq.cfg.name}: synthetic {seq.nbus}-bus grid KKT [[H+Dx,J^T],[J,-Dy]], "
+                    f"n={seq.n}, nnz={seq.nnz}, {seq.M}-matrix same-pattern sequence, "
+                    f"Dx spread widening 1e+-{seq.cfg.s_first:g}..1e+-{seq.cfg.s_last:g}, "
+                    f"FGMRES({RESTART}) to NRBE<={TOL:g}, FP64",
+        "n": seq.n, "nnz": seq.nnz, "sequence": seq.M, "restart": RESTART, "tol": TOL,
+        "l2": "flushed between timed steps (256 MiB write, outside the per-step events)",
+    }
+
+
+# -------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    import paper_2401_13926_b300 as K
+    from paper_2401_13926_b300.workload import KKTSequence
+
+    seq = KKTSequence(args.workload, instance=rank)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    solver = K.KKTSolver(restart=RESTART, device=local, stream=stream, timing=True)
+    solver.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
+    info0 = solver.info()
+    # inputs resident in HBM before the timed region
+    vals = [torch.from_numpy(seq.values(k)).cuda() for k in range(seq.M)]
+    rhs = [torch.from_numpy(seq.rhs(k, vals[k].cpu().numpy())[0]).cuda() for k in range(seq.M)]
+    x = torch.empty(seq.n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step(k):
+        solver.refactor(vals[k % seq.M])
+        _, it, nr = solver.solve(rhs[k % seq.M], x=x, tol=TOL)
+        return it, nr
+
+    for w in range(args.warmup):
+        step(w)
+    torch.cuda.synchronize()
+    solver.phase_times(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    launches0 = solver.info()["launches"]
+    iters, nrbes = [], []
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        it, nr = step(i)
+        ev[i][1].record(stream)
+        iters.append(it)
+        nrbes.append(nr)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    barrier(world)
+    clk = clocks.stop()
+    launches = solver.info()["launches"] - launches0
+    per_step = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(per_step) / 1000.0
+    phases = solver.phase_times(reset=True)
+    units, secs = aggregate(float(args.steps), dev_s, world)
+
+    # ---- end to end through the C ABI with pinned host buffers
+    n_e2e = min(args.e2e_steps, seq.M)
+    hv = [torch.from_numpy(seq.values(k)).pin_memory().numpy() for k in range(n_e2e)]
+    hb = [torch.from_numpy(seq.rhs(k)[0]).pin_memory().numpy() for k in range(n_e2e)]
+    hx = torch.empty(seq.n, dtype=torch.float64).pin_memory().numpy()
+    info_a = solver.info()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for k in range(n_e2e):
+        solver.refactor(hv[k])
+        solver.solve(hb[k], x=hx, tol=TOL)
+    e2e_s = time.perf_counter() - t
+    info_b = solver.info()
+    e2e_units, e2e_secs = aggregate(float(n_e2e), e2e_s, world)
+    if rank != 0:
+        return
+
+    # ---- roofline of the dominant kernel group
+    hbm, peak_kind = peaks()
+    lay = info0
+    n = seq.n
+    tot = {p: phases[p][0] for p in phases}
+    dom = max(("refactor", "lsolve", "usolve", "spmv", "ortho"), key=lambda p: tot[p])
+    ms, cnt = phases[dom]
+    per_launch_ms = ms / max(cnt, 1)
+    if dom == "lsolve":
+        bytes_ = 12 * lay["nnz_l"] + 36 * n
+    elif dom == "usolve":
+        bytes_ = 12 * lay["nnz_u"] + 44 * n
+    elif dom == "refactor":
+        bytes_ = 20 * (lay["nnz_l"] + lay["nnz_u"]) + 24 * n
+    elif dom == "spmv":
+        bytes_ = 12 * seq.nnz + 28 * n
+    else:
+        bytes_ = 8 * n * (2 * RESTART)
+    achieved = bytes_ / (per_launch_ms * 1e-3) / 1e9
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+            "bytes_per_launch": bytes_, "ms_per_launch": per_launch_ms,
+            "phase_ms": {p: round(phases[p][0] / args.steps, 4) for p in phases},
+            "phase_launches": {p: phases[p][1] for p in phases}}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        done, tcpu, t_an, _ = oracle_sample(KKTSequence(args.workload), args.cpu_seconds)
+        cpu = {"value": done / tcpu, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": f"{done} matrices of the {args.workload} sequence (about {args.cpu_seconds:g} s), "
+                         f"oracle analysis ({t_an:.1f} s) excluded, single thread"}
+
+    lat = sorted(per_step)
+    line = {
+        "metric": "KKT solves/sec (refactor+FGMRES to NRBE<=1e-12)",
+        "value": units / secs, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {**workload_config(seq), "parallelism": f"replicas{world}"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "iters_mean": float(np.mean(iters)), "max_nrbe": float(np.max(nrbes)),
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_units / e2e_secs, "unit": "solves/s",
+                "h2d_bytes_per_step": (info_b["h2d_bytes"] - info_a["h2d_bytes"]) // n_e2e,
+                "d2h_bytes_per_step": (info_b["d2h_bytes"] - info_a["d2h_bytes"]) // n_e2e},
+        "gpu_launches": launches, "clocks": clk, "wall_s": t_wall,
+        "analysis": {"analyze_ms": lay["analyze_ms"], "nnz_l": lay["nnz_l"], "nnz_u": lay["nnz_u"],
+                     "levels_l": lay["levels_l"], "levels_u": lay["levels_u"],
+                     "refactor_updates": lay["refactor_updates"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

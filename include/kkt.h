@@ -72,9 +72,22 @@ typedef struct {
                              sign(u_jj) boost_eps ||K||_inf (sign(0)=+1); 0 = off (default),
                              then an exact zero pivot is KKT_ERR_ZERO_PIVOT */
     int device;           /* CUDA device ordinal (default 0) */
-    void* stream;         /* cudaStream_t to use; NULL = the context creates its own */
+    int create_stream;    /* 1 (default): the context creates its own non-blocking stream;
+                             0: use `stream` as given (NULL = the legacy default stream) */
+    void* stream;         /* cudaStream_t to use when create_stream == 0 */
     int64_t spin_limit;   /* polls before a device wait gives up (KKT_ERR_TIMEOUT); 0 = default */
+    int timing;           /* 1 = record CUDA events around each kernel group (kkt_get_phase_times) */
 } kkt_opts;
+
+/* Kernel groups timed when kkt_opts.timing is set. */
+#define KKT_PHASE_GATHER 0    /* value gather + ||K||_inf */
+#define KKT_PHASE_REFACTOR 1  /* numeric refactorization */
+#define KKT_PHASE_LSOLVE 2    /* L^{-1} P (one launch per preconditioner apply) */
+#define KKT_PHASE_USOLVE 3    /* Q U^{-1} */
+#define KKT_PHASE_SPMV 4      /* products with K and residuals */
+#define KKT_PHASE_ORTHO 5     /* CGS2 passes, normalisation, Givens */
+#define KKT_PHASE_UPDATE 6    /* cycle start and end (v_0, y = R^{-1} g, x += Z y) */
+#define KKT_NUM_PHASES 7
 
 typedef struct {
     int32_t n;
@@ -92,6 +105,9 @@ typedef struct {
     double last_rnorm0;    /* ||r - K x0|| of the last kkt_solve */
     double norm_a_inf;     /* ||K||_inf of the last refactored matrix */
     double analyze_ms;     /* host time of kkt_analyze */
+    int64_t launches;      /* kernels this context has launched so far */
+    int64_t h2d_bytes;     /* host->device bytes copied by refactor/solve calls so far */
+    int64_t d2h_bytes;     /* device->host bytes copied by refactor/solve calls so far */
 } kkt_info;
 
 /* Fill *o with the defaults above. */
@@ -159,6 +175,14 @@ int kkt_get_factors(kkt_ctx* c, int64_t* Lp, int32_t* Li, double* Lx,
                     int64_t* Up, int32_t* Ui, double* Ux);
 
 int kkt_query(kkt_ctx* c, kkt_info* info);
+
+/*
+ * Accumulated device time (ms) and launch count of each kernel group since
+ * the last reset (arrays of KKT_NUM_PHASES; either may be NULL).  Needs
+ * kkt_opts.timing = 1; times come from CUDA events on the context's stream.
+ * reset != 0 clears the accumulators after reading.
+ */
+int kkt_get_phase_times(kkt_ctx* c, double* ms, int64_t* counts, int reset);
 void kkt_destroy(kkt_ctx* c);
 const char* kkt_strerror(int code);
 const char* kkt_last_error_detail(kkt_ctx* c);

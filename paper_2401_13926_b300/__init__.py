@@ -33,14 +33,17 @@ EXPORTS = [
     "kkt_default_opts", "kkt_create", "kkt_analyze", "kkt_refactor", "kkt_solve", "kkt_lu_solve",
     "kkt_matvec", "kkt_get_perm", "kkt_get_factor_sizes", "kkt_get_factors", "kkt_query",
     "kkt_destroy", "kkt_strerror", "kkt_last_error_detail", "kkt_order", "kkt_pivot",
+    "kkt_get_phase_times",
 ]
+PHASES = ["gather", "refactor", "lsolve", "usolve", "spmv", "ortho", "update"]
 
 
 class _Opts(C.Structure):
     _fields_ = [
         ("restart", C.c_int), ("max_cycles", C.c_int), ("stop_mode", C.c_int), ("precision", C.c_int),
         ("refine_delta", C.c_double), ("pivot_tol", C.c_double), ("boost_eps", C.c_double),
-        ("device", C.c_int), ("stream", C.c_void_p), ("spin_limit", C.c_int64),
+        ("device", C.c_int), ("create_stream", C.c_int), ("stream", C.c_void_p), ("spin_limit", C.c_int64),
+        ("timing", C.c_int),
     ]
 
 
@@ -50,7 +53,8 @@ class _Info(C.Structure):
         ("levels_l", C.c_int32), ("levels_u", C.c_int32), ("refactor_updates", C.c_double),
         ("device_bytes", C.c_int64), ("nboost", C.c_int32), ("last_iters", C.c_int32),
         ("last_cycles", C.c_int32), ("last_nrbe", C.c_double), ("last_rnorm0", C.c_double),
-        ("norm_a_inf", C.c_double), ("analyze_ms", C.c_double),
+        ("norm_a_inf", C.c_double), ("analyze_ms", C.c_double), ("launches", C.c_int64),
+        ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
     ]
 
 
@@ -92,11 +96,24 @@ def lib():
     L.kkt_last_error_detail.restype = C.c_char_p
     L.kkt_order.argtypes = [i32, vp, vp, vp]
     L.kkt_pivot.argtypes = [i32, vp, vp, vp, vp, d, vp, C.POINTER(i64), C.POINTER(i64)]
+    L.kkt_get_phase_times.argtypes = [vp, vp, vp, ip]
     for name in EXPORTS:
         if name not in ("kkt_default_opts", "kkt_destroy", "kkt_strerror", "kkt_last_error_detail"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
+
+
+def _torch_current_stream(device):
+    """torch's current stream on `device`, if torch has CUDA; device tensors
+    made by torch are then ordered with the solver's kernels."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream(device)
+    except Exception:
+        pass
+    return None
 
 
 def _host(a, dtype):
@@ -153,14 +170,19 @@ class KKTSolver:
     every matrix of the sequence (Sections 1.3 and 2.1)."""
 
     def __init__(self, restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3,
-                 boost_eps=0.0, device=0, stream=None, spin_limit=0):
+                 boost_eps=0.0, device=0, stream=None, spin_limit=0, timing=False):
         L = lib()
         o = _Opts()
         L.kkt_default_opts(C.byref(o))
         o.restart, o.max_cycles, o.stop_mode = int(restart), int(max_cycles), STOP[stop_mode]
         o.refine_delta, o.pivot_tol, o.boost_eps = float(refine_delta), float(pivot_tol), float(boost_eps)
-        o.device, o.spin_limit = int(device), int(spin_limit)
-        o.stream = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        o.device, o.spin_limit, o.timing = int(device), int(spin_limit), int(bool(timing))
+        if stream is None:
+            stream = _torch_current_stream(device)
+        if stream is None:
+            o.create_stream, o.stream = 1, None
+        else:   # order every device operation with the caller's (torch's) stream
+            o.create_stream, o.stream = 0, int(getattr(stream, "cuda_stream", stream)) or None
         h = C.c_void_p()
         rc = L.kkt_create(C.byref(h), C.byref(o))
         if rc:
@@ -248,6 +270,14 @@ class KKTSolver:
         self._check(lib().kkt_get_factors(self._h, Lp.ctypes.data, Li.ctypes.data, Lx.ctypes.data,
                                           Up.ctypes.data, Ui.ctypes.data, Ux.ctypes.data), "kkt_get_factors")
         return dict(Lp=Lp, Li=Li[:nl.value], Lx=Lx[:nl.value], Up=Up, Ui=Ui[:nu.value], Ux=Ux[:nu.value])
+
+    def phase_times(self, reset=False):
+        """{phase: (ms, launches)} accumulated by the library's CUDA events."""
+        ms = np.zeros(len(PHASES))
+        cnt = np.zeros(len(PHASES), np.int64)
+        self._check(lib().kkt_get_phase_times(self._h, ms.ctypes.data, cnt.ctypes.data, int(bool(reset))),
+                    "kkt_get_phase_times")
+        return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
 
     def info(self):
         inf = _Info()

@@ -214,6 +214,7 @@ __global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t*
             for (int64_t q = dk + 1 + lane; q < ek; q += 32) {
                 const int32_t c = __ldg(&Fj[q]);
                 const int64_t pos = find_col(Fj, p + 1, e, c);
+                if (pos >= e || __ldg(&Fj[pos]) != c) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
                 __stcg(&Fx[pos], __ldcg(&Fx[pos]) - lik * __ldcg(&Fx[q]));
             }
             __threadfence();

@@ -46,6 +46,14 @@ struct kkt_ctx {
     std::string detail;
     int nboost = 0, last_iters = 0, last_cycles = 0;
     double last_nrbe = 0, last_rnorm0 = 0, norm_a = 0, analyze_ms = 0;
+    int64_t launches = 0, h2d = 0, d2h = 0;
+    // phase timing (opts.timing): event pairs recorded on the stream and
+    // drained at the next host synchronisation
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_phase;     // phase of each pending pair
+    size_t ev_used = 0;
+    double phase_ms[KKT_NUM_PHASES] = {0};
+    int64_t phase_n[KKT_NUM_PHASES] = {0};
 };
 
 namespace {
@@ -64,6 +72,9 @@ int cuda_fail(kkt_ctx* c, cudaError_t e, const char* what) {
     } while (0)
 
 void free_device(kkt_ctx* c) {
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    c->ev_pool.clear();
+    c->ev_used = 0;
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
     if (c->h_s) { cudaFreeHost(c->h_s); c->h_s = nullptr; }
@@ -91,9 +102,13 @@ int upload(kkt_ctx* c, T** p, const std::vector<T>& v) {
     return KKT_OK;
 }
 
+void phase_drain(kkt_ctx* c);
+
 int read_scalars(kkt_ctx* c) {
     CK(cudaMemcpyAsync(c->h_s, c->d_s, sizeof(DevScal), cudaMemcpyDeviceToHost, c->stream));
+    c->d2h += (int64_t)sizeof(DevScal);
     CK(cudaStreamSynchronize(c->stream));
+    phase_drain(c);
     return KKT_OK;
 }
 
@@ -104,6 +119,33 @@ int device_error(kkt_ctx* c) {
         return e;
     }
     return KKT_OK;
+}
+
+constexpr size_t EV_PAIRS = 512;
+
+// Phase timer: a start event now, the matching end event from the returned
+// index after the launches of the phase.
+int phase_begin(kkt_ctx* c, int phase) {
+    if (!c->o.timing || c->ev_pool.empty()) return -1;
+    if (c->ev_used >= EV_PAIRS) return -1;   // pool full until the next drain
+    size_t i = c->ev_used++;
+    c->ev_phase[i] = phase;
+    cudaEventRecord(c->ev_pool[2 * i], c->stream);
+    return (int)i;
+}
+void phase_end(kkt_ctx* c, int i) {
+    if (i >= 0) cudaEventRecord(c->ev_pool[2 * i + 1], c->stream);
+}
+// Called after a stream synchronisation: all pending events are complete.
+void phase_drain(kkt_ctx* c) {
+    for (size_t i = 0; i < c->ev_used; i++) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]) == cudaSuccess) {
+            c->phase_ms[c->ev_phase[i]] += ms;
+            c->phase_n[c->ev_phase[i]] += 1;
+        }
+    }
+    c->ev_used = 0;
 }
 
 long long spin(const kkt_ctx* c) { return c->o.spin_limit > 0 ? (long long)c->o.spin_limit : DEFAULT_SPIN; }
@@ -123,10 +165,15 @@ void lu_apply(kkt_ctx* c, const double* rhs, double* out) {
     const int n = c->A.n;
     const int g = persist_grid(c);
     kkt::k_trsv_prep<<<1, 1, 0, c->stream>>>(c->d_s);
+    int t = phase_begin(c, KKT_PHASE_LSOLVE);
     kkt::k_lsolve<<<g, PERSIST_THREADS, 0, c->stream>>>(n, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_P, rhs,
                                                        c->d_y, c->d_done_l, c->d_s, spin(c));
+    phase_end(c, t);
+    t = phase_begin(c, KKT_PHASE_USOLVE);
     kkt::k_usolve<<<g, PERSIST_THREADS, 0, c->stream>>>(n, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_Q,
                                                        c->d_y, c->d_xp, out, c->d_done_u, c->d_s, spin(c));
+    phase_end(c, t);
+    c->launches += 3;
 }
 
 int check_ctx(kkt_ctx* c, bool need_factors) {
@@ -153,6 +200,7 @@ void kkt_default_opts(kkt_opts* o) {
     o->pivot_tol = 1e-3;
     o->boost_eps = 0.0;
     o->device = 0;
+    o->create_stream = 1;
     o->stream = nullptr;
     o->spin_limit = 0;
 }
@@ -191,7 +239,7 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
     cudaError_t e = cudaSetDevice(c->dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev);
     if (e == cudaSuccess) {
-        if (c->o.stream) c->stream = (cudaStream_t)c->o.stream;
+        if (!c->o.create_stream) c->stream = (cudaStream_t)c->o.stream;
         else { e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking); c->own_stream = true; }
     }
     if (e != cudaSuccess) { delete c; return KKT_ERR_CUDA; }
@@ -210,7 +258,7 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
 void kkt_destroy(kkt_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->dev);
-    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->stream);
     free_device(c);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -321,6 +369,11 @@ int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* col
     if ((rc = dalloc(c, &c->d_s, 1))) return rc;
     CK(cudaMemsetAsync(c->d_s, 0, sizeof(DevScal), c->stream));
     CK(cudaMallocHost(&c->h_s, sizeof(DevScal)));
+    if (c->o.timing) {
+        c->ev_pool.resize(2 * EV_PAIRS);
+        c->ev_phase.assign(EV_PAIRS, 0);
+        for (auto& e : c->ev_pool) CK(cudaEventCreate(&e));
+    }
     CK(cudaStreamSynchronize(c->stream));
     c->analyzed = true;
     c->factored = false;
@@ -336,15 +389,21 @@ int kkt_refactor(kkt_ctx* c, const double* values, int values_on_device) {
     const double* vals = values;
     if (!values_on_device) {
         CK(cudaMemcpyAsync(c->d_vals, values, sizeof(double) * (size_t)c->nnz_a, cudaMemcpyHostToDevice, c->stream));
+        c->h2d += (int64_t)sizeof(double) * c->nnz_a;
         vals = c->d_vals;
     }
     const int n = c->A.n;
     const int64_t nnzF = (int64_t)c->lay.Fj.size();
     kkt::k_refactor_prep<<<1, 1, 0, c->stream>>>(c->d_s);
+    int t = phase_begin(c, KKT_PHASE_GATHER);
     kkt::k_gather<<<2 * c->num_sms, 256, 0, c->stream>>>(vals, c->d_fsrc, nnzF, c->d_Fx, c->d_Arp, c->d_asrc,
                                                          c->d_Ax, n, c->d_s);
+    phase_end(c, t);
+    t = phase_begin(c, KKT_PHASE_REFACTOR);
     kkt::k_refactor<<<persist_grid(c), PERSIST_THREADS, 0, c->stream>>>(
         n, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_done_f, c->d_s, c->o.boost_eps, spin(c));
+    phase_end(c, t);
+    c->launches += 3;
     CK(cudaGetLastError());
     if ((rc = read_scalars(c))) return rc;
     c->nboost = c->h_s->nboost;
@@ -363,13 +422,17 @@ int kkt_lu_solve(kkt_ctx* c, const double* b, double* x, int on_device) {
     double* xd = x;
     if (!on_device) {
         CK(cudaMemcpyAsync(c->d_b, b, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        c->h2d += (int64_t)sizeof(double) * n;
         bd = c->d_b;
         xd = c->d_x;
     }
     CK(cudaMemsetAsync(&c->d_s->err, 0, sizeof(int) * 3, c->stream));
     lu_apply(c, bd, xd);
     CK(cudaGetLastError());
-    if (!on_device) CK(cudaMemcpyAsync(x, c->d_x, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) {
+        CK(cudaMemcpyAsync(x, c->d_x, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+        c->d2h += (int64_t)sizeof(double) * n;
+    }
     if ((rc = read_scalars(c))) return rc;
     return device_error(c);
 }
@@ -383,13 +446,21 @@ int kkt_matvec(kkt_ctx* c, const double* x, double* y, int on_device) {
     double* yd = y;
     if (!on_device) {
         CK(cudaMemcpyAsync(c->d_b, x, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        c->h2d += (int64_t)sizeof(double) * n;
         xd = c->d_b;
         yd = c->d_w;
     }
+    int t = phase_begin(c, KKT_PHASE_SPMV);
     kkt::k_spmv<<<red_blocks(c), kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, xd, yd);
+    phase_end(c, t);
+    c->launches += 1;
     CK(cudaGetLastError());
-    if (!on_device) CK(cudaMemcpyAsync(y, c->d_w, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) {
+        CK(cudaMemcpyAsync(y, c->d_w, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+        c->d2h += (int64_t)sizeof(double) * n;
+    }
     CK(cudaStreamSynchronize(c->stream));
+    phase_drain(c);
     return KKT_OK;
 }
 
@@ -403,6 +474,7 @@ int kkt_solve(kkt_ctx* c, const double* b, double* x, int on_device, double tol,
     double* xd = x;
     if (!on_device) {
         CK(cudaMemcpyAsync(c->d_b, b, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        c->h2d += (int64_t)sizeof(double) * n;
         bd = c->d_b;
         xd = c->d_x;
     }
@@ -411,9 +483,12 @@ int kkt_solve(kkt_ctx* c, const double* b, double* x, int on_device, double tol,
     CK(cudaMemsetAsync(&c->d_s->err, 0, sizeof(int) * 3, c->stream));
     // x0 = (LU)^{-1} b, its residual and the refine-or-not decision
     lu_apply(c, bd, xd);
+    int t = phase_begin(c, KKT_PHASE_SPMV);
     kkt::k_residual<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, bd, xd, c->d_r,
                                                             c->d_part, c->d_s);
+    phase_end(c, t);
     kkt::k_decide<<<1, 1, 0, c->stream>>>(c->d_s, 0, tol, stop, c->o.refine_delta);
+    c->launches += 2;
     CK(cudaGetLastError());
     if ((rc = read_scalars(c))) return rc;
     if ((rc = device_error(c))) return rc;
@@ -422,34 +497,51 @@ int kkt_solve(kkt_ctx* c, const double* b, double* x, int on_device, double tol,
     while (!c->h_s->done) {
         if (cycles >= c->o.max_cycles) { status = KKT_ERR_NOT_CONVERGED; break; }
         cycles++;
+        t = phase_begin(c, KKT_PHASE_UPDATE);
         kkt::k_cycle_init<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_r, c->d_V, c->d_s, tol, stop);
+        phase_end(c, t);
+        c->launches += 1;
         for (int j = 0; j < m; j++) {
             double* vj = c->d_V + (int64_t)j * c->ld;
             double* zj = c->d_Z + (int64_t)j * c->ld;
             lu_apply(c, vj, zj);
+            t = phase_begin(c, KKT_PHASE_SPMV);
             kkt::k_spmv<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, zj, c->d_w);
+            phase_end(c, t);
+            t = phase_begin(c, KKT_PHASE_ORTHO);
             kkt::k_cgs_dots<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_V, c->ld, c->d_w, c->d_part, c->d_s);
             kkt::k_cgs_update<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_V, c->ld, c->d_w, 0, c->d_part,
                                                                       c->d_s, m, stop);
             kkt::k_cgs_update<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_V, c->ld, c->d_w, 1, c->d_part,
                                                                       c->d_s, m, stop);
             kkt::k_normalize<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_w, c->d_V, c->ld, c->d_s);
+            phase_end(c, t);
+            c->launches += 5;
             CK(cudaGetLastError());
             if ((rc = read_scalars(c))) return rc;
             if ((rc = device_error(c))) return rc;
             if (c->h_s->met || c->h_s->hn == 0.0) break;
         }
+        t = phase_begin(c, KKT_PHASE_UPDATE);
         kkt::k_hess_solve<<<1, 32, 0, c->stream>>>(c->d_s);
         kkt::k_update_x<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Z, c->ld, xd, c->d_s);
+        phase_end(c, t);
+        t = phase_begin(c, KKT_PHASE_SPMV);
         kkt::k_residual<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, bd, xd, c->d_r,
                                                                 c->d_part, c->d_s);
+        phase_end(c, t);
         kkt::k_decide<<<1, 1, 0, c->stream>>>(c->d_s, 1, tol, stop, c->o.refine_delta);
+        c->launches += 4;
         CK(cudaGetLastError());
         if ((rc = read_scalars(c))) return rc;
         if ((rc = device_error(c))) return rc;
     }
-    if (!on_device) CK(cudaMemcpyAsync(x, c->d_x, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) {
+        CK(cudaMemcpyAsync(x, c->d_x, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+        c->d2h += (int64_t)sizeof(double) * n;
+    }
     CK(cudaStreamSynchronize(c->stream));
+    phase_drain(c);
     c->last_iters = c->h_s->iters;
     c->last_cycles = cycles;
     c->last_nrbe = c->h_s->nrbe;
@@ -517,6 +609,24 @@ int kkt_query(kkt_ctx* c, kkt_info* info) {
     info->last_rnorm0 = c->last_rnorm0;
     info->norm_a_inf = c->norm_a;
     info->analyze_ms = c->analyze_ms;
+    info->launches = c->launches;
+    info->h2d_bytes = c->h2d;
+    info->d2h_bytes = c->d2h;
+    return KKT_OK;
+}
+
+int kkt_get_phase_times(kkt_ctx* c, double* ms, int64_t* counts, int reset) {
+    if (!c) return KKT_ERR_INVALID;
+    if (c->analyzed) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+    }
+    phase_drain(c);
+    for (int p = 0; p < KKT_NUM_PHASES; p++) {
+        if (ms) ms[p] = c->phase_ms[p];
+        if (counts) counts[p] = c->phase_n[p];
+        if (reset) { c->phase_ms[p] = 0; c->phase_n[p] = 0; }
+    }
     return KKT_OK;
 }
 
