@@ -11,6 +11,11 @@
  *                      solver steps of Section 1.3): exact minimum degree on
  *                      the column-intersection graph (pattern of A^T A),
  *                      explicit elimination graph, ties by smallest index.
+ * Update order and rounding: the paper fixes neither.  Both factorizations
+ * apply the finished columns in ascending pivot order -- one valid
+ * topological order of the elimination graph -- and every update
+ * x_i <- x_i - l_ik x_k is a single fused multiply-add (one rounding).
+ *
  *   or_lu           -- first numeric factorization with threshold partial
  *                      pivoting (Section 1.3, "full symbolic analysis and
  *                      numerical factorization with pivoting for the first
@@ -205,13 +210,16 @@ void *or_lu(int n, const int *Ap, const int *Ai, const double *Ax,
         int top = n;
         reach(n, seeds, ns, pinv, F->Lp, Li.a, mark, j, stack, pos, out, &top);
         for (int p = Ap[c]; p < Ap[c + 1]; p++) x[Ai[p]] += Ax[p];
-        /* numeric: eliminate with the finished columns in topological order */
-        for (int t = top; t < n; t++) {
-            int r = out[t];
-            int k = pinv[r];
-            if (k < 0) continue;
-            double xr = x[r];
-            for (int p = F->Lp[k]; p < F->Lp[k + 1]; p++) x[Li.a[p]] -= Lx.a[p] * xr;
+        /* numeric: eliminate with the finished columns of the reach in
+         * ascending pivot order (a topological order of the graph of L);
+         * each update is one fused multiply-add */
+        int npiv = 0;
+        for (int t = top; t < n; t++) if (pinv[out[t]] >= 0) seeds[npiv++] = pinv[out[t]];
+        qsort(seeds, (size_t)npiv, sizeof(int), cmp_int);
+        for (int a = 0; a < npiv; a++) {
+            int k = seeds[a];
+            double xr = x[P[k]];
+            for (int p = F->Lp[k]; p < F->Lp[k + 1]; p++) x[Li.a[p]] = fma(-Lx.a[p], xr, x[Li.a[p]]);
         }
         /* pivot search among the rows not yet pivotal */
         double amax = 0.0;
@@ -303,11 +311,14 @@ void *or_refactor(int n, const int *Ap, const int *Ai, const double *Ax,
         /* permuted row i < j has children = rows of L(:, i) */
         reach(n, seeds, ns, colof, F->Lp, Li.a, mark, j, stack, pos, out, &top);
         for (int p = Ap[c]; p < Ap[c + 1]; p++) x[pinv[Ai[p]]] += Ax[p];
+        /* finished columns in ascending pivot order (a topological order of
+         * the graph of L), one fused multiply-add per update */
+        qsort(out + top, (size_t)(n - top), sizeof(int), cmp_int);
         for (int t = top; t < n; t++) {
             int i = out[t];
-            if (i >= j) continue;
+            if (i >= j) break;
             double xi = x[i];
-            for (int p = F->Lp[i]; p < F->Lp[i + 1]; p++) x[Li.a[p]] -= Lx.a[p] * xi;
+            for (int p = F->Lp[i]; p < F->Lp[i + 1]; p++) x[Li.a[p]] = fma(-Lx.a[p], xi, x[Li.a[p]]);
         }
         if (mark[j] != j) { *status = OR_ERR_SINGULAR; goto fail; }
         double d = x[j];

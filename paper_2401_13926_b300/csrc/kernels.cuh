@@ -215,7 +215,7 @@ __global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t*
                 const int32_t c = __ldg(&Fj[q]);
                 const int64_t pos = find_col(Fj, p + 1, e, c);
                 if (pos >= e || __ldg(&Fj[pos]) != c) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
-                __stcg(&Fx[pos], __ldcg(&Fx[pos]) - lik * __ldcg(&Fx[q]));
+                __stcg(&Fx[pos], fma(-lik, __ldcg(&Fx[q]), __ldcg(&Fx[pos])));
             }
             __threadfence();
             __syncwarp();
