@@ -187,6 +187,44 @@ void kkt_destroy(kkt_ctx* c);
 const char* kkt_strerror(int code);
 const char* kkt_last_error_detail(kkt_ctx* c);
 
+/* ---- triangular solve without any device allocation ---- */
+
+/*
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory -- an application whose device memory
+ * belongs to its own arena allocator, or a latency-critical loop in which a
+ * cudaMalloc/cudaFree could synchronise the device.
+ *
+ * x = Q U^{-1} L^{-1} P b, the same result as kkt_lu_solve, computed from
+ * factors the caller already holds on the current device, in the combined
+ * row layout the solver uses internally: F = L + U - I of B = K(P,Q), CSR
+ * over the permuted rows with columns ascending in each row; row i holds
+ * L(i,k<i) (unit diagonal not stored), then U(i,i) at Fdiag[i], then
+ * U(i,j>i).
+ *   n        rows, 1 <= n <= KKT_NOALLOC_MAX_N; larger n returns
+ *            KKT_ERR_INVALID without launching anything.
+ *   Fp[n+1], Fdiag[n] (int64), Fj[nnz] (int32), Fx[nnz] (double),
+ *   P[n], Q[n] (int32), b[n] (double): device pointers, read only.
+ *   x[n]     device pointer, written.
+ *   stream   cudaStream_t (NULL = the legacy default stream); the call
+ *            returns after the solve has finished on it.
+ * Working memory is one static device array of KKT_NOALLOC_SCRATCH_BYTES in
+ * the library image, held by every GPU that loads the library until the
+ * process exits; the call makes no cudaMalloc or cudaFree.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress)
+ * with the device current and caches it: make that first call before any
+ * stream capture.  All calls on a device share the array, so calls that
+ * overlap on the GPU (other streams, other threads) race and give wrong
+ * results: serialise them.  Each call clears the flags and counters it uses.
+ * Errors: KKT_ERR_INVALID, KKT_ERR_TIMEOUT (a bounded wait ran out),
+ * KKT_ERR_CUDA.
+ */
+#define KKT_NOALLOC_MAX_N 65536
+#define KKT_NOALLOC_SCRATCH_BYTES (256 + (KKT_NOALLOC_MAX_N) * 24)
+int kkt_lu_solve_noalloc(int32_t n, const int64_t* Fp, const int32_t* Fj, const int64_t* Fdiag,
+                         const double* Fx, const int32_t* P, const int32_t* Q, const double* b,
+                         double* x, void* stream);
+
 /* ---- host-only helpers (no GPU needed) ---- */
 
 /* Column order of kkt_analyze (approximate minimum degree on K^T K). */

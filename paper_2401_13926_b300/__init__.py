@@ -33,8 +33,9 @@ EXPORTS = [
     "kkt_default_opts", "kkt_create", "kkt_analyze", "kkt_refactor", "kkt_solve", "kkt_lu_solve",
     "kkt_matvec", "kkt_get_perm", "kkt_get_factor_sizes", "kkt_get_factors", "kkt_query",
     "kkt_destroy", "kkt_strerror", "kkt_last_error_detail", "kkt_order", "kkt_pivot",
-    "kkt_get_phase_times",
+    "kkt_get_phase_times", "kkt_lu_solve_noalloc",
 ]
+NOALLOC_MAX_N = 65536
 PHASES = ["gather", "refactor", "lsolve", "usolve", "spmv", "ortho", "update"]
 
 
@@ -97,6 +98,7 @@ def lib():
     L.kkt_order.argtypes = [i32, vp, vp, vp]
     L.kkt_pivot.argtypes = [i32, vp, vp, vp, vp, d, vp, C.POINTER(i64), C.POINTER(i64)]
     L.kkt_get_phase_times.argtypes = [vp, vp, vp, ip]
+    L.kkt_lu_solve_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("kkt_default_opts", "kkt_destroy", "kkt_strerror", "kkt_last_error_detail"):
             getattr(L, name).restype = C.c_int
@@ -163,6 +165,22 @@ def pivot(rowptr, colind, values, Q=None, tol=1e-3):
     if rc:
         raise KKTError(rc, "kkt_pivot")
     return P, nl.value, nu.value
+
+
+def lu_solve_noalloc(Fp, Fj, Fdiag, Fx, P, Q, b, x, stream=None):
+    """kkt_lu_solve_noalloc: x = Q U^{-1} L^{-1} P b from caller-held device
+    factors in the combined row layout, with no device allocation (for
+    callers whose device memory is owned elsewhere).  All arguments are
+    CUDA tensors; n = len(b) <= NOALLOC_MAX_N."""
+    if stream is None:
+        stream = _torch_current_stream(b.device.index)
+    st = int(getattr(stream, "cuda_stream", stream or 0)) or None
+    n = int(b.numel())
+    rc = lib().kkt_lu_solve_noalloc(n, Fp.data_ptr(), Fj.data_ptr(), Fdiag.data_ptr(), Fx.data_ptr(),
+                                    P.data_ptr(), Q.data_ptr(), b.data_ptr(), x.data_ptr(), st)
+    if rc:
+        raise KKTError(rc, "kkt_lu_solve_noalloc")
+    return x
 
 
 class KKTSolver:
