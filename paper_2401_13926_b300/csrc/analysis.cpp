@@ -414,6 +414,7 @@ int build_layout(const Csr& A, const std::vector<int32_t>& P, const std::vector<
     }
     out->levelsL = n ? ml : 0;
     out->updates = upd;
+    out->levL = lev;
     int32_t mu = 0;
     for (int32_t i = n - 1; i >= 0; i--) {
         int32_t l = 0;
@@ -422,6 +423,7 @@ int build_layout(const Csr& A, const std::vector<int32_t>& P, const std::vector<
         mu = std::max(mu, l + 1);
     }
     out->levelsU = n ? mu : 0;
+    out->levU = lev;
     return KKT_OK;
 }
 

@@ -64,6 +64,8 @@ struct Layout {
     std::vector<int64_t> Fsrc;     // F slot -> canonical A entry, -1 for fill
     int64_t nnzL = 0, nnzU = 0;    // strict lower, upper incl. diagonal
     int32_t levelsL = 0, levelsU = 0;
+    std::vector<int32_t> levL;     // L-solve DAG level of each row (rows ascending)
+    std::vector<int32_t> levU;     // U-solve DAG level of each row (rows descending)
     double updates = 0;            // multiply-adds of one refactorization
 };
 

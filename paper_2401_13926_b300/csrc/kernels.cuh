@@ -48,7 +48,7 @@ struct DevScal {
     int met;               // inner criterion met in this cycle
     int done;              // solve finished (converged or nothing to do)
     // sync-free scheduling
-    unsigned gen_fact, gen_l, gen_u;
+    unsigned gen_fact;
     unsigned ticket_fact, ticket_l, ticket_u;
     unsigned red_count;
     // errors
@@ -130,6 +130,23 @@ __device__ __forceinline__ double reduce_partials(const double* part, int slot, 
     return block_sum(v, sh);
 }
 
+// A factor or solve value that is not final yet holds SENTINEL (a NaN
+// payload no arithmetic produces); readers spin on the value itself.
+constexpr unsigned long long SENTINEL_BITS = 0x7ff4dead5ca1ab1eull;
+
+__device__ __forceinline__ double sentinel() { return __longlong_as_double((long long)SENTINEL_BITS); }
+__device__ __forceinline__ bool is_sentinel(double v) {
+    return (unsigned long long)__double_as_longlong(v) == SENTINEL_BITS;
+}
+__device__ __forceinline__ double ld_relaxed_f64(const double* p) {
+    double v;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_f64(double* p, double v) {
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
 // ---------------------------------------------------------------- K0: gather
 // Start of a refactorization: new generation, tickets and error words.
 __global__ void k_refactor_prep(DevScal* s) {
@@ -144,12 +161,16 @@ __global__ void k_refactor_prep(DevScal* s) {
 
 // Fx[t] = caller value of the entry of A that lands in factor slot t (0 for
 // fill); Ax[e] = caller value of canonical entry e; ||K||_inf from row sums.
+// Slots from tail_begin on belong to the rows the tail kernel factors in
+// shared memory; they are armed with SENTINEL instead (the tail kernel
+// gathers their values itself and publishes each row when it is final).
 __global__ void k_gather(const double* __restrict__ vals, const int64_t* __restrict__ fsrc, int64_t nnzF,
-                         double* __restrict__ Fx, const int32_t* __restrict__ Arp,
+                         int64_t tail_begin, double* __restrict__ Fx, const int32_t* __restrict__ Arp,
                          const int64_t* __restrict__ asrc, double* __restrict__ Ax, int n, DevScal* s) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = tid; t < nnzF; t += stride) {
+        if (t >= tail_begin) { Fx[t] = sentinel(); continue; }
         int64_t q = fsrc[t];
         Fx[t] = (q >= 0) ? vals[q] : 0.0;
     }
@@ -190,6 +211,7 @@ __device__ __forceinline__ int64_t find_col(const int32_t* __restrict__ Fj, int6
 __global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
                            const int64_t* __restrict__ Fdiag, double* Fx, unsigned* done, DevScal* s,
                            double boost_eps, long long limit) {
+    // rows [0, n) of the bulk: warp per row, factor values in global memory
     const int lane = threadIdx.x & 31;
     const unsigned gen = *(volatile unsigned*)&s->gen_fact;
     const double boost = boost_eps * *(volatile double*)&s->normA;
@@ -236,73 +258,309 @@ __global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t*
     }
 }
 
+// Tail rows [t0, nrows): one block per row.  The row's values live in
+// shared memory (w), and a shared map gives the position of every column
+// >= t0 of the row, so an update from a tail row costs one shared load and
+// one shared read-modify-write per entry.  Updates still go in ascending k,
+// each one fused multiply-add (the same arithmetic as the bulk kernel).  A
+// finished tail row writes its values, then its diagonal last: the diagonal
+// (armed with SENTINEL by the gather) is the row's completion flag.
+constexpr int TAIL_THREADS = 256;
+
+__global__ void k_refactor_prep_tail(DevScal* s) { s->ticket_fact = 0; }
+
+__global__ void __launch_bounds__(TAIL_THREADS)
+k_refactor_tail(int t0, int nrows, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
+                const int64_t* __restrict__ Fdiag, double* Fx, const double* __restrict__ vals,
+                const int64_t* __restrict__ fsrc, DevScal* s, double boost_eps, long long limit) {
+    extern __shared__ double tail_sh[];
+    __shared__ double s_l;
+    __shared__ int s_row, s_ok;
+    const int T = nrows - t0;
+    const int tid = threadIdx.x;
+    short* map = reinterpret_cast<short*>(tail_sh);                   // T entries
+    double* w = tail_sh + ((2 * (size_t)T + 7) / 8);                  // row values
+    for (int c = tid; c < T; c += blockDim.x) map[c] = -1;
+    const double boost = boost_eps * *(volatile double*)&s->normA;
+    __syncthreads();
+    for (;;) {
+        if (tid == 0) {
+            s_row = t0 + (int)atomicAdd(&s->ticket_fact, 1u);
+            s_ok = ld_volatile_int(&s->abort) ? 0 : 1;
+        }
+        __syncthreads();
+        const int row = s_row;
+        if (row >= nrows || !s_ok) return;
+        const int64_t b = Fp[row], d = Fdiag[row], e = Fp[row + 1];
+        const int len = (int)(e - b);
+        for (int q = tid; q < len; q += blockDim.x) {
+            const int64_t src = fsrc[b + q];
+            w[q] = src >= 0 ? vals[src] : 0.0;
+            const int c = Fj[b + q];
+            if (c >= t0) map[c - t0] = (short)q;
+        }
+        __syncthreads();
+        int bad = 0;
+        for (int64_t p = b; p < d; p++) {
+            const int k = Fj[p];
+            const int64_t dk = Fdiag[k], ek = Fp[k + 1];
+            if (tid == 0) {
+                double ukk;
+                if (k >= t0) {   // wait for the diagonal: tail row k is final once it is
+                    ukk = ld_relaxed_f64(&Fx[dk]);
+                    for (long long it = 0; is_sentinel(ukk); it++) {
+                        if (ld_volatile_int(&s->abort)) { bad = 1; break; }
+                        if (it >= limit) { raise_error(s, KKT_ERR_TIMEOUT, row); bad = 1; break; }
+                        __nanosleep(32);
+                        ukk = ld_relaxed_f64(&Fx[dk]);
+                    }
+                    __threadfence();
+                } else {
+                    ukk = __ldcg(&Fx[dk]);
+                }
+                const double l = w[p - b] / ukk;
+                w[p - b] = l;
+                s_l = l;
+                s_ok = !bad;
+            }
+            __syncthreads();
+            if (!s_ok) return;
+            const double l = s_l;
+            if (k >= t0) {
+                for (int64_t q = dk + 1 + tid; q < ek; q += blockDim.x) {
+                    const int pos = map[Fj[q] - t0];
+                    if (pos < 0) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
+                    w[pos] = fma(-l, __ldcg(&Fx[q]), w[pos]);
+                }
+            } else {
+                for (int64_t q = dk + 1 + tid; q < ek; q += blockDim.x) {
+                    const int c = Fj[q];
+                    int pos;
+                    if (c >= t0) pos = map[c - t0];
+                    else {
+                        const int64_t f = find_col(Fj, p + 1, e, c);
+                        pos = (f < e && Fj[f] == c) ? (int)(f - b) : -1;
+                    }
+                    if (pos < 0) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
+                    w[pos] = fma(-l, __ldcg(&Fx[q]), w[pos]);
+                }
+            }
+            __syncthreads();
+        }
+        // pivot, then publish: values first, the diagonal last
+        if (tid == 0) {
+            double u = w[d - b];
+            int fail = 0;
+            if (!isfinite(u)) { raise_error(s, KKT_ERR_NONFINITE, row); fail = 1; }
+            else if (boost > 0.0) {
+                if (fabs(u) < boost) { u = (u < 0.0) ? -boost : boost; atomicAdd(&s->nboost, 1); }
+            } else if (u == 0.0) { raise_error(s, KKT_ERR_ZERO_PIVOT, row); fail = 1; }
+            w[d - b] = u;
+            s_ok = !fail;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        for (int q = tid; q < len; q += blockDim.x) {
+            if (b + q != d) __stcg(&Fx[b + q], w[q]);
+            const int c = Fj[b + q];
+            if (c >= t0) map[c - t0] = -1;
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) st_relaxed_f64(&Fx[d], w[d - b]);
+    }
+}
+
 // ---------------------------------------------------------------- K2/K3: triangular solves
+// Rows are split by their depth in the dependency DAG.  The wide part runs
+// sync-free over the whole GPU (warps take rows from a ticket in dependency
+// order); the long narrow chain -- the dense separators the fill-reducing
+// order puts last -- runs in ONE block whose warps hand values to each other
+// through shared memory, where a hand-off costs tens of cycles instead of a
+// round trip to L2.  L-solve: bulk first, then the chain (the highest
+// levels).  U-solve: the chain first (the lowest levels, rows near n), then
+// the bulk.
+//
+// A value that is not computed yet holds SENTINEL (a NaN payload that no
+// arithmetic produces); consumers spin on the value itself, so one load
+// both synchronises and delivers the operand.  Each solve re-arms the other
+// one's vector: the L-solve sets xp[i] = SENTINEL, the U-solve sets
+// y[i] = SENTINEL after reading it.
+// Wait for a value produced by another warp anywhere on the GPU.
+__device__ __forceinline__ bool wait_value(const double* p, double* out, DevScal* s, long long limit, int row) {
+    double v = ld_relaxed_f64(p);
+    for (long long it = 0; is_sentinel(v); it++) {
+        if (ld_volatile_int(&s->abort)) return false;
+        if (it >= limit) { raise_error(s, KKT_ERR_TIMEOUT, row); return false; }
+        __nanosleep(32);
+        v = ld_relaxed_f64(p);
+    }
+    *out = v;
+    return true;
+}
+
+// Wait for a value produced by another warp of this block (shared memory).
+__device__ __forceinline__ bool wait_shared(const volatile double* p, double* out, DevScal* s, long long limit,
+                                            int row) {
+    double v = *p;
+    for (long long it = 0; is_sentinel(v); it++) {
+        if ((it & 1023) == 0 && ld_volatile_int(&s->abort)) return false;
+        if (it >= 4 * limit) { raise_error(s, KKT_ERR_TIMEOUT, row); return false; }
+        v = *p;
+    }
+    *out = v;
+    return true;
+}
+
 __global__ void k_trsv_prep(DevScal* s) {
-    s->gen_l += 1;
-    s->gen_u += 1;
     s->ticket_l = 0;
     s->ticket_u = 0;
 }
 
-// y = L^{-1} (P rhs): y_i = rhs[P[i]] - sum_{k<i} L_ik y_k, unit L.
-__global__ void k_lsolve(int n, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
-                         const int64_t* __restrict__ Fdiag, const double* __restrict__ Fx,
-                         const int32_t* __restrict__ P, const double* __restrict__ rhs, double* y,
-                         unsigned* done, DevScal* s, long long limit) {
+__global__ void k_fill_sentinel(double* a, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = sentinel();
+}
+
+// y_i = rhs[P[i]] - sum_{k<i} L_ik y_k over the bulk rows (ascending list).
+__global__ void k_lsolve_bulk(int nrows, const int32_t* __restrict__ rows, const int64_t* __restrict__ Fp,
+                              const int32_t* __restrict__ Fj, const int64_t* __restrict__ Fdiag,
+                              const double* __restrict__ Fx, const int32_t* __restrict__ P,
+                              const double* __restrict__ rhs, double* y, double* xp, DevScal* s, long long limit) {
     const int lane = threadIdx.x & 31;
-    const unsigned gen = *(volatile unsigned*)&s->gen_l;
     for (;;) {
-        int row = 0;
-        if (lane == 0) row = (int)atomicAdd(&s->ticket_l, 1u);
-        row = __shfl_sync(0xffffffffu, row, 0);
-        if (row >= n) return;
+        int t = 0;
+        if (lane == 0) t = (int)atomicAdd(&s->ticket_l, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= nrows) return;
+        const int row = rows[t];
         const int64_t b = Fp[row], d = Fdiag[row];
         double acc = 0.0;
         int ok = 1;
         for (int64_t p = b + lane; p < d; p += 32) {
             const int32_t k = __ldg(&Fj[p]);
-            if (!wait_flag(&done[k], gen, s, limit, row)) { ok = 0; break; }
-            acc += __ldg(&Fx[p]) * __ldcg(&y[k]);
+            const double a = __ldg(&Fx[p]);
+            double v;
+            if (!wait_value(&y[k], &v, s, limit, row)) { ok = 0; break; }
+            acc = fma(a, v, acc);
         }
         if (!__all_sync(0xffffffffu, ok)) return;
         acc = warp_sum(acc);
         if (lane == 0) {
-            __stcg(&y[row], rhs[P[row]] - acc);
-            __threadfence();
-            st_release(&done[row], gen);
+            xp[row] = sentinel();
+            st_relaxed_f64(&y[row], rhs[P[row]] - acc);
         }
     }
 }
 
-// x' = U^{-1} y (rows descending), out[Q[i]] = x'_i.
-__global__ void k_usolve(int n, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
-                         const int64_t* __restrict__ Fdiag, const double* __restrict__ Fx,
-                         const int32_t* __restrict__ Q, const double* __restrict__ y, double* xp,
-                         double* __restrict__ out, unsigned* done, DevScal* s, long long limit) {
-    const int lane = threadIdx.x & 31;
-    const unsigned gen = *(volatile unsigned*)&s->gen_u;
-    for (;;) {
-        int t = 0;
-        if (lane == 0) t = (int)atomicAdd(&s->ticket_u, 1u);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= n) return;
-        const int row = n - 1 - t;
+// The narrow chain of the L-solve in one block: warp w takes chain slots
+// w, w + nwarps, ... in order; a dependency inside the chain is read from
+// shared memory (xs), one outside it from y (finished by the bulk kernel).
+__global__ void k_lsolve_chain(int nt, const int32_t* __restrict__ rows, const int32_t* __restrict__ slot,
+                               const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
+                               const int64_t* __restrict__ Fdiag, const double* __restrict__ Fx,
+                               const int32_t* __restrict__ P, const double* __restrict__ rhs, double* y,
+                               double* xp, DevScal* s, long long limit) {
+    extern __shared__ double xs_dyn[];
+    volatile double* xs = xs_dyn;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) xs[t] = sentinel();
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int t = warp; t < nt; t += nw) {
+        const int row = rows[t];
+        const int64_t b = Fp[row], d = Fdiag[row];
+        double acc = 0.0;
+        int ok = 1;
+        for (int64_t p = b + lane; p < d; p += 32) {
+            const int32_t k = __ldg(&Fj[p]);
+            const double a = __ldg(&Fx[p]);
+            const int tk = __ldg(&slot[k]);
+            double v;
+            if (tk >= 0) { if (!wait_shared(&xs[tk], &v, s, limit, row)) { ok = 0; break; } }
+            else v = __ldcg(&y[k]);
+            acc = fma(a, v, acc);
+        }
+        if (!__all_sync(0xffffffffu, ok)) return;
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            const double yi = rhs[P[row]] - acc;
+            xp[row] = sentinel();
+            y[row] = yi;
+            xs[t] = yi;
+        }
+        __syncwarp();
+    }
+}
+
+// The narrow chain of the U-solve (rows near n, descending list): every
+// dependency of a chain row is itself in the chain.
+__global__ void k_usolve_chain(int nt, const int32_t* __restrict__ rows, const int32_t* __restrict__ slot,
+                               const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
+                               const int64_t* __restrict__ Fdiag, const double* __restrict__ Fx,
+                               const int32_t* __restrict__ Q, double* y, double* xp, double* __restrict__ out,
+                               DevScal* s, long long limit) {
+    extern __shared__ double xs_dyn[];
+    volatile double* xs = xs_dyn;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) xs[t] = sentinel();
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int t = warp; t < nt; t += nw) {
+        const int row = rows[t];
         const int64_t d = Fdiag[row], e = Fp[row + 1];
         double acc = 0.0;
         int ok = 1;
         for (int64_t p = d + 1 + lane; p < e; p += 32) {
             const int32_t j = __ldg(&Fj[p]);
-            if (!wait_flag(&done[j], gen, s, limit, row)) { ok = 0; break; }
-            acc += __ldg(&Fx[p]) * __ldcg(&xp[j]);
+            const double a = __ldg(&Fx[p]);
+            const int tj = __ldg(&slot[j]);
+            double v;
+            if (tj >= 0) { if (!wait_shared(&xs[tj], &v, s, limit, row)) { ok = 0; break; } }
+            else v = __ldcg(&xp[j]);
+            acc = fma(a, v, acc);
         }
         if (!__all_sync(0xffffffffu, ok)) return;
         acc = warp_sum(acc);
         if (lane == 0) {
             const double xi = (__ldcg(&y[row]) - acc) / __ldg(&Fx[d]);
-            __stcg(&xp[row], xi);
+            y[row] = sentinel();
+            xp[row] = xi;
             out[Q[row]] = xi;
-            __threadfence();
-            st_release(&done[row], gen);
+            xs[t] = xi;
+        }
+        __syncwarp();
+    }
+}
+
+// x'_i = (y_i - sum_{j>i} U_ij x'_j) / U_ii over the bulk rows (descending
+// list); out[Q[i]] = x'_i.
+__global__ void k_usolve_bulk(int nrows, const int32_t* __restrict__ rows, const int64_t* __restrict__ Fp,
+                              const int32_t* __restrict__ Fj, const int64_t* __restrict__ Fdiag,
+                              const double* __restrict__ Fx, const int32_t* __restrict__ Q, double* y, double* xp,
+                              double* __restrict__ out, DevScal* s, long long limit) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = (int)atomicAdd(&s->ticket_u, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= nrows) return;
+        const int row = rows[t];
+        const int64_t d = Fdiag[row], e = Fp[row + 1];
+        double acc = 0.0;
+        int ok = 1;
+        for (int64_t p = d + 1 + lane; p < e; p += 32) {
+            const int32_t j = __ldg(&Fj[p]);
+            const double a = __ldg(&Fx[p]);
+            double v;
+            if (!wait_value(&xp[j], &v, s, limit, row)) { ok = 0; break; }
+            acc = fma(a, v, acc);
+        }
+        if (!__all_sync(0xffffffffu, ok)) return;
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            const double xi = (__ldcg(&y[row]) - acc) / __ldg(&Fx[d]);
+            y[row] = sentinel();
+            out[Q[row]] = xi;
+            st_relaxed_f64(&xp[row], xi);
         }
     }
 }

@@ -36,7 +36,16 @@ struct kkt_ctx {
     double *d_Fx = nullptr, *d_Ax = nullptr, *d_vals = nullptr;
     double *d_b = nullptr, *d_x = nullptr, *d_y = nullptr, *d_xp = nullptr, *d_r = nullptr, *d_w = nullptr;
     double *d_V = nullptr, *d_Z = nullptr, *d_part = nullptr;
-    unsigned *d_done_f = nullptr, *d_done_l = nullptr, *d_done_u = nullptr;
+    unsigned* d_done_f = nullptr;
+    // triangular-solve schedule: bulk rows (sync-free) and the narrow chain
+    // (one block); slot[i] = position of row i in its chain or -1
+    int32_t *d_rowsLb = nullptr, *d_rowsLc = nullptr, *d_rowsUc = nullptr, *d_rowsUb = nullptr;
+    int32_t *d_slotL = nullptr, *d_slotU = nullptr;
+    int nLb = 0, nLc = 0, nUc = 0, nUb = 0;
+    // refactorization split: rows [0, t0) warp per row, [t0, n) block per row
+    int t0 = 0;
+    size_t tail_smem = 0;
+    int tail_blocks = 0;
     DevScal* d_s = nullptr;
     DevScal* h_s = nullptr;   // pinned mirror
     int64_t ld = 0;
@@ -59,6 +68,46 @@ struct kkt_ctx {
 namespace {
 
 constexpr int PERSIST_THREADS = 256;
+constexpr int CHAIN_THREADS = 1024;
+constexpr int TAIL_MAX_ROWS = 8192;      // rows factored one block per row
+constexpr size_t TAIL_SMEM_MAX = 200 * 1024;
+constexpr int CHAIN_MAX = 12288;       // rows of a chain (8 bytes of shared memory each)
+constexpr int CHAIN_WIDTH = 32;        // a level belongs to the chain if it has at most this many rows
+
+// Split rows for the triangular solves.  L: the chain is the highest levels
+// whose widths are all <= CHAIN_WIDTH; U: the lowest such levels.
+void split_chain(const std::vector<int32_t>& lev, bool lower, int cap, std::vector<int32_t>* bulk,
+                 std::vector<int32_t>* chain, std::vector<int32_t>* slot) {
+    const int32_t n = (int32_t)lev.size();
+    int32_t nl = 0;
+    for (int32_t v : lev) nl = std::max(nl, v + 1);
+    std::vector<int64_t> w(nl, 0);
+    for (int32_t v : lev) w[v]++;
+    // chain levels: [l0, nl) for L, [0, l1) for U
+    int32_t lo = nl, hi = 0;
+    int64_t count = 0;
+    if (lower) {
+        while (lo > 0 && w[lo - 1] <= CHAIN_WIDTH && count + w[lo - 1] <= cap) { lo--; count += w[lo]; }
+        hi = nl;
+    } else {
+        lo = 0;
+        while (hi < nl && w[hi] <= CHAIN_WIDTH && count + w[hi] <= cap) { count += w[hi]; hi++; }
+    }
+    bulk->clear();
+    chain->clear();
+    slot->assign(n, -1);
+    if (lower) {
+        for (int32_t i = 0; i < n; i++) {
+            if (lev[i] >= lo && lev[i] < hi) { (*slot)[i] = (int32_t)chain->size(); chain->push_back(i); }
+            else bulk->push_back(i);
+        }
+    } else {
+        for (int32_t i = n - 1; i >= 0; i--) {
+            if (lev[i] >= lo && lev[i] < hi) { (*slot)[i] = (int32_t)chain->size(); chain->push_back(i); }
+            else bulk->push_back(i);
+        }
+    }
+}
 constexpr long long DEFAULT_SPIN = 1ll << 25;
 
 int cuda_fail(kkt_ctx* c, cudaError_t e, const char* what) {
@@ -155,25 +204,50 @@ int red_blocks(const kkt_ctx* c) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(kkt::RED_BLOCKS, need));
 }
 
-int persist_grid(const kkt_ctx* c) {
-    int64_t need = (c->A.n + (PERSIST_THREADS / 32) - 1) / (PERSIST_THREADS / 32);
+
+int grid_for(const kkt_ctx* c, int rows) {
+    int64_t need = ((int64_t)rows + (PERSIST_THREADS / 32) - 1) / (PERSIST_THREADS / 32);
     return (int)std::max<int64_t>(1, std::min<int64_t>(c->persist_blocks, need));
 }
 
-// x = Q U^{-1} L^{-1} P rhs  (three launches: prep, L-solve, U-solve)
+// x = Q U^{-1} L^{-1} P rhs: L bulk, L chain, U chain, U bulk.
 void lu_apply(kkt_ctx* c, const double* rhs, double* out) {
-    const int n = c->A.n;
-    const int g = persist_grid(c);
     kkt::k_trsv_prep<<<1, 1, 0, c->stream>>>(c->d_s);
+    c->launches += 1;
     int t = phase_begin(c, KKT_PHASE_LSOLVE);
-    kkt::k_lsolve<<<g, PERSIST_THREADS, 0, c->stream>>>(n, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_P, rhs,
-                                                       c->d_y, c->d_done_l, c->d_s, spin(c));
+    if (c->nLb) {
+        kkt::k_lsolve_bulk<<<grid_for(c, c->nLb), PERSIST_THREADS, 0, c->stream>>>(
+            c->nLb, c->d_rowsLb, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_P, rhs, c->d_y, c->d_xp, c->d_s, spin(c));
+        c->launches += 1;
+    }
+    if (c->nLc) {
+        kkt::k_lsolve_chain<<<1, CHAIN_THREADS, sizeof(double) * c->nLc, c->stream>>>(
+            c->nLc, c->d_rowsLc, c->d_slotL, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_P, rhs, c->d_y, c->d_xp,
+            c->d_s, spin(c));
+        c->launches += 1;
+    }
     phase_end(c, t);
     t = phase_begin(c, KKT_PHASE_USOLVE);
-    kkt::k_usolve<<<g, PERSIST_THREADS, 0, c->stream>>>(n, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_Q,
-                                                       c->d_y, c->d_xp, out, c->d_done_u, c->d_s, spin(c));
+    if (c->nUc) {
+        kkt::k_usolve_chain<<<1, CHAIN_THREADS, sizeof(double) * c->nUc, c->stream>>>(
+            c->nUc, c->d_rowsUc, c->d_slotU, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_Q, c->d_y, c->d_xp, out,
+            c->d_s, spin(c));
+        c->launches += 1;
+    }
+    if (c->nUb) {
+        kkt::k_usolve_bulk<<<grid_for(c, c->nUb), PERSIST_THREADS, 0, c->stream>>>(
+            c->nUb, c->d_rowsUb, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_Q, c->d_y, c->d_xp, out, c->d_s, spin(c));
+        c->launches += 1;
+    }
     phase_end(c, t);
-    c->launches += 3;
+}
+
+// After a failed solve some values may still be live: re-arm the L-solve's
+// vector so the next solve starts from sentinels everywhere.
+void rearm(kkt_ctx* c) {
+    kkt::k_fill_sentinel<<<64, 256, 0, c->stream>>>(c->d_y, c->A.n);
+    c->launches += 1;
+    cudaStreamSynchronize(c->stream);
 }
 
 int check_ctx(kkt_ctx* c, bool need_factors) {
@@ -244,11 +318,16 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
     }
     if (e != cudaSuccess) { delete c; return KKT_ERR_CUDA; }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kkt::k_lsolve, PERSIST_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kkt::k_lsolve_bulk, PERSIST_THREADS, 0);
     int per_sm2 = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kkt::k_refactor, PERSIST_THREADS, 0);
     int per_sm3 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, kkt::k_usolve, PERSIST_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, kkt::k_usolve_bulk, PERSIST_THREADS, 0);
+    cudaFuncSetAttribute(kkt::k_lsolve_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(double) * CHAIN_MAX));
+    cudaFuncSetAttribute(kkt::k_usolve_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(double) * CHAIN_MAX));
+    cudaFuncSetAttribute(kkt::k_refactor_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TAIL_SMEM_MAX);
     per_sm = std::max(1, std::min(per_sm, std::min(per_sm2, per_sm3)));
     c->persist_blocks = c->num_sms * per_sm;
     *out = c;
@@ -362,9 +441,40 @@ int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* col
     if ((rc = dalloc(c, &c->d_V, (size_t)c->ld * (c->m + 1)))) return rc;
     if ((rc = dalloc(c, &c->d_Z, (size_t)c->ld * c->m))) return rc;
     if ((rc = dalloc(c, &c->d_part, (size_t)kkt::RED_BLOCKS * kkt::RED_SLOTS))) return rc;
-    for (unsigned** p : {&c->d_done_f, &c->d_done_l, &c->d_done_u}) {
-        if ((rc = dalloc(c, p, (size_t)n))) return rc;
-        CK(cudaMemsetAsync(*p, 0, sizeof(unsigned) * (size_t)n, c->stream));
+    if ((rc = dalloc(c, &c->d_done_f, (size_t)n))) return rc;
+    CK(cudaMemsetAsync(c->d_done_f, 0, sizeof(unsigned) * (size_t)n, c->stream));
+    {
+        std::vector<int32_t> lb, lc, ub, uc, sl, su;
+        split_chain(c->lay.levL, true, CHAIN_MAX, &lb, &lc, &sl);
+        split_chain(c->lay.levU, false, CHAIN_MAX, &ub, &uc, &su);
+        c->nLb = (int)lb.size(); c->nLc = (int)lc.size();
+        c->nUb = (int)ub.size(); c->nUc = (int)uc.size();
+        if ((rc = upload(c, &c->d_rowsLb, lb))) return rc;
+        if ((rc = upload(c, &c->d_rowsLc, lc))) return rc;
+        if ((rc = upload(c, &c->d_rowsUb, ub))) return rc;
+        if ((rc = upload(c, &c->d_rowsUc, uc))) return rc;
+        if ((rc = upload(c, &c->d_slotL, sl))) return rc;
+        if ((rc = upload(c, &c->d_slotU, su))) return rc;
+    }
+    kkt::k_fill_sentinel<<<64, 256, 0, c->stream>>>(c->d_y, n);
+    {   // refactorization tail: the last rows, if their longest row fits in shared memory
+        int T = std::min<int>(n, TAIL_MAX_ROWS);
+        c->t0 = n;
+        c->tail_smem = 0;
+        while (T > 0) {
+            int t0 = n - T;
+            int64_t maxlen = 0;
+            for (int32_t i = t0; i < n; i++) maxlen = std::max<int64_t>(maxlen, c->lay.Fp[i + 1] - c->lay.Fp[i]);
+            size_t smem = ((2 * (size_t)T + 7) / 8) * 8 + 8 * (size_t)maxlen;
+            if (smem <= TAIL_SMEM_MAX && maxlen <= 32767) { c->t0 = t0; c->tail_smem = smem; break; }
+            T /= 2;
+        }
+        if (c->t0 < n) {
+            int per_sm = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kkt::k_refactor_tail, kkt::TAIL_THREADS,
+                                                             c->tail_smem));
+            c->tail_blocks = std::max(1, per_sm) * c->num_sms;
+        }
     }
     if ((rc = dalloc(c, &c->d_s, 1))) return rc;
     CK(cudaMemsetAsync(c->d_s, 0, sizeof(DevScal), c->stream));
@@ -396,14 +506,26 @@ int kkt_refactor(kkt_ctx* c, const double* values, int values_on_device) {
     const int64_t nnzF = (int64_t)c->lay.Fj.size();
     kkt::k_refactor_prep<<<1, 1, 0, c->stream>>>(c->d_s);
     int t = phase_begin(c, KKT_PHASE_GATHER);
-    kkt::k_gather<<<2 * c->num_sms, 256, 0, c->stream>>>(vals, c->d_fsrc, nnzF, c->d_Fx, c->d_Arp, c->d_asrc,
-                                                         c->d_Ax, n, c->d_s);
+    const int64_t tail_begin = c->t0 < n ? c->lay.Fp[c->t0] : nnzF;
+    kkt::k_gather<<<2 * c->num_sms, 256, 0, c->stream>>>(vals, c->d_fsrc, nnzF, tail_begin, c->d_Fx, c->d_Arp,
+                                                         c->d_asrc, c->d_Ax, n, c->d_s);
     phase_end(c, t);
     t = phase_begin(c, KKT_PHASE_REFACTOR);
-    kkt::k_refactor<<<persist_grid(c), PERSIST_THREADS, 0, c->stream>>>(
-        n, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_done_f, c->d_s, c->o.boost_eps, spin(c));
+    c->launches += 2;
+    if (c->t0 > 0) {
+        kkt::k_refactor<<<grid_for(c, c->t0), PERSIST_THREADS, 0, c->stream>>>(
+            c->t0, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_done_f, c->d_s, c->o.boost_eps, spin(c));
+        c->launches += 1;
+    }
+    if (c->t0 < n) {
+        // the bulk kernel left ticket_fact at >= t0; restart it for the tail
+        kkt::k_refactor_prep_tail<<<1, 1, 0, c->stream>>>(c->d_s);
+        const int blocks = std::min(n - c->t0, c->tail_blocks);
+        kkt::k_refactor_tail<<<blocks, kkt::TAIL_THREADS, c->tail_smem, c->stream>>>(
+            c->t0, n, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, vals, c->d_fsrc, c->d_s, c->o.boost_eps, spin(c));
+        c->launches += 2;
+    }
     phase_end(c, t);
-    c->launches += 3;
     CK(cudaGetLastError());
     if ((rc = read_scalars(c))) return rc;
     c->nboost = c->h_s->nboost;
@@ -434,7 +556,8 @@ int kkt_lu_solve(kkt_ctx* c, const double* b, double* x, int on_device) {
         c->d2h += (int64_t)sizeof(double) * n;
     }
     if ((rc = read_scalars(c))) return rc;
-    return device_error(c);
+    if ((rc = device_error(c))) rearm(c);
+    return rc;
 }
 
 int kkt_matvec(kkt_ctx* c, const double* x, double* y, int on_device) {
@@ -491,7 +614,7 @@ int kkt_solve(kkt_ctx* c, const double* b, double* x, int on_device, double tol,
     c->launches += 2;
     CK(cudaGetLastError());
     if ((rc = read_scalars(c))) return rc;
-    if ((rc = device_error(c))) return rc;
+    if ((rc = device_error(c))) { rearm(c); return rc; }
     int cycles = 0;
     int status = KKT_OK;
     while (!c->h_s->done) {
@@ -519,7 +642,7 @@ int kkt_solve(kkt_ctx* c, const double* b, double* x, int on_device, double tol,
             c->launches += 5;
             CK(cudaGetLastError());
             if ((rc = read_scalars(c))) return rc;
-            if ((rc = device_error(c))) return rc;
+            if ((rc = device_error(c))) { rearm(c); return rc; }
             if (c->h_s->met || c->h_s->hn == 0.0) break;
         }
         t = phase_begin(c, KKT_PHASE_UPDATE);
