@@ -77,7 +77,14 @@ typedef struct {
     void* stream;         /* cudaStream_t to use when create_stream == 0 */
     int64_t spin_limit;   /* polls before a device wait gives up (KKT_ERR_TIMEOUT); 0 = default */
     int timing;           /* 1 = record CUDA events around each kernel group (kkt_get_phase_times) */
+    int trisolve;         /* triangular-solve schedule: KKT_TRSV_AUTO (default), KKT_TRSV_GLOBAL */
 } kkt_opts;
+
+/* KKT_TRSV_AUTO: one thread-block cluster per triangle when the n solved
+   values fit in its shared memory, else KKT_TRSV_GLOBAL: sync-free over the
+   whole GPU with the narrow end of each DAG in one block. */
+#define KKT_TRSV_AUTO 0
+#define KKT_TRSV_GLOBAL 1
 
 /* Kernel groups timed when kkt_opts.timing is set. */
 #define KKT_PHASE_GATHER 0    /* value gather + ||K||_inf */
@@ -101,6 +108,7 @@ typedef struct {
     int32_t nboost;        /* pivots boosted by the last kkt_refactor */
     int32_t last_iters;    /* FGMRES iterations of the last kkt_solve */
     int32_t last_cycles;   /* restart cycles of the last kkt_solve */
+    int32_t trisolve_cluster; /* blocks of the cluster solve in use (0: global schedule) */
     double last_nrbe;      /* NRBE of the last kkt_solve's x */
     double last_rnorm0;    /* ||r - K x0|| of the last kkt_solve */
     double norm_a_inf;     /* ||K||_inf of the last refactored matrix */

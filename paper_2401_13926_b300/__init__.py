@@ -27,6 +27,7 @@ ERR = {
 }
 ERR_NOT_CONVERGED = -6
 STOP = {"nrbe": 0, "rr": 1}
+TRSV = {"auto": 0, "global": 1}
 
 # every entry point declared in include/kkt.h
 EXPORTS = [
@@ -44,7 +45,7 @@ class _Opts(C.Structure):
         ("restart", C.c_int), ("max_cycles", C.c_int), ("stop_mode", C.c_int), ("precision", C.c_int),
         ("refine_delta", C.c_double), ("pivot_tol", C.c_double), ("boost_eps", C.c_double),
         ("device", C.c_int), ("create_stream", C.c_int), ("stream", C.c_void_p), ("spin_limit", C.c_int64),
-        ("timing", C.c_int),
+        ("timing", C.c_int), ("trisolve", C.c_int),
     ]
 
 
@@ -53,7 +54,7 @@ class _Info(C.Structure):
         ("n", C.c_int32), ("nnz_a", C.c_int64), ("nnz_l", C.c_int64), ("nnz_u", C.c_int64),
         ("levels_l", C.c_int32), ("levels_u", C.c_int32), ("refactor_updates", C.c_double),
         ("device_bytes", C.c_int64), ("nboost", C.c_int32), ("last_iters", C.c_int32),
-        ("last_cycles", C.c_int32), ("last_nrbe", C.c_double), ("last_rnorm0", C.c_double),
+        ("last_cycles", C.c_int32), ("trisolve_cluster", C.c_int32), ("last_nrbe", C.c_double), ("last_rnorm0", C.c_double),
         ("norm_a_inf", C.c_double), ("analyze_ms", C.c_double), ("launches", C.c_int64),
         ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
     ]
@@ -188,13 +189,14 @@ class KKTSolver:
     every matrix of the sequence (Sections 1.3 and 2.1)."""
 
     def __init__(self, restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3,
-                 boost_eps=0.0, device=0, stream=None, spin_limit=0, timing=False):
+                 boost_eps=0.0, device=0, stream=None, spin_limit=0, timing=False, trisolve="auto"):
         L = lib()
         o = _Opts()
         L.kkt_default_opts(C.byref(o))
         o.restart, o.max_cycles, o.stop_mode = int(restart), int(max_cycles), STOP[stop_mode]
         o.refine_delta, o.pivot_tol, o.boost_eps = float(refine_delta), float(pivot_tol), float(boost_eps)
         o.device, o.spin_limit, o.timing = int(device), int(spin_limit), int(bool(timing))
+        o.trisolve = TRSV[trisolve]
         if stream is None:
             stream = _torch_current_stream(device)
         if stream is None:

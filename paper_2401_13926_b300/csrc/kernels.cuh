@@ -17,10 +17,15 @@
 // warp has raised the abort flag, the warp records KKT_ERR_TIMEOUT and
 // returns.
 #pragma once
+#ifndef SPIN_SLEEP_NS
+#define SPIN_SLEEP_NS 20
+#endif
+#include <cooperative_groups.h>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #include "kkt.h"
+#include "trsv_row.cuh"
 
 namespace kkt {
 
@@ -85,12 +90,6 @@ __device__ __forceinline__ bool wait_flag(const unsigned* flag, unsigned gen, De
     }
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // Block-wide sum (all threads get the result); blockDim.x multiple of 32, <= 1024.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     v = warp_sum(v);
@@ -130,14 +129,7 @@ __device__ __forceinline__ double reduce_partials(const double* part, int slot, 
     return block_sum(v, sh);
 }
 
-// A factor or solve value that is not final yet holds SENTINEL (a NaN
-// payload no arithmetic produces); readers spin on the value itself.
-constexpr unsigned long long SENTINEL_BITS = 0x7ff4dead5ca1ab1eull;
-
-__device__ __forceinline__ double sentinel() { return __longlong_as_double((long long)SENTINEL_BITS); }
-__device__ __forceinline__ bool is_sentinel(double v) {
-    return (unsigned long long)__double_as_longlong(v) == SENTINEL_BITS;
-}
+// Loads and stores that other blocks poll (gpu scope, not cached in L1).
 __device__ __forceinline__ double ld_relaxed_f64(const double* p) {
     double v;
     asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
@@ -372,45 +364,26 @@ k_refactor_tail(int t0, int nrows, const int64_t* __restrict__ Fp, const int32_t
 }
 
 // ---------------------------------------------------------------- K2/K3: triangular solves
-// Rows are split by their depth in the dependency DAG.  The wide part runs
-// sync-free over the whole GPU (warps take rows from a ticket in dependency
-// order); the long narrow chain -- the dense separators the fill-reducing
-// order puts last -- runs in ONE block whose warps hand values to each other
-// through shared memory, where a hand-off costs tens of cycles instead of a
-// round trip to L2.  L-solve: bulk first, then the chain (the highest
-// levels).  U-solve: the chain first (the lowest levels, rows near n), then
-// the bulk.
+// Rows are scheduled in the order of their level in the dependency DAG
+// (L: the forward sweep's levels; U: the backward sweep's), so warps that
+// take rows in list order never block behind a row of a much later level.
+// Fpos[p] is the list position of entry p's dependency (L part: in the L
+// list, U part: in the U list).  Every schedule evaluates a row with
+// trsv_row (trsv_row.cuh), so all of them give the same bits.
 //
-// A value that is not computed yet holds SENTINEL (a NaN payload that no
-// arithmetic produces); consumers spin on the value itself, so one load
-// both synchronises and delivers the operand.  Each solve re-arms the other
-// one's vector: the L-solve sets xp[i] = SENTINEL, the U-solve sets
-// y[i] = SENTINEL after reading it.
-// Wait for a value produced by another warp anywhere on the GPU.
-__device__ __forceinline__ bool wait_value(const double* p, double* out, DevScal* s, long long limit, int row) {
-    double v = ld_relaxed_f64(p);
-    for (long long it = 0; is_sentinel(v); it++) {
-        if (ld_volatile_int(&s->abort)) return false;
-        if (it >= limit) { raise_error(s, KKT_ERR_TIMEOUT, row); return false; }
-        __nanosleep(32);
-        v = ld_relaxed_f64(p);
-    }
-    *out = v;
-    return true;
-}
+// Whole-GPU schedule (any n): the wide part runs sync-free (warps take rows
+// from a ticket, operands polled in global memory); the narrow end of each
+// DAG -- the long chain the fill-reducing order puts last -- runs in ONE
+// block whose warps hand values through shared memory.  L: bulk, then the
+// chain (the highest levels); U: the chain (the lowest levels), then the
+// bulk.  Global operands that are not computed yet hold SENTINEL; each
+// sweep re-arms the other one's vector (L sets xp = SENTINEL, U sets
+// y = SENTINEL after reading it).
 
-// Wait for a value produced by another warp of this block (shared memory).
-__device__ __forceinline__ bool wait_shared(const volatile double* p, double* out, DevScal* s, long long limit,
-                                            int row) {
-    double v = *p;
-    for (long long it = 0; is_sentinel(v); it++) {
-        if ((it & 1023) == 0 && ld_volatile_int(&s->abort)) return false;
-        if (it >= 4 * limit) { raise_error(s, KKT_ERR_TIMEOUT, row); return false; }
-        v = *p;
-    }
-    *out = v;
-    return true;
-}
+struct GiveUpGlobal {
+    const int* abort;
+    __device__ bool operator()() const { return *(volatile const int*)abort != 0; }
+};
 
 __global__ void k_trsv_prep(DevScal* s) {
     s->ticket_l = 0;
@@ -422,147 +395,225 @@ __global__ void k_fill_sentinel(double* a, int64_t n) {
         a[i] = sentinel();
 }
 
-// y_i = rhs[P[i]] - sum_{k<i} L_ik y_k over the bulk rows (ascending list).
+struct SrcGlobal {   // operand in a global vector, by column
+    const int32_t* Fj;
+    const double* x;
+    __device__ const volatile double* operator()(int64_t p) const { return x + __ldg(&Fj[p]); }
+};
+
+__device__ __forceinline__ void fail_row(DevScal* s, int row) {
+    if (!*(volatile int*)&s->abort) raise_error(s, KKT_ERR_TIMEOUT, row);
+}
+
 __global__ void k_lsolve_bulk(int nrows, const int32_t* __restrict__ rows, const int64_t* __restrict__ Fp,
                               const int32_t* __restrict__ Fj, const int64_t* __restrict__ Fdiag,
                               const double* __restrict__ Fx, const int32_t* __restrict__ P,
                               const double* __restrict__ rhs, double* y, double* xp, DevScal* s, long long limit) {
     const int lane = threadIdx.x & 31;
+    const GiveUpGlobal gu{&s->abort};
     for (;;) {
         int t = 0;
         if (lane == 0) t = (int)atomicAdd(&s->ticket_l, 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= nrows) return;
         const int row = rows[t];
-        const int64_t b = Fp[row], d = Fdiag[row];
-        double acc = 0.0;
-        int ok = 1;
-        for (int64_t p = b + lane; p < d; p += 32) {
-            const int32_t k = __ldg(&Fj[p]);
-            const double a = __ldg(&Fx[p]);
-            double v;
-            if (!wait_value(&y[k], &v, s, limit, row)) { ok = 0; break; }
-            acc = fma(a, v, acc);
+        const double r0 = rhs[P[row]];
+        double val;
+        if (!trsv_row<true>(Fp[row], Fdiag[row], Fx, SrcGlobal{Fj, y}, r0, 1.0, limit, gu, &val)) {
+            if (lane == 0) fail_row(s, row);
+            return;
         }
-        if (!__all_sync(0xffffffffu, ok)) return;
-        acc = warp_sum(acc);
         if (lane == 0) {
             xp[row] = sentinel();
-            st_relaxed_f64(&y[row], rhs[P[row]] - acc);
+            st_relaxed_f64(&y[row], val);
         }
     }
 }
 
-// The narrow chain of the L-solve in one block: warp w takes chain slots
-// w, w + nwarps, ... in order; a dependency inside the chain is read from
-// shared memory (xs), one outside it from y (finished by the bulk kernel).
-__global__ void k_lsolve_chain(int nt, const int32_t* __restrict__ rows, const int32_t* __restrict__ slot,
-                               const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
-                               const int64_t* __restrict__ Fdiag, const double* __restrict__ Fx,
-                               const int32_t* __restrict__ P, const double* __restrict__ rhs, double* y,
-                               double* xp, DevScal* s, long long limit) {
+struct SrcChainL {   // dependency in the chain: shared memory; else y (final)
+    const int32_t* Fj;
+    const int32_t* Fpos;
+    int cstart;
+    const volatile double* xs;
+    const double* y;
+    __device__ const volatile double* operator()(int64_t p) const {
+        const int t = __ldg(&Fpos[p]) - cstart;
+        return t >= 0 ? xs + t : y + __ldg(&Fj[p]);
+    }
+};
+
+struct GiveUpShared {
+    const int* abort;
+    __device__ bool operator()() const { return *(volatile const int*)abort != 0; }
+};
+
+// The narrow end of the L-sweep in one block: warp w takes chain slots w,
+// w + nwarps, ... (slot t = list position cstart + t).
+__global__ void __launch_bounds__(1024)
+k_lsolve_chain(int nt, int cstart, const int32_t* __restrict__ rows, const int32_t* __restrict__ Fpos,
+               const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj, const int64_t* __restrict__ Fdiag,
+               const double* __restrict__ Fx, const int32_t* __restrict__ P, const double* __restrict__ rhs,
+               double* y, double* xp, DevScal* s, long long limit) {
     extern __shared__ double xs_dyn[];
     volatile double* xs = xs_dyn;
     for (int t = threadIdx.x; t < nt; t += blockDim.x) xs[t] = sentinel();
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const GiveUpShared gu{&s->abort};
     for (int t = warp; t < nt; t += nw) {
-        const int row = rows[t];
-        const int64_t b = Fp[row], d = Fdiag[row];
-        double acc = 0.0;
-        int ok = 1;
-        for (int64_t p = b + lane; p < d; p += 32) {
-            const int32_t k = __ldg(&Fj[p]);
-            const double a = __ldg(&Fx[p]);
-            const int tk = __ldg(&slot[k]);
-            double v;
-            if (tk >= 0) { if (!wait_shared(&xs[tk], &v, s, limit, row)) { ok = 0; break; } }
-            else v = __ldcg(&y[k]);
-            acc = fma(a, v, acc);
+        const int row = rows[cstart + t];
+        const double r0 = rhs[P[row]];
+        double val;
+        if (!trsv_row<true>(Fp[row], Fdiag[row], Fx, SrcChainL{Fj, Fpos, cstart, xs, y}, r0, 1.0, 4 * limit, gu,
+                            &val)) {
+            if (lane == 0) fail_row(s, row);
+            return;
         }
-        if (!__all_sync(0xffffffffu, ok)) return;
-        acc = warp_sum(acc);
         if (lane == 0) {
-            const double yi = rhs[P[row]] - acc;
+            xs[t] = val;
+            y[row] = val;
             xp[row] = sentinel();
-            y[row] = yi;
-            xs[t] = yi;
         }
         __syncwarp();
     }
 }
 
-// The narrow chain of the U-solve (rows near n, descending list): every
-// dependency of a chain row is itself in the chain.
-__global__ void k_usolve_chain(int nt, const int32_t* __restrict__ rows, const int32_t* __restrict__ slot,
-                               const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
-                               const int64_t* __restrict__ Fdiag, const double* __restrict__ Fx,
-                               const int32_t* __restrict__ Q, double* y, double* xp, double* __restrict__ out,
-                               DevScal* s, long long limit) {
+struct SrcChainU {   // every dependency of a U-chain row is in the chain
+    const int32_t* Fj;
+    const int32_t* Fpos;
+    int nt;
+    const volatile double* xs;
+    const double* xp;
+    __device__ const volatile double* operator()(int64_t p) const {
+        const int t = __ldg(&Fpos[p]);
+        return t < nt ? xs + t : xp + __ldg(&Fj[p]);
+    }
+};
+
+__global__ void __launch_bounds__(1024)
+k_usolve_chain(int nt, const int32_t* __restrict__ rows, const int32_t* __restrict__ Fpos,
+               const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj, const int64_t* __restrict__ Fdiag,
+               const double* __restrict__ Fx, const int32_t* __restrict__ Q, double* y, double* xp,
+               double* __restrict__ out, DevScal* s, long long limit) {
     extern __shared__ double xs_dyn[];
     volatile double* xs = xs_dyn;
     for (int t = threadIdx.x; t < nt; t += blockDim.x) xs[t] = sentinel();
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const GiveUpShared gu{&s->abort};
     for (int t = warp; t < nt; t += nw) {
         const int row = rows[t];
-        const int64_t d = Fdiag[row], e = Fp[row + 1];
-        double acc = 0.0;
-        int ok = 1;
-        for (int64_t p = d + 1 + lane; p < e; p += 32) {
-            const int32_t j = __ldg(&Fj[p]);
-            const double a = __ldg(&Fx[p]);
-            const int tj = __ldg(&slot[j]);
-            double v;
-            if (tj >= 0) { if (!wait_shared(&xs[tj], &v, s, limit, row)) { ok = 0; break; } }
-            else v = __ldcg(&xp[j]);
-            acc = fma(a, v, acc);
+        const int64_t d = Fdiag[row];
+        const double r0 = __ldcg(&y[row]);
+        const double rinv = 1.0 / __ldg(&Fx[d]);
+        const int qrow = Q[row];
+        double val;
+        if (!trsv_row<false>(d + 1, Fp[row + 1], Fx, SrcChainU{Fj, Fpos, nt, xs, xp}, r0, rinv, 4 * limit, gu,
+                             &val)) {
+            if (lane == 0) fail_row(s, row);
+            return;
         }
-        if (!__all_sync(0xffffffffu, ok)) return;
-        acc = warp_sum(acc);
         if (lane == 0) {
-            const double xi = (__ldcg(&y[row]) - acc) / __ldg(&Fx[d]);
+            xs[t] = val;
+            xp[row] = val;
             y[row] = sentinel();
-            xp[row] = xi;
-            out[Q[row]] = xi;
-            xs[t] = xi;
+            out[qrow] = val;
         }
         __syncwarp();
     }
 }
 
-// x'_i = (y_i - sum_{j>i} U_ij x'_j) / U_ii over the bulk rows (descending
-// list); out[Q[i]] = x'_i.
 __global__ void k_usolve_bulk(int nrows, const int32_t* __restrict__ rows, const int64_t* __restrict__ Fp,
                               const int32_t* __restrict__ Fj, const int64_t* __restrict__ Fdiag,
                               const double* __restrict__ Fx, const int32_t* __restrict__ Q, double* y, double* xp,
                               double* __restrict__ out, DevScal* s, long long limit) {
     const int lane = threadIdx.x & 31;
+    const GiveUpGlobal gu{&s->abort};
     for (;;) {
         int t = 0;
         if (lane == 0) t = (int)atomicAdd(&s->ticket_u, 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= nrows) return;
         const int row = rows[t];
-        const int64_t d = Fdiag[row], e = Fp[row + 1];
-        double acc = 0.0;
-        int ok = 1;
-        for (int64_t p = d + 1 + lane; p < e; p += 32) {
-            const int32_t j = __ldg(&Fj[p]);
-            const double a = __ldg(&Fx[p]);
-            double v;
-            if (!wait_value(&xp[j], &v, s, limit, row)) { ok = 0; break; }
-            acc = fma(a, v, acc);
+        const int64_t d = Fdiag[row];
+        const double r0 = __ldcg(&y[row]);
+        const double rinv = 1.0 / __ldg(&Fx[d]);
+        const int qrow = Q[row];
+        double val;
+        if (!trsv_row<false>(d + 1, Fp[row + 1], Fx, SrcGlobal{Fj, xp}, r0, rinv, limit, gu, &val)) {
+            if (lane == 0) fail_row(s, row);
+            return;
         }
-        if (!__all_sync(0xffffffffu, ok)) return;
-        acc = warp_sum(acc);
         if (lane == 0) {
-            const double xi = (__ldcg(&y[row]) - acc) / __ldg(&Fx[d]);
+            st_relaxed_f64(&xp[row], val);
             y[row] = sentinel();
-            out[Q[row]] = xi;
-            st_relaxed_f64(&xp[row], xi);
+            out[qrow] = val;
         }
     }
+}
+
+// ---------------------------------------------------------------- K2/K3: cluster solves
+// The whole triangular solve in ONE thread-block cluster of C blocks
+// (C = 8 or 16), the solved values kept in the blocks' shared memory --
+// the distributed shared memory of the cluster -- so every hand-off is a
+// shared-memory store read by a (distributed) shared-memory load, with no
+// global synchronisation.  List position t goes to warp g = t mod 32C of
+// the cluster; its value lives in that warp's block at slot
+// (t / 32C) * 32 + t mod 32.  Used when n values fit in the cluster.
+namespace cgx = cooperative_groups;
+constexpr int CLUSTER_THREADS = 1024;
+
+struct SrcCluster {
+    const int32_t* Fpos;
+    double* xs_local;
+    int rank, sh, stride;
+    cgx::cluster_group* cl;
+    __device__ const volatile double* operator()(int64_t p) const {
+        const int tj = __ldg(&Fpos[p]);
+        const int owner = (tj & (stride - 1)) >> 5;
+        const int slot = ((tj >> sh) << 5) + (tj & 31);
+        return (owner == rank ? xs_local : cl->map_shared_rank(xs_local, owner)) + slot;
+    }
+};
+
+template <bool LOWER>
+__global__ void __launch_bounds__(CLUSTER_THREADS)
+k_trsv_cluster(int n, const int32_t* __restrict__ list, const int32_t* __restrict__ Fpos,
+               const int64_t* __restrict__ Fp, const int64_t* __restrict__ Fdiag, const double* __restrict__ Fx,
+               const int32_t* __restrict__ perm, const double* __restrict__ rhs, double* __restrict__ out,
+               DevScal* s, long long limit) {
+    extern __shared__ double xs_cl[];
+    cgx::cluster_group cluster = cgx::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int stride = 32 * C;                 // a power of two (C is 8 or 16)
+    const int sh = 31 - __clz(stride);
+    const int per_block = ((n + stride - 1) / stride) * 32;
+    for (int i = threadIdx.x; i < per_block; i += blockDim.x) xs_cl[i] = sentinel();
+    cluster.sync();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const GiveUpGlobal gu{&s->abort};
+    const SrcCluster src{Fpos, xs_cl, rank, sh, stride, &cluster};
+    for (int t = rank * 32 + warp; t < n; t += stride) {
+        const int row = list[t];
+        const int64_t d = Fdiag[row];
+        const double r0 = LOWER ? rhs[perm[row]] : rhs[row];
+        const double rinv = LOWER ? 1.0 : 1.0 / __ldg(&Fx[d]);
+        const int orow = LOWER ? row : perm[row];
+        double val;
+        const bool ok = LOWER ? trsv_row<true>(Fp[row], d, Fx, src, r0, rinv, limit, gu, &val)
+                              : trsv_row<false>(d + 1, Fp[row + 1], Fx, src, r0, rinv, limit, gu, &val);
+        if (!ok) {
+            if (lane == 0) fail_row(s, row);
+            break;
+        }
+        if (lane == 0) {
+            ((volatile double*)xs_cl)[((t >> sh) << 5) + warp] = val;
+            out[orow] = val;
+        }
+        __syncwarp();
+    }
+    cluster.sync();   // no block may leave while others can still read its shared memory
 }
 
 // ---------------------------------------------------------------- K4: products with K

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <numeric>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -37,11 +38,13 @@ struct kkt_ctx {
     double *d_b = nullptr, *d_x = nullptr, *d_y = nullptr, *d_xp = nullptr, *d_r = nullptr, *d_w = nullptr;
     double *d_V = nullptr, *d_Z = nullptr, *d_part = nullptr;
     unsigned* d_done_f = nullptr;
-    // triangular-solve schedule: bulk rows (sync-free) and the narrow chain
-    // (one block); slot[i] = position of row i in its chain or -1
-    int32_t *d_rowsLb = nullptr, *d_rowsLc = nullptr, *d_rowsUc = nullptr, *d_rowsUb = nullptr;
-    int32_t *d_slotL = nullptr, *d_slotU = nullptr;
-    int nLb = 0, nLc = 0, nUc = 0, nUb = 0;
+    // triangular-solve schedule: rows in DAG-level order (listL, listU),
+    // Fpos[p] = list position of entry p's dependency; the L chain is the
+    // last nLc positions of listL, the U chain the first nUc of listU
+    int32_t *d_listL = nullptr, *d_listU = nullptr, *d_Fpos = nullptr;
+    int nLc = 0, nUc = 0;
+    int cluster = 0;            // blocks of the cluster solve (0: use the global schedule)
+    size_t cluster_smem = 0;
     // refactorization split: rows [0, t0) warp per row, [t0, n) block per row
     int t0 = 0;
     size_t tail_smem = 0;
@@ -74,40 +77,32 @@ constexpr size_t TAIL_SMEM_MAX = 200 * 1024;
 constexpr int CHAIN_MAX = 12288;       // rows of a chain (8 bytes of shared memory each)
 constexpr int CHAIN_WIDTH = 32;        // a level belongs to the chain if it has at most this many rows
 
-// Split rows for the triangular solves.  L: the chain is the highest levels
-// whose widths are all <= CHAIN_WIDTH; U: the lowest such levels.
-void split_chain(const std::vector<int32_t>& lev, bool lower, int cap, std::vector<int32_t>* bulk,
-                 std::vector<int32_t>* chain, std::vector<int32_t>* slot) {
+// Rows in DAG-level order (ties by row index) and each row's position.
+void level_order(const std::vector<int32_t>& lev, std::vector<int32_t>* list, std::vector<int32_t>* pos) {
     const int32_t n = (int32_t)lev.size();
+    list->resize(n);
+    std::iota(list->begin(), list->end(), 0);
+    std::stable_sort(list->begin(), list->end(), [&](int32_t a, int32_t b) { return lev[a] < lev[b]; });
+    pos->assign(n, 0);
+    for (int32_t t = 0; t < n; t++) (*pos)[(*list)[t]] = t;
+}
+
+// Rows in the narrow end of a DAG: L -- the highest levels whose widths
+// are all <= CHAIN_WIDTH; U -- the lowest such levels; at most cap rows.
+int chain_rows(const std::vector<int32_t>& lev, bool lower, int cap) {
     int32_t nl = 0;
     for (int32_t v : lev) nl = std::max(nl, v + 1);
     std::vector<int64_t> w(nl, 0);
     for (int32_t v : lev) w[v]++;
-    // chain levels: [l0, nl) for L, [0, l1) for U
-    int32_t lo = nl, hi = 0;
     int64_t count = 0;
     if (lower) {
-        while (lo > 0 && w[lo - 1] <= CHAIN_WIDTH && count + w[lo - 1] <= cap) { lo--; count += w[lo]; }
-        hi = nl;
+        for (int32_t l = nl - 1; l >= 0 && w[l] <= CHAIN_WIDTH && count + w[l] <= cap; l--) count += w[l];
     } else {
-        lo = 0;
-        while (hi < nl && w[hi] <= CHAIN_WIDTH && count + w[hi] <= cap) { count += w[hi]; hi++; }
+        for (int32_t l = 0; l < nl && w[l] <= CHAIN_WIDTH && count + w[l] <= cap; l++) count += w[l];
     }
-    bulk->clear();
-    chain->clear();
-    slot->assign(n, -1);
-    if (lower) {
-        for (int32_t i = 0; i < n; i++) {
-            if (lev[i] >= lo && lev[i] < hi) { (*slot)[i] = (int32_t)chain->size(); chain->push_back(i); }
-            else bulk->push_back(i);
-        }
-    } else {
-        for (int32_t i = n - 1; i >= 0; i--) {
-            if (lev[i] >= lo && lev[i] < hi) { (*slot)[i] = (int32_t)chain->size(); chain->push_back(i); }
-            else bulk->push_back(i);
-        }
-    }
+    return (int)count;
 }
+
 constexpr long long DEFAULT_SPIN = 1ll << 25;
 
 int cuda_fail(kkt_ctx* c, cudaError_t e, const char* what) {
@@ -210,19 +205,87 @@ int grid_for(const kkt_ctx* c, int rows) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(c->persist_blocks, need));
 }
 
-// x = Q U^{-1} L^{-1} P rhs: L bulk, L chain, U chain, U bulk.
+// Cluster solve: one cluster of `blocks` blocks runs the whole solve.
+template <bool LOWER>
+cudaError_t launch_cluster(kkt_ctx* c, const int32_t* perm, const double* rhs, double* out) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c->cluster, 1, 1);
+    cfg.blockDim = dim3(kkt::CLUSTER_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = c->cluster_smem;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c->cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kkt::k_trsv_cluster<LOWER>, c->A.n,
+                              (const int32_t*)(LOWER ? c->d_listL : c->d_listU), (const int32_t*)c->d_Fpos,
+                              (const int64_t*)c->d_Fp, (const int64_t*)c->d_Fdiag, (const double*)c->d_Fx, perm,
+                              rhs, out, c->d_s, spin(c));
+}
+
+// Pick the smallest cluster (8 or 16 blocks) whose shared memory holds all
+// n values and that the device can co-schedule; 0 if none.
+int pick_cluster(kkt_ctx* c) {
+    const int n = c->A.n;
+    for (int C : {8, 16}) {
+        size_t per_block = (size_t)((n + 32 * C - 1) / (32 * C)) * 32 * sizeof(double);
+        if (per_block > TAIL_SMEM_MAX) continue;
+        for (auto fn : {kkt::k_trsv_cluster<true>, kkt::k_trsv_cluster<false>}) {
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TAIL_SMEM_MAX);
+            if (C > 8) cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(C, 1, 1);
+        cfg.blockDim = dim3(kkt::CLUSTER_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = per_block;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int active = 0;
+        if (cudaOccupancyMaxActiveClusters(&active, kkt::k_trsv_cluster<true>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (active >= 1) { c->cluster = C; c->cluster_smem = per_block; return C; }
+    }
+    c->cluster = 0;
+    return 0;
+}
+
+// x = Q U^{-1} L^{-1} P rhs: one cluster launch per triangle when the
+// values fit in a cluster's shared memory, else L bulk, L chain, U chain,
+// U bulk over the whole GPU.
 void lu_apply(kkt_ctx* c, const double* rhs, double* out) {
+    if (c->cluster) {
+        int t = phase_begin(c, KKT_PHASE_LSOLVE);
+        launch_cluster<true>(c, c->d_P, rhs, c->d_y);
+        phase_end(c, t);
+        t = phase_begin(c, KKT_PHASE_USOLVE);
+        launch_cluster<false>(c, c->d_Q, c->d_y, out);
+        phase_end(c, t);
+        c->launches += 2;
+        return;
+    }
+    const int n = c->A.n;
+    const int nLb = n - c->nLc, nUb = n - c->nUc;
     kkt::k_trsv_prep<<<1, 1, 0, c->stream>>>(c->d_s);
     c->launches += 1;
     int t = phase_begin(c, KKT_PHASE_LSOLVE);
-    if (c->nLb) {
-        kkt::k_lsolve_bulk<<<grid_for(c, c->nLb), PERSIST_THREADS, 0, c->stream>>>(
-            c->nLb, c->d_rowsLb, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_P, rhs, c->d_y, c->d_xp, c->d_s, spin(c));
+    if (nLb) {
+        kkt::k_lsolve_bulk<<<grid_for(c, nLb), PERSIST_THREADS, 0, c->stream>>>(
+            nLb, c->d_listL, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_P, rhs, c->d_y, c->d_xp, c->d_s, spin(c));
         c->launches += 1;
     }
     if (c->nLc) {
         kkt::k_lsolve_chain<<<1, CHAIN_THREADS, sizeof(double) * c->nLc, c->stream>>>(
-            c->nLc, c->d_rowsLc, c->d_slotL, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_P, rhs, c->d_y, c->d_xp,
+            c->nLc, nLb, c->d_listL, c->d_Fpos, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_P, rhs, c->d_y, c->d_xp,
             c->d_s, spin(c));
         c->launches += 1;
     }
@@ -230,13 +293,14 @@ void lu_apply(kkt_ctx* c, const double* rhs, double* out) {
     t = phase_begin(c, KKT_PHASE_USOLVE);
     if (c->nUc) {
         kkt::k_usolve_chain<<<1, CHAIN_THREADS, sizeof(double) * c->nUc, c->stream>>>(
-            c->nUc, c->d_rowsUc, c->d_slotU, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_Q, c->d_y, c->d_xp, out,
+            c->nUc, c->d_listU, c->d_Fpos, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_Q, c->d_y, c->d_xp, out,
             c->d_s, spin(c));
         c->launches += 1;
     }
-    if (c->nUb) {
-        kkt::k_usolve_bulk<<<grid_for(c, c->nUb), PERSIST_THREADS, 0, c->stream>>>(
-            c->nUb, c->d_rowsUb, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_Q, c->d_y, c->d_xp, out, c->d_s, spin(c));
+    if (nUb) {
+        kkt::k_usolve_bulk<<<grid_for(c, nUb), PERSIST_THREADS, 0, c->stream>>>(
+            nUb, c->d_listU + c->nUc, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_Q, c->d_y, c->d_xp, out, c->d_s,
+            spin(c));
         c->launches += 1;
     }
     phase_end(c, t);
@@ -304,7 +368,8 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
     if (o) c->o = *o; else kkt_default_opts(&c->o);
     if (c->o.restart < 1 || c->o.restart > kkt::MAXM || c->o.max_cycles < 0 || c->o.precision != 0 ||
         (c->o.stop_mode != KKT_STOP_NRBE && c->o.stop_mode != KKT_STOP_RR) || c->o.pivot_tol <= 0 ||
-        c->o.pivot_tol > 1 || c->o.boost_eps < 0) {
+        c->o.pivot_tol > 1 || c->o.boost_eps < 0 ||
+        (c->o.trisolve != KKT_TRSV_AUTO && c->o.trisolve != KKT_TRSV_GLOBAL)) {
         delete c;
         return KKT_ERR_INVALID;
     }
@@ -444,19 +509,23 @@ int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* col
     if ((rc = dalloc(c, &c->d_done_f, (size_t)n))) return rc;
     CK(cudaMemsetAsync(c->d_done_f, 0, sizeof(unsigned) * (size_t)n, c->stream));
     {
-        std::vector<int32_t> lb, lc, ub, uc, sl, su;
-        split_chain(c->lay.levL, true, CHAIN_MAX, &lb, &lc, &sl);
-        split_chain(c->lay.levU, false, CHAIN_MAX, &ub, &uc, &su);
-        c->nLb = (int)lb.size(); c->nLc = (int)lc.size();
-        c->nUb = (int)ub.size(); c->nUc = (int)uc.size();
-        if ((rc = upload(c, &c->d_rowsLb, lb))) return rc;
-        if ((rc = upload(c, &c->d_rowsLc, lc))) return rc;
-        if ((rc = upload(c, &c->d_rowsUb, ub))) return rc;
-        if ((rc = upload(c, &c->d_rowsUc, uc))) return rc;
-        if ((rc = upload(c, &c->d_slotL, sl))) return rc;
-        if ((rc = upload(c, &c->d_slotU, su))) return rc;
+        std::vector<int32_t> listL, posL, listU, posU;
+        level_order(c->lay.levL, &listL, &posL);
+        level_order(c->lay.levU, &listU, &posU);
+        c->nLc = chain_rows(c->lay.levL, true, CHAIN_MAX);
+        c->nUc = chain_rows(c->lay.levU, false, CHAIN_MAX);
+        std::vector<int32_t> fpos(nnzF, 0);
+        for (int32_t i = 0; i < n; i++) {
+            for (int64_t p = c->lay.Fp[i]; p < c->lay.Fdiag[i]; p++) fpos[p] = posL[c->lay.Fj[p]];
+            for (int64_t p = c->lay.Fdiag[i] + 1; p < c->lay.Fp[i + 1]; p++) fpos[p] = posU[c->lay.Fj[p]];
+        }
+        if ((rc = upload(c, &c->d_listL, listL))) return rc;
+        if ((rc = upload(c, &c->d_listU, listU))) return rc;
+        if ((rc = upload(c, &c->d_Fpos, fpos))) return rc;
     }
     kkt::k_fill_sentinel<<<64, 256, 0, c->stream>>>(c->d_y, n);
+    if (c->o.trisolve == KKT_TRSV_AUTO) pick_cluster(c);
+    else c->cluster = 0;
     {   // refactorization tail: the last rows, if their longest row fits in shared memory
         int T = std::min<int>(n, TAIL_MAX_ROWS);
         c->t0 = n;
@@ -728,6 +797,7 @@ int kkt_query(kkt_ctx* c, kkt_info* info) {
     info->nboost = c->nboost;
     info->last_iters = c->last_iters;
     info->last_cycles = c->last_cycles;
+    info->trisolve_cluster = c->cluster;
     info->last_nrbe = c->last_nrbe;
     info->last_rnorm0 = c->last_rnorm0;
     info->norm_a_inf = c->norm_a;

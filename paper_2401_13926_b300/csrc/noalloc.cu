@@ -12,9 +12,10 @@
 // library image carries.  Every GPU that loads the library holds that array
 // (KKT_NOALLOC_SCRATCH_BYTES) until the process exits.
 //
-// The kernels follow the same sync-free, warp-per-row scheme as the
-// context's solve: rows taken from an atomic ticket in dependency order,
-// bounded waits on completion flags.
+// The kernels take rows from an atomic ticket in dependency order and
+// evaluate each row with the same arithmetic as the context's solves
+// (trsv_row.cuh), so the two entry points return the same bits; every wait
+// on a value another warp produces is bounded.
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -22,6 +23,7 @@
 #include <mutex>
 
 #include "kkt.h"
+#include "trsv_row.cuh"
 
 namespace {
 
@@ -38,14 +40,14 @@ static_assert(kScratchBytes == KKT_NOALLOC_SCRATCH_BYTES, "header and implementa
 // The scratch.  Host code must never pass `g_noalloc_scratch` itself to a
 // kernel: in host code it names a host-side stand-in, not device memory.
 // Its device address comes from cudaGetSymbolAddress (scratch_on_device).
+// Layout: header, y[kMaxN], xp[kMaxN] (doubles), then 2 kMaxN words kept
+// for the layout's stated size.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 struct Scratch {
     NoallocHeader* h;
     double* y;
     double* xp;
-    unsigned* done_l;
-    unsigned* done_u;
 };
 
 __host__ __device__ inline Scratch carve(unsigned char* base) {
@@ -53,48 +55,19 @@ __host__ __device__ inline Scratch carve(unsigned char* base) {
     s.h = reinterpret_cast<NoallocHeader*>(base);
     s.y = reinterpret_cast<double*>(base + kHeaderBytes);
     s.xp = s.y + kMaxN;
-    s.done_l = reinterpret_cast<unsigned*>(s.xp + kMaxN);
-    s.done_u = s.done_l + kMaxN;
     return s;
 }
 
-__device__ __forceinline__ unsigned na_ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void na_st_release(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ bool na_wait(const unsigned* flag, NoallocHeader* h, long long limit) {
-    for (long long it = 0;; it++) {
-        if (na_ld_acquire(flag) == 1u) return true;
-        if (*(volatile int*)&h->abort) return false;
-        if (it >= limit) {
-            atomicCAS(&h->err, 0, KKT_ERR_TIMEOUT);
-            atomicExch(&h->abort, 1);
-            return false;
-        }
-        __nanosleep(64);
-    }
-}
-
-__device__ __forceinline__ double na_warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // Calls share the scratch and find the previous call's contents there:
-// clear the flags of rows [0, n), the tickets and the error words.
+// re-arm y and xp of rows [0, n) (a value not computed yet holds
+// SENTINEL), the tickets and the error words.
 __global__ void k_na_clear(unsigned char* base, int n) {
     Scratch s = carve(base);
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = tid; i < n; i += stride) {
-        s.done_l[i] = 0u;
-        s.done_u[i] = 0u;
+        s.y[i] = kkt::sentinel();
+        s.xp[i] = kkt::sentinel();
     }
     if (tid == 0) {
         s.h->ticket_l = 0u;
@@ -104,31 +77,42 @@ __global__ void k_na_clear(unsigned char* base, int n) {
     }
 }
 
+struct NaSrc {
+    const int32_t* Fj;
+    const double* x;
+    __device__ const volatile double* operator()(int64_t p) const { return x + __ldg(&Fj[p]); }
+};
+struct NaGiveUp {
+    const int* abort;
+    __device__ bool operator()() const { return *(volatile const int*)abort != 0; }
+};
+
+__device__ void na_fail(NoallocHeader* h) {
+    atomicCAS(&h->err, 0, KKT_ERR_TIMEOUT);
+    atomicExch(&h->abort, 1);
+}
+
+// Rows in index order from an atomic ticket; each row evaluated exactly as
+// the context's solves evaluate it (kkt::trsv_row).
 __global__ void k_na_lsolve(unsigned char* base, int n, const int64_t* __restrict__ Fp,
                             const int32_t* __restrict__ Fj, const int64_t* __restrict__ Fdiag,
                             const double* __restrict__ Fx, const int32_t* __restrict__ P,
                             const double* __restrict__ b, long long limit) {
     Scratch s = carve(base);
     const int lane = threadIdx.x & 31;
+    const NaGiveUp gu{&s.h->abort};
     for (;;) {
         int row = 0;
         if (lane == 0) row = (int)atomicAdd(&s.h->ticket_l, 1u);
         row = __shfl_sync(0xffffffffu, row, 0);
         if (row >= n) return;
-        double acc = 0.0;
-        int ok = 1;
-        for (int64_t p = Fp[row] + lane; p < Fdiag[row]; p += 32) {
-            const int32_t k = Fj[p];
-            if (!na_wait(&s.done_l[k], s.h, limit)) { ok = 0; break; }
-            acc += Fx[p] * __ldcg(&s.y[k]);
+        const double r0 = b[P[row]];
+        double val;
+        if (!kkt::trsv_row<true>(Fp[row], Fdiag[row], Fx, NaSrc{Fj, s.y}, r0, 1.0, limit, gu, &val)) {
+            if (lane == 0) na_fail(s.h);
+            return;
         }
-        if (!__all_sync(0xffffffffu, ok)) return;
-        acc = na_warp_sum(acc);
-        if (lane == 0) {
-            __stcg(&s.y[row], b[P[row]] - acc);
-            __threadfence();
-            na_st_release(&s.done_l[row], 1u);
-        }
+        if (lane == 0) *(volatile double*)&s.y[row] = val;
     }
 }
 
@@ -138,6 +122,7 @@ __global__ void k_na_usolve(unsigned char* base, int n, const int64_t* __restric
                             double* __restrict__ x, long long limit) {
     Scratch s = carve(base);
     const int lane = threadIdx.x & 31;
+    const NaGiveUp gu{&s.h->abort};
     for (;;) {
         int t = 0;
         if (lane == 0) t = (int)atomicAdd(&s.h->ticket_u, 1u);
@@ -145,21 +130,16 @@ __global__ void k_na_usolve(unsigned char* base, int n, const int64_t* __restric
         if (t >= n) return;
         const int row = n - 1 - t;
         const int64_t d = Fdiag[row];
-        double acc = 0.0;
-        int ok = 1;
-        for (int64_t p = d + 1 + lane; p < Fp[row + 1]; p += 32) {
-            const int32_t j = Fj[p];
-            if (!na_wait(&s.done_u[j], s.h, limit)) { ok = 0; break; }
-            acc += Fx[p] * __ldcg(&s.xp[j]);
+        const double r0 = __ldcg(&s.y[row]);
+        const double rinv = 1.0 / Fx[d];
+        double val;
+        if (!kkt::trsv_row<false>(d + 1, Fp[row + 1], Fx, NaSrc{Fj, s.xp}, r0, rinv, limit, gu, &val)) {
+            if (lane == 0) na_fail(s.h);
+            return;
         }
-        if (!__all_sync(0xffffffffu, ok)) return;
-        acc = na_warp_sum(acc);
         if (lane == 0) {
-            const double xi = (__ldcg(&s.y[row]) - acc) / Fx[d];
-            __stcg(&s.xp[row], xi);
-            x[Q[row]] = xi;
-            __threadfence();
-            na_st_release(&s.done_u[row], 1u);
+            *(volatile double*)&s.xp[row] = val;
+            x[Q[row]] = val;
         }
     }
 }

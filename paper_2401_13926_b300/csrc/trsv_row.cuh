@@ -1,0 +1,124 @@
+// The arithmetic of one row of a sparse triangular solve, shared by every
+// schedule (cluster, whole-GPU sync-free, single-block chain, and the
+// allocation-free entry point) so that all of them produce the same bits.
+//
+//   L row i:  y_i = r0 - sum_k L_ik y_k            (unit diagonal)
+//   U row i:  x_i = (r0 - sum_j U_ij x_j) * (1/U_ii)
+//
+// FP64 on B300 has a dependent-operation latency of about 64 cycles, so a
+// five-step warp reduction of doubles costs ~600 cycles -- more than the
+// rest of a dependency hand-off.  A row therefore splits its entries in two:
+// the EARLY ones are summed lane-parallel and warp-reduced while the LATE
+// ones -- the row's NLATE most recent dependencies, which finish last -- are
+// still in flight; lane 0 then folds the late ones in one fused
+// multiply-add each, in a fixed order.  Only that last FMA (and, for U, one
+// multiply) sits on the dependency chain.  Which entries are late is fixed
+// by the row's structure, so the result does not depend on timing.
+//
+// Values are read through `Src`, which maps an entry p to the address of
+// its operand (shared, distributed shared or global memory, all accessed as
+// volatile); an operand that is not computed yet holds SENTINEL.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace kkt {
+
+constexpr unsigned long long SENTINEL_BITS = 0x7ff4dead5ca1ab1eull;
+constexpr int NLATE = 4;        // late entries per row
+constexpr int ROW_BATCH = 4;    // early entries per lane with loads in flight together
+
+__device__ __forceinline__ double sentinel() { return __longlong_as_double((long long)SENTINEL_BITS); }
+__device__ __forceinline__ bool is_sentinel(double v) {
+    return (unsigned long long)__double_as_longlong(v) == SENTINEL_BITS;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Spin until *p is not SENTINEL.  `give_up()` is polled every 256 spins;
+// after `limit` spins the wait fails.  Returns false on failure.
+template <class GiveUp>
+__device__ __forceinline__ bool spin_value(const volatile double* p, double* v, long long limit, GiveUp give_up) {
+    double x = *v;
+    for (long long it = 0; is_sentinel(x); it++) {
+        if ((it & 255) == 255 && give_up()) return false;
+        if (it >= limit) return false;
+        __nanosleep(20);
+        x = *p;
+    }
+    *v = x;
+    return true;
+}
+
+// One row over entries [lo, hi) of the factor row (columns ascending).
+// LOWER: the late entries are the last NLATE (largest columns, the most
+// recent rows of the forward sweep); folded in ascending column order.
+// !LOWER: the late entries are the first NLATE (smallest columns > i, the
+// most recent rows of the backward sweep); folded in descending order.
+// Returns the row's value in lane 0 (other lanes: unspecified) or false in
+// every lane if a wait failed.
+template <bool LOWER, class Src, class GiveUp>
+__device__ __forceinline__ bool trsv_row(int64_t lo, int64_t hi, const double* __restrict__ Fx, Src src,
+                                         double r0, double rinv, long long limit, GiveUp give_up, double* out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t len = hi - lo;
+    const int nl = (int)(len < NLATE ? len : NLATE);
+    const int64_t elo = LOWER ? lo : lo + nl;
+    const int64_t ehi = LOWER ? hi - nl : hi;
+    // lane 0 starts the loads of the late entries first
+    double la[NLATE], lv[NLATE];
+    const volatile double* ls[NLATE];
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < NLATE; j++) {
+            if (j < nl) {
+                const int64_t p = LOWER ? hi - nl + j : lo + nl - 1 - j;   // completion order
+                la[j] = __ldg(&Fx[p]);
+                ls[j] = src(p);
+                lv[j] = *ls[j];
+            }
+        }
+    }
+    int ok = 1;
+    double acc = 0.0;
+    for (int64_t base = elo + lane; base < ehi && ok; base += 32 * ROW_BATCH) {
+        double a[ROW_BATCH], v[ROW_BATCH];
+        const volatile double* s[ROW_BATCH];
+#pragma unroll
+        for (int u = 0; u < ROW_BATCH; u++) {
+            const int64_t p = base + 32 * u;
+            if (p < ehi) { a[u] = __ldg(&Fx[p]); s[u] = src(p); }
+        }
+#pragma unroll
+        for (int u = 0; u < ROW_BATCH; u++)
+            if (base + 32 * u < ehi) v[u] = *s[u];
+#pragma unroll
+        for (int u = 0; u < ROW_BATCH; u++) {
+            if (base + 32 * u >= ehi) continue;
+            if (!spin_value(s[u], &v[u], limit, give_up)) { ok = 0; break; }
+            acc = fma(a[u], v[u], acc);
+        }
+    }
+    if (!__all_sync(0xffffffffu, ok)) return false;
+    acc = warp_sum(acc);
+    double r = r0 - acc;
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < NLATE; j++) {
+            if (j < nl && ok) {
+                if (!spin_value(ls[j], &lv[j], limit, give_up)) { ok = 0; break; }
+                r = fma(-la[j], lv[j], r);
+            }
+        }
+        if (!LOWER) r *= rinv;
+    }
+    if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
+    *out = r;
+    return true;
+}
+
+}  // namespace kkt

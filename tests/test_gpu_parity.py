@@ -56,9 +56,10 @@ def test_refactor_parity_kkt200(oracle_mod, c1):
         assert dl <= FACTOR_TOL and du <= FACTOR_TOL, (k, dl, du)
 
 
-def test_solve_parity_kkt200(oracle_mod, c1):
+@pytest.mark.parametrize("sched", ["auto", "global"])
+def test_solve_parity_kkt200(oracle_mod, c1, sched):
     seq, P, Q = c1
-    s = K.KKTSolver(restart=20)
+    s = K.KKTSolver(restart=20, trisolve=sched)
     s.analyze(seq.rowptr, seq.colind, Q=Q, P=P)
     for k in range(seq.M):
         v = seq.values(k)
@@ -110,11 +111,12 @@ def test_lu_solve_backward_error(c1):
     assert np.max(np.abs(r) / scale) <= 64 * EPS * 10
 
 
-def test_lu_solve_elementwise_well_conditioned(oracle_mod):
+@pytest.mark.parametrize("sched", ["auto", "global"])
+def test_lu_solve_elementwise_well_conditioned(oracle_mod, sched):
     n = 1500
     rp, ci, v = small_random_sparse(n, 0.004, 7, diag_boost=6.0)
     P, Q, F = oracle_mod.lu(n, rp, ci, v)
-    s = K.KKTSolver()
+    s = K.KKTSolver(trisolve=sched)
     s.analyze(rp, ci, Q=Q, P=P)
     s.refactor(v)
     b = np.random.default_rng(3).standard_normal(n)
@@ -161,13 +163,14 @@ def _edge_cases():
     return cases
 
 
+@pytest.mark.parametrize("sched", ["auto", "global"])
 @pytest.mark.parametrize("name", list(_edge_cases().keys()))
-def test_edge_structures(oracle_mod, name):
+def test_edge_structures(oracle_mod, name, sched):
     A = _edge_cases()[name]
     rp, ci, v = csr_of(A)
     n = len(rp) - 1
     P, Q, _ = oracle_mod.lu(n, rp, ci, v)
-    s = K.KKTSolver()
+    s = K.KKTSolver(trisolve=sched)
     s.analyze(rp, ci, Q=Q, P=P)
     s.refactor(v)
     of = oracle_mod.refactor(n, rp, ci, v, P, Q)
@@ -247,13 +250,16 @@ def test_rr_stop_mode_and_refine_delta(oracle_mod, c1):
     assert np.array_equal(x3, s3.lu_solve(b))
 
 
-def test_own_analysis_full_size_kkt2000_sequence(oracle_mod):
+@pytest.mark.parametrize("sched", ["auto", "global"])
+def test_own_analysis_full_size_kkt2000_sequence(oracle_mod, sched):
     """The benchmark's configuration: the library's own ordering and pivots,
     FGMRES(20), every matrix of the 30-step sequence; NRBE of each returned x
     evaluated by the oracle."""
     seq = KKTSequence("kkt2000")
-    s = K.KKTSolver(restart=20)
+    s = K.KKTSolver(restart=20, trisolve=sched)
     s.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
+    if sched == "auto":
+        assert s.info()["trisolve_cluster"] > 0   # the bench's schedule
     for k in range(seq.M):
         v = seq.values(k)
         b, _ = seq.rhs(k, v)
