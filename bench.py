@@ -269,14 +269,14 @@ def run_ours(args):
     lay = info0
     n = seq.n
     tot = {p: phases[p][0] for p in phases}
-    dom = max(("refactor", "lsolve", "usolve", "spmv", "ortho"), key=lambda p: tot[p])
+    dom = max(("refactor", "refactor_tail", "lsolve", "usolve", "spmv", "ortho"), key=lambda p: tot[p])
     ms, cnt = phases[dom]
     per_launch_ms = ms / max(cnt, 1)
     if dom == "lsolve":
         bytes_ = 12 * lay["nnz_l"] + 36 * n
     elif dom == "usolve":
         bytes_ = 12 * lay["nnz_u"] + 44 * n
-    elif dom == "refactor":
+    elif dom in ("refactor", "refactor_tail"):
         bytes_ = 20 * (lay["nnz_l"] + lay["nnz_u"]) + 24 * n
     elif dom == "spmv":
         bytes_ = 12 * seq.nnz + 28 * n

@@ -78,6 +78,9 @@ typedef struct {
     int64_t spin_limit;   /* polls before a device wait gives up (KKT_ERR_TIMEOUT); 0 = default */
     int timing;           /* 1 = record CUDA events around each kernel group (kkt_get_phase_times) */
     int trisolve;         /* triangular-solve schedule: KKT_TRSV_AUTO (default), KKT_TRSV_GLOBAL */
+    int tail_rows;        /* rows refactored one block per row at the end of the order
+                             (0 = default 32767, the most; fewer if a row does not fit
+                             in shared memory) */
 } kkt_opts;
 
 /* KKT_TRSV_AUTO: one thread-block cluster per triangle when the n solved
@@ -94,7 +97,8 @@ typedef struct {
 #define KKT_PHASE_SPMV 4      /* products with K and residuals */
 #define KKT_PHASE_ORTHO 5     /* CGS2 passes, normalisation, Givens */
 #define KKT_PHASE_UPDATE 6    /* cycle start and end (v_0, y = R^{-1} g, x += Z y) */
-#define KKT_NUM_PHASES 7
+#define KKT_PHASE_REFACTOR_TAIL 7  /* the part of the refactorization done one block per row */
+#define KKT_NUM_PHASES 8
 
 typedef struct {
     int32_t n;

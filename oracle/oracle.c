@@ -15,6 +15,9 @@
  * apply the finished columns in ascending pivot order -- one valid
  * topological order of the elimination graph -- and every update
  * x_i <- x_i - l_ik x_k is a single fused multiply-add (one rounding).
+ * Column j of L is x_i * (1/u_jj): the pivot's reciprocal is formed once
+ * (correctly rounded division) and each entry is one multiplication, the
+ * scaling LAPACK's getf2 uses.
  *
  *   or_lu           -- first numeric factorization with threshold partial
  *                      pivoting (Section 1.3, "full symbolic analysis and
@@ -236,6 +239,7 @@ void *or_lu(int n, const int *Ap, const int *Ai, const double *Ax,
         int rd = c;   /* the original diagonal entry of this column */
         if (pinv[rd] < 0 && mark[rd] == j && fabs(x[rd]) >= tol * amax) piv = rd;
         double d = x[piv];
+        double dinv = 1.0 / d;   /* L(:,j) is scaled by the pivot's reciprocal */
         /* U(:,j): pivotal rows of the reach, then the diagonal */
         for (int t = top; t < n; t++) {
             int r = out[t];
@@ -248,7 +252,7 @@ void *or_lu(int n, const int *Ap, const int *Ai, const double *Ax,
         for (int t = top; t < n; t++) {
             int r = out[t];
             if (pinv[r] < 0 && r != piv) {
-                if (!ivec_push(&Li, r) || !dvec_push(&Lx, x[r] / d)) goto fail;
+                if (!ivec_push(&Li, r) || !dvec_push(&Lx, x[r] * dinv)) goto fail;
             }
         }
         pinv[piv] = j;
@@ -333,10 +337,11 @@ void *or_refactor(int n, const int *Ap, const int *Ai, const double *Ax,
             if (i < j) { if (!ivec_push(&Ui, i) || !dvec_push(&Ux, x[i])) goto fail; }
         }
         if (!ivec_push(&Ui, j) || !dvec_push(&Ux, d)) goto fail;
+        double rd = 1.0 / d;   /* L(:,j) is scaled by the pivot's reciprocal */
         for (int t = top; t < n; t++) {
             int i = out[t];
             if (i > j) {
-                double l = x[i] / d;
+                double l = x[i] * rd;
                 if (!isfinite(l)) { *status = OR_ERR_NONFINITE; goto fail; }
                 if (!ivec_push(&Li, i) || !dvec_push(&Lx, l)) goto fail;
             }

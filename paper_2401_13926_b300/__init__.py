@@ -37,7 +37,7 @@ EXPORTS = [
     "kkt_get_phase_times", "kkt_lu_solve_noalloc",
 ]
 NOALLOC_MAX_N = 65536
-PHASES = ["gather", "refactor", "lsolve", "usolve", "spmv", "ortho", "update"]
+PHASES = ["gather", "refactor", "lsolve", "usolve", "spmv", "ortho", "update", "refactor_tail"]
 
 
 class _Opts(C.Structure):
@@ -45,7 +45,7 @@ class _Opts(C.Structure):
         ("restart", C.c_int), ("max_cycles", C.c_int), ("stop_mode", C.c_int), ("precision", C.c_int),
         ("refine_delta", C.c_double), ("pivot_tol", C.c_double), ("boost_eps", C.c_double),
         ("device", C.c_int), ("create_stream", C.c_int), ("stream", C.c_void_p), ("spin_limit", C.c_int64),
-        ("timing", C.c_int), ("trisolve", C.c_int),
+        ("timing", C.c_int), ("trisolve", C.c_int), ("tail_rows", C.c_int),
     ]
 
 
@@ -189,7 +189,8 @@ class KKTSolver:
     every matrix of the sequence (Sections 1.3 and 2.1)."""
 
     def __init__(self, restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3,
-                 boost_eps=0.0, device=0, stream=None, spin_limit=0, timing=False, trisolve="auto"):
+                 boost_eps=0.0, device=0, stream=None, spin_limit=0, timing=False, trisolve="auto",
+                 tail_rows=0):
         L = lib()
         o = _Opts()
         L.kkt_default_opts(C.byref(o))
@@ -197,6 +198,7 @@ class KKTSolver:
         o.refine_delta, o.pivot_tol, o.boost_eps = float(refine_delta), float(pivot_tol), float(boost_eps)
         o.device, o.spin_limit, o.timing = int(device), int(spin_limit), int(bool(timing))
         o.trisolve = TRSV[trisolve]
+        o.tail_rows = int(tail_rows)
         if stream is None:
             stream = _torch_current_stream(device)
         if stream is None:

@@ -158,9 +158,11 @@ __global__ void k_refactor_prep(DevScal* s) {
 // gathers their values itself and publishes each row when it is final).
 __global__ void k_gather(const double* __restrict__ vals, const int64_t* __restrict__ fsrc, int64_t nnzF,
                          int64_t tail_begin, double* __restrict__ Fx, const int32_t* __restrict__ Arp,
-                         const int64_t* __restrict__ asrc, double* __restrict__ Ax, int n, DevScal* s) {
+                         const int64_t* __restrict__ asrc, double* __restrict__ Ax, int n, int t0,
+                         double* __restrict__ rinv, DevScal* s) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = t0 + tid; i < n; i += stride) rinv[i] = sentinel();   // tail rows publish 1/u_ii last
     for (int64_t t = tid; t < nnzF; t += stride) {
         if (t >= tail_begin) { Fx[t] = sentinel(); continue; }
         int64_t q = fsrc[t];
@@ -201,7 +203,7 @@ __device__ __forceinline__ int64_t find_col(const int32_t* __restrict__ Fj, int6
 }
 
 __global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
-                           const int64_t* __restrict__ Fdiag, double* Fx, unsigned* done, DevScal* s,
+                           const int64_t* __restrict__ Fdiag, double* Fx, double* rinv, unsigned* done, DevScal* s,
                            double boost_eps, long long limit) {
     // rows [0, n) of the bulk: warp per row, factor values in global memory
     const int lane = threadIdx.x & 31;
@@ -222,7 +224,7 @@ __global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t*
             if (!ok) return;
             __threadfence();
             const int64_t dk = __ldg(&Fdiag[k]), ek = __ldg(&Fp[k + 1]);
-            const double lik = __ldcg(&Fx[p]) / __ldcg(&Fx[dk]);
+            const double lik = __ldcg(&Fx[p]) * __ldcg(&rinv[k]);   // l_ik = w_k * (1/u_kk)
             __syncwarp();
             if (lane == 0) __stcg(&Fx[p], lik);
             for (int64_t q = dk + 1 + lane; q < ek; q += 32) {
@@ -242,6 +244,7 @@ __global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t*
                 if (fabs(u) < boost) { u = (u < 0.0) ? -boost : boost; atomicAdd(&s->nboost, 1); __stcg(&Fx[d], u); }
             } else if (u == 0.0) { raise_error(s, KKT_ERR_ZERO_PIVOT, row); fail = true; }
             if (!fail) {
+                __stcg(&rinv[row], __drcp_rn(u));
                 __threadfence();
                 st_release(&done[row], gen);
             }
@@ -261,13 +264,64 @@ constexpr int TAIL_THREADS = 256;
 
 __global__ void k_refactor_prep_tail(DevScal* s) { s->ticket_fact = 0; }
 
+// One step's worth of U(k,:) for one thread: up to TAIL_E entries
+// (columns and values) and the pivot reciprocal of row k, loaded two steps
+// ahead.  Tail rows publish their U values and 1/u_kk with no ordering
+// between them -- every datum is armed with SENTINEL by the gather and is
+// final once it is not -- so a consumer spins on exactly the values it uses.
+constexpr int TAIL_E = 4;
+struct TailStage {
+    int64_t dk, ek;
+    int k;
+    double rk;
+    int32_t col[TAIL_E];
+    double val[TAIL_E];
+};
+
+__device__ __forceinline__ void tail_load(TailStage& st, int s, int nsteps, int64_t b,
+                                          const int32_t* __restrict__ Fj, const int64_t* __restrict__ Fp,
+                                          const int64_t* __restrict__ Fdiag, const double* Fx, const double* rinv) {
+    if (s >= nsteps) { st.k = -1; return; }
+    const int k = Fj[b + s];
+    st.k = k;
+    st.dk = Fdiag[k];
+    st.ek = Fp[k + 1];
+    st.rk = ld_relaxed_f64(&rinv[k]);
+#pragma unroll
+    for (int j = 0; j < TAIL_E; j++) {
+        const int64_t q = st.dk + 1 + threadIdx.x + (int64_t)j * TAIL_THREADS;
+        if (q < st.ek) { st.col[j] = Fj[q]; st.val[j] = ld_relaxed_f64(&Fx[q]); }
+    }
+}
+
+// position in row i (base b) of column c: the shared map for c >= t0, a
+// binary search of the row's columns after position lo otherwise
+__device__ __forceinline__ int tail_pos(int c, int t0, const short* map, const int32_t* __restrict__ Fj,
+                                        int64_t b, int64_t lo, int64_t e) {
+    if (c >= t0) return map[c - t0];
+    const int64_t f = find_col(Fj, lo, e, c);
+    return (f < e && Fj[f] == c) ? (int)(f - b) : -1;
+}
+
+// Spin until a published datum is not SENTINEL (bounded; abort-aware).
+__device__ __forceinline__ bool tail_wait(const double* p, double* v, DevScal* s, long long limit, int row) {
+    double x = *v;
+    for (long long it = 0; is_sentinel(x); it++) {
+        if ((it & 63) == 63 && ld_volatile_int(&s->abort)) return false;
+        if (it >= limit) { raise_error(s, KKT_ERR_TIMEOUT, row); return false; }
+        __nanosleep(20);
+        x = ld_relaxed_f64(p);
+    }
+    *v = x;
+    return true;
+}
+
 __global__ void __launch_bounds__(TAIL_THREADS)
 k_refactor_tail(int t0, int nrows, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
-                const int64_t* __restrict__ Fdiag, double* Fx, const double* __restrict__ vals,
+                const int64_t* __restrict__ Fdiag, double* Fx, double* rinv, const double* __restrict__ vals,
                 const int64_t* __restrict__ fsrc, DevScal* s, double boost_eps, long long limit) {
     extern __shared__ double tail_sh[];
-    __shared__ double s_l;
-    __shared__ int s_row, s_ok;
+    __shared__ int s_row;
     const int T = nrows - t0;
     const int tid = threadIdx.x;
     short* map = reinterpret_cast<short*>(tail_sh);                   // T entries
@@ -276,70 +330,73 @@ k_refactor_tail(int t0, int nrows, const int64_t* __restrict__ Fp, const int32_t
     const double boost = boost_eps * *(volatile double*)&s->normA;
     __syncthreads();
     for (;;) {
-        if (tid == 0) {
-            s_row = t0 + (int)atomicAdd(&s->ticket_fact, 1u);
-            s_ok = ld_volatile_int(&s->abort) ? 0 : 1;
-        }
+        if (tid == 0) s_row = t0 + (int)atomicAdd(&s->ticket_fact, 1u);
         __syncthreads();
         const int row = s_row;
-        if (row >= nrows || !s_ok) return;
+        const int stop = __syncthreads_or(row >= nrows || ld_volatile_int(&s->abort));
+        if (stop) return;
         const int64_t b = Fp[row], d = Fdiag[row], e = Fp[row + 1];
         const int len = (int)(e - b);
+        const int nsteps = (int)(d - b);
         for (int q = tid; q < len; q += blockDim.x) {
             const int64_t src = fsrc[b + q];
             w[q] = src >= 0 ? vals[src] : 0.0;
             const int c = Fj[b + q];
             if (c >= t0) map[c - t0] = (short)q;
         }
+        TailStage A, B;
+        tail_load(A, 0, nsteps, b, Fj, Fp, Fdiag, Fx, rinv);
+        tail_load(B, 1, nsteps, b, Fj, Fp, Fdiag, Fx, rinv);
         __syncthreads();
-        int bad = 0;
-        for (int64_t p = b; p < d; p++) {
-            const int k = Fj[p];
-            const int64_t dk = Fdiag[k], ek = Fp[k + 1];
-            if (tid == 0) {
-                double ukk;
-                if (k >= t0) {   // wait for the diagonal: tail row k is final once it is
-                    ukk = ld_relaxed_f64(&Fx[dk]);
-                    for (long long it = 0; is_sentinel(ukk); it++) {
-                        if (ld_volatile_int(&s->abort)) { bad = 1; break; }
-                        if (it >= limit) { raise_error(s, KKT_ERR_TIMEOUT, row); bad = 1; break; }
-                        __nanosleep(32);
-                        ukk = ld_relaxed_f64(&Fx[dk]);
+        int step = 0;
+        // One elimination step: every thread forms l_ik = w_k * (1/u_kk)
+        // itself (thread 0 also stores it), then applies its entries of U(k,:).
+        auto run_step = [&](TailStage& st) -> bool {
+            const int64_t p = b + step;
+            int ok = tail_wait(&rinv[st.k], &st.rk, s, limit, row);
+            const double l = w[step] * st.rk;
+            if (ok) {
+#pragma unroll
+                for (int j = 0; j < TAIL_E; j++) {
+                    const int64_t q = st.dk + 1 + tid + (int64_t)j * TAIL_THREADS;
+                    if (q < st.ek && ok) {
+                        double v = st.val[j];
+                        if (!tail_wait(&Fx[q], &v, s, limit, row)) { ok = 0; break; }
+                        const int pos = tail_pos(st.col[j], t0, map, Fj, b, p + 1, e);
+                        if (pos < 0) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
+                        w[pos] = fma(-l, v, w[pos]);
                     }
-                    __threadfence();
-                } else {
-                    ukk = __ldcg(&Fx[dk]);
                 }
-                const double l = w[p - b] / ukk;
-                w[p - b] = l;
-                s_l = l;
-                s_ok = !bad;
-            }
-            __syncthreads();
-            if (!s_ok) return;
-            const double l = s_l;
-            if (k >= t0) {
-                for (int64_t q = dk + 1 + tid; q < ek; q += blockDim.x) {
-                    const int pos = map[Fj[q] - t0];
+                for (int64_t q = st.dk + 1 + tid + (int64_t)TAIL_E * TAIL_THREADS; q < st.ek && ok;
+                     q += TAIL_THREADS) {
+                    double v = ld_relaxed_f64(&Fx[q]);
+                    if (!tail_wait(&Fx[q], &v, s, limit, row)) { ok = 0; break; }
+                    const int pos = tail_pos(Fj[q], t0, map, Fj, b, p + 1, e);
                     if (pos < 0) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
-                    w[pos] = fma(-l, __ldcg(&Fx[q]), w[pos]);
-                }
-            } else {
-                for (int64_t q = dk + 1 + tid; q < ek; q += blockDim.x) {
-                    const int c = Fj[q];
-                    int pos;
-                    if (c >= t0) pos = map[c - t0];
-                    else {
-                        const int64_t f = find_col(Fj, p + 1, e, c);
-                        pos = (f < e && Fj[f] == c) ? (int)(f - b) : -1;
-                    }
-                    if (pos < 0) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
-                    w[pos] = fma(-l, __ldcg(&Fx[q]), w[pos]);
+                    w[pos] = fma(-l, v, w[pos]);
                 }
             }
-            __syncthreads();
+            const int any_fail = __syncthreads_or(!ok);   // uniform decision for the block
+            if (tid == 0) w[step] = l;   // nobody else touches position `step` any more
+            step++;
+            return !any_fail;
+        };
+        bool ok = true;
+        while (step < nsteps && ok) {
+            ok = run_step(A);
+            tail_load(A, step + 1, nsteps, b, Fj, Fp, Fdiag, Fx, rinv);
+            if (!ok || step >= nsteps) break;
+            ok = run_step(B);
+            tail_load(B, step + 1, nsteps, b, Fj, Fp, Fdiag, Fx, rinv);
         }
-        // pivot, then publish: values first, the diagonal last
+        if (!ok) return;
+        __syncthreads();   // the last L value written by thread 0 is visible
+        // publish: every value but the diagonal, then (thread 0) the pivot
+        for (int q = tid; q < len; q += blockDim.x) {
+            if (b + q != d) st_relaxed_f64(&Fx[b + q], w[q]);
+            const int c = Fj[b + q];
+            if (c >= t0) map[c - t0] = -1;
+        }
         if (tid == 0) {
             double u = w[d - b];
             int fail = 0;
@@ -347,19 +404,11 @@ k_refactor_tail(int t0, int nrows, const int64_t* __restrict__ Fp, const int32_t
             else if (boost > 0.0) {
                 if (fabs(u) < boost) { u = (u < 0.0) ? -boost : boost; atomicAdd(&s->nboost, 1); }
             } else if (u == 0.0) { raise_error(s, KKT_ERR_ZERO_PIVOT, row); fail = 1; }
-            w[d - b] = u;
-            s_ok = !fail;
+            if (!fail) {
+                st_relaxed_f64(&Fx[d], u);
+                st_relaxed_f64(&rinv[row], __drcp_rn(u));
+            }
         }
-        __syncthreads();
-        if (!s_ok) return;
-        for (int q = tid; q < len; q += blockDim.x) {
-            if (b + q != d) __stcg(&Fx[b + q], w[q]);
-            const int c = Fj[b + q];
-            if (c >= t0) map[c - t0] = -1;
-        }
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) st_relaxed_f64(&Fx[d], w[d - b]);
     }
 }
 
@@ -505,7 +554,7 @@ k_usolve_chain(int nt, const int32_t* __restrict__ rows, const int32_t* __restri
         const int row = rows[t];
         const int64_t d = Fdiag[row];
         const double r0 = __ldcg(&y[row]);
-        const double rinv = 1.0 / __ldg(&Fx[d]);
+        const double rinv = __drcp_rn(__ldg(&Fx[d]));
         const int qrow = Q[row];
         double val;
         if (!trsv_row<false>(d + 1, Fp[row + 1], Fx, SrcChainU{Fj, Fpos, nt, xs, xp}, r0, rinv, 4 * limit, gu,
@@ -537,7 +586,7 @@ __global__ void k_usolve_bulk(int nrows, const int32_t* __restrict__ rows, const
         const int row = rows[t];
         const int64_t d = Fdiag[row];
         const double r0 = __ldcg(&y[row]);
-        const double rinv = 1.0 / __ldg(&Fx[d]);
+        const double rinv = __drcp_rn(__ldg(&Fx[d]));
         const int qrow = Q[row];
         double val;
         if (!trsv_row<false>(d + 1, Fp[row + 1], Fx, SrcGlobal{Fj, xp}, r0, rinv, limit, gu, &val)) {
@@ -598,7 +647,7 @@ k_trsv_cluster(int n, const int32_t* __restrict__ list, const int32_t* __restric
         const int row = list[t];
         const int64_t d = Fdiag[row];
         const double r0 = LOWER ? rhs[perm[row]] : rhs[row];
-        const double rinv = LOWER ? 1.0 : 1.0 / __ldg(&Fx[d]);
+        const double rinv = LOWER ? 1.0 : __drcp_rn(__ldg(&Fx[d]));
         const int orow = LOWER ? row : perm[row];
         double val;
         const bool ok = LOWER ? trsv_row<true>(Fp[row], d, Fx, src, r0, rinv, limit, gu, &val)

@@ -35,6 +35,7 @@ struct kkt_ctx {
     int64_t *d_Fp = nullptr, *d_Fdiag = nullptr, *d_fsrc = nullptr, *d_asrc = nullptr;
     int32_t *d_Fj = nullptr, *d_Arp = nullptr, *d_Aci = nullptr, *d_P = nullptr, *d_Q = nullptr;
     double *d_Fx = nullptr, *d_Ax = nullptr, *d_vals = nullptr;
+    double* d_rinv = nullptr;   // 1/u_ii of every row; tail rows publish it last
     double *d_b = nullptr, *d_x = nullptr, *d_y = nullptr, *d_xp = nullptr, *d_r = nullptr, *d_w = nullptr;
     double *d_V = nullptr, *d_Z = nullptr, *d_part = nullptr;
     unsigned* d_done_f = nullptr;
@@ -72,7 +73,7 @@ namespace {
 
 constexpr int PERSIST_THREADS = 256;
 constexpr int CHAIN_THREADS = 1024;
-constexpr int TAIL_MAX_ROWS = 8192;      // rows factored one block per row
+constexpr int TAIL_MAX_ROWS = 32767;     // rows factored one block per row
 constexpr size_t TAIL_SMEM_MAX = 200 * 1024;
 constexpr int CHAIN_MAX = 12288;       // rows of a chain (8 bytes of shared memory each)
 constexpr int CHAIN_WIDTH = 32;        // a level belongs to the chain if it has at most this many rows
@@ -369,7 +370,7 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
     if (c->o.restart < 1 || c->o.restart > kkt::MAXM || c->o.max_cycles < 0 || c->o.precision != 0 ||
         (c->o.stop_mode != KKT_STOP_NRBE && c->o.stop_mode != KKT_STOP_RR) || c->o.pivot_tol <= 0 ||
         c->o.pivot_tol > 1 || c->o.boost_eps < 0 ||
-        (c->o.trisolve != KKT_TRSV_AUTO && c->o.trisolve != KKT_TRSV_GLOBAL)) {
+        (c->o.trisolve != KKT_TRSV_AUTO && c->o.trisolve != KKT_TRSV_GLOBAL) || c->o.tail_rows < 0) {
         delete c;
         return KKT_ERR_INVALID;
     }
@@ -499,6 +500,7 @@ int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* col
     if ((rc = upload(c, &c->d_P, c->P))) return rc;
     if ((rc = upload(c, &c->d_Q, c->Q))) return rc;
     if ((rc = dalloc(c, &c->d_Fx, nnzF))) return rc;
+    if ((rc = dalloc(c, &c->d_rinv, (size_t)n))) return rc;
     if ((rc = dalloc(c, &c->d_Ax, c->nnz_a))) return rc;
     if ((rc = dalloc(c, &c->d_vals, c->nnz_a))) return rc;
     for (double** p : {&c->d_b, &c->d_x, &c->d_y, &c->d_xp, &c->d_r, &c->d_w})
@@ -527,7 +529,7 @@ int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* col
     if (c->o.trisolve == KKT_TRSV_AUTO) pick_cluster(c);
     else c->cluster = 0;
     {   // refactorization tail: the last rows, if their longest row fits in shared memory
-        int T = std::min<int>(n, TAIL_MAX_ROWS);
+        int T = std::min<int>(n, c->o.tail_rows > 0 ? std::min(c->o.tail_rows, 32767) : TAIL_MAX_ROWS);
         c->t0 = n;
         c->tail_smem = 0;
         while (T > 0) {
@@ -577,21 +579,24 @@ int kkt_refactor(kkt_ctx* c, const double* values, int values_on_device) {
     int t = phase_begin(c, KKT_PHASE_GATHER);
     const int64_t tail_begin = c->t0 < n ? c->lay.Fp[c->t0] : nnzF;
     kkt::k_gather<<<2 * c->num_sms, 256, 0, c->stream>>>(vals, c->d_fsrc, nnzF, tail_begin, c->d_Fx, c->d_Arp,
-                                                         c->d_asrc, c->d_Ax, n, c->d_s);
+                                                         c->d_asrc, c->d_Ax, n, c->t0, c->d_rinv, c->d_s);
     phase_end(c, t);
     t = phase_begin(c, KKT_PHASE_REFACTOR);
     c->launches += 2;
     if (c->t0 > 0) {
         kkt::k_refactor<<<grid_for(c, c->t0), PERSIST_THREADS, 0, c->stream>>>(
-            c->t0, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_done_f, c->d_s, c->o.boost_eps, spin(c));
+            c->t0, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_rinv, c->d_done_f, c->d_s, c->o.boost_eps, spin(c));
         c->launches += 1;
     }
+    phase_end(c, t);
+    t = phase_begin(c, KKT_PHASE_REFACTOR_TAIL);
     if (c->t0 < n) {
         // the bulk kernel left ticket_fact at >= t0; restart it for the tail
         kkt::k_refactor_prep_tail<<<1, 1, 0, c->stream>>>(c->d_s);
         const int blocks = std::min(n - c->t0, c->tail_blocks);
         kkt::k_refactor_tail<<<blocks, kkt::TAIL_THREADS, c->tail_smem, c->stream>>>(
-            c->t0, n, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, vals, c->d_fsrc, c->d_s, c->o.boost_eps, spin(c));
+            c->t0, n, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_rinv, vals, c->d_fsrc, c->d_s, c->o.boost_eps,
+            spin(c));
         c->launches += 2;
     }
     phase_end(c, t);

@@ -131,7 +131,7 @@ __global__ void k_na_usolve(unsigned char* base, int n, const int64_t* __restric
         const int row = n - 1 - t;
         const int64_t d = Fdiag[row];
         const double r0 = __ldcg(&s.y[row]);
-        const double rinv = 1.0 / Fx[d];
+        const double rinv = __drcp_rn(Fx[d]);
         double val;
         if (!kkt::trsv_row<false>(d + 1, Fp[row + 1], Fx, NaSrc{Fj, s.xp}, r0, rinv, limit, gu, &val)) {
             if (lane == 0) na_fail(s.h);
