@@ -78,6 +78,8 @@ typedef struct {
     int64_t spin_limit;   /* polls before a device wait gives up (KKT_ERR_TIMEOUT); 0 = default */
     int timing;           /* 1 = record CUDA events around each kernel group (kkt_get_phase_times) */
     int trisolve;         /* triangular-solve schedule: KKT_TRSV_AUTO (default), KKT_TRSV_GLOBAL */
+    int cluster_blocks;   /* blocks of the cluster solve: 0 = 16 if it fits and can be
+                             scheduled, else 8; 8 or 16 to force one */
     int tail_rows;        /* rows refactored one block per row at the end of the order
                              (0 = default 32767, the most; fewer if a row does not fit
                              in shared memory) */
@@ -195,9 +197,28 @@ int kkt_query(kkt_ctx* c, kkt_info* info);
  * reset != 0 clears the accumulators after reading.
  */
 int kkt_get_phase_times(kkt_ctx* c, double* ms, int64_t* counts, int reset);
+
+/*
+ * Profiling: kkt_refactor, with the GPU's global timer (ns) recorded when
+ * each row of the block-per-row part starts and when it publishes its
+ * pivot.  t_start[n], t_publish[n] (host) get the stamps (-1 for rows of
+ * the other part); *t0_out = first row of the block-per-row part.  Makes
+ * one temporary device allocation for the stamps.
+ */
+int kkt_trace_refactor(kkt_ctx* c, const double* values, int values_on_device, int64_t* t_start,
+                       int64_t* t_publish, int32_t* t0_out);
 void kkt_destroy(kkt_ctx* c);
 const char* kkt_strerror(int code);
 const char* kkt_last_error_detail(kkt_ctx* c);
+
+/*
+ * Self-test of the bounded waits (no counterpart in the paper): launches,
+ * on the context's stream, one warp that waits with the library's wait
+ * primitive for a completion flag that nothing ever sets, with `limit`
+ * polls.  Returns KKT_ERR_TIMEOUT (the wait gave up and reported it, the
+ * GPU and the context stay usable) or KKT_OK if it did not time out.
+ */
+int kkt_selftest_wait(kkt_ctx* c, int64_t limit);
 
 /* ---- triangular solve without any device allocation ---- */
 

@@ -34,7 +34,7 @@ EXPORTS = [
     "kkt_default_opts", "kkt_create", "kkt_analyze", "kkt_refactor", "kkt_solve", "kkt_lu_solve",
     "kkt_matvec", "kkt_get_perm", "kkt_get_factor_sizes", "kkt_get_factors", "kkt_query",
     "kkt_destroy", "kkt_strerror", "kkt_last_error_detail", "kkt_order", "kkt_pivot",
-    "kkt_get_phase_times", "kkt_lu_solve_noalloc",
+    "kkt_get_phase_times", "kkt_lu_solve_noalloc", "kkt_selftest_wait", "kkt_trace_refactor",
 ]
 NOALLOC_MAX_N = 65536
 PHASES = ["gather", "refactor", "lsolve", "usolve", "spmv", "ortho", "update", "refactor_tail"]
@@ -45,7 +45,7 @@ class _Opts(C.Structure):
         ("restart", C.c_int), ("max_cycles", C.c_int), ("stop_mode", C.c_int), ("precision", C.c_int),
         ("refine_delta", C.c_double), ("pivot_tol", C.c_double), ("boost_eps", C.c_double),
         ("device", C.c_int), ("create_stream", C.c_int), ("stream", C.c_void_p), ("spin_limit", C.c_int64),
-        ("timing", C.c_int), ("trisolve", C.c_int), ("tail_rows", C.c_int),
+        ("timing", C.c_int), ("trisolve", C.c_int), ("cluster_blocks", C.c_int), ("tail_rows", C.c_int),
     ]
 
 
@@ -100,6 +100,8 @@ def lib():
     L.kkt_pivot.argtypes = [i32, vp, vp, vp, vp, d, vp, C.POINTER(i64), C.POINTER(i64)]
     L.kkt_get_phase_times.argtypes = [vp, vp, vp, ip]
     L.kkt_lu_solve_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.kkt_selftest_wait.argtypes = [vp, i64]
+    L.kkt_trace_refactor.argtypes = [vp, vp, ip, vp, vp, C.POINTER(i32)]
     for name in EXPORTS:
         if name not in ("kkt_default_opts", "kkt_destroy", "kkt_strerror", "kkt_last_error_detail"):
             getattr(L, name).restype = C.c_int
@@ -190,7 +192,7 @@ class KKTSolver:
 
     def __init__(self, restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3,
                  boost_eps=0.0, device=0, stream=None, spin_limit=0, timing=False, trisolve="auto",
-                 tail_rows=0):
+                 tail_rows=0, cluster_blocks=0):
         L = lib()
         o = _Opts()
         L.kkt_default_opts(C.byref(o))
@@ -199,6 +201,7 @@ class KKTSolver:
         o.device, o.spin_limit, o.timing = int(device), int(spin_limit), int(bool(timing))
         o.trisolve = TRSV[trisolve]
         o.tail_rows = int(tail_rows)
+        o.cluster_blocks = int(cluster_blocks)
         if stream is None:
             stream = _torch_current_stream(device)
         if stream is None:
@@ -300,6 +303,21 @@ class KKTSolver:
         self._check(lib().kkt_get_phase_times(self._h, ms.ctypes.data, cnt.ctypes.data, int(bool(reset))),
                     "kkt_get_phase_times")
         return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
+
+    def trace_refactor(self, values):
+        """kkt_refactor with per-row start/publish stamps (ns) of the
+        block-per-row part: (t_start, t_publish, t0)."""
+        keep, p, dev = _ptr(values, np.float64)
+        ts = np.zeros(self.n, np.int64)
+        tp = np.zeros(self.n, np.int64)
+        t0 = C.c_int32()
+        self._check(lib().kkt_trace_refactor(self._h, p, dev, ts.ctypes.data, tp.ctypes.data, C.byref(t0)),
+                    "kkt_trace_refactor")
+        return ts, tp, t0.value
+
+    def selftest_wait(self, limit):
+        """Return code of kkt_selftest_wait (KKT_ERR_TIMEOUT = -7 expected)."""
+        return lib().kkt_selftest_wait(self._h, int(limit))
 
     def info(self):
         inf = _Info()

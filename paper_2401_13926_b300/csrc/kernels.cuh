@@ -73,6 +73,11 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_volatile_int(const int* p) { return *(volatile const int*)p; }
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ void raise_error(DevScal* s, int code, int row) {
     if (atomicCAS(&s->err, 0, code) == 0) s->err_row = row;
@@ -266,41 +271,45 @@ __global__ void k_refactor_prep_tail(DevScal* s) { s->ticket_fact = 0; }
 
 // One step's worth of U(k,:) for one thread: up to TAIL_E entries
 // (columns and values) and the pivot reciprocal of row k, loaded two steps
-// ahead.  Tail rows publish their U values and 1/u_kk with no ordering
-// between them -- every datum is armed with SENTINEL by the gather and is
-// final once it is not -- so a consumer spins on exactly the values it uses.
+// ahead from addresses staged in shared memory, so issuing the loads never
+// waits for an earlier load.  Tail rows publish their U values and 1/u_kk
+// with no ordering between them -- every datum is armed with SENTINEL by the
+// gather and is final once it is not -- so a consumer spins on exactly the
+// values it uses, all of them in one pass per round trip.
 constexpr int TAIL_E = 4;
 struct TailStage {
-    int64_t dk, ek;
-    int k;
     double rk;
     int32_t col[TAIL_E];
     double val[TAIL_E];
 };
 
-__device__ __forceinline__ void tail_load(TailStage& st, int s, int nsteps, int64_t b,
-                                          const int32_t* __restrict__ Fj, const int64_t* __restrict__ Fp,
-                                          const int64_t* __restrict__ Fdiag, const double* Fx, const double* rinv) {
-    if (s >= nsteps) { st.k = -1; return; }
-    const int k = Fj[b + s];
-    st.k = k;
-    st.dk = Fdiag[k];
-    st.ek = Fp[k + 1];
-    st.rk = ld_relaxed_f64(&rinv[k]);
+struct StepDesc {     // staged per L entry of the row: the step's source row
+    int64_t dk;       // position of U(k,k)
+    int32_t k, cnt;   // k, |U(k, >k)|
+};
+
+__device__ __forceinline__ void tail_load(TailStage& st, int s, int nsteps, const StepDesc* sd,
+                                          const int32_t* __restrict__ Fj, const double* Fx, const double* rinv) {
+    if (s >= nsteps) return;
+    const StepDesc d = sd[s];
+    st.rk = ld_relaxed_f64(&rinv[d.k]);
 #pragma unroll
     for (int j = 0; j < TAIL_E; j++) {
-        const int64_t q = st.dk + 1 + threadIdx.x + (int64_t)j * TAIL_THREADS;
-        if (q < st.ek) { st.col[j] = Fj[q]; st.val[j] = ld_relaxed_f64(&Fx[q]); }
+        const int e = threadIdx.x + j * TAIL_THREADS;
+        if (e < d.cnt) { st.col[j] = Fj[d.dk + 1 + e]; st.val[j] = ld_relaxed_f64(&Fx[d.dk + 1 + e]); }
     }
 }
 
-// position in row i (base b) of column c: the shared map for c >= t0, a
-// binary search of the row's columns after position lo otherwise
-__device__ __forceinline__ int tail_pos(int c, int t0, const short* map, const int32_t* __restrict__ Fj,
-                                        int64_t b, int64_t lo, int64_t e) {
-    if (c >= t0) return map[c - t0];
-    const int64_t f = find_col(Fj, lo, e, c);
-    return (f < e && Fj[f] == c) ? (int)(f - b) : -1;
+// position in the row of column c: the shared map for c >= mlo, else a
+// binary search of the row's columns (staged in shared memory) from lo
+__device__ __forceinline__ int tail_pos(int c, int mlo, const short* map, const int32_t* cols, int lo, int len) {
+    if (c >= mlo) return map[c - mlo];
+    int hi = len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cols[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    return (lo < len && cols[lo] == c) ? lo : -1;
 }
 
 // Spin until a published datum is not SENTINEL (bounded; abort-aware).
@@ -317,16 +326,20 @@ __device__ __forceinline__ bool tail_wait(const double* p, double* v, DevScal* s
 }
 
 __global__ void __launch_bounds__(TAIL_THREADS)
-k_refactor_tail(int t0, int nrows, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
+k_refactor_tail(int t0, int nrows, int mlo, int max_steps, int max_len, const int64_t* __restrict__ Fp,
+                const int32_t* __restrict__ Fj,
                 const int64_t* __restrict__ Fdiag, double* Fx, double* rinv, const double* __restrict__ vals,
-                const int64_t* __restrict__ fsrc, DevScal* s, double boost_eps, long long limit) {
+                const int64_t* __restrict__ fsrc, DevScal* s, double boost_eps, long long limit,
+                unsigned long long* trace) {
     extern __shared__ double tail_sh[];
     __shared__ int s_row;
-    const int T = nrows - t0;
+    const int M = nrows - mlo;   // columns [mlo, nrows) have an O(1) position map
     const int tid = threadIdx.x;
-    short* map = reinterpret_cast<short*>(tail_sh);                   // T entries
-    double* w = tail_sh + ((2 * (size_t)T + 7) / 8);                  // row values
-    for (int c = tid; c < T; c += blockDim.x) map[c] = -1;
+    StepDesc* sd = reinterpret_cast<StepDesc*>(tail_sh);                          // max_steps
+    double* w = reinterpret_cast<double*>(sd + max_steps);                        // row values, max_len
+    int32_t* cols = reinterpret_cast<int32_t*>(w + max_len);                      // row columns, max_len
+    short* map = reinterpret_cast<short*>(cols + max_len);                        // M entries
+    for (int c = tid; c < M; c += blockDim.x) map[c] = -1;
     const double boost = boost_eps * *(volatile double*)&s->normA;
     __syncthreads();
     for (;;) {
@@ -335,6 +348,7 @@ k_refactor_tail(int t0, int nrows, const int64_t* __restrict__ Fp, const int32_t
         const int row = s_row;
         const int stop = __syncthreads_or(row >= nrows || ld_volatile_int(&s->abort));
         if (stop) return;
+        if (trace && tid == 0) trace[2 * (size_t)(row - t0)] = globaltimer_ns();
         const int64_t b = Fp[row], d = Fdiag[row], e = Fp[row + 1];
         const int len = (int)(e - b);
         const int nsteps = (int)(d - b);
@@ -342,36 +356,56 @@ k_refactor_tail(int t0, int nrows, const int64_t* __restrict__ Fp, const int32_t
             const int64_t src = fsrc[b + q];
             w[q] = src >= 0 ? vals[src] : 0.0;
             const int c = Fj[b + q];
-            if (c >= t0) map[c - t0] = (short)q;
+            cols[q] = c;
+            if (c >= mlo) map[c - mlo] = (short)q;
+            if (q < nsteps) {
+                const int64_t dk = Fdiag[c];
+                sd[q] = StepDesc{dk, c, (int32_t)(Fp[c + 1] - dk - 1)};
+            }
         }
-        TailStage A, B;
-        tail_load(A, 0, nsteps, b, Fj, Fp, Fdiag, Fx, rinv);
-        tail_load(B, 1, nsteps, b, Fj, Fp, Fdiag, Fx, rinv);
         __syncthreads();
+        TailStage A, B;
+        tail_load(A, 0, nsteps, sd, Fj, Fx, rinv);
+        tail_load(B, 1, nsteps, sd, Fj, Fx, rinv);
         int step = 0;
         // One elimination step: every thread forms l_ik = w_k * (1/u_kk)
         // itself (thread 0 also stores it), then applies its entries of U(k,:).
         auto run_step = [&](TailStage& st) -> bool {
-            const int64_t p = b + step;
-            int ok = tail_wait(&rinv[st.k], &st.rk, s, limit, row);
-            const double l = w[step] * st.rk;
+            const StepDesc dsc = sd[step];
+            int ok = 1;
+            // anything still SENTINEL is re-read, all of it in one pass
+            for (long long it = 0;; it++) {
+                bool pending = is_sentinel(st.rk);
+#pragma unroll
+                for (int j = 0; j < TAIL_E; j++)
+                    if (tid + j * TAIL_THREADS < dsc.cnt && is_sentinel(st.val[j])) pending = true;
+                if (!pending) break;
+                if ((it & 63) == 63 && ld_volatile_int(&s->abort)) { ok = 0; break; }
+                if (it >= limit) { raise_error(s, KKT_ERR_TIMEOUT, row); ok = 0; break; }
+                __nanosleep(20);
+                if (is_sentinel(st.rk)) st.rk = ld_relaxed_f64(&rinv[dsc.k]);
+#pragma unroll
+                for (int j = 0; j < TAIL_E; j++) {
+                    const int e2 = tid + j * TAIL_THREADS;
+                    if (e2 < dsc.cnt && is_sentinel(st.val[j])) st.val[j] = ld_relaxed_f64(&Fx[dsc.dk + 1 + e2]);
+                }
+            }
+            const double l = w[step] * st.rk;   // l_ik = w_k * (1/u_kk)
             if (ok) {
 #pragma unroll
                 for (int j = 0; j < TAIL_E; j++) {
-                    const int64_t q = st.dk + 1 + tid + (int64_t)j * TAIL_THREADS;
-                    if (q < st.ek && ok) {
-                        double v = st.val[j];
-                        if (!tail_wait(&Fx[q], &v, s, limit, row)) { ok = 0; break; }
-                        const int pos = tail_pos(st.col[j], t0, map, Fj, b, p + 1, e);
+                    const int e2 = tid + j * TAIL_THREADS;
+                    if (e2 < dsc.cnt) {
+                        const int pos = tail_pos(st.col[j], mlo, map, cols, step + 1, len);
                         if (pos < 0) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
-                        w[pos] = fma(-l, v, w[pos]);
+                        w[pos] = fma(-l, st.val[j], w[pos]);
                     }
                 }
-                for (int64_t q = st.dk + 1 + tid + (int64_t)TAIL_E * TAIL_THREADS; q < st.ek && ok;
-                     q += TAIL_THREADS) {
+                for (int e2 = tid + TAIL_E * TAIL_THREADS; e2 < dsc.cnt && ok; e2 += TAIL_THREADS) {
+                    const int64_t q = dsc.dk + 1 + e2;
                     double v = ld_relaxed_f64(&Fx[q]);
                     if (!tail_wait(&Fx[q], &v, s, limit, row)) { ok = 0; break; }
-                    const int pos = tail_pos(Fj[q], t0, map, Fj, b, p + 1, e);
+                    const int pos = tail_pos(Fj[q], mlo, map, cols, step + 1, len);
                     if (pos < 0) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
                     w[pos] = fma(-l, v, w[pos]);
                 }
@@ -384,18 +418,18 @@ k_refactor_tail(int t0, int nrows, const int64_t* __restrict__ Fp, const int32_t
         bool ok = true;
         while (step < nsteps && ok) {
             ok = run_step(A);
-            tail_load(A, step + 1, nsteps, b, Fj, Fp, Fdiag, Fx, rinv);
+            tail_load(A, step + 1, nsteps, sd, Fj, Fx, rinv);
             if (!ok || step >= nsteps) break;
             ok = run_step(B);
-            tail_load(B, step + 1, nsteps, b, Fj, Fp, Fdiag, Fx, rinv);
+            tail_load(B, step + 1, nsteps, sd, Fj, Fx, rinv);
         }
         if (!ok) return;
         __syncthreads();   // the last L value written by thread 0 is visible
         // publish: every value but the diagonal, then (thread 0) the pivot
         for (int q = tid; q < len; q += blockDim.x) {
             if (b + q != d) st_relaxed_f64(&Fx[b + q], w[q]);
-            const int c = Fj[b + q];
-            if (c >= t0) map[c - t0] = -1;
+            const int c = cols[q];
+            if (c >= mlo) map[c - mlo] = -1;
         }
         if (tid == 0) {
             double u = w[d - b];
@@ -407,6 +441,7 @@ k_refactor_tail(int t0, int nrows, const int64_t* __restrict__ Fp, const int32_t
             if (!fail) {
                 st_relaxed_f64(&Fx[d], u);
                 st_relaxed_f64(&rinv[row], __drcp_rn(u));
+                if (trace) trace[2 * (size_t)(row - t0) + 1] = globaltimer_ns();
             }
         }
     }
@@ -663,6 +698,17 @@ k_trsv_cluster(int n, const int32_t* __restrict__ list, const int32_t* __restric
         __syncwarp();
     }
     cluster.sync();   // no block may leave while others can still read its shared memory
+}
+
+// ---------------------------------------------------------------- self-test of bounded waits
+// One warp waits, with the same primitives the kernels use, for a value and
+// a flag that nothing sets; both waits must give up and record the error.
+__global__ void k_selftest_wait(DevScal* s, const double* never, const unsigned* never_flag, long long limit) {
+    double v = ld_relaxed_f64(never);
+    const GiveUpGlobal gu{&s->abort};
+    const bool got_value = spin_value(never, &v, limit, gu);
+    const bool got_flag = wait_flag(never_flag, 0xffffffffu, s, limit, -1);
+    if (threadIdx.x == 0 && (!got_value || !got_flag)) raise_error(s, KKT_ERR_TIMEOUT, -1);
 }
 
 // ---------------------------------------------------------------- K4: products with K

@@ -50,6 +50,7 @@ struct kkt_ctx {
     int t0 = 0;
     size_t tail_smem = 0;
     int tail_blocks = 0;
+    int tail_max_steps = 1, tail_max_len = 1, tail_mlo = 0;
     DevScal* d_s = nullptr;
     DevScal* h_s = nullptr;   // pinned mirror
     int64_t ld = 0;
@@ -75,6 +76,7 @@ constexpr int PERSIST_THREADS = 256;
 constexpr int CHAIN_THREADS = 1024;
 constexpr int TAIL_MAX_ROWS = 32767;     // rows factored one block per row
 constexpr size_t TAIL_SMEM_MAX = 200 * 1024;
+constexpr int TAIL_MAP_COLS = 16384;     // columns with an O(1) position map in the tail kernel
 constexpr int CHAIN_MAX = 12288;       // rows of a chain (8 bytes of shared memory each)
 constexpr int CHAIN_WIDTH = 32;        // a level belongs to the chain if it has at most this many rows
 
@@ -227,11 +229,13 @@ cudaError_t launch_cluster(kkt_ctx* c, const int32_t* perm, const double* rhs, d
                               rhs, out, c->d_s, spin(c));
 }
 
-// Pick the smallest cluster (8 or 16 blocks) whose shared memory holds all
-// n values and that the device can co-schedule; 0 if none.
+// Pick the cluster (16 blocks, else 8) whose shared memory holds all n
+// values and that the device can co-schedule; 0 if none.  16 blocks give
+// the sweep twice the FP64 pipes of 8 (measured faster on kkt2000).
 int pick_cluster(kkt_ctx* c) {
     const int n = c->A.n;
-    for (int C : {8, 16}) {
+    for (int C : {16, 8}) {
+        if (c->o.cluster_blocks && C != c->o.cluster_blocks) continue;
         size_t per_block = (size_t)((n + 32 * C - 1) / (32 * C)) * 32 * sizeof(double);
         if (per_block > TAIL_SMEM_MAX) continue;
         for (auto fn : {kkt::k_trsv_cluster<true>, kkt::k_trsv_cluster<false>}) {
@@ -370,7 +374,8 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
     if (c->o.restart < 1 || c->o.restart > kkt::MAXM || c->o.max_cycles < 0 || c->o.precision != 0 ||
         (c->o.stop_mode != KKT_STOP_NRBE && c->o.stop_mode != KKT_STOP_RR) || c->o.pivot_tol <= 0 ||
         c->o.pivot_tol > 1 || c->o.boost_eps < 0 ||
-        (c->o.trisolve != KKT_TRSV_AUTO && c->o.trisolve != KKT_TRSV_GLOBAL) || c->o.tail_rows < 0) {
+        (c->o.trisolve != KKT_TRSV_AUTO && c->o.trisolve != KKT_TRSV_GLOBAL) || c->o.tail_rows < 0 ||
+        (c->o.cluster_blocks != 0 && c->o.cluster_blocks != 8 && c->o.cluster_blocks != 16)) {
         delete c;
         return KKT_ERR_INVALID;
     }
@@ -534,10 +539,24 @@ int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* col
         c->tail_smem = 0;
         while (T > 0) {
             int t0 = n - T;
-            int64_t maxlen = 0;
-            for (int32_t i = t0; i < n; i++) maxlen = std::max<int64_t>(maxlen, c->lay.Fp[i + 1] - c->lay.Fp[i]);
-            size_t smem = ((2 * (size_t)T + 7) / 8) * 8 + 8 * (size_t)maxlen;
-            if (smem <= TAIL_SMEM_MAX && maxlen <= 32767) { c->t0 = t0; c->tail_smem = smem; break; }
+            int64_t maxlen = 0, maxsteps = 0;
+            for (int32_t i = t0; i < n; i++) {
+                maxlen = std::max<int64_t>(maxlen, c->lay.Fp[i + 1] - c->lay.Fp[i]);
+                maxsteps = std::max<int64_t>(maxsteps, c->lay.Fdiag[i] - c->lay.Fp[i]);
+            }
+            // shared memory: step descriptors, row values and columns, and a
+            // position map for the last (at most TAIL_MAP_COLS) columns
+            const int mlo = std::max(t0, n - TAIL_MAP_COLS);
+            size_t smem = 16 * (size_t)std::max<int64_t>(maxsteps, 1) + 12 * (size_t)maxlen +
+                          2 * (size_t)(n - mlo);
+            if (smem <= TAIL_SMEM_MAX && maxlen <= 32767) {
+                c->t0 = t0;
+                c->tail_mlo = mlo;
+                c->tail_smem = smem;
+                c->tail_max_steps = (int)std::max<int64_t>(maxsteps, 1);
+                c->tail_max_len = (int)maxlen;
+                break;
+            }
             T /= 2;
         }
         if (c->t0 < n) {
@@ -562,7 +581,42 @@ int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* col
     return KKT_OK;
 }
 
+namespace {
+int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsigned long long* trace);
+}
+
 int kkt_refactor(kkt_ctx* c, const double* values, int values_on_device) {
+    return refactor_impl(c, values, values_on_device, nullptr);
+}
+
+int kkt_trace_refactor(kkt_ctx* c, const double* values, int values_on_device, int64_t* t_start,
+                       int64_t* t_publish, int32_t* t0_out) {
+    int rc = check_ctx(c, false);
+    if (rc) return rc;
+    if (!t_start || !t_publish || !t0_out) return KKT_ERR_INVALID;
+    const int n = c->A.n;
+    const int T = n - c->t0;
+    *t0_out = c->t0;
+    std::fill(t_start, t_start + n, (int64_t)-1);
+    std::fill(t_publish, t_publish + n, (int64_t)-1);
+    if (T <= 0) return refactor_impl(c, values, values_on_device, nullptr);
+    unsigned long long* d_trace = nullptr;   // profiling only: a buffer of its own
+    CK(cudaMalloc(&d_trace, sizeof(unsigned long long) * 2 * (size_t)T));
+    CK(cudaMemsetAsync(d_trace, 0, sizeof(unsigned long long) * 2 * (size_t)T, c->stream));
+    rc = refactor_impl(c, values, values_on_device, d_trace);
+    std::vector<unsigned long long> h(2 * (size_t)T);
+    cudaError_t e = cudaMemcpy(h.data(), d_trace, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost);
+    cudaFree(d_trace);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy");
+    for (int r = 0; r < T; r++) {
+        t_start[c->t0 + r] = (int64_t)h[2 * (size_t)r];
+        t_publish[c->t0 + r] = (int64_t)h[2 * (size_t)r + 1];
+    }
+    return rc;
+}
+
+namespace {
+int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsigned long long* trace) {
     int rc = check_ctx(c, false);
     if (rc) return rc;
     if (!values) return KKT_ERR_INVALID;
@@ -595,8 +649,8 @@ int kkt_refactor(kkt_ctx* c, const double* values, int values_on_device) {
         kkt::k_refactor_prep_tail<<<1, 1, 0, c->stream>>>(c->d_s);
         const int blocks = std::min(n - c->t0, c->tail_blocks);
         kkt::k_refactor_tail<<<blocks, kkt::TAIL_THREADS, c->tail_smem, c->stream>>>(
-            c->t0, n, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_rinv, vals, c->d_fsrc, c->d_s, c->o.boost_eps,
-            spin(c));
+            c->t0, n, c->tail_mlo, c->tail_max_steps, c->tail_max_len, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_rinv, vals, c->d_fsrc, c->d_s, c->o.boost_eps,
+            spin(c), trace);
         c->launches += 2;
     }
     phase_end(c, t);
@@ -608,6 +662,7 @@ int kkt_refactor(kkt_ctx* c, const double* values, int values_on_device) {
     c->factored = true;
     return KKT_OK;
 }
+}  // namespace
 
 int kkt_lu_solve(kkt_ctx* c, const double* b, double* x, int on_device) {
     int rc = check_ctx(c, true);
@@ -811,6 +866,24 @@ int kkt_query(kkt_ctx* c, kkt_info* info) {
     info->h2d_bytes = c->h2d;
     info->d2h_bytes = c->d2h;
     return KKT_OK;
+}
+
+int kkt_selftest_wait(kkt_ctx* c, int64_t limit) {
+    int rc = check_ctx(c, false);
+    if (rc) return rc;
+    if (limit < 0) return KKT_ERR_INVALID;
+    // d_w holds no live data between calls: arm one entry with SENTINEL as
+    // the value nobody writes; done_f[0] can never hold the generation ~0u
+    kkt::k_fill_sentinel<<<1, 32, 0, c->stream>>>(c->d_w, 1);
+    CK(cudaMemsetAsync(&c->d_s->err, 0, sizeof(int) * 3, c->stream));
+    kkt::k_selftest_wait<<<1, 32, 0, c->stream>>>(c->d_s, c->d_w, c->d_done_f, (long long)limit);
+    c->launches += 2;
+    CK(cudaGetLastError());
+    if ((rc = read_scalars(c))) return rc;
+    rc = c->h_s->err;
+    CK(cudaMemsetAsync(&c->d_s->err, 0, sizeof(int) * 3, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return rc;
 }
 
 int kkt_get_phase_times(kkt_ctx* c, double* ms, int64_t* counts, int reset) {

@@ -7,9 +7,10 @@
 //
 // FP64 on B300 has a dependent-operation latency of about 64 cycles, so a
 // five-step warp reduction of doubles costs ~600 cycles -- more than the
-// rest of a dependency hand-off.  A row therefore splits its entries in two:
+// rest of a dependency hand-off -- and the FP64 pipe is scarce (about 1.6
+// fused multiply-adds per clock per SM).  A row therefore splits its entries in two:
 // the EARLY ones are summed lane-parallel and warp-reduced while the LATE
-// ones -- the row's NLATE most recent dependencies, which finish last -- are
+// ones -- the row's few most recent dependencies, which finish last -- are
 // still in flight; lane 0 then folds the late ones in one fused
 // multiply-add each, in a fixed order.  Only that last FMA (and, for U, one
 // multiply) sits on the dependency chain.  Which entries are late is fixed
@@ -25,7 +26,9 @@
 namespace kkt {
 
 constexpr unsigned long long SENTINEL_BITS = 0x7ff4dead5ca1ab1eull;
-constexpr int NLATE = 4;        // late entries per row
+// late entries per row, tuned per sweep (L: 2, U: 4; swept 2..16 on kkt2000)
+constexpr int NLATE_L = 2;
+constexpr int NLATE_U = 4;
 constexpr int ROW_BATCH = 4;    // early entries per lane with loads in flight together
 
 __device__ __forceinline__ double sentinel() { return __longlong_as_double((long long)SENTINEL_BITS); }
@@ -55,15 +58,16 @@ __device__ __forceinline__ bool spin_value(const volatile double* p, double* v, 
 }
 
 // One row over entries [lo, hi) of the factor row (columns ascending).
-// LOWER: the late entries are the last NLATE (largest columns, the most
+// LOWER: the late entries are the last NLATE (NLATE_L) (largest columns, the most
 // recent rows of the forward sweep); folded in ascending column order.
-// !LOWER: the late entries are the first NLATE (smallest columns > i, the
+// !LOWER: the late entries are the first NLATE (NLATE_U; smallest columns > i, the
 // most recent rows of the backward sweep); folded in descending order.
 // Returns the row's value in lane 0 (other lanes: unspecified) or false in
 // every lane if a wait failed.
 template <bool LOWER, class Src, class GiveUp>
 __device__ __forceinline__ bool trsv_row(int64_t lo, int64_t hi, const double* __restrict__ Fx, Src src,
                                          double r0, double rinv, long long limit, GiveUp give_up, double* out) {
+    constexpr int NLATE = LOWER ? NLATE_L : NLATE_U;
     const int lane = threadIdx.x & 31;
     const int64_t len = hi - lo;
     const int nl = (int)(len < NLATE ? len : NLATE);
@@ -104,7 +108,15 @@ __device__ __forceinline__ bool trsv_row(int64_t lo, int64_t hi, const double* _
         }
     }
     if (!__all_sync(0xffffffffu, ok)) return false;
-    acc = warp_sum(acc);
+    // lanes past the m-th early entry hold exact zeros: reduce over the
+    // first 2^ceil(log2 m) lanes only (same sum, fewer FP64 steps)
+    const int64_t m = ehi - elo;
+    if (m > 0) {
+        const int span = m >= 32 ? 32 : (int)m;
+        int o = 1;
+        while (o < span) o <<= 1;
+        for (o >>= 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    }
     double r = r0 - acc;
     if (lane == 0) {
 #pragma unroll
