@@ -129,6 +129,71 @@ def peaks():
         return 6400.0, "fallback"
 
 
+# FP64 peak of a B300 from the profiling recipe's nominal table (1.25 TFLOP/s
+# dense FP64); the DFMA probe in the design doc measured 0.95 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.25
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "trsv_row.cuh"):
+        with open(os.path.join(ROOT, "paper_2401_13926_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when the kernel source changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "traffic_kkt2000.txt")
+    try:
+        rows = {}
+        for line in open(path):
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                rows[k.strip()] = v.strip()
+        if rows.get("kernel_source_sha256_16") != kernel_source_hash():
+            return None
+        return float(rows[kernel + ".dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def roofline(phases, info, seq, steps):
+    """Roofline of the dominant kernel group, from the library's own CUDA
+    event timers over the timed region.
+
+    refactorization (gather + bulk + block-per-row kernels): FP64 ALU bound,
+      2 x multiply-adds of one refactorization per launch;
+    triangular solves: HBM, 12 bytes per factor entry + 36 (L) / 44 (U)
+      bytes per row per launch."""
+    hbm, peak_kind = peaks()
+    n = seq.n
+    ref_ms = phases["gather"][0] + phases["refactor"][0] + phases["refactor_tail"][0]
+    ref_n = max(phases["refactor_tail"][1], phases["refactor"][1], 1)
+    groups = {"refactor": (ref_ms, ref_n), "lsolve": phases["lsolve"], "usolve": phases["usolve"]}
+    dom = max(groups, key=lambda g: groups[g][0])
+    ms, cnt = groups[dom]
+    per_ms = ms / max(cnt, 1)
+    extra = {"kernel_group": dom, "ms_per_launch": per_ms,
+             "phase_ms_per_step": {p: round(phases[p][0] / steps, 4) for p in phases},
+             "phase_launches": {p: phases[p][1] for p in phases}}
+    if dom == "refactor":
+        flops = 2.0 * info["refactor_updates"]
+        ach = flops / (per_ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": measured_traffic("k_refactor_tail"),
+                "peak_kind": "nominal FP64 (recipe table)", "flops_per_launch": flops, **extra}
+    nnz = info["nnz_l"] if dom == "lsolve" else info["nnz_u"]
+    bytes_ = 12 * nnz + (36 if dom == "lsolve" else 44) * n
+    ach = bytes_ / (per_ms * 1e-3) / 1e9
+    kern = "k_trsv_cluster<1>" if dom == "lsolve" else "k_trsv_cluster<0>"
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": measured_traffic(kern), "peak_kind": peak_kind + " hbm_gbs", "bytes_per_launch": bytes_,
+            **extra}
+
+
 # -------------------------------------------------------------------- oracle
 def oracle_sample(seq, seconds, steps=None):
     """The CPU oracle as it stands: analysis once (not timed), then refactor +
@@ -265,30 +330,7 @@ def run_ours(args):
         return
 
     # ---- roofline of the dominant kernel group
-    hbm, peak_kind = peaks()
-    lay = info0
-    n = seq.n
-    tot = {p: phases[p][0] for p in phases}
-    dom = max(("refactor", "refactor_tail", "lsolve", "usolve", "spmv", "ortho"), key=lambda p: tot[p])
-    ms, cnt = phases[dom]
-    per_launch_ms = ms / max(cnt, 1)
-    if dom == "lsolve":
-        bytes_ = 12 * lay["nnz_l"] + 36 * n
-    elif dom == "usolve":
-        bytes_ = 12 * lay["nnz_u"] + 44 * n
-    elif dom in ("refactor", "refactor_tail"):
-        bytes_ = 20 * (lay["nnz_l"] + lay["nnz_u"]) + 24 * n
-    elif dom == "spmv":
-        bytes_ = 12 * seq.nnz + 28 * n
-    else:
-        bytes_ = 8 * n * (2 * RESTART)
-    achieved = bytes_ / (per_launch_ms * 1e-3) / 1e9
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
-            "bytes_per_launch": bytes_, "ms_per_launch": per_launch_ms,
-            "phase_ms": {p: round(phases[p][0] / args.steps, 4) for p in phases},
-            "phase_launches": {p: phases[p][1] for p in phases}}
-
+    roof = roofline(phases, info0, seq, args.steps)
     cpu = None
     if not args.no_cpu_baseline:
         done, tcpu, t_an, _ = oracle_sample(KKTSequence(args.workload), args.cpu_seconds)
@@ -310,9 +352,9 @@ def run_ours(args):
                 "h2d_bytes_per_step": (info_b["h2d_bytes"] - info_a["h2d_bytes"]) // n_e2e,
                 "d2h_bytes_per_step": (info_b["d2h_bytes"] - info_a["d2h_bytes"]) // n_e2e},
         "gpu_launches": launches, "clocks": clk, "wall_s": t_wall,
-        "analysis": {"analyze_ms": lay["analyze_ms"], "nnz_l": lay["nnz_l"], "nnz_u": lay["nnz_u"],
-                     "levels_l": lay["levels_l"], "levels_u": lay["levels_u"],
-                     "refactor_updates": lay["refactor_updates"]},
+        "analysis": {"analyze_ms": info0["analyze_ms"], "nnz_l": info0["nnz_l"], "nnz_u": info0["nnz_u"],
+                     "levels_l": info0["levels_l"], "levels_u": info0["levels_u"],
+                     "refactor_updates": info0["refactor_updates"]},
     }
     print(json.dumps(line), flush=True)
 
