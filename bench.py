@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "kkt2000"
 TOL = 1e-12
 RESTART = 20
+ALT_MAX_CYCLES = 2      # cycle cap of the side-by-side mixed-precision run
 L2_FLUSH_BYTES = 256 << 20   # larger than the 126 MB L2
 
 
@@ -42,6 +43,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="factor precision of the headline line")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the side-by-side mixed-precision run")
     return ap.parse_args()
 
 
@@ -269,7 +273,7 @@ def run_ours(args):
     seq = KKTSequence(args.workload, instance=rank)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    solver = K.KKTSolver(restart=RESTART, device=local, stream=stream, timing=True)
+    solver = K.KKTSolver(restart=RESTART, device=local, stream=stream, timing=True, precision=args.precision)
     solver.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
     info0 = solver.info()
     # inputs resident in HBM before the timed region
@@ -280,7 +284,8 @@ def run_ours(args):
 
     def step(k):
         solver.refactor(vals[k % seq.M])
-        _, it, nr = solver.solve(rhs[k % seq.M], x=x, tol=TOL)
+        # a mixed-precision headline reports unconverged solves instead of stopping
+        _, it, nr = solver.solve(rhs[k % seq.M], x=x, tol=TOL, allow_not_converged=args.precision == "mixed")
         return it, nr
 
     for w in range(args.warmup):
@@ -326,6 +331,44 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t
     info_b = solver.info()
     e2e_units, e2e_secs = aggregate(float(n_e2e), e2e_s, world)
+
+    # ---- the other precision on the same workload, same protocol (device time)
+    other = None
+    if not args.no_mixed:
+        alt = "mixed" if args.precision == "fp64" else "fp64"
+        # FP32-preconditioned refinement stalls above 1e-12 on some of these
+        # ill-conditioned matrices, so this run caps the cycles and reports
+        # how many solves reached the tolerance
+        cyc2 = ALT_MAX_CYCLES if alt == "mixed" else 50
+        s2 = K.KKTSolver(restart=RESTART, device=local, stream=stream, timing=True, precision=alt,
+                         max_cycles=cyc2)
+        s2.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
+        for w in range(args.warmup):
+            s2.refactor(vals[w % seq.M])
+            s2.solve(rhs[w % seq.M], x=x, tol=TOL, allow_not_converged=True)
+        s2.phase_times(reset=True)
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(seq.M)]
+        it2, nr2, ok2 = [], [], 0
+        torch.cuda.synchronize()
+        for i in range(seq.M):
+            flush.zero_()
+            ev2[i][0].record(stream)
+            s2.refactor(vals[i])
+            _, it, nr = s2.solve(rhs[i], x=x, tol=TOL, allow_not_converged=True)
+            ev2[i][1].record(stream)
+            it2.append(it)
+            nr2.append(nr)
+            ok2 += s2.last_status == K.OK
+        torch.cuda.synchronize()
+        ms2 = [a.elapsed_time(b) for a, b in ev2]
+        ph2 = s2.phase_times(reset=True)
+        other = {"precision": alt, "value": seq.M / (sum(ms2) / 1000.0), "unit": "solves/s",
+                 "steps": seq.M, "latency_ms": {"p50": float(np.percentile(ms2, 50)),
+                                                "p99": float(np.percentile(ms2, 99))},
+                 "iters_mean": float(np.mean(it2)), "max_nrbe": float(np.max(nr2)),
+                 "converged": ok2, "max_cycles": cyc2, "nrbe": [float(f"{v:.3g}") for v in nr2],
+                 "phase_ms_per_step": {p: round(ph2[p][0] / seq.M, 4) for p in ph2}}
+        s2.close()
     if rank != 0:
         return
 
@@ -343,8 +386,9 @@ def run_ours(args):
         "metric": "KKT solves/sec (refactor+FGMRES to NRBE<=1e-12)",
         "value": units / secs, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {**workload_config(seq), "parallelism": f"replicas{world}"},
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32-factors/f64",
+        "data": "synthetic",
+        "config": {**workload_config(seq), "parallelism": f"replicas{world}", "precision": args.precision},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "iters_mean": float(np.mean(iters)), "max_nrbe": float(np.max(nrbes)),
         "roofline": roof, "cpu_baseline": cpu,
@@ -352,6 +396,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": (info_b["h2d_bytes"] - info_a["h2d_bytes"]) // n_e2e,
                 "d2h_bytes_per_step": (info_b["d2h_bytes"] - info_a["d2h_bytes"]) // n_e2e},
         "gpu_launches": launches, "clocks": clk, "wall_s": t_wall,
+        "precision": args.precision, "other_precision": other,
         "analysis": {"analyze_ms": info0["analyze_ms"], "nnz_l": info0["nnz_l"], "nnz_u": info0["nnz_u"],
                      "levels_l": info0["levels_l"], "levels_u": info0["levels_u"],
                      "refactor_updates": info0["refactor_updates"]},

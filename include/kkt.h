@@ -56,6 +56,14 @@ extern "C" {
 #define KKT_ERR_CUDA (-8)           /* CUDA runtime error */
 #define KKT_ERR_STATE (-9)          /* call out of order (e.g. solve before refactor) */
 
+/* Factor precision.  FP64: factors, triangular solves and refinement in
+   FP64.  MIXED: the factors are refactored and the triangular solves (the
+   FGMRES preconditioner) run in FP32, while the residual, CGS2, the
+   Hessenberg least squares and the solution update stay FP64 -- the
+   inexact-factor use of FGMRES the paper's method allows (Section 2.1). */
+#define KKT_PRECISION_FP64 0
+#define KKT_PRECISION_MIXED 1
+
 #define KKT_STOP_NRBE 0   /* Eq. (nbre) <= tol, checked on the true residual */
 #define KKT_STOP_RR 1     /* estimated ||rho_i|| < tol ||rho_0|| (the paper's rule) */
 
@@ -65,7 +73,7 @@ typedef struct {
     int restart;          /* FGMRES restart length m (default 20, 1..64) */
     int max_cycles;       /* restart cycles before KKT_ERR_NOT_CONVERGED (default 50) */
     int stop_mode;        /* KKT_STOP_NRBE (default) or KKT_STOP_RR */
-    int precision;        /* 0 = FP64 (default); others reserved */
+    int precision;        /* KKT_PRECISION_FP64 (default) or KKT_PRECISION_MIXED */
     double refine_delta;  /* Section 2.3: skip refinement if ||r - K x0|| < delta ||r||; 0 = off */
     double pivot_tol;     /* threshold partial pivoting in kkt_analyze (default 1e-3) */
     double boost_eps;     /* static-pivot boost: |u_jj| < boost_eps ||K||_inf becomes
@@ -181,7 +189,8 @@ int kkt_get_perm(kkt_ctx* c, int32_t* P, int32_t* Q);
 int kkt_get_factor_sizes(kkt_ctx* c, int64_t* nnz_l, int64_t* nnz_u);
 
 /*
- * Host copies of the current factors in CSC, permuted space, rows sorted:
+ * Host copies of the current factors (FP32 factors are widened exactly to
+ * double) in CSC, permuted space, rows sorted:
  * L strictly lower (Lp[n+1], Li/Lx[nnz_l]), U with diagonal (Up[n+1],
  * Ui/Ux[nnz_u]).  For tests and inspection.
  */

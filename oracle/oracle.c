@@ -30,6 +30,9 @@
  *                      factorization, reusing the pivot sequence and the
  *                      symbolic analysis of the first system), with an
  *                      optional static-pivot boost.
+ *   or_refactor_f32 -- the same refactorization in FP32 arithmetic (the
+ *                      mixed-precision factors used as an inexact
+ *                      preconditioner, Section 2.1).
  *   or_solve        -- the triangular solve (step 3 of Section 1.3):
  *                      x = Q U^{-1} L^{-1} P b.
  *   or_fgmres       -- iterative refinement by FGMRES with the LU factors as
@@ -360,6 +363,103 @@ void *or_refactor(int n, const int *Ap, const int *Ai, const double *Ax,
     return F;
 fail:
     free(pinv); free(colof); free(mark); free(stack); free(pos); free(out); free(seeds); free(x);
+    free(Li.a); free(Lx.a); free(Ui.a); free(Ux.a);
+    if (F) { F->Li = NULL; F->Lx = NULL; F->Ui = NULL; F->Ux = NULL; or_factor_free(F); }
+    return NULL;
+}
+
+/* ------------------------------------------------------------------ */
+/* The same refactorization in FP32 arithmetic (mixed precision: FP32   */
+/* factors as the FGMRES preconditioner, Section 2.1's inexact factors). */
+/* Values are rounded to float, every update is fmaf, the L column is   */
+/* scaled by the float reciprocal 1.0f / u_jj; the factors are returned */
+/* widened (exactly) to double.  boost_abs as in or_refactor.            */
+void *or_refactor_f32(int n, const int *Ap, const int *Ai, const double *Ax,
+                      const int *P, const int *Q, double boost_abs, int *status) {
+    *status = OR_ERR_OOM;
+    or_factors *F = (or_factors *)calloc(1, sizeof(or_factors));
+    int *pinv = (int *)malloc(sizeof(int) * (size_t)n);
+    int *colof = (int *)malloc(sizeof(int) * (size_t)n);
+    int *mark = (int *)malloc(sizeof(int) * (size_t)n);
+    int *stack = (int *)malloc(sizeof(int) * (size_t)n);
+    int *pos = (int *)malloc(sizeof(int) * (size_t)n);
+    int *out = (int *)malloc(sizeof(int) * (size_t)n);
+    int *seeds = (int *)malloc(sizeof(int) * (size_t)n);
+    float *x = (float *)calloc((size_t)n, sizeof(float));
+    float *lxf = NULL;   /* L values in float while factorizing */
+    long lcap = 0;
+    ivec Li = {0}, Ui = {0};
+    dvec Lx = {0}, Ux = {0};
+    const float boost = (float)boost_abs;
+    if (!F || !pinv || !colof || !mark || !stack || !pos || !out || !seeds || !x) goto fail;
+    F->n = n;
+    F->Lp = (int *)malloc(sizeof(int) * (size_t)(n + 1));
+    F->Up = (int *)malloc(sizeof(int) * (size_t)(n + 1));
+    if (!F->Lp || !F->Up) goto fail;
+    for (int i = 0; i < n; i++) { pinv[i] = -1; mark[i] = -1; colof[i] = -1; }
+    for (int k = 0; k < n; k++) {
+        if (P[k] < 0 || P[k] >= n || pinv[P[k]] >= 0) { *status = OR_ERR_PATTERN; goto fail; }
+        pinv[P[k]] = k;
+    }
+    F->Lp[0] = 0; F->Up[0] = 0;
+    for (int j = 0; j < n; j++) {
+        int c = Q[j];
+        int ns = 0;
+        for (int p = Ap[c]; p < Ap[c + 1]; p++) seeds[ns++] = pinv[Ai[p]];
+        int top = n;
+        reach(n, seeds, ns, colof, F->Lp, Li.a, mark, j, stack, pos, out, &top);
+        for (int p = Ap[c]; p < Ap[c + 1]; p++) x[pinv[Ai[p]]] = (float)Ax[p];
+        qsort(out + top, (size_t)(n - top), sizeof(int), cmp_int);
+        for (int t = top; t < n; t++) {
+            int i = out[t];
+            if (i >= j) break;
+            float xi = x[i];
+            for (int p = F->Lp[i]; p < F->Lp[i + 1]; p++) x[Li.a[p]] = fmaf(-lxf[p], xi, x[Li.a[p]]);
+        }
+        if (mark[j] != j) { *status = OR_ERR_SINGULAR; goto fail; }
+        float d = x[j];
+        if (!isfinite(d)) { *status = OR_ERR_NONFINITE; goto fail; }
+        if (boost > 0.0f) {
+            if (fabsf(d) < boost) { d = (d < 0.0f) ? -boost : boost; F->nboost++; }
+        } else if (d == 0.0f) {
+            *status = OR_ERR_SINGULAR; goto fail;
+        }
+        for (int t = top; t < n; t++) {
+            int i = out[t];
+            if (i < j) { if (!ivec_push(&Ui, i) || !dvec_push(&Ux, (double)x[i])) goto fail; }
+        }
+        if (!ivec_push(&Ui, j) || !dvec_push(&Ux, (double)d)) goto fail;
+        float dinv = 1.0f / d;
+        for (int t = top; t < n; t++) {
+            int i = out[t];
+            if (i > j) {
+                float l = x[i] * dinv;
+                if (!isfinite(l)) { *status = OR_ERR_NONFINITE; goto fail; }
+                if (!ivec_push(&Li, i) || !dvec_push(&Lx, (double)l)) goto fail;
+                if (Li.n > lcap) {
+                    long nc = lcap ? 2 * lcap : 1024;
+                    while (nc < Li.n) nc *= 2;
+                    float *q = (float *)realloc(lxf, sizeof(float) * (size_t)nc);
+                    if (!q) goto fail;
+                    lxf = q; lcap = nc;
+                }
+                lxf[Li.n - 1] = l;
+            }
+        }
+        colof[j] = j;
+        for (int t = top; t < n; t++) x[out[t]] = 0.0f;
+        F->Lp[j + 1] = (int)Li.n;
+        F->Up[j + 1] = (int)Ui.n;
+    }
+    F->Li = Li.a; F->Lx = Lx.a; F->Ui = Ui.a; F->Ux = Ux.a;
+    if (!F->Li) { F->Li = (int *)malloc(sizeof(int)); F->Lx = (double *)malloc(sizeof(double)); }
+    sort_columns(n, F->Lp, F->Li, F->Lx);
+    sort_columns(n, F->Up, F->Ui, F->Ux);
+    free(pinv); free(colof); free(mark); free(stack); free(pos); free(out); free(seeds); free(x); free(lxf);
+    *status = OR_OK;
+    return F;
+fail:
+    free(pinv); free(colof); free(mark); free(stack); free(pos); free(out); free(seeds); free(x); free(lxf);
     free(Li.a); free(Lx.a); free(Ui.a); free(Ux.a);
     if (F) { F->Li = NULL; F->Lx = NULL; F->Ui = NULL; F->Ux = NULL; or_factor_free(F); }
     return NULL;

@@ -35,6 +35,8 @@ def lib():
         L.or_lu.argtypes = [C.c_int, _i32, _i32, _f64, _i32, C.c_double, _i32, C.POINTER(C.c_int)]
         L.or_refactor.restype = C.c_void_p
         L.or_refactor.argtypes = [C.c_int, _i32, _i32, _f64, _i32, _i32, C.c_double, C.POINTER(C.c_int)]
+        L.or_refactor_f32.restype = C.c_void_p
+        L.or_refactor_f32.argtypes = [C.c_int, _i32, _i32, _f64, _i32, _i32, C.c_double, C.POINTER(C.c_int)]
         L.or_factor_free.argtypes = [C.c_void_p]
         L.or_factor_sizes.argtypes = [C.c_void_p, C.POINTER(C.c_long), C.POINTER(C.c_long), C.POINTER(C.c_int)]
         L.or_factor_copy.argtypes = [C.c_void_p, _i32, _i32, _f64, _i32, _i32, _f64]
@@ -160,6 +162,17 @@ def refactor(n, rowptr, colind, values, P, Q, boost_abs=0.0):
                           np.ascontiguousarray(Q, np.int32), float(boost_abs), C.byref(st))
     if not h:
         raise OracleError(st.value, "refactor")
+    return _factors_from_handle(n, h)
+
+
+def refactor_f32(n, rowptr, colind, values, P, Q, boost_abs=0.0):
+    """Refactorization in FP32 arithmetic (factors returned widened to double)."""
+    Ap, Ai, Ax = csr_to_csc(n, rowptr, colind, values)
+    st = C.c_int()
+    h = lib().or_refactor_f32(n, Ap, Ai, Ax, np.ascontiguousarray(P, np.int32),
+                              np.ascontiguousarray(Q, np.int32), float(boost_abs), C.byref(st))
+    if not h:
+        raise OracleError(st.value, "refactor_f32")
     return _factors_from_handle(n, h)
 
 

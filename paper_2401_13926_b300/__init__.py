@@ -28,6 +28,7 @@ ERR = {
 ERR_NOT_CONVERGED = -6
 STOP = {"nrbe": 0, "rr": 1}
 TRSV = {"auto": 0, "global": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
 
 # every entry point declared in include/kkt.h
 EXPORTS = [
@@ -192,7 +193,7 @@ class KKTSolver:
 
     def __init__(self, restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3,
                  boost_eps=0.0, device=0, stream=None, spin_limit=0, timing=False, trisolve="auto",
-                 tail_rows=0, cluster_blocks=0):
+                 tail_rows=0, cluster_blocks=0, precision="fp64"):
         L = lib()
         o = _Opts()
         L.kkt_default_opts(C.byref(o))
@@ -202,6 +203,7 @@ class KKTSolver:
         o.trisolve = TRSV[trisolve]
         o.tail_rows = int(tail_rows)
         o.cluster_blocks = int(cluster_blocks)
+        o.precision = PRECISION[precision]
         if stream is None:
             stream = _torch_current_stream(device)
         if stream is None:

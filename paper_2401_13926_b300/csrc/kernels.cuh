@@ -143,6 +143,16 @@ __device__ __forceinline__ double ld_relaxed_f64(const double* p) {
 __device__ __forceinline__ void st_relaxed_f64(double* p, double v) {
     asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
+__device__ __forceinline__ double ld_relaxed(const double* p) { return ld_relaxed_f64(p); }
+__device__ __forceinline__ void st_relaxed(double* p, double v) { st_relaxed_f64(p, v); }
+__device__ __forceinline__ float ld_relaxed(const float* p) {
+    float v;
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(float* p, float v) {
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
 
 // ---------------------------------------------------------------- K0: gather
 // Start of a refactorization: new generation, tickets and error words.
@@ -161,17 +171,20 @@ __global__ void k_refactor_prep(DevScal* s) {
 // Slots from tail_begin on belong to the rows the tail kernel factors in
 // shared memory; they are armed with SENTINEL instead (the tail kernel
 // gathers their values itself and publishes each row when it is final).
+// T is the factor type: double, or float in mixed precision (the caller's
+// FP64 values are rounded to nearest here).
+template <typename T>
 __global__ void k_gather(const double* __restrict__ vals, const int64_t* __restrict__ fsrc, int64_t nnzF,
-                         int64_t tail_begin, double* __restrict__ Fx, const int32_t* __restrict__ Arp,
+                         int64_t tail_begin, T* __restrict__ Fx, const int32_t* __restrict__ Arp,
                          const int64_t* __restrict__ asrc, double* __restrict__ Ax, int n, int t0,
-                         double* __restrict__ rinv, DevScal* s) {
+                         T* __restrict__ rinv, DevScal* s) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = t0 + tid; i < n; i += stride) rinv[i] = sentinel();   // tail rows publish 1/u_ii last
+    for (int64_t i = t0 + tid; i < n; i += stride) rinv[i] = sentinel_of<T>();   // tail rows publish 1/u_ii last
     for (int64_t t = tid; t < nnzF; t += stride) {
-        if (t >= tail_begin) { Fx[t] = sentinel(); continue; }
+        if (t >= tail_begin) { Fx[t] = sentinel_of<T>(); continue; }
         int64_t q = fsrc[t];
-        Fx[t] = (q >= 0) ? vals[q] : 0.0;
+        Fx[t] = (q >= 0) ? (T)vals[q] : T(0);
     }
     const int lane = threadIdx.x & 31;
     const int64_t warp = tid >> 5, nwarps = stride >> 5;
@@ -207,13 +220,14 @@ __device__ __forceinline__ int64_t find_col(const int32_t* __restrict__ Fj, int6
     return lo;
 }
 
+template <typename T>
 __global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
-                           const int64_t* __restrict__ Fdiag, double* Fx, double* rinv, unsigned* done, DevScal* s,
+                           const int64_t* __restrict__ Fdiag, T* Fx, T* rinv, unsigned* done, DevScal* s,
                            double boost_eps, long long limit) {
     // rows [0, n) of the bulk: warp per row, factor values in global memory
     const int lane = threadIdx.x & 31;
     const unsigned gen = *(volatile unsigned*)&s->gen_fact;
-    const double boost = boost_eps * *(volatile double*)&s->normA;
+    const T boost = (T)(boost_eps * *(volatile double*)&s->normA);
     for (;;) {
         int row = 0;
         if (lane == 0) row = (int)atomicAdd(&s->ticket_fact, 1u);
@@ -229,7 +243,7 @@ __global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t*
             if (!ok) return;
             __threadfence();
             const int64_t dk = __ldg(&Fdiag[k]), ek = __ldg(&Fp[k + 1]);
-            const double lik = __ldcg(&Fx[p]) * __ldcg(&rinv[k]);   // l_ik = w_k * (1/u_kk)
+            const T lik = __ldcg(&Fx[p]) * __ldcg(&rinv[k]);   // l_ik = w_k * (1/u_kk)
             __syncwarp();
             if (lane == 0) __stcg(&Fx[p], lik);
             for (int64_t q = dk + 1 + lane; q < ek; q += 32) {
@@ -242,14 +256,14 @@ __global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t*
             __syncwarp();
         }
         if (lane == 0) {
-            double u = __ldcg(&Fx[d]);
+            T u = __ldcg(&Fx[d]);
             bool fail = false;
             if (!isfinite(u)) { raise_error(s, KKT_ERR_NONFINITE, row); fail = true; }
             else if (boost > 0.0) {
                 if (fabs(u) < boost) { u = (u < 0.0) ? -boost : boost; atomicAdd(&s->nboost, 1); __stcg(&Fx[d], u); }
             } else if (u == 0.0) { raise_error(s, KKT_ERR_ZERO_PIVOT, row); fail = true; }
             if (!fail) {
-                __stcg(&rinv[row], __drcp_rn(u));
+                __stcg(&rinv[row], rcp_rn(u));
                 __threadfence();
                 st_release(&done[row], gen);
             }
@@ -277,10 +291,11 @@ __global__ void k_refactor_prep_tail(DevScal* s) { s->ticket_fact = 0; }
 // gather and is final once it is not -- so a consumer spins on exactly the
 // values it uses, all of them in one pass per round trip.
 constexpr int TAIL_E = 4;
+template <typename T>
 struct TailStage {
-    double rk;
+    T rk;
     int32_t col[TAIL_E];
-    double val[TAIL_E];
+    T val[TAIL_E];
 };
 
 struct StepDesc {     // staged per L entry of the row: the step's source row
@@ -288,15 +303,16 @@ struct StepDesc {     // staged per L entry of the row: the step's source row
     int32_t k, cnt;   // k, |U(k, >k)|
 };
 
-__device__ __forceinline__ void tail_load(TailStage& st, int s, int nsteps, const StepDesc* sd,
-                                          const int32_t* __restrict__ Fj, const double* Fx, const double* rinv) {
+template <typename T>
+__device__ __forceinline__ void tail_load(TailStage<T>& st, int s, int nsteps, const StepDesc* sd,
+                                          const int32_t* __restrict__ Fj, const T* Fx, const T* rinv) {
     if (s >= nsteps) return;
     const StepDesc d = sd[s];
-    st.rk = ld_relaxed_f64(&rinv[d.k]);
+    st.rk = ld_relaxed(&rinv[d.k]);
 #pragma unroll
     for (int j = 0; j < TAIL_E; j++) {
         const int e = threadIdx.x + j * TAIL_THREADS;
-        if (e < d.cnt) { st.col[j] = Fj[d.dk + 1 + e]; st.val[j] = ld_relaxed_f64(&Fx[d.dk + 1 + e]); }
+        if (e < d.cnt) { st.col[j] = Fj[d.dk + 1 + e]; st.val[j] = ld_relaxed(&Fx[d.dk + 1 + e]); }
     }
 }
 
@@ -313,34 +329,36 @@ __device__ __forceinline__ int tail_pos(int c, int mlo, const short* map, const 
 }
 
 // Spin until a published datum is not SENTINEL (bounded; abort-aware).
-__device__ __forceinline__ bool tail_wait(const double* p, double* v, DevScal* s, long long limit, int row) {
-    double x = *v;
+template <typename T>
+__device__ __forceinline__ bool tail_wait(const T* p, T* v, DevScal* s, long long limit, int row) {
+    T x = *v;
     for (long long it = 0; is_sentinel(x); it++) {
         if ((it & 63) == 63 && ld_volatile_int(&s->abort)) return false;
         if (it >= limit) { raise_error(s, KKT_ERR_TIMEOUT, row); return false; }
         __nanosleep(20);
-        x = ld_relaxed_f64(p);
+        x = ld_relaxed(p);
     }
     *v = x;
     return true;
 }
 
+template <typename T>
 __global__ void __launch_bounds__(TAIL_THREADS)
 k_refactor_tail(int t0, int nrows, int mlo, int max_steps, int max_len, const int64_t* __restrict__ Fp,
                 const int32_t* __restrict__ Fj,
-                const int64_t* __restrict__ Fdiag, double* Fx, double* rinv, const double* __restrict__ vals,
+                const int64_t* __restrict__ Fdiag, T* Fx, T* rinv, const double* __restrict__ vals,
                 const int64_t* __restrict__ fsrc, DevScal* s, double boost_eps, long long limit,
                 unsigned long long* trace) {
-    extern __shared__ double tail_sh[];
+    extern __shared__ __align__(16) unsigned char tail_sh[];
     __shared__ int s_row;
     const int M = nrows - mlo;   // columns [mlo, nrows) have an O(1) position map
     const int tid = threadIdx.x;
     StepDesc* sd = reinterpret_cast<StepDesc*>(tail_sh);                          // max_steps
-    double* w = reinterpret_cast<double*>(sd + max_steps);                        // row values, max_len
+    T* w = reinterpret_cast<T*>(sd + max_steps);                                  // row values, max_len
     int32_t* cols = reinterpret_cast<int32_t*>(w + max_len);                      // row columns, max_len
     short* map = reinterpret_cast<short*>(cols + max_len);                        // M entries
     for (int c = tid; c < M; c += blockDim.x) map[c] = -1;
-    const double boost = boost_eps * *(volatile double*)&s->normA;
+    const T boost = (T)(boost_eps * *(volatile double*)&s->normA);
     __syncthreads();
     for (;;) {
         if (tid == 0) s_row = t0 + (int)atomicAdd(&s->ticket_fact, 1u);
@@ -354,7 +372,7 @@ k_refactor_tail(int t0, int nrows, int mlo, int max_steps, int max_len, const in
         const int nsteps = (int)(d - b);
         for (int q = tid; q < len; q += blockDim.x) {
             const int64_t src = fsrc[b + q];
-            w[q] = src >= 0 ? vals[src] : 0.0;
+            w[q] = src >= 0 ? (T)vals[src] : T(0);
             const int c = Fj[b + q];
             cols[q] = c;
             if (c >= mlo) map[c - mlo] = (short)q;
@@ -364,13 +382,13 @@ k_refactor_tail(int t0, int nrows, int mlo, int max_steps, int max_len, const in
             }
         }
         __syncthreads();
-        TailStage A, B;
+        TailStage<T> A, B;
         tail_load(A, 0, nsteps, sd, Fj, Fx, rinv);
         tail_load(B, 1, nsteps, sd, Fj, Fx, rinv);
         int step = 0;
         // One elimination step: every thread forms l_ik = w_k * (1/u_kk)
         // itself (thread 0 also stores it), then applies its entries of U(k,:).
-        auto run_step = [&](TailStage& st) -> bool {
+        auto run_step = [&](TailStage<T>& st) -> bool {
             const StepDesc dsc = sd[step];
             int ok = 1;
             // anything still SENTINEL is re-read, all of it in one pass
@@ -383,14 +401,14 @@ k_refactor_tail(int t0, int nrows, int mlo, int max_steps, int max_len, const in
                 if ((it & 63) == 63 && ld_volatile_int(&s->abort)) { ok = 0; break; }
                 if (it >= limit) { raise_error(s, KKT_ERR_TIMEOUT, row); ok = 0; break; }
                 __nanosleep(20);
-                if (is_sentinel(st.rk)) st.rk = ld_relaxed_f64(&rinv[dsc.k]);
+                if (is_sentinel(st.rk)) st.rk = ld_relaxed(&rinv[dsc.k]);
 #pragma unroll
                 for (int j = 0; j < TAIL_E; j++) {
                     const int e2 = tid + j * TAIL_THREADS;
-                    if (e2 < dsc.cnt && is_sentinel(st.val[j])) st.val[j] = ld_relaxed_f64(&Fx[dsc.dk + 1 + e2]);
+                    if (e2 < dsc.cnt && is_sentinel(st.val[j])) st.val[j] = ld_relaxed(&Fx[dsc.dk + 1 + e2]);
                 }
             }
-            const double l = w[step] * st.rk;   // l_ik = w_k * (1/u_kk)
+            const T l = w[step] * st.rk;   // l_ik = w_k * (1/u_kk)
             if (ok) {
 #pragma unroll
                 for (int j = 0; j < TAIL_E; j++) {
@@ -403,7 +421,7 @@ k_refactor_tail(int t0, int nrows, int mlo, int max_steps, int max_len, const in
                 }
                 for (int e2 = tid + TAIL_E * TAIL_THREADS; e2 < dsc.cnt && ok; e2 += TAIL_THREADS) {
                     const int64_t q = dsc.dk + 1 + e2;
-                    double v = ld_relaxed_f64(&Fx[q]);
+                    T v = ld_relaxed(&Fx[q]);
                     if (!tail_wait(&Fx[q], &v, s, limit, row)) { ok = 0; break; }
                     const int pos = tail_pos(Fj[q], mlo, map, cols, step + 1, len);
                     if (pos < 0) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
@@ -427,20 +445,20 @@ k_refactor_tail(int t0, int nrows, int mlo, int max_steps, int max_len, const in
         __syncthreads();   // the last L value written by thread 0 is visible
         // publish: every value but the diagonal, then (thread 0) the pivot
         for (int q = tid; q < len; q += blockDim.x) {
-            if (b + q != d) st_relaxed_f64(&Fx[b + q], w[q]);
+            if (b + q != d) st_relaxed(&Fx[b + q], w[q]);
             const int c = cols[q];
             if (c >= mlo) map[c - mlo] = -1;
         }
         if (tid == 0) {
-            double u = w[d - b];
+            T u = w[d - b];
             int fail = 0;
             if (!isfinite(u)) { raise_error(s, KKT_ERR_NONFINITE, row); fail = 1; }
             else if (boost > 0.0) {
                 if (fabs(u) < boost) { u = (u < 0.0) ? -boost : boost; atomicAdd(&s->nboost, 1); }
             } else if (u == 0.0) { raise_error(s, KKT_ERR_ZERO_PIVOT, row); fail = 1; }
             if (!fail) {
-                st_relaxed_f64(&Fx[d], u);
-                st_relaxed_f64(&rinv[row], __drcp_rn(u));
+                st_relaxed(&Fx[d], u);
+                st_relaxed(&rinv[row], rcp_rn(u));
                 if (trace) trace[2 * (size_t)(row - t0) + 1] = globaltimer_ns();
             }
         }
@@ -474,25 +492,30 @@ __global__ void k_trsv_prep(DevScal* s) {
     s->ticket_u = 0;
 }
 
-__global__ void k_fill_sentinel(double* a, int64_t n) {
+template <typename T>
+__global__ void k_fill_sentinel(T* a, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        a[i] = sentinel();
+        a[i] = sentinel_of<T>();
 }
 
+template <typename T>
 struct SrcGlobal {   // operand in a global vector, by column
     const int32_t* Fj;
-    const double* x;
-    __device__ const volatile double* operator()(int64_t p) const { return x + __ldg(&Fj[p]); }
+    const T* x;
+    __device__ const volatile T* operator()(int64_t p) const { return x + __ldg(&Fj[p]); }
 };
 
 __device__ __forceinline__ void fail_row(DevScal* s, int row) {
     if (!*(volatile int*)&s->abort) raise_error(s, KKT_ERR_TIMEOUT, row);
 }
 
+// T: factor and solve type (double, or float in mixed precision); the
+// right-hand side and the result of a sweep pair stay double.
+template <typename T>
 __global__ void k_lsolve_bulk(int nrows, const int32_t* __restrict__ rows, const int64_t* __restrict__ Fp,
                               const int32_t* __restrict__ Fj, const int64_t* __restrict__ Fdiag,
-                              const double* __restrict__ Fx, const int32_t* __restrict__ P,
-                              const double* __restrict__ rhs, double* y, double* xp, DevScal* s, long long limit) {
+                              const T* __restrict__ Fx, const int32_t* __restrict__ P,
+                              const double* __restrict__ rhs, T* y, T* xp, DevScal* s, long long limit) {
     const int lane = threadIdx.x & 31;
     const GiveUpGlobal gu{&s->abort};
     for (;;) {
@@ -501,26 +524,27 @@ __global__ void k_lsolve_bulk(int nrows, const int32_t* __restrict__ rows, const
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= nrows) return;
         const int row = rows[t];
-        const double r0 = rhs[P[row]];
-        double val;
-        if (!trsv_row<true>(Fp[row], Fdiag[row], Fx, SrcGlobal{Fj, y}, r0, 1.0, limit, gu, &val)) {
+        const T r0 = (T)rhs[P[row]];
+        T val;
+        if (!trsv_row<true>(Fp[row], Fdiag[row], Fx, SrcGlobal<T>{Fj, y}, r0, T(1), limit, gu, &val)) {
             if (lane == 0) fail_row(s, row);
             return;
         }
         if (lane == 0) {
-            xp[row] = sentinel();
-            st_relaxed_f64(&y[row], val);
+            xp[row] = sentinel_of<T>();
+            st_relaxed(&y[row], val);
         }
     }
 }
 
+template <typename T>
 struct SrcChainL {   // dependency in the chain: shared memory; else y (final)
     const int32_t* Fj;
     const int32_t* Fpos;
     int cstart;
-    const volatile double* xs;
-    const double* y;
-    __device__ const volatile double* operator()(int64_t p) const {
+    const volatile T* xs;
+    const T* y;
+    __device__ const volatile T* operator()(int64_t p) const {
         const int t = __ldg(&Fpos[p]) - cstart;
         return t >= 0 ? xs + t : y + __ldg(&Fj[p]);
     }
@@ -533,66 +557,69 @@ struct GiveUpShared {
 
 // The narrow end of the L-sweep in one block: warp w takes chain slots w,
 // w + nwarps, ... (slot t = list position cstart + t).
+template <typename T>
 __global__ void __launch_bounds__(1024)
 k_lsolve_chain(int nt, int cstart, const int32_t* __restrict__ rows, const int32_t* __restrict__ Fpos,
                const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj, const int64_t* __restrict__ Fdiag,
-               const double* __restrict__ Fx, const int32_t* __restrict__ P, const double* __restrict__ rhs,
-               double* y, double* xp, DevScal* s, long long limit) {
-    extern __shared__ double xs_dyn[];
-    volatile double* xs = xs_dyn;
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) xs[t] = sentinel();
+               const T* __restrict__ Fx, const int32_t* __restrict__ P, const double* __restrict__ rhs,
+               T* y, T* xp, DevScal* s, long long limit) {
+    extern __shared__ __align__(16) unsigned char chain_sh[];
+    volatile T* xs = reinterpret_cast<T*>(chain_sh);
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) xs[t] = sentinel_of<T>();
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const GiveUpShared gu{&s->abort};
     for (int t = warp; t < nt; t += nw) {
         const int row = rows[cstart + t];
-        const double r0 = rhs[P[row]];
-        double val;
-        if (!trsv_row<true>(Fp[row], Fdiag[row], Fx, SrcChainL{Fj, Fpos, cstart, xs, y}, r0, 1.0, 4 * limit, gu,
-                            &val)) {
+        const T r0 = (T)rhs[P[row]];
+        T val;
+        if (!trsv_row<true>(Fp[row], Fdiag[row], Fx, SrcChainL<T>{Fj, Fpos, cstart, xs, y}, r0, T(1), 4 * limit,
+                            gu, &val)) {
             if (lane == 0) fail_row(s, row);
             return;
         }
         if (lane == 0) {
             xs[t] = val;
             y[row] = val;
-            xp[row] = sentinel();
+            xp[row] = sentinel_of<T>();
         }
         __syncwarp();
     }
 }
 
+template <typename T>
 struct SrcChainU {   // every dependency of a U-chain row is in the chain
     const int32_t* Fj;
     const int32_t* Fpos;
     int nt;
-    const volatile double* xs;
-    const double* xp;
-    __device__ const volatile double* operator()(int64_t p) const {
+    const volatile T* xs;
+    const T* xp;
+    __device__ const volatile T* operator()(int64_t p) const {
         const int t = __ldg(&Fpos[p]);
         return t < nt ? xs + t : xp + __ldg(&Fj[p]);
     }
 };
 
+template <typename T>
 __global__ void __launch_bounds__(1024)
 k_usolve_chain(int nt, const int32_t* __restrict__ rows, const int32_t* __restrict__ Fpos,
                const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj, const int64_t* __restrict__ Fdiag,
-               const double* __restrict__ Fx, const int32_t* __restrict__ Q, double* y, double* xp,
-               double* __restrict__ out, DevScal* s, long long limit) {
-    extern __shared__ double xs_dyn[];
-    volatile double* xs = xs_dyn;
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) xs[t] = sentinel();
+               const T* __restrict__ Fx, const int32_t* __restrict__ Q, T* y, T* xp, double* __restrict__ out,
+               DevScal* s, long long limit) {
+    extern __shared__ __align__(16) unsigned char chain_sh[];
+    volatile T* xs = reinterpret_cast<T*>(chain_sh);
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) xs[t] = sentinel_of<T>();
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const GiveUpShared gu{&s->abort};
     for (int t = warp; t < nt; t += nw) {
         const int row = rows[t];
         const int64_t d = Fdiag[row];
-        const double r0 = __ldcg(&y[row]);
-        const double rinv = __drcp_rn(__ldg(&Fx[d]));
+        const T r0 = __ldcg(&y[row]);
+        const T rinv = rcp_rn(__ldg(&Fx[d]));
         const int qrow = Q[row];
-        double val;
-        if (!trsv_row<false>(d + 1, Fp[row + 1], Fx, SrcChainU{Fj, Fpos, nt, xs, xp}, r0, rinv, 4 * limit, gu,
+        T val;
+        if (!trsv_row<false>(d + 1, Fp[row + 1], Fx, SrcChainU<T>{Fj, Fpos, nt, xs, xp}, r0, rinv, 4 * limit, gu,
                              &val)) {
             if (lane == 0) fail_row(s, row);
             return;
@@ -600,16 +627,17 @@ k_usolve_chain(int nt, const int32_t* __restrict__ rows, const int32_t* __restri
         if (lane == 0) {
             xs[t] = val;
             xp[row] = val;
-            y[row] = sentinel();
-            out[qrow] = val;
+            y[row] = sentinel_of<T>();
+            out[qrow] = (double)val;
         }
         __syncwarp();
     }
 }
 
+template <typename T>
 __global__ void k_usolve_bulk(int nrows, const int32_t* __restrict__ rows, const int64_t* __restrict__ Fp,
                               const int32_t* __restrict__ Fj, const int64_t* __restrict__ Fdiag,
-                              const double* __restrict__ Fx, const int32_t* __restrict__ Q, double* y, double* xp,
+                              const T* __restrict__ Fx, const int32_t* __restrict__ Q, T* y, T* xp,
                               double* __restrict__ out, DevScal* s, long long limit) {
     const int lane = threadIdx.x & 31;
     const GiveUpGlobal gu{&s->abort};
@@ -620,18 +648,18 @@ __global__ void k_usolve_bulk(int nrows, const int32_t* __restrict__ rows, const
         if (t >= nrows) return;
         const int row = rows[t];
         const int64_t d = Fdiag[row];
-        const double r0 = __ldcg(&y[row]);
-        const double rinv = __drcp_rn(__ldg(&Fx[d]));
+        const T r0 = __ldcg(&y[row]);
+        const T rinv = rcp_rn(__ldg(&Fx[d]));
         const int qrow = Q[row];
-        double val;
-        if (!trsv_row<false>(d + 1, Fp[row + 1], Fx, SrcGlobal{Fj, xp}, r0, rinv, limit, gu, &val)) {
+        T val;
+        if (!trsv_row<false>(d + 1, Fp[row + 1], Fx, SrcGlobal<T>{Fj, xp}, r0, rinv, limit, gu, &val)) {
             if (lane == 0) fail_row(s, row);
             return;
         }
         if (lane == 0) {
-            st_relaxed_f64(&xp[row], val);
-            y[row] = sentinel();
-            out[qrow] = val;
+            st_relaxed(&xp[row], val);
+            y[row] = sentinel_of<T>();
+            out[qrow] = (double)val;
         }
     }
 }
@@ -644,15 +672,18 @@ __global__ void k_usolve_bulk(int nrows, const int32_t* __restrict__ rows, const
 // global synchronisation.  List position t goes to warp g = t mod 32C of
 // the cluster; its value lives in that warp's block at slot
 // (t / 32C) * 32 + t mod 32.  Used when n values fit in the cluster.
+// L: reads the double right-hand side, writes y (type T); U: reads y,
+// writes the double result.
 namespace cgx = cooperative_groups;
 constexpr int CLUSTER_THREADS = 1024;
 
+template <typename T>
 struct SrcCluster {
     const int32_t* Fpos;
-    double* xs_local;
+    T* xs_local;
     int rank, sh, stride;
     cgx::cluster_group* cl;
-    __device__ const volatile double* operator()(int64_t p) const {
+    __device__ const volatile T* operator()(int64_t p) const {
         const int tj = __ldg(&Fpos[p]);
         const int owner = (tj & (stride - 1)) >> 5;
         const int slot = ((tj >> sh) << 5) + (tj & 31);
@@ -660,31 +691,32 @@ struct SrcCluster {
     }
 };
 
-template <bool LOWER>
+template <bool LOWER, typename T, typename TIN, typename TOUT>
 __global__ void __launch_bounds__(CLUSTER_THREADS)
 k_trsv_cluster(int n, const int32_t* __restrict__ list, const int32_t* __restrict__ Fpos,
-               const int64_t* __restrict__ Fp, const int64_t* __restrict__ Fdiag, const double* __restrict__ Fx,
-               const int32_t* __restrict__ perm, const double* __restrict__ rhs, double* __restrict__ out,
+               const int64_t* __restrict__ Fp, const int64_t* __restrict__ Fdiag, const T* __restrict__ Fx,
+               const int32_t* __restrict__ perm, const TIN* __restrict__ rhs, TOUT* __restrict__ out,
                DevScal* s, long long limit) {
-    extern __shared__ double xs_cl[];
+    extern __shared__ __align__(16) unsigned char cl_sh[];
+    T* xs_cl = reinterpret_cast<T*>(cl_sh);
     cgx::cluster_group cluster = cgx::this_cluster();
     const int C = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
     const int stride = 32 * C;                 // a power of two (C is 8 or 16)
     const int sh = 31 - __clz(stride);
     const int per_block = ((n + stride - 1) / stride) * 32;
-    for (int i = threadIdx.x; i < per_block; i += blockDim.x) xs_cl[i] = sentinel();
+    for (int i = threadIdx.x; i < per_block; i += blockDim.x) xs_cl[i] = sentinel_of<T>();
     cluster.sync();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const GiveUpGlobal gu{&s->abort};
-    const SrcCluster src{Fpos, xs_cl, rank, sh, stride, &cluster};
+    const SrcCluster<T> src{Fpos, xs_cl, rank, sh, stride, &cluster};
     for (int t = rank * 32 + warp; t < n; t += stride) {
         const int row = list[t];
         const int64_t d = Fdiag[row];
-        const double r0 = LOWER ? rhs[perm[row]] : rhs[row];
-        const double rinv = LOWER ? 1.0 : __drcp_rn(__ldg(&Fx[d]));
+        const T r0 = LOWER ? (T)rhs[perm[row]] : (T)rhs[row];
+        const T rinv = LOWER ? T(1) : rcp_rn(__ldg(&Fx[d]));
         const int orow = LOWER ? row : perm[row];
-        double val;
+        T val;
         const bool ok = LOWER ? trsv_row<true>(Fp[row], d, Fx, src, r0, rinv, limit, gu, &val)
                               : trsv_row<false>(d + 1, Fp[row + 1], Fx, src, r0, rinv, limit, gu, &val);
         if (!ok) {
@@ -692,8 +724,8 @@ k_trsv_cluster(int n, const int32_t* __restrict__ list, const int32_t* __restric
             break;
         }
         if (lane == 0) {
-            ((volatile double*)xs_cl)[((t >> sh) << 5) + warp] = val;
-            out[orow] = val;
+            ((volatile T*)xs_cl)[((t >> sh) << 5) + warp] = val;
+            out[orow] = (TOUT)val;
         }
         __syncwarp();
     }

@@ -34,8 +34,12 @@ struct kkt_ctx {
     int64_t dev_bytes = 0;
     int64_t *d_Fp = nullptr, *d_Fdiag = nullptr, *d_fsrc = nullptr, *d_asrc = nullptr;
     int32_t *d_Fj = nullptr, *d_Arp = nullptr, *d_Aci = nullptr, *d_P = nullptr, *d_Q = nullptr;
-    double *d_Fx = nullptr, *d_Ax = nullptr, *d_vals = nullptr;
-    double* d_rinv = nullptr;   // 1/u_ii of every row; tail rows publish it last
+    // factor values and pivot reciprocals in the factor type: double, or
+    // float with precision = KKT_PRECISION_MIXED
+    void* d_Fx = nullptr;
+    void* d_rinv = nullptr;     // 1/u_ii of every row; tail rows publish it last
+    double *d_Ax = nullptr, *d_vals = nullptr;
+    bool mixed = false;
     double *d_b = nullptr, *d_x = nullptr, *d_y = nullptr, *d_xp = nullptr, *d_r = nullptr, *d_w = nullptr;
     double *d_V = nullptr, *d_Z = nullptr, *d_part = nullptr;
     unsigned* d_done_f = nullptr;
@@ -209,8 +213,8 @@ int grid_for(const kkt_ctx* c, int rows) {
 }
 
 // Cluster solve: one cluster of `blocks` blocks runs the whole solve.
-template <bool LOWER>
-cudaError_t launch_cluster(kkt_ctx* c, const int32_t* perm, const double* rhs, double* out) {
+template <bool LOWER, typename T, typename TIN, typename TOUT>
+cudaError_t launch_cluster(kkt_ctx* c, const int32_t* perm, const TIN* rhs, TOUT* out) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c->cluster, 1, 1);
     cfg.blockDim = dim3(kkt::CLUSTER_THREADS, 1, 1);
@@ -223,25 +227,32 @@ cudaError_t launch_cluster(kkt_ctx* c, const int32_t* perm, const double* rhs, d
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kkt::k_trsv_cluster<LOWER>, c->A.n,
+    return cudaLaunchKernelEx(&cfg, kkt::k_trsv_cluster<LOWER, T, TIN, TOUT>, c->A.n,
                               (const int32_t*)(LOWER ? c->d_listL : c->d_listU), (const int32_t*)c->d_Fpos,
-                              (const int64_t*)c->d_Fp, (const int64_t*)c->d_Fdiag, (const double*)c->d_Fx, perm,
+                              (const int64_t*)c->d_Fp, (const int64_t*)c->d_Fdiag, (const T*)c->d_Fx, perm,
                               rhs, out, c->d_s, spin(c));
 }
 
 // Pick the cluster (16 blocks, else 8) whose shared memory holds all n
 // values and that the device can co-schedule; 0 if none.  16 blocks give
 // the sweep twice the FP64 pipes of 8 (measured faster on kkt2000).
+template <typename T>
+void cluster_attributes(int C) {
+    for (auto fn : {(const void*)kkt::k_trsv_cluster<true, T, double, T>,
+                    (const void*)kkt::k_trsv_cluster<false, T, T, double>}) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TAIL_SMEM_MAX);
+        if (C > 8) cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    }
+}
+
 int pick_cluster(kkt_ctx* c) {
     const int n = c->A.n;
+    const size_t vsize = c->mixed ? sizeof(float) : sizeof(double);
     for (int C : {16, 8}) {
         if (c->o.cluster_blocks && C != c->o.cluster_blocks) continue;
-        size_t per_block = (size_t)((n + 32 * C - 1) / (32 * C)) * 32 * sizeof(double);
+        size_t per_block = (size_t)((n + 32 * C - 1) / (32 * C)) * 32 * vsize;
         if (per_block > TAIL_SMEM_MAX) continue;
-        for (auto fn : {kkt::k_trsv_cluster<true>, kkt::k_trsv_cluster<false>}) {
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TAIL_SMEM_MAX);
-            if (C > 8) cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        }
+        if (c->mixed) cluster_attributes<float>(C); else cluster_attributes<double>(C);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(C, 1, 1);
         cfg.blockDim = dim3(kkt::CLUSTER_THREADS, 1, 1);
@@ -254,7 +265,9 @@ int pick_cluster(kkt_ctx* c) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int active = 0;
-        if (cudaOccupancyMaxActiveClusters(&active, kkt::k_trsv_cluster<true>, &cfg) != cudaSuccess) {
+        const void* probe = c->mixed ? (const void*)kkt::k_trsv_cluster<true, float, double, float>
+                                     : (const void*)kkt::k_trsv_cluster<true, double, double, double>;
+        if (cudaOccupancyMaxActiveClusters(&active, probe, &cfg) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
@@ -264,16 +277,21 @@ int pick_cluster(kkt_ctx* c) {
     return 0;
 }
 
-// x = Q U^{-1} L^{-1} P rhs: one cluster launch per triangle when the
-// values fit in a cluster's shared memory, else L bulk, L chain, U chain,
-// U bulk over the whole GPU.
-void lu_apply(kkt_ctx* c, const double* rhs, double* out) {
+// x = Q U^{-1} L^{-1} P rhs (double in, double out; the sweeps in the
+// factor type T): one cluster launch per triangle when the values fit in a
+// cluster's shared memory, else L bulk, L chain, U chain, U bulk over the
+// whole GPU.
+template <typename T>
+void lu_apply_t(kkt_ctx* c, const double* rhs, double* out) {
+    T* y = (T*)c->d_y;
+    T* xp = (T*)c->d_xp;
+    const T* Fx = (const T*)c->d_Fx;
     if (c->cluster) {
         int t = phase_begin(c, KKT_PHASE_LSOLVE);
-        launch_cluster<true>(c, c->d_P, rhs, c->d_y);
+        launch_cluster<true, T, double, T>(c, c->d_P, rhs, y);
         phase_end(c, t);
         t = phase_begin(c, KKT_PHASE_USOLVE);
-        launch_cluster<false>(c, c->d_Q, c->d_y, out);
+        launch_cluster<false, T, T, double>(c, c->d_Q, y, out);
         phase_end(c, t);
         c->launches += 2;
         return;
@@ -284,37 +302,45 @@ void lu_apply(kkt_ctx* c, const double* rhs, double* out) {
     c->launches += 1;
     int t = phase_begin(c, KKT_PHASE_LSOLVE);
     if (nLb) {
-        kkt::k_lsolve_bulk<<<grid_for(c, nLb), PERSIST_THREADS, 0, c->stream>>>(
-            nLb, c->d_listL, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_P, rhs, c->d_y, c->d_xp, c->d_s, spin(c));
+        kkt::k_lsolve_bulk<T><<<grid_for(c, nLb), PERSIST_THREADS, 0, c->stream>>>(
+            nLb, c->d_listL, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, c->d_P, rhs, y, xp, c->d_s, spin(c));
         c->launches += 1;
     }
     if (c->nLc) {
-        kkt::k_lsolve_chain<<<1, CHAIN_THREADS, sizeof(double) * c->nLc, c->stream>>>(
-            c->nLc, nLb, c->d_listL, c->d_Fpos, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_P, rhs, c->d_y, c->d_xp,
-            c->d_s, spin(c));
+        kkt::k_lsolve_chain<T><<<1, CHAIN_THREADS, sizeof(T) * c->nLc, c->stream>>>(
+            c->nLc, nLb, c->d_listL, c->d_Fpos, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, c->d_P, rhs, y, xp, c->d_s,
+            spin(c));
         c->launches += 1;
     }
     phase_end(c, t);
     t = phase_begin(c, KKT_PHASE_USOLVE);
     if (c->nUc) {
-        kkt::k_usolve_chain<<<1, CHAIN_THREADS, sizeof(double) * c->nUc, c->stream>>>(
-            c->nUc, c->d_listU, c->d_Fpos, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_Q, c->d_y, c->d_xp, out,
-            c->d_s, spin(c));
+        kkt::k_usolve_chain<T><<<1, CHAIN_THREADS, sizeof(T) * c->nUc, c->stream>>>(
+            c->nUc, c->d_listU, c->d_Fpos, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, c->d_Q, y, xp, out, c->d_s, spin(c));
         c->launches += 1;
     }
     if (nUb) {
-        kkt::k_usolve_bulk<<<grid_for(c, nUb), PERSIST_THREADS, 0, c->stream>>>(
-            nUb, c->d_listU + c->nUc, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_Q, c->d_y, c->d_xp, out, c->d_s,
-            spin(c));
+        kkt::k_usolve_bulk<T><<<grid_for(c, nUb), PERSIST_THREADS, 0, c->stream>>>(
+            nUb, c->d_listU + c->nUc, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, c->d_Q, y, xp, out, c->d_s, spin(c));
         c->launches += 1;
     }
     phase_end(c, t);
 }
 
+void lu_apply(kkt_ctx* c, const double* rhs, double* out) {
+    if (c->mixed) lu_apply_t<float>(c, rhs, out);
+    else lu_apply_t<double>(c, rhs, out);
+}
+
+void fill_y_sentinel(kkt_ctx* c) {
+    if (c->mixed) kkt::k_fill_sentinel<float><<<64, 256, 0, c->stream>>>((float*)c->d_y, c->A.n);
+    else kkt::k_fill_sentinel<double><<<64, 256, 0, c->stream>>>(c->d_y, c->A.n);
+}
+
 // After a failed solve some values may still be live: re-arm the L-solve's
 // vector so the next solve starts from sentinels everywhere.
 void rearm(kkt_ctx* c) {
-    kkt::k_fill_sentinel<<<64, 256, 0, c->stream>>>(c->d_y, c->A.n);
+    fill_y_sentinel(c);
     c->launches += 1;
     cudaStreamSynchronize(c->stream);
 }
@@ -371,7 +397,8 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
     *out = nullptr;
     kkt_ctx* c = new kkt_ctx();
     if (o) c->o = *o; else kkt_default_opts(&c->o);
-    if (c->o.restart < 1 || c->o.restart > kkt::MAXM || c->o.max_cycles < 0 || c->o.precision != 0 ||
+    if (c->o.restart < 1 || c->o.restart > kkt::MAXM || c->o.max_cycles < 0 ||
+        (c->o.precision != KKT_PRECISION_FP64 && c->o.precision != KKT_PRECISION_MIXED) ||
         (c->o.stop_mode != KKT_STOP_NRBE && c->o.stop_mode != KKT_STOP_RR) || c->o.pivot_tol <= 0 ||
         c->o.pivot_tol > 1 || c->o.boost_eps < 0 ||
         (c->o.trisolve != KKT_TRSV_AUTO && c->o.trisolve != KKT_TRSV_GLOBAL) || c->o.tail_rows < 0 ||
@@ -388,17 +415,22 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
         else { e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking); c->own_stream = true; }
     }
     if (e != cudaSuccess) { delete c; return KKT_ERR_CUDA; }
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kkt::k_lsolve_bulk, PERSIST_THREADS, 0);
-    int per_sm2 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kkt::k_refactor, PERSIST_THREADS, 0);
-    int per_sm3 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, kkt::k_usolve_bulk, PERSIST_THREADS, 0);
-    cudaFuncSetAttribute(kkt::k_lsolve_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(double) * CHAIN_MAX));
-    cudaFuncSetAttribute(kkt::k_usolve_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(double) * CHAIN_MAX));
-    cudaFuncSetAttribute(kkt::k_refactor_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TAIL_SMEM_MAX);
+    c->mixed = c->o.precision == KKT_PRECISION_MIXED;
+    int per_sm = 0, per_sm2 = 0, per_sm3 = 0;
+    if (c->mixed) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kkt::k_lsolve_bulk<float>, PERSIST_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kkt::k_refactor<float>, PERSIST_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, kkt::k_usolve_bulk<float>, PERSIST_THREADS, 0);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kkt::k_lsolve_bulk<double>, PERSIST_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kkt::k_refactor<double>, PERSIST_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, kkt::k_usolve_bulk<double>, PERSIST_THREADS, 0);
+    }
+    for (const void* fn : {(const void*)kkt::k_lsolve_chain<double>, (const void*)kkt::k_usolve_chain<double>,
+                           (const void*)kkt::k_lsolve_chain<float>, (const void*)kkt::k_usolve_chain<float>})
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * CHAIN_MAX));
+    for (const void* fn : {(const void*)kkt::k_refactor_tail<double>, (const void*)kkt::k_refactor_tail<float>})
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TAIL_SMEM_MAX);
     per_sm = std::max(1, std::min(per_sm, std::min(per_sm2, per_sm3)));
     c->persist_blocks = c->num_sms * per_sm;
     *out = c;
@@ -504,8 +536,19 @@ int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* col
     if ((rc = upload(c, &c->d_Aci, c->A.colind))) return rc;
     if ((rc = upload(c, &c->d_P, c->P))) return rc;
     if ((rc = upload(c, &c->d_Q, c->Q))) return rc;
-    if ((rc = dalloc(c, &c->d_Fx, nnzF))) return rc;
-    if ((rc = dalloc(c, &c->d_rinv, (size_t)n))) return rc;
+    if (c->mixed) {
+        float *fx = nullptr, *ri = nullptr;
+        if ((rc = dalloc(c, &fx, nnzF))) return rc;
+        if ((rc = dalloc(c, &ri, (size_t)n))) return rc;
+        c->d_Fx = fx;
+        c->d_rinv = ri;
+    } else {
+        double *fx = nullptr, *ri = nullptr;
+        if ((rc = dalloc(c, &fx, nnzF))) return rc;
+        if ((rc = dalloc(c, &ri, (size_t)n))) return rc;
+        c->d_Fx = fx;
+        c->d_rinv = ri;
+    }
     if ((rc = dalloc(c, &c->d_Ax, c->nnz_a))) return rc;
     if ((rc = dalloc(c, &c->d_vals, c->nnz_a))) return rc;
     for (double** p : {&c->d_b, &c->d_x, &c->d_y, &c->d_xp, &c->d_r, &c->d_w})
@@ -530,7 +573,7 @@ int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* col
         if ((rc = upload(c, &c->d_listU, listU))) return rc;
         if ((rc = upload(c, &c->d_Fpos, fpos))) return rc;
     }
-    kkt::k_fill_sentinel<<<64, 256, 0, c->stream>>>(c->d_y, n);
+    fill_y_sentinel(c);
     if (c->o.trisolve == KKT_TRSV_AUTO) pick_cluster(c);
     else c->cluster = 0;
     {   // refactorization tail: the last rows, if their longest row fits in shared memory
@@ -547,7 +590,8 @@ int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* col
             // shared memory: step descriptors, row values and columns, and a
             // position map for the last (at most TAIL_MAP_COLS) columns
             const int mlo = std::max(t0, n - TAIL_MAP_COLS);
-            size_t smem = 16 * (size_t)std::max<int64_t>(maxsteps, 1) + 12 * (size_t)maxlen +
+            const size_t vsize = c->mixed ? sizeof(float) : sizeof(double);
+            size_t smem = 16 * (size_t)std::max<int64_t>(maxsteps, 1) + (vsize + 4) * (size_t)maxlen +
                           2 * (size_t)(n - mlo);
             if (smem <= TAIL_SMEM_MAX && maxlen <= 32767) {
                 c->t0 = t0;
@@ -561,8 +605,9 @@ int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* col
         }
         if (c->t0 < n) {
             int per_sm = 0;
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kkt::k_refactor_tail, kkt::TAIL_THREADS,
-                                                             c->tail_smem));
+            const void* fn = c->mixed ? (const void*)kkt::k_refactor_tail<float>
+                                      : (const void*)kkt::k_refactor_tail<double>;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kkt::TAIL_THREADS, c->tail_smem));
             c->tail_blocks = std::max(1, per_sm) * c->num_sms;
         }
     }
@@ -615,6 +660,43 @@ int kkt_trace_refactor(kkt_ctx* c, const double* values, int values_on_device, i
     return rc;
 }
 
+extern "C++" {
+namespace {
+// gather, bulk rows (warp per row), tail rows (block per row), in type T
+template <typename T>
+void refactor_launch(kkt_ctx* c, const double* vals, unsigned long long* trace) {
+    const int n = c->A.n;
+    const int64_t nnzF = (int64_t)c->lay.Fj.size();
+    T* Fx = (T*)c->d_Fx;
+    T* rinv = (T*)c->d_rinv;
+    int t = phase_begin(c, KKT_PHASE_GATHER);
+    const int64_t tail_begin = c->t0 < n ? c->lay.Fp[c->t0] : nnzF;
+    kkt::k_gather<T><<<2 * c->num_sms, 256, 0, c->stream>>>(vals, c->d_fsrc, nnzF, tail_begin, Fx, c->d_Arp,
+                                                            c->d_asrc, c->d_Ax, n, c->t0, rinv, c->d_s);
+    phase_end(c, t);
+    t = phase_begin(c, KKT_PHASE_REFACTOR);
+    c->launches += 2;
+    if (c->t0 > 0) {
+        kkt::k_refactor<T><<<grid_for(c, c->t0), PERSIST_THREADS, 0, c->stream>>>(
+            c->t0, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, c->d_done_f, c->d_s, c->o.boost_eps, spin(c));
+        c->launches += 1;
+    }
+    phase_end(c, t);
+    t = phase_begin(c, KKT_PHASE_REFACTOR_TAIL);
+    if (c->t0 < n) {
+        // the bulk kernel left ticket_fact at >= t0; restart it for the tail
+        kkt::k_refactor_prep_tail<<<1, 1, 0, c->stream>>>(c->d_s);
+        const int blocks = std::min(n - c->t0, c->tail_blocks);
+        kkt::k_refactor_tail<T><<<blocks, kkt::TAIL_THREADS, c->tail_smem, c->stream>>>(
+            c->t0, n, c->tail_mlo, c->tail_max_steps, c->tail_max_len, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, vals,
+            c->d_fsrc, c->d_s, c->o.boost_eps, spin(c), trace);
+        c->launches += 2;
+    }
+    phase_end(c, t);
+}
+}  // namespace
+}  // extern "C++"
+
 namespace {
 int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsigned long long* trace) {
     int rc = check_ctx(c, false);
@@ -627,33 +709,9 @@ int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsign
         c->h2d += (int64_t)sizeof(double) * c->nnz_a;
         vals = c->d_vals;
     }
-    const int n = c->A.n;
-    const int64_t nnzF = (int64_t)c->lay.Fj.size();
     kkt::k_refactor_prep<<<1, 1, 0, c->stream>>>(c->d_s);
-    int t = phase_begin(c, KKT_PHASE_GATHER);
-    const int64_t tail_begin = c->t0 < n ? c->lay.Fp[c->t0] : nnzF;
-    kkt::k_gather<<<2 * c->num_sms, 256, 0, c->stream>>>(vals, c->d_fsrc, nnzF, tail_begin, c->d_Fx, c->d_Arp,
-                                                         c->d_asrc, c->d_Ax, n, c->t0, c->d_rinv, c->d_s);
-    phase_end(c, t);
-    t = phase_begin(c, KKT_PHASE_REFACTOR);
-    c->launches += 2;
-    if (c->t0 > 0) {
-        kkt::k_refactor<<<grid_for(c, c->t0), PERSIST_THREADS, 0, c->stream>>>(
-            c->t0, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_rinv, c->d_done_f, c->d_s, c->o.boost_eps, spin(c));
-        c->launches += 1;
-    }
-    phase_end(c, t);
-    t = phase_begin(c, KKT_PHASE_REFACTOR_TAIL);
-    if (c->t0 < n) {
-        // the bulk kernel left ticket_fact at >= t0; restart it for the tail
-        kkt::k_refactor_prep_tail<<<1, 1, 0, c->stream>>>(c->d_s);
-        const int blocks = std::min(n - c->t0, c->tail_blocks);
-        kkt::k_refactor_tail<<<blocks, kkt::TAIL_THREADS, c->tail_smem, c->stream>>>(
-            c->t0, n, c->tail_mlo, c->tail_max_steps, c->tail_max_len, c->d_Fp, c->d_Fj, c->d_Fdiag, c->d_Fx, c->d_rinv, vals, c->d_fsrc, c->d_s, c->o.boost_eps,
-            spin(c), trace);
-        c->launches += 2;
-    }
-    phase_end(c, t);
+    if (c->mixed) refactor_launch<float>(c, vals, trace);
+    else refactor_launch<double>(c, vals, trace);
     CK(cudaGetLastError());
     if ((rc = read_scalars(c))) return rc;
     c->nboost = c->h_s->nboost;
@@ -825,8 +883,15 @@ int kkt_get_factors(kkt_ctx* c, int64_t* Lp, int32_t* Li, double* Lx, int64_t* U
     const int n = c->A.n;
     const auto& L = c->lay;
     std::vector<double> fx(L.Fj.size());
-    CK(cudaMemcpyAsync(fx.data(), c->d_Fx, sizeof(double) * fx.size(), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    if (c->mixed) {
+        std::vector<float> f32(L.Fj.size());
+        CK(cudaMemcpyAsync(f32.data(), c->d_Fx, sizeof(float) * f32.size(), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (size_t i = 0; i < f32.size(); i++) fx[i] = (double)f32[i];
+    } else {
+        CK(cudaMemcpyAsync(fx.data(), c->d_Fx, sizeof(double) * fx.size(), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
     std::fill(Lp, Lp + n + 1, 0);
     std::fill(Up, Up + n + 1, 0);
     for (int32_t i = 0; i < n; i++) {
@@ -874,7 +939,7 @@ int kkt_selftest_wait(kkt_ctx* c, int64_t limit) {
     if (limit < 0) return KKT_ERR_INVALID;
     // d_w holds no live data between calls: arm one entry with SENTINEL as
     // the value nobody writes; done_f[0] can never hold the generation ~0u
-    kkt::k_fill_sentinel<<<1, 32, 0, c->stream>>>(c->d_w, 1);
+    kkt::k_fill_sentinel<double><<<1, 32, 0, c->stream>>>(c->d_w, 1);
     CK(cudaMemsetAsync(&c->d_s->err, 0, sizeof(int) * 3, c->stream));
     kkt::k_selftest_wait<<<1, 32, 0, c->stream>>>(c->d_s, c->d_w, c->d_done_f, (long long)limit);
     c->launches += 2;

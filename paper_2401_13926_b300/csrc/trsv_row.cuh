@@ -26,6 +26,7 @@
 namespace kkt {
 
 constexpr unsigned long long SENTINEL_BITS = 0x7ff4dead5ca1ab1eull;
+constexpr unsigned SENTINEL_BITS_F32 = 0x7fa5ca1eu;   // the FP32 (mixed precision) counterpart
 // late entries per row, tuned per sweep (L: 2, U: 4; swept 2..16 on kkt2000)
 constexpr int NLATE_L = 2;
 constexpr int NLATE_U = 4;
@@ -35,6 +36,16 @@ __device__ __forceinline__ double sentinel() { return __longlong_as_double((long
 __device__ __forceinline__ bool is_sentinel(double v) {
     return (unsigned long long)__double_as_longlong(v) == SENTINEL_BITS;
 }
+__device__ __forceinline__ bool is_sentinel(float v) { return __float_as_uint(v) == SENTINEL_BITS_F32; }
+
+// SENTINEL of the value type T (double for FP64 factors, float for FP32)
+template <typename T> __device__ __forceinline__ T sentinel_of();
+template <> __device__ __forceinline__ double sentinel_of<double>() { return sentinel(); }
+template <> __device__ __forceinline__ float sentinel_of<float>() { return __uint_as_float(SENTINEL_BITS_F32); }
+
+// correctly rounded reciprocal (same bits as 1/x)
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -44,9 +55,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Spin until *p is not SENTINEL.  `give_up()` is polled every 256 spins;
 // after `limit` spins the wait fails.  Returns false on failure.
-template <class GiveUp>
-__device__ __forceinline__ bool spin_value(const volatile double* p, double* v, long long limit, GiveUp give_up) {
-    double x = *v;
+template <typename T, class GiveUp>
+__device__ __forceinline__ bool spin_value(const volatile T* p, T* v, long long limit, GiveUp give_up) {
+    T x = *v;
     for (long long it = 0; is_sentinel(x); it++) {
         if ((it & 255) == 255 && give_up()) return false;
         if (it >= limit) return false;
@@ -64,9 +75,11 @@ __device__ __forceinline__ bool spin_value(const volatile double* p, double* v, 
 // most recent rows of the backward sweep); folded in descending order.
 // Returns the row's value in lane 0 (other lanes: unspecified) or false in
 // every lane if a wait failed.
-template <bool LOWER, class Src, class GiveUp>
-__device__ __forceinline__ bool trsv_row(int64_t lo, int64_t hi, const double* __restrict__ Fx, Src src,
-                                         double r0, double rinv, long long limit, GiveUp give_up, double* out) {
+// T is the value type of the factors and of the solve (double, or float in
+// mixed precision); the arithmetic is the same in both.
+template <bool LOWER, typename T, class Src, class GiveUp>
+__device__ __forceinline__ bool trsv_row(int64_t lo, int64_t hi, const T* __restrict__ Fx, Src src,
+                                         T r0, T rinv, long long limit, GiveUp give_up, T* out) {
     constexpr int NLATE = LOWER ? NLATE_L : NLATE_U;
     const int lane = threadIdx.x & 31;
     const int64_t len = hi - lo;
@@ -74,8 +87,8 @@ __device__ __forceinline__ bool trsv_row(int64_t lo, int64_t hi, const double* _
     const int64_t elo = LOWER ? lo : lo + nl;
     const int64_t ehi = LOWER ? hi - nl : hi;
     // lane 0 starts the loads of the late entries first
-    double la[NLATE], lv[NLATE];
-    const volatile double* ls[NLATE];
+    T la[NLATE], lv[NLATE];
+    const volatile T* ls[NLATE];
     if (lane == 0) {
 #pragma unroll
         for (int j = 0; j < NLATE; j++) {
@@ -88,10 +101,10 @@ __device__ __forceinline__ bool trsv_row(int64_t lo, int64_t hi, const double* _
         }
     }
     int ok = 1;
-    double acc = 0.0;
+    T acc = T(0);
     for (int64_t base = elo + lane; base < ehi && ok; base += 32 * ROW_BATCH) {
-        double a[ROW_BATCH], v[ROW_BATCH];
-        const volatile double* s[ROW_BATCH];
+        T a[ROW_BATCH], v[ROW_BATCH];
+        const volatile T* s[ROW_BATCH];
 #pragma unroll
         for (int u = 0; u < ROW_BATCH; u++) {
             const int64_t p = base + 32 * u;
@@ -117,7 +130,7 @@ __device__ __forceinline__ bool trsv_row(int64_t lo, int64_t hi, const double* _
         while (o < span) o <<= 1;
         for (o >>= 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     }
-    double r = r0 - acc;
+    T r = r0 - acc;
     if (lane == 0) {
 #pragma unroll
         for (int j = 0; j < NLATE; j++) {

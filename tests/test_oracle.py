@@ -331,3 +331,35 @@ def test_order_md_reduces_fill_on_kkt(oracle_mod):
     _, _, Fn = oracle_mod.lu(seq.n, seq.rowptr, seq.colind, v, Q=nat)
     _, _, Fm = oracle_mod.lu(seq.n, seq.rowptr, seq.colind, v)
     assert len(Fm.Li) + len(Fm.Ui) < 0.5 * (len(Fn.Li) + len(Fn.Ui))
+
+
+# ---------------------------------------------------------------- FP32 refactor
+def test_refactor_f32_close_to_fp64_and_is_an_lu(oracle_mod):
+    """FP32 refactorization (mixed precision): same pattern as FP64, values
+    within float rounding (times growth) of the FP64 factors, and L U equal to
+    the float-rounded matrix to float accuracy."""
+    seq = KKTSequence("kkt200", buses=20, steps=3)
+    P, Q, _ = oracle_mod.lu(seq.n, seq.rowptr, seq.colind, seq.values(0))
+    v = seq.values(2)
+    F64 = oracle_mod.refactor(seq.n, seq.rowptr, seq.colind, v, P, Q)
+    F32 = oracle_mod.refactor_f32(seq.n, seq.rowptr, seq.colind, v, P, Q)
+    assert np.array_equal(F64.Lp, F32.Lp) and np.array_equal(F64.Li, F32.Li)
+    assert np.array_equal(F64.Up, F32.Up) and np.array_equal(F64.Ui, F32.Ui)
+    # every value is exactly a float
+    assert np.all(F32.Lx.astype(np.float32).astype(np.float64) == F32.Lx)
+    assert np.all(F32.Ux.astype(np.float32).astype(np.float64) == F32.Ux)
+    A = dense(seq.n, seq.rowptr, seq.colind, v.astype(np.float32).astype(np.float64))
+    scale = np.abs(F32.dense_L()).max() * np.abs(F32.dense_U()).max()
+    assert np.abs(lu_product(F32, seq.n) - A[np.ix_(P, Q)]).max() <= 64 * 1.2e-7 * scale
+
+
+def test_refactor_f32_exact_on_small_integers(oracle_mod):
+    """A 3x3 case whose FP32 and exact factors coincide (all quantities exact
+    in float): the FP32 path must reproduce them exactly."""
+    A = np.array([[4.0, 2.0, 0.0], [2.0, 5.0, 1.0], [0.0, 1.0, 3.0]])
+    rp, ci, v = csr(A)
+    I = np.arange(3, dtype=np.int32)
+    F = oracle_mod.refactor_f32(3, rp, ci, v, I, I)
+    # l21 = 2/4 = 0.5, u22 = 5 - 0.5*2 = 4, l32 = 1/4, u33 = 3 - 0.25*1 = 2.75
+    assert np.array_equal(F.dense_L(), np.array([[1, 0, 0], [0.5, 1, 0], [0, 0.25, 1]]))
+    assert np.array_equal(F.dense_U(), np.array([[4, 2, 0], [0, 4, 1], [0, 0, 2.75]]))
