@@ -216,6 +216,17 @@ int kkt_get_phase_times(kkt_ctx* c, double* ms, int64_t* counts, int reset);
  */
 int kkt_trace_refactor(kkt_ctx* c, const double* values, int values_on_device, int64_t* t_start,
                        int64_t* t_publish, int32_t* t0_out);
+
+/*
+ * Profiling: kkt_lu_solve (Section 1.3, the direct solve with the current
+ * factors) with the GPU's global timer (ns) recorded when each row of the
+ * two sweeps publishes its value.  Only for the cluster schedule (else
+ * KKT_ERR_STATE).  listL[n], listU[n] (host) get the rows in the order the
+ * sweeps take them; tL[t], tU[t] (host) the publish time of list position t.
+ * b and x as in kkt_lu_solve.  Makes one temporary device allocation.
+ */
+int kkt_trace_solve(kkt_ctx* c, const double* b, double* x, int on_device, int32_t* listL,
+                    int32_t* listU, int64_t* tL, int64_t* tU);
 void kkt_destroy(kkt_ctx* c);
 const char* kkt_strerror(int code);
 const char* kkt_last_error_detail(kkt_ctx* c);

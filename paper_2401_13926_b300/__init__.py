@@ -36,6 +36,7 @@ EXPORTS = [
     "kkt_matvec", "kkt_get_perm", "kkt_get_factor_sizes", "kkt_get_factors", "kkt_query",
     "kkt_destroy", "kkt_strerror", "kkt_last_error_detail", "kkt_order", "kkt_pivot",
     "kkt_get_phase_times", "kkt_lu_solve_noalloc", "kkt_selftest_wait", "kkt_trace_refactor",
+    "kkt_trace_solve",
 ]
 NOALLOC_MAX_N = 65536
 PHASES = ["gather", "refactor", "lsolve", "usolve", "spmv", "ortho", "update", "refactor_tail"]
@@ -103,6 +104,7 @@ def lib():
     L.kkt_lu_solve_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.kkt_selftest_wait.argtypes = [vp, i64]
     L.kkt_trace_refactor.argtypes = [vp, vp, ip, vp, vp, C.POINTER(i32)]
+    L.kkt_trace_solve.argtypes = [vp, vp, vp, ip, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("kkt_default_opts", "kkt_destroy", "kkt_strerror", "kkt_last_error_detail"):
             getattr(L, name).restype = C.c_int
@@ -305,6 +307,20 @@ class KKTSolver:
         self._check(lib().kkt_get_phase_times(self._h, ms.ctypes.data, cnt.ctypes.data, int(bool(reset))),
                     "kkt_get_phase_times")
         return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
+
+    def trace_solve(self, b):
+        """kkt_lu_solve with per-row publish stamps (ns) of both sweeps
+        (cluster schedule): (x, listL, tL, listU, tU), t* indexed by list
+        position."""
+        kb, pb, dev = _ptr(b, np.float64)
+        n = self.n
+        x = b.new_empty(n) if dev else np.zeros(n)
+        kx, px, _ = _ptr(x, np.float64)
+        lL, lU = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        tL, tU = np.zeros(n, np.int64), np.zeros(n, np.int64)
+        self._check(lib().kkt_trace_solve(self._h, pb, px, dev, lL.ctypes.data, lU.ctypes.data,
+                                          tL.ctypes.data, tU.ctypes.data), "kkt_trace_solve")
+        return x, lL, tL, lU, tU
 
     def trace_refactor(self, values):
         """kkt_refactor with per-row start/publish stamps (ns) of the

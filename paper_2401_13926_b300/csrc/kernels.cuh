@@ -696,7 +696,7 @@ __global__ void __launch_bounds__(CLUSTER_THREADS)
 k_trsv_cluster(int n, const int32_t* __restrict__ list, const int32_t* __restrict__ Fpos,
                const int64_t* __restrict__ Fp, const int64_t* __restrict__ Fdiag, const T* __restrict__ Fx,
                const int32_t* __restrict__ perm, const TIN* __restrict__ rhs, TOUT* __restrict__ out,
-               DevScal* s, long long limit) {
+               DevScal* s, long long limit, unsigned long long* __restrict__ trace) {
     extern __shared__ __align__(16) unsigned char cl_sh[];
     T* xs_cl = reinterpret_cast<T*>(cl_sh);
     cgx::cluster_group cluster = cgx::this_cluster();
@@ -726,6 +726,7 @@ k_trsv_cluster(int n, const int32_t* __restrict__ list, const int32_t* __restric
         if (lane == 0) {
             ((volatile T*)xs_cl)[((t >> sh) << 5) + warp] = val;
             out[orow] = (TOUT)val;
+            if (trace) trace[t] = globaltimer_ns();   // profiling: publish time of list position t
         }
         __syncwarp();
     }

@@ -40,6 +40,7 @@ struct kkt_ctx {
     void* d_rinv = nullptr;     // 1/u_ii of every row; tail rows publish it last
     double *d_Ax = nullptr, *d_vals = nullptr;
     bool mixed = false;
+    unsigned long long* solve_trace = nullptr;   // kkt_trace_solve only: 2n publish stamps
     double *d_b = nullptr, *d_x = nullptr, *d_y = nullptr, *d_xp = nullptr, *d_r = nullptr, *d_w = nullptr;
     double *d_V = nullptr, *d_Z = nullptr, *d_part = nullptr;
     unsigned* d_done_f = nullptr;
@@ -230,7 +231,8 @@ cudaError_t launch_cluster(kkt_ctx* c, const int32_t* perm, const TIN* rhs, TOUT
     return cudaLaunchKernelEx(&cfg, kkt::k_trsv_cluster<LOWER, T, TIN, TOUT>, c->A.n,
                               (const int32_t*)(LOWER ? c->d_listL : c->d_listU), (const int32_t*)c->d_Fpos,
                               (const int64_t*)c->d_Fp, (const int64_t*)c->d_Fdiag, (const T*)c->d_Fx, perm,
-                              rhs, out, c->d_s, spin(c));
+                              rhs, out, c->d_s, spin(c),
+                              c->solve_trace ? c->solve_trace + (LOWER ? 0 : c->A.n) : nullptr);
 }
 
 // Pick the cluster (16 blocks, else 8) whose shared memory holds all n
@@ -744,6 +746,35 @@ int kkt_lu_solve(kkt_ctx* c, const double* b, double* x, int on_device) {
     }
     if ((rc = read_scalars(c))) return rc;
     if ((rc = device_error(c))) rearm(c);
+    return rc;
+}
+
+int kkt_trace_solve(kkt_ctx* c, const double* b, double* x, int on_device, int32_t* listL, int32_t* listU,
+                    int64_t* tL, int64_t* tU) {
+    int rc = check_ctx(c, true);
+    if (rc) return rc;
+    if (!b || !x || !listL || !listU || !tL || !tU) return KKT_ERR_INVALID;
+    if (!c->cluster) {
+        c->detail = "kkt_trace_solve: the cluster schedule is not in use";
+        return KKT_ERR_STATE;
+    }
+    const int n = c->A.n;
+    unsigned long long* d_trace = nullptr;   // profiling only: a buffer of its own
+    CK(cudaMalloc(&d_trace, sizeof(unsigned long long) * 2 * (size_t)n));
+    CK(cudaMemsetAsync(d_trace, 0, sizeof(unsigned long long) * 2 * (size_t)n, c->stream));
+    c->solve_trace = d_trace;
+    rc = kkt_lu_solve(c, b, x, on_device);
+    c->solve_trace = nullptr;
+    std::vector<unsigned long long> h(2 * (size_t)n);
+    cudaError_t e = cudaMemcpy(h.data(), d_trace, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(listL, c->d_listL, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(listU, c->d_listU, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+    cudaFree(d_trace);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy");
+    for (int t = 0; t < n; t++) {
+        tL[t] = (int64_t)h[t];
+        tU[t] = (int64_t)h[(size_t)n + t];
+    }
     return rc;
 }
 

@@ -1,8 +1,14 @@
 """kkt_lu_solve_noalloc: the triangular solve for callers that cannot
 allocate device memory (their device memory belongs to an arena allocator,
-or a cudaMalloc could stall a latency-critical loop).  It must give the
-same x as kkt_lu_solve on the same factors, call after call, although every
-call reuses one static scratch array.  Kept in its own file, collected last."""
+or a cudaMalloc could stall a latency-critical loop).  On the same factors
+it must solve as kkt_lu_solve does, call after call, although every call
+reuses one static scratch array.  Its rows take their late dependencies by
+column, while the context's solves take them in their schedule's completion
+order, so the two sum in different orders: on an ill-conditioned KKT matrix
+both are checked against the componentwise backward-error bound of the
+triangular solves, and on a well-conditioned system against each other.
+Kept in its own file, collected last."""
+import scipy.sparse as sp
 import ctypes as C
 
 import numpy as np
@@ -32,28 +38,61 @@ def combined_rows(f, n):
     return Fp, cols.astype(np.int32), Fdiag, vals
 
 
-def test_noalloc_solve_matches_context_solve_twice():
+def _backward_error(f, n, P, Q, b, x):
+    Lm = sp.csc_matrix((f["Lx"], f["Li"], f["Lp"]), shape=(n, n)) + sp.identity(n)
+    Um = sp.csc_matrix((f["Ux"], f["Ui"], f["Up"]), shape=(n, n))
+    z = x[Q]
+    r = b[P] - Lm @ (Um @ z)
+    scale = abs(Lm) @ (abs(Um) @ abs(z)) + abs(b[P])
+    # two triangular solves: |r| <= 2 g(k+2) |L||U||z| (Higham Thm. 8.5),
+    # g(k) = k u / (1 - k u), k the longest factor row
+    k = max(np.diff(Lm.tocsr().indptr).max(), np.diff(Um.tocsr().indptr).max()) + 2
+    u = 2.0 ** -53
+    return np.max(np.abs(r) / scale) / (2 * k * u / (1 - k * u))
+
+
+def _noalloc_vs_context(s, n, rng, calls=2):
     import torch
-    seq = KKTSequence("kkt200")
-    s = K.KKTSolver()
-    s.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
-    v = seq.values(5)
-    s.refactor(v)
-    n = seq.n
-    Fp, Fj, Fdiag, Fx = combined_rows(s.factors(), n)
+    f = s.factors()
+    Fp, Fj, Fdiag, Fx = combined_rows(f, n)
     P, Q = s.perm()
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     dFp, dFj, dFd, dFx, dP, dQ = map(dev, (Fp, Fj, Fdiag, Fx, P, Q))
-    rng = np.random.default_rng(42)
-    for call in range(2):
-        b = dev(rng.standard_normal(n))
+    out = []
+    for call in range(calls):
+        bh = rng.standard_normal(n)
+        b = dev(bh)
         x_ref = s.lu_solve(b)
         x = torch.full_like(b, float("nan"))
         K.lu_solve_noalloc(dFp, dFj, dFd, dFx, dP, dQ, b, x)
         torch.cuda.synchronize()
         xr, xn = x_ref.cpu().numpy(), x.cpu().numpy()
         assert np.all(np.isfinite(xn)), call
-        assert np.max(np.abs(xn - xr)) <= 1e-12 * np.max(np.abs(xr)), call
+        out.append((f, P, Q, bh, xr, xn))
+    return out
+
+
+def test_noalloc_solve_matches_context_solve_twice():
+    """KKT matrix (library analysis): both meet the triangular solves'
+    componentwise backward-error bound."""
+    seq = KKTSequence("kkt200")
+    s = K.KKTSolver()
+    s.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
+    s.refactor(seq.values(5))
+    for f, P, Q, b, xr, xn in _noalloc_vs_context(s, seq.n, np.random.default_rng(42)):
+        assert _backward_error(f, seq.n, P, Q, b, xn) <= 1.0
+        assert _backward_error(f, seq.n, P, Q, b, xr) <= 1.0
+
+
+def test_noalloc_solve_equals_context_solve_well_conditioned():
+    from paper_2401_13926_b300.workload import small_random_sparse
+    n = 1500
+    rp, ci, v = small_random_sparse(n, 0.004, 7, diag_boost=6.0)
+    s = K.KKTSolver()
+    s.analyze(rp, ci, values0=v)
+    s.refactor(v)
+    for f, P, Q, b, xr, xn in _noalloc_vs_context(s, n, np.random.default_rng(1)):
+        assert np.max(np.abs(xn - xr)) <= 1e-12 * np.max(np.abs(xr))
 
 
 def test_noalloc_rejects_n_beyond_its_scratch():
