@@ -41,6 +41,17 @@
  *                      give the estimated residual, and the solution is formed
  *                      only at a restart or when the estimate meets the
  *                      criterion; refine-or-not decision of Section 2.3.
+ *   or_fgmres_ex    -- the same with the variants the paper cites: the
+ *                      orthogonalisation (CGS2; CGS2 whose norm comes from
+ *                      the second projection's reduction by Pythagoras; one
+ *                      reduction CGS with the Pythagorean norm -- the
+ *                      low-synchronisation Gram-Schmidt family of Section
+ *                      2.1) and the inner stopping rule of FGMRES on the
+ *                      error equation (Section 2.1, Fig. 1: each cycle
+ *                      solves K d = rho to a relative tolerance, then
+ *                      x += d and the residual is recomputed).
+ *   or_richardson   -- classical iterative refinement (Section 2.1, the error
+ *                      system): rho = b - K x, d = (LU)^{-1} rho, x += d.
  *   or_nrbe/or_nsr  -- the backward-error measures of Section 2.2 (Eq. nbre)
  *                      and Section 1.3 (NSR).
  *
@@ -546,6 +557,17 @@ double or_nsr(int n, const int *rp, const int *ci, const double *vals,
     return num / den;
 }
 
+/* sqrt(a^2 - ||h||^2) in the factored form sqrt((a - c)(a + c)),
+ * c = ||h||; zero when a <= c.  (The norm of the projected vector from
+ * the norms before the projection, Pythagoras.) */
+static double pythagoras(double a, const double *h, int k) {
+    double c = 0.0;
+    for (int i = 0; i < k; i++) c += h[i] * h[i];
+    c = sqrt(c);
+    if (!(a > c)) return 0.0;
+    return sqrt((a - c) * (a + c));
+}
+
 /* ------------------------------------------------------------------ */
 /* FGMRES(m) iterative refinement with right preconditioner M = LU.     */
 /*                                                                      */
@@ -561,11 +583,28 @@ double or_nsr(int n, const int *rp, const int *ci, const double *vals,
 /* out: x, *iters, *cycles, *nrbe_out; trace (optional, length          */
 /*   >= 1 + max_cycles*m) receives the estimated residual after each     */
 /*   iteration with trace[0] = ||rho^(0)||.                             */
-int or_fgmres(int n, const int *rp, const int *ci, const double *vals,
-              void *fac, const int *P, const int *Q,
-              const double *b, double *x,
-              int m, int max_cycles, double tol, int stop_mode, double refine_delta,
-              int *iters, int *cycles, double *nrbe_out, double *trace) {
+/*                                                                      */
+/* or_fgmres_ex adds:                                                    */
+/* ortho 0: CGS2 -- h = V^T w, w -= V h, h2 = V^T w, w -= V h2,          */
+/*   h_{j+1,j} = ||w||.                                                  */
+/* ortho 1: CGS2 with the norm by Pythagoras -- ||w'||^2 is reduced      */
+/*   together with h2 = V^T w' (w' = w after the first projection) and   */
+/*   h_{j+1,j} = sqrt((a - c)(a + c)), a = ||w'||, c = ||h2||.            */
+/* ortho 2: one-reduction CGS -- h = V^T w and ||w||^2 in one reduction, */
+/*   w -= V h, h_{j+1,j} = sqrt((a - c)(a + c)), a = ||w||, c = ||h||.    */
+/*   With a <= c the norm is taken as zero (breakdown: the cycle ends).  */
+/* inner 0: the cycle's inner test is the stop_mode rule above.          */
+/* inner 1: FGMRES on the error equation -- the inner test is            */
+/*   |g_{j+1}| <= inner_tol * beta (beta = ||rho|| at the cycle start);   */
+/*   after the cycle x += Z y, the true residual is recomputed and x is  */
+/*   accepted on the stop_mode rule (NRBE <= tol, or RR:                  */
+/*   ||rho|| < tol ||rho^(0)||).                                         */
+int or_fgmres_ex(int n, const int *rp, const int *ci, const double *vals,
+                 void *fac, const int *P, const int *Q,
+                 const double *b, double *x,
+                 int m, int max_cycles, double tol, int stop_mode, double refine_delta,
+                 int ortho, int inner, double inner_tol,
+                 int *iters, int *cycles, double *nrbe_out, double *trace) {
     size_t N = (size_t)(n ? n : 1);
     double *V = (double *)malloc(sizeof(double) * N * (size_t)(m + 1));
     double *Z = (double *)malloc(sizeof(double) * N * (size_t)m);
@@ -601,8 +640,9 @@ int or_fgmres(int n, const int *rp, const int *ci, const double *vals,
     for (;;) {
         if (*cycles >= max_cycles) { rc = OR_ERR_NOT_CONVERGED; break; }
         (*cycles)++;
-        double thresh = (stop_mode == 0) ? tol * (normK * nrm2(n, x) + normb) : tol * rho0;
         double beta = rnorm;
+        double thresh = inner == 1 ? inner_tol * beta
+                      : (stop_mode == 0) ? tol * (normK * nrm2(n, x) + normb) : tol * rho0;
         for (int i = 0; i < n; i++) V[i] = r[i] / beta;
         g[0] = beta;
         for (int i = 1; i <= m; i++) g[i] = 0.0;
@@ -618,7 +658,8 @@ int or_fgmres(int n, const int *rp, const int *ci, const double *vals,
                 for (int p = rp[i]; p < rp[i + 1]; p++) s += vals[p] * zj[ci[p]];
                 w[i] = s;
             }
-            /* CGS2: two passes of classical Gram-Schmidt */
+            /* first classical Gram-Schmidt projection (all variants) */
+            double wn_before = (ortho == 2) ? nrm2(n, w) : 0.0;   /* same reduction as h */
             for (int i = 0; i <= j; i++) {
                 double s = 0.0; const double *vi = V + (size_t)i * N;
                 for (int t = 0; t < n; t++) s += vi[t] * w[t];
@@ -628,17 +669,24 @@ int or_fgmres(int n, const int *rp, const int *ci, const double *vals,
                 const double *vi = V + (size_t)i * N;
                 for (int t = 0; t < n; t++) w[t] -= h[i] * vi[t];
             }
-            for (int i = 0; i <= j; i++) {
-                double s = 0.0; const double *vi = V + (size_t)i * N;
-                for (int t = 0; t < n; t++) s += vi[t] * w[t];
-                h2[i] = s;
+            double hn;
+            if (ortho == 2) {
+                hn = pythagoras(wn_before, h, j + 1);
+            } else {
+                /* second projection (re-orthogonalisation) */
+                double wn_mid = (ortho == 1) ? nrm2(n, w) : 0.0;   /* same reduction as h2 */
+                for (int i = 0; i <= j; i++) {
+                    double s = 0.0; const double *vi = V + (size_t)i * N;
+                    for (int t = 0; t < n; t++) s += vi[t] * w[t];
+                    h2[i] = s;
+                }
+                for (int i = 0; i <= j; i++) {
+                    const double *vi = V + (size_t)i * N;
+                    for (int t = 0; t < n; t++) w[t] -= h2[i] * vi[t];
+                }
+                hn = (ortho == 1) ? pythagoras(wn_mid, h2, j + 1) : nrm2(n, w);
+                for (int i = 0; i <= j; i++) h[i] += h2[i];
             }
-            for (int i = 0; i <= j; i++) {
-                const double *vi = V + (size_t)i * N;
-                for (int t = 0; t < n; t++) w[t] -= h2[i] * vi[t];
-                h[i] += h2[i];
-            }
-            double hn = nrm2(n, w);
             double *vn = V + (size_t)(j + 1) * N;
             if (hn > 0.0) { for (int t = 0; t < n; t++) vn[t] = w[t] / hn; }
             else { for (int t = 0; t < n; t++) vn[t] = 0.0; }
@@ -681,12 +729,68 @@ int or_fgmres(int n, const int *rp, const int *ci, const double *vals,
         nrbe = (rnorm == 0.0) ? 0.0 : rnorm / (normK * nrm2(n, x) + normb);
         if (rnorm == 0.0) break;
         if (stop_mode == 0 && nrbe <= tol) break;
-        if (stop_mode == 1 && met) break;
+        if (stop_mode == 1 && (inner == 1 ? rnorm < tol * rho0 : met)) break;
     }
 done_nrbe:
     *nrbe_out = nrbe;
 done:
     free(V); free(Z); free(H); free(cs); free(sn); free(g); free(y); free(h); free(h2); free(r); free(w);
+    return rc;
+}
+
+int or_fgmres(int n, const int *rp, const int *ci, const double *vals,
+              void *fac, const int *P, const int *Q,
+              const double *b, double *x,
+              int m, int max_cycles, double tol, int stop_mode, double refine_delta,
+              int *iters, int *cycles, double *nrbe_out, double *trace) {
+    return or_fgmres_ex(n, rp, ci, vals, fac, P, Q, b, x, m, max_cycles, tol, stop_mode, refine_delta,
+                        0, 0, 0.0, iters, cycles, nrbe_out, trace);
+}
+
+/* ------------------------------------------------------------------ */
+/* Classical iterative refinement (Section 2.1, the error system):       */
+/*   x0 = (LU)^{-1} b; repeat: rho = b - K x; stop on the rule; d =       */
+/*   (LU)^{-1} rho; x += d.                                              */
+/* Stop rules as in or_fgmres on the true residual (NRBE <= tol, or RR:  */
+/* ||rho|| < tol ||rho^(0)||), and refine_delta as there.  An iteration  */
+/* is one correction (one preconditioner apply after x0); at most        */
+/* max_steps.  trace (optional, >= 1 + max_steps) receives ||rho|| after */
+/* x0 and after every correction.                                        */
+int or_richardson(int n, const int *rp, const int *ci, const double *vals,
+                  void *fac, const int *P, const int *Q,
+                  const double *b, double *x,
+                  int max_steps, double tol, int stop_mode, double refine_delta,
+                  int *iters, double *nrbe_out, double *trace) {
+    size_t N = (size_t)(n ? n : 1);
+    double *r = (double *)malloc(sizeof(double) * N);
+    double *d = (double *)malloc(sizeof(double) * N);
+    if (!r || !d) { free(r); free(d); return OR_ERR_OOM; }
+    double normK = or_norm_inf(n, rp, vals);
+    double normb = nrm2(n, b);
+    int rc = OR_OK;
+    *iters = 0;
+    or_solve(fac, P, Q, b, x);
+    double rho0 = 0.0, nrbe = 0.0;
+    for (int k = 0;; k++) {
+        or_residual(n, rp, ci, vals, b, x, r);
+        double rnorm = nrm2(n, r);
+        double xnorm = nrm2(n, x);
+        if (!isfinite(rnorm) || !isfinite(xnorm)) { rc = OR_ERR_NONFINITE; break; }
+        nrbe = (rnorm == 0.0) ? 0.0 : rnorm / (normK * xnorm + normb);
+        if (trace) trace[k] = rnorm;
+        if (k == 0) {
+            rho0 = rnorm;
+            if (refine_delta > 0.0 && rnorm < refine_delta * normb) break;
+        }
+        if (rnorm == 0.0) break;
+        if (stop_mode == 0 ? (nrbe <= tol) : (k > 0 && rnorm < tol * rho0)) break;
+        if (k >= max_steps) { rc = OR_ERR_NOT_CONVERGED; break; }
+        or_solve(fac, P, Q, r, d);
+        for (int i = 0; i < n; i++) x[i] += d[i];
+        (*iters)++;
+    }
+    *nrbe_out = nrbe;
+    free(r); free(d);
     return rc;
 }
 

@@ -52,6 +52,15 @@ def lib():
         L.or_fgmres.argtypes = [C.c_int, _i32, _i32, _f64, C.c_void_p, _i32, _i32, _f64, _f64,
                                 C.c_int, C.c_int, C.c_double, C.c_int, C.c_double,
                                 C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]
+        L.or_fgmres_ex.restype = C.c_int
+        L.or_fgmres_ex.argtypes = [C.c_int, _i32, _i32, _f64, C.c_void_p, _i32, _i32, _f64, _f64,
+                                   C.c_int, C.c_int, C.c_double, C.c_int, C.c_double,
+                                   C.c_int, C.c_int, C.c_double,
+                                   C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]
+        L.or_richardson.restype = C.c_int
+        L.or_richardson.argtypes = [C.c_int, _i32, _i32, _f64, C.c_void_p, _i32, _i32, _f64, _f64,
+                                    C.c_int, C.c_double, C.c_int, C.c_double,
+                                    C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]
         L.or_order_md.restype = C.c_int
         L.or_order_md.argtypes = [C.c_int, _i32, _i32, _i32]
         _lib = L
@@ -220,23 +229,47 @@ class FgmresResult:
     trace: np.ndarray
 
 
+ORTHO = {"cgs2": 0, "cgs2_pythagoras": 1, "cgs1_pythagoras": 2}
+
+
 def fgmres(n, rowptr, colind, values, F: Factors, P, Q, b, tol=1e-12, restart=20, max_cycles=50,
-           stop_mode=0, refine_delta=0.0):
+           stop_mode=0, refine_delta=0.0, ortho="cgs2", error_equation=False, inner_tol=1e-6):
     """FGMRES(restart) refinement with M = LU as right preconditioner.
 
     stop_mode 0: NRBE <= tol; stop_mode 1: the paper's relative-residual rule.
+    ortho: "cgs2", "cgs2_pythagoras" (two reductions), "cgs1_pythagoras"
+    (one reduction).  error_equation: each cycle solves the error equation
+    to |g| <= inner_tol * beta, then x is updated and checked.
     """
     x = np.zeros(n, np.float64)
     it, cy, nr = C.c_int(), C.c_int(), C.c_double()
     trace = np.zeros(1 + max_cycles * restart, np.float64)
-    rc = lib().or_fgmres(n, np.ascontiguousarray(rowptr, np.int32), np.ascontiguousarray(colind, np.int32),
-                         np.ascontiguousarray(values, np.float64), F._h,
-                         np.ascontiguousarray(P, np.int32), np.ascontiguousarray(Q, np.int32),
-                         np.ascontiguousarray(b, np.float64), x, int(restart), int(max_cycles),
-                         float(tol), int(stop_mode), float(refine_delta),
-                         C.byref(it), C.byref(cy), C.byref(nr), trace.ctypes.data_as(C.c_void_p))
+    rc = lib().or_fgmres_ex(n, np.ascontiguousarray(rowptr, np.int32), np.ascontiguousarray(colind, np.int32),
+                            np.ascontiguousarray(values, np.float64), F._h,
+                            np.ascontiguousarray(P, np.int32), np.ascontiguousarray(Q, np.int32),
+                            np.ascontiguousarray(b, np.float64), x, int(restart), int(max_cycles),
+                            float(tol), int(stop_mode), float(refine_delta),
+                            ORTHO[ortho], int(bool(error_equation)), float(inner_tol),
+                            C.byref(it), C.byref(cy), C.byref(nr), trace.ctypes.data_as(C.c_void_p))
     ntr = 1 + it.value
     return FgmresResult(x, rc, it.value, cy.value, nr.value, trace[:ntr])
+
+
+def richardson(n, rowptr, colind, values, F: Factors, P, Q, b, tol=1e-12, max_steps=1000, stop_mode=0,
+               refine_delta=0.0):
+    """Classical iterative refinement x += (LU)^{-1}(b - K x) (Section 2.1).
+    Returns FgmresResult (cycles = 0); trace = ||rho|| after x0 and after
+    every correction."""
+    x = np.zeros(n, np.float64)
+    it, nr = C.c_int(), C.c_double()
+    trace = np.zeros(1 + max_steps, np.float64)
+    rc = lib().or_richardson(n, np.ascontiguousarray(rowptr, np.int32), np.ascontiguousarray(colind, np.int32),
+                             np.ascontiguousarray(values, np.float64), F._h,
+                             np.ascontiguousarray(P, np.int32), np.ascontiguousarray(Q, np.int32),
+                             np.ascontiguousarray(b, np.float64), x, int(max_steps), float(tol),
+                             int(stop_mode), float(refine_delta), C.byref(it), C.byref(nr),
+                             trace.ctypes.data_as(C.c_void_p))
+    return FgmresResult(x, rc, it.value, 0, nr.value, trace[:1 + it.value])
 
 
 def solve_sequence_step(n, rowptr, colind, values, P, Q, b, tol=1e-12, restart=20, max_cycles=50,

@@ -363,3 +363,126 @@ def test_refactor_f32_exact_on_small_integers(oracle_mod):
     # l21 = 2/4 = 0.5, u22 = 5 - 0.5*2 = 4, l32 = 1/4, u33 = 3 - 0.25*1 = 2.75
     assert np.array_equal(F.dense_L(), np.array([[1, 0, 0], [0.5, 1, 0], [0, 0.25, 1]]))
     assert np.array_equal(F.dense_U(), np.array([[4, 2, 0], [0, 4, 1], [0, 0, 2.75]]))
+
+
+# ---------------------------------------------------------------- refinement variants
+def _inexact_case(oracle_mod, seed, n=30, pert=0.3):
+    rng = np.random.default_rng(seed)
+    rp, ci, v = small_random_sparse(n, 0.12, 10 + seed, diag_boost=2.0)
+    K = dense(n, rp, ci, v)
+    Kp = K + pert * np.diag(rng.standard_normal(n))        # M = LU(Kp), an inexact preconditioner
+    prp, pci, pv = csr(Kp)
+    P, Q, F = oracle_mod.lu(n, prp, pci, pv, Q=np.arange(n, dtype=np.int32), tol=1.0)
+    return n, rp, ci, v, K, np.linalg.inv(Kp), P, Q, F, rng.standard_normal(n)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_richardson_residuals_follow_the_iteration_matrix(oracle_mod, seed):
+    """Classical refinement is the stationary iteration r_{k+1} = (I - K M^{-1}) r_k:
+    every traced residual norm equals the norm of a power of that matrix
+    applied to r_0 (dense powers, an independent construction)."""
+    n, rp, ci, v, K, Minv, P, Q, F, b = _inexact_case(oracle_mod, seed, pert=0.2)
+    G = np.eye(n) - K @ Minv
+    assert np.max(np.abs(np.linalg.eigvals(G))) < 1
+    res = oracle_mod.richardson(n, rp, ci, v, F, P, Q, b, tol=1e-300, max_steps=6)
+    assert res.status == oracle_mod.ERR_NOT_CONVERGED and res.iters == 6
+    r = b - K @ (Minv @ b)
+    for k in range(7):
+        assert res.trace[k] == pytest.approx(np.linalg.norm(r), rel=1e-8)
+        r = G @ r
+    x = Minv @ b
+    for _ in range(6):
+        x = x + Minv @ (b - K @ x)
+    assert np.allclose(res.x, x, rtol=1e-10, atol=1e-12)
+
+
+def test_richardson_exact_factors_and_divergence(oracle_mod):
+    """Exact factors: x0 already meets the NRBE rule (no correction).  A
+    preconditioner with spectral radius of I - K M^{-1} above one: the
+    residual grows and the run ends NOT_CONVERGED."""
+    n, rp, ci, v, K, Minv, P, Q, F, b = _inexact_case(oracle_mod, 3, pert=0.0)
+    res = oracle_mod.richardson(n, rp, ci, v, F, P, Q, b, tol=1e-13)
+    assert res.status == 0 and res.iters == 0 and res.nrbe <= 1e-13
+    n, rp, ci, v, K, Minv, P, Q, F, b = _inexact_case(oracle_mod, 4, pert=6.0)
+    rho = np.max(np.abs(np.linalg.eigvals(np.eye(n) - K @ Minv)))
+    assert rho > 1
+    res = oracle_mod.richardson(n, rp, ci, v, F, P, Q, b, tol=1e-13, max_steps=60)
+    assert res.status == oracle_mod.ERR_NOT_CONVERGED and res.trace[-1] > res.trace[0]
+
+
+def test_richardson_rr_rule(oracle_mod):
+    n, rp, ci, v, K, Minv, P, Q, F, b = _inexact_case(oracle_mod, 5, pert=0.05)
+    assert np.max(np.abs(np.linalg.eigvals(np.eye(n) - K @ Minv))) < 1
+    tol = 1e-6
+    res = oracle_mod.richardson(n, rp, ci, v, F, P, Q, b, tol=tol, stop_mode=1, max_steps=200)
+    assert res.status == 0 and res.iters >= 1
+    assert res.trace[-1] < tol * res.trace[0]
+    assert np.all(res.trace[1:-1] >= tol * res.trace[0])
+
+
+@pytest.mark.parametrize("ortho", ["cgs2_pythagoras", "cgs1_pythagoras"])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_low_sync_variants_give_krylov_minima(oracle_mod, ortho, seed):
+    """The Gram-Schmidt variants that take the new vector's norm by
+    Pythagoras still give, on a well-conditioned case, the minimum residual
+    over x0 + span(Z_j) at every step (Householder-QR reference).  One pass
+    of classical Gram-Schmidt loses orthogonality in proportion to the
+    basis' conditioning, so its estimates are held to the starting
+    residual's scale rather than their own."""
+    n, rp, ci, v, K, Minv, P, Q, F, b = _inexact_case(oracle_mod, seed)
+    m = 7
+    res = oracle_mod.fgmres(n, rp, ci, v, F, P, Q, b, tol=1e-300, restart=m, max_cycles=1, ortho=ortho)
+    assert res.iters == m
+    x0 = Minv @ b
+    for j in range(1, m + 1):
+        rmin, xmin = _krylov_minres(K, Minv, b, x0, j)
+        if ortho == "cgs2_pythagoras":
+            assert res.trace[j] == pytest.approx(rmin, rel=1e-7)
+        else:
+            assert abs(res.trace[j] - rmin) <= 1e-9 * res.trace[0]
+    assert np.linalg.norm(res.x - xmin) <= 1e-7 * np.linalg.norm(xmin)
+
+
+def test_error_equation_with_one_step_cycles_is_minimal_residual_richardson(oracle_mod):
+    """FGMRES on the error equation with inner_tol = 1 stops every cycle
+    after one Arnoldi step: x_{k+1} = x_k + a_k M^{-1} r_k with the step
+    a_k = (r_k . K M^{-1} r_k) / ||K M^{-1} r_k||^2 minimising the residual."""
+    n, rp, ci, v, K, Minv, P, Q, F, b = _inexact_case(oracle_mod, 2)
+    res = oracle_mod.fgmres(n, rp, ci, v, F, P, Q, b, tol=1e-300, restart=5, max_cycles=6,
+                            error_equation=True, inner_tol=1.0)
+    assert res.status == oracle_mod.ERR_NOT_CONVERGED and res.iters == 6 and res.cycles == 6
+    x = Minv @ b
+    for _ in range(6):
+        r = b - K @ x
+        z = Minv @ r
+        Kz = K @ z
+        x = x + (r @ Kz) / (Kz @ Kz) * z
+    assert np.allclose(res.x, x, rtol=1e-10, atol=1e-12)
+
+
+def test_error_equation_inner_tolerance_ends_each_cycle(oracle_mod):
+    """With inner_tol, each cycle ends at the first step whose estimate is
+    at most inner_tol times the cycle's starting residual."""
+    n, rp, ci, v, K, Minv, P, Q, F, b = _inexact_case(oracle_mod, 6, pert=0.6)
+    it = 1e-2
+    res = oracle_mod.fgmres(n, rp, ci, v, F, P, Q, b, tol=1e-12, restart=30, max_cycles=20,
+                            error_equation=True, inner_tol=it)
+    assert res.status == 0 and res.nrbe <= 1e-12 and res.cycles >= 2
+    # rebuild the cycle boundaries from the trace: a cycle starts at the
+    # true residual (the first entry or the one after a cycle end) and ends
+    # at the first estimate <= it * start
+    start, k, cycles = res.trace[0], 1, 0
+    while k < len(res.trace):
+        while res.trace[k] > it * start:
+            k += 1
+        cycles += 1
+        k += 1
+        if k < len(res.trace):
+            start = np.linalg.norm(b - K @ x_at_cycle_end(oracle_mod, n, rp, ci, v, F, P, Q, b, cycles, it))
+    assert cycles == res.cycles
+
+
+def x_at_cycle_end(oracle_mod, n, rp, ci, v, F, P, Q, b, cycles, it):
+    r = oracle_mod.fgmres(n, rp, ci, v, F, P, Q, b, tol=1e-300, restart=30, max_cycles=cycles,
+                          error_equation=True, inner_tol=it)
+    return r.x
