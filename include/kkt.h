@@ -70,7 +70,7 @@ extern "C" {
 typedef struct kkt_ctx kkt_ctx;
 
 typedef struct {
-    int restart;          /* FGMRES restart length m (default 20, 1..64) */
+    int restart;          /* FGMRES restart length m (default 20, 1..32) */
     int max_cycles;       /* restart cycles before KKT_ERR_NOT_CONVERGED (default 50) */
     int stop_mode;        /* KKT_STOP_NRBE (default) or KKT_STOP_RR */
     int precision;        /* KKT_PRECISION_FP64 (default) or KKT_PRECISION_MIXED */
@@ -91,7 +91,40 @@ typedef struct {
     int tail_rows;        /* rows refactored one block per row at the end of the order
                              (0 = default 32767, the most; fewer if a row does not fit
                              in shared memory) */
+    int method;           /* refinement after x0 = (LU)^{-1} b: KKT_METHOD_FGMRES (default),
+                             KKT_METHOD_RICHARDSON, KKT_METHOD_FGMRES_EE */
+    int ortho;            /* Arnoldi orthogonalisation: KKT_ORTHO_CGS2 (default),
+                             KKT_ORTHO_CGS2_PYTH, KKT_ORTHO_CGS1_PYTH */
+    double inner_tol;     /* KKT_METHOD_FGMRES_EE: a cycle ends when its estimated residual
+                             is <= inner_tol times the residual at the cycle start
+                             (default 1e-6) */
+    int repivot;          /* 1: when kkt_refactor meets a zero pivot, or kkt_solve does not
+                             converge, re-run the pivoting factorization on the current
+                             values (Q kept; kkt_repivot) and retry once; 0 = off (default) */
 } kkt_opts;
+
+/* Refinement methods (Section 2.1).  FGMRES: FGMRES(m) with M = LU as right
+   preconditioner from x0, restarted until the stopping rule holds (the
+   paper's method).  RICHARDSON: classical iterative refinement on the error
+   system, x += (LU)^{-1}(b - K x), at most max_cycles * restart corrections
+   (an iteration is one correction).  FGMRES_EE: FGMRES on the error
+   equation -- each cycle solves K d = rho to the relative tolerance
+   inner_tol, then x += d and the true residual decides (an outer
+   refinement step per cycle). */
+#define KKT_METHOD_FGMRES 0
+#define KKT_METHOD_RICHARDSON 1
+#define KKT_METHOD_FGMRES_EE 2
+
+/* Gram-Schmidt in the Arnoldi step.  CGS2: two classical projections and a
+   norm -- three reductions.  CGS2_PYTH: the norm is reduced together with
+   the second projection's dot products and taken by Pythagoras,
+   sqrt((a - c)(a + c)) with a = ||w'||, c = ||h2|| -- two reductions.
+   CGS1_PYTH: one projection, its dot products and ||w|| in one reduction,
+   the norm by Pythagoras -- one reduction (the low-synchronisation end of
+   the family; loses orthogonality with the basis' conditioning). */
+#define KKT_ORTHO_CGS2 0
+#define KKT_ORTHO_CGS2_PYTH 1
+#define KKT_ORTHO_CGS1_PYTH 2
 
 /* KKT_TRSV_AUTO: one thread-block cluster per triangle when the n solved
    values fit in its shared memory, else KKT_TRSV_GLOBAL: sync-free over the
@@ -130,6 +163,7 @@ typedef struct {
     int64_t launches;      /* kernels this context has launched so far */
     int64_t h2d_bytes;     /* host->device bytes copied by refactor/solve calls so far */
     int64_t d2h_bytes;     /* device->host bytes copied by refactor/solve calls so far */
+    int32_t repivots;      /* pivoting refactorizations run by kkt_repivot so far */
 } kkt_info;
 
 /* Fill *o with the defaults above. */
@@ -162,6 +196,20 @@ int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* col
  * Errors: KKT_ERR_ZERO_PIVOT, KKT_ERR_NONFINITE, KKT_ERR_TIMEOUT.
  */
 int kkt_refactor(kkt_ctx* c, const double* values, int values_on_device);
+
+/*
+ * Re-pivot (the paper refactors with pivoting only for the first one or two
+ * matrices of a sequence, Section 3.1.1; this restarts that choice later):
+ * the threshold-pivoting factorization of kkt_analyze runs again on the
+ * host with `values` (caller's entry order, the analysed pattern; host, or
+ * device when values_on_device != 0), keeping the column order Q; the new
+ * P, factor structure, schedules and device buffers replace the old ones
+ * (device memory is re-allocated), and the factors are computed on the GPU
+ * as kkt_refactor(values) would.  Returns the kkt_refactor code, or a
+ * kkt_analyze error.  kkt_opts.repivot = 1 calls it automatically once
+ * when kkt_refactor meets a zero pivot or kkt_solve does not converge.
+ */
+int kkt_repivot(kkt_ctx* c, const double* values, int values_on_device);
 
 /*
  * Solve K x = b with the current factors (Sections 2.1-2.3):

@@ -29,6 +29,8 @@ ERR_NOT_CONVERGED = -6
 STOP = {"nrbe": 0, "rr": 1}
 TRSV = {"auto": 0, "global": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
+METHOD = {"fgmres": 0, "richardson": 1, "fgmres_ee": 2}
+ORTHO = {"cgs2": 0, "cgs2_pythagoras": 1, "cgs1_pythagoras": 2}
 
 # every entry point declared in include/kkt.h
 EXPORTS = [
@@ -36,7 +38,7 @@ EXPORTS = [
     "kkt_matvec", "kkt_get_perm", "kkt_get_factor_sizes", "kkt_get_factors", "kkt_query",
     "kkt_destroy", "kkt_strerror", "kkt_last_error_detail", "kkt_order", "kkt_pivot",
     "kkt_get_phase_times", "kkt_lu_solve_noalloc", "kkt_selftest_wait", "kkt_trace_refactor",
-    "kkt_trace_solve",
+    "kkt_trace_solve", "kkt_repivot",
 ]
 NOALLOC_MAX_N = 65536
 PHASES = ["gather", "refactor", "lsolve", "usolve", "spmv", "ortho", "update", "refactor_tail"]
@@ -48,6 +50,7 @@ class _Opts(C.Structure):
         ("refine_delta", C.c_double), ("pivot_tol", C.c_double), ("boost_eps", C.c_double),
         ("device", C.c_int), ("create_stream", C.c_int), ("stream", C.c_void_p), ("spin_limit", C.c_int64),
         ("timing", C.c_int), ("trisolve", C.c_int), ("cluster_blocks", C.c_int), ("tail_rows", C.c_int),
+        ("method", C.c_int), ("ortho", C.c_int), ("inner_tol", C.c_double), ("repivot", C.c_int),
     ]
 
 
@@ -58,7 +61,7 @@ class _Info(C.Structure):
         ("device_bytes", C.c_int64), ("nboost", C.c_int32), ("last_iters", C.c_int32),
         ("last_cycles", C.c_int32), ("trisolve_cluster", C.c_int32), ("last_nrbe", C.c_double), ("last_rnorm0", C.c_double),
         ("norm_a_inf", C.c_double), ("analyze_ms", C.c_double), ("launches", C.c_int64),
-        ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
+        ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("repivots", C.c_int32),
     ]
 
 
@@ -105,6 +108,7 @@ def lib():
     L.kkt_selftest_wait.argtypes = [vp, i64]
     L.kkt_trace_refactor.argtypes = [vp, vp, ip, vp, vp, C.POINTER(i32)]
     L.kkt_trace_solve.argtypes = [vp, vp, vp, ip, vp, vp, vp, vp]
+    L.kkt_repivot.argtypes = [vp, vp, ip]
     for name in EXPORTS:
         if name not in ("kkt_default_opts", "kkt_destroy", "kkt_strerror", "kkt_last_error_detail"):
             getattr(L, name).restype = C.c_int
@@ -195,7 +199,8 @@ class KKTSolver:
 
     def __init__(self, restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3,
                  boost_eps=0.0, device=0, stream=None, spin_limit=0, timing=False, trisolve="auto",
-                 tail_rows=0, cluster_blocks=0, precision="fp64"):
+                 tail_rows=0, cluster_blocks=0, precision="fp64", method="fgmres", ortho="cgs2",
+                 inner_tol=1e-6, repivot=False):
         L = lib()
         o = _Opts()
         L.kkt_default_opts(C.byref(o))
@@ -206,6 +211,8 @@ class KKTSolver:
         o.tail_rows = int(tail_rows)
         o.cluster_blocks = int(cluster_blocks)
         o.precision = PRECISION[precision]
+        o.method, o.ortho, o.inner_tol = METHOD[method], ORTHO[ortho], float(inner_tol)
+        o.repivot = int(bool(repivot))
         if stream is None:
             stream = _torch_current_stream(device)
         if stream is None:
@@ -251,6 +258,12 @@ class KKTSolver:
     def refactor(self, values):
         keep, p, dev = _ptr(values, np.float64)
         self._check(lib().kkt_refactor(self._h, p, dev), "kkt_refactor")
+
+    def repivot(self, values):
+        """kkt_repivot: pivoting factorization of `values` on the host (Q
+        kept), new device layout, then the GPU refactorization."""
+        keep, p, dev = _ptr(values, np.float64)
+        self._check(lib().kkt_repivot(self._h, p, dev), "kkt_repivot")
 
     def solve(self, b, x=None, tol=1e-12, allow_not_converged=False):
         """Returns (x, iters, nrbe).  x is written in place when given."""

@@ -191,15 +191,18 @@ __global__ void k_gather(const double* __restrict__ vals, const int64_t* __restr
     double rmax = 0.0;
     bool bad = false;
     for (int64_t i = warp; i < n; i += nwarps) {
-        double acc = 0.0;
         for (int64_t e = Arp[i] + lane; e < Arp[i + 1]; e += 32) {
             double v = vals[asrc ? asrc[e] : e];
             Ax[e] = v;
             if (!isfinite(v)) bad = true;
-            acc += fabs(v);
         }
-        acc = warp_sum(acc);
-        rmax = fmax(rmax, acc);
+        // the row's sum of |a_ij| in column order, as the definition reads
+        // (so the boost threshold boost_eps * ||K||_inf is reproducible)
+        if (lane == 0) {
+            double acc = 0.0;
+            for (int64_t e = Arp[i]; e < Arp[i + 1]; e++) acc += fabs(vals[asrc ? asrc[e] : e]);
+            rmax = fmax(rmax, acc);
+        }
     }
     if (bad) raise_error(s, KKT_ERR_NONFINITE, -1);
     if (lane == 0 && rmax > 0.0)   // non-negative doubles order like their bit patterns
@@ -822,7 +825,9 @@ __global__ void k_residual(int n, const int32_t* __restrict__ Arp, const int32_t
 // ---------------------------------------------------------------- K5-K7: FGMRES
 // Decision after a residual: NRBE of the current x, refine-or-not (initial
 // solve, Section 2.3) or accept/restart (cycle end).
-// mode 0: after x0; mode 1: after a cycle.  tol, stop_mode, refine_delta.
+// mode 0: after x0; mode 1: after a cycle; mode 2: after a Richardson
+// correction (counted as an iteration); mode 3: after a cycle of FGMRES on
+// the error equation (RR is then tested on the true residual).
 __global__ void k_decide(DevScal* s, int mode, double tol, int stop_mode, double refine_delta) {
     const double rn = s->rnorm, xn = s->xnorm, bn = s->normb;
     const double nrbe = (rn == 0.0) ? 0.0 : rn / (s->normA * xn + bn);
@@ -836,15 +841,26 @@ __global__ void k_decide(DevScal* s, int mode, double tol, int stop_mode, double
         else if (refine_delta > 0.0 && rn < refine_delta * bn) s->done = 1;
         else if (stop_mode == KKT_STOP_NRBE && nrbe <= tol) s->done = 1;
     } else {
+        if (mode == 2) s->iters += 1;
+        const int rr_met = (mode == 1) ? s->met : (rn < tol * s->rnorm0);
         if (rn == 0.0) s->done = 1;
         else if (stop_mode == KKT_STOP_NRBE && nrbe <= tol) s->done = 1;
-        else if (stop_mode == KKT_STOP_RR && s->met) s->done = 1;
+        else if (stop_mode == KKT_STOP_RR && rr_met) s->done = 1;
     }
 }
 
+// x += d (Richardson correction)
+__global__ void k_axpy(int n, const double* __restrict__ d, double* __restrict__ x) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = tid; t < n; t += stride) x[t] += d[t];
+}
+
 // v_0 = r / ||r||, g = (||r||, 0, ...), threshold of the inner test.
+// inner_rel > 0 (FGMRES on the error equation): the cycle's inner test is
+// |g_{j+1}| <= inner_rel * beta.
 __global__ void k_cycle_init(int n, const double* __restrict__ r, double* __restrict__ v0, DevScal* s,
-                             double tol, int stop_mode) {
+                             double tol, int stop_mode, double inner_rel) {
     const double beta = *(volatile double*)&s->rnorm;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -852,15 +868,56 @@ __global__ void k_cycle_init(int n, const double* __restrict__ r, double* __rest
     if (tid == 0) {
         s->g[0] = beta;
         for (int i = 1; i <= MAXM; i++) s->g[i] = 0.0;
-        s->thresh = (stop_mode == KKT_STOP_NRBE) ? tol * (s->normA * s->xnorm + s->normb) : tol * s->rnorm0;
+        s->thresh = inner_rel > 0.0 ? inner_rel * beta
+                  : (stop_mode == KKT_STOP_NRBE) ? tol * (s->normA * s->xnorm + s->normb) : tol * s->rnorm0;
         s->j = 0;
         s->met = 0;
     }
 }
 
+// sqrt(a^2 - ||h[0..k)||^2) as sqrt((a - c)(a + c)), c = ||h||; 0 if a <= c
+// (the norm of a projected vector from norms taken before the projection).
+__device__ __forceinline__ double pythagoras(double a, const double* h, int k) {
+    double c = 0.0;
+    for (int i = 0; i < k; i++) c += h[i] * h[i];
+    c = sqrt(c);
+    if (!(a > c)) return 0.0;
+    return sqrt((a - c) * (a + c));
+}
+
+// End of Arnoldi step j (one thread): H(:,j) = h (+ h2), h_{j+1,j} = hn,
+// previous Givens rotations applied, new rotation formed, g updated, the
+// inner stopping test sets s->met, j advances.
+__device__ void arnoldi_finish(DevScal* s, int j, double hn, bool add_h2, int stop_mode) {
+    s->hn = hn;
+    double* Hj = s->H + j * (MAXM + 1);
+    for (int i = 0; i <= j; i++) Hj[i] = add_h2 ? s->h[i] + s->h2[i] : s->h[i];
+    Hj[j + 1] = hn;
+    for (int i = 0; i < j; i++) {
+        const double a = Hj[i], bb = Hj[i + 1];
+        Hj[i] = s->cs[i] * a + s->sn[i] * bb;
+        Hj[i + 1] = -s->sn[i] * a + s->cs[i] * bb;
+    }
+    const double a = Hj[j], bb = Hj[j + 1];
+    const double rr = hypot(a, bb);
+    if (rr == 0.0) { s->cs[j] = 1.0; s->sn[j] = 0.0; }
+    else { s->cs[j] = a / rr; s->sn[j] = bb / rr; }
+    Hj[j] = rr;
+    Hj[j + 1] = 0.0;
+    s->g[j + 1] = -s->sn[j] * s->g[j];
+    s->g[j] = s->cs[j] * s->g[j];
+    s->iters += 1;
+    const double est = fabs(s->g[j + 1]);
+    const int met = (stop_mode == KKT_STOP_NRBE) ? (est <= s->thresh) : (est < s->thresh);
+    s->met = met;
+    s->j = j + 1;
+}
+
 // Classical Gram-Schmidt, first projection: h_i = v_i . w for i <= j.
+// with_norm (one-reduction CGS): ||w||^2 is reduced with the h_i and the
+// last block finishes the Arnoldi step with h_{j+1,j} by Pythagoras.
 __global__ void k_cgs_dots(int n, const double* __restrict__ V, int64_t ld, const double* __restrict__ w,
-                           double* part, DevScal* s) {
+                           double* part, DevScal* s, int with_norm, int stop_mode) {
     __shared__ double sh[33];
     const int j = *(volatile int*)&s->j;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -872,19 +929,32 @@ __global__ void k_cgs_dots(int n, const double* __restrict__ V, int64_t ld, cons
         acc = block_sum(acc, sh);
         if (threadIdx.x == 0) part[blockIdx.x * RED_SLOTS + i] = acc;
     }
+    if (with_norm) {
+        double acc = 0.0;
+        for (int64_t t = tid; t < n; t += stride) acc += w[t] * w[t];
+        acc = block_sum(acc, sh);
+        if (threadIdx.x == 0) part[blockIdx.x * RED_SLOTS + j + 1] = acc;
+    }
     if (!last_block(s)) return;
     for (int i = 0; i <= j; i++) {
         double v = reduce_partials(part, i, sh);
         if (threadIdx.x == 0) s->h[i] = v;
     }
+    if (!with_norm) return;
+    const double nn = reduce_partials(part, j + 1, sh);
+    if (threadIdx.x == 0) arnoldi_finish(s, j, pythagoras(sqrt(nn), s->h, j + 1), false, stop_mode);
 }
 
 // w -= V h (pass 0: h, then h2_i = v_i . w) or (pass 1: h2, then ||w||^2);
 // the last block of pass 1 finishes the Arnoldi step: H(:,j) = h + h2 and
 // h_{j+1,j} = ||w||, previous Givens rotations applied, new rotation
 // formed, g updated; the inner stopping test sets s->met.
+// with_norm (pass 0 only; CGS2 with the norm by Pythagoras): ||w||^2 after
+// the first projection is reduced with the h2_i and the last block finishes
+// the Arnoldi step; the second projection then comes with the normalisation
+// (k_project_normalize).
 __global__ void k_cgs_update(int n, const double* __restrict__ V, int64_t ld, double* __restrict__ w, int pass,
-                             double* part, DevScal* s, int m, int stop_mode) {
+                             double* part, DevScal* s, int m, int stop_mode, int with_norm) {
     __shared__ double sh[33];
     __shared__ double hc[MAXM + 1];
     const int j = *(volatile int*)&s->j;
@@ -907,6 +977,12 @@ __global__ void k_cgs_update(int n, const double* __restrict__ V, int64_t ld, do
             acc = block_sum(acc, sh);
             if (threadIdx.x == 0) part[blockIdx.x * RED_SLOTS + i] = acc;
         }
+        if (with_norm) {
+            double acc = 0.0;
+            for (int64_t t = tid; t < n; t += stride) acc += w[t] * w[t];
+            acc = block_sum(acc, sh);
+            if (threadIdx.x == 0) part[blockIdx.x * RED_SLOTS + j + 1] = acc;
+        }
     } else {
         double acc = 0.0;
         for (int64_t t = tid; t < n; t += stride) acc += w[t] * w[t];
@@ -919,33 +995,36 @@ __global__ void k_cgs_update(int n, const double* __restrict__ V, int64_t ld, do
             double v = reduce_partials(part, i, sh);
             if (threadIdx.x == 0) s->h2[i] = v;
         }
+        if (!with_norm) return;
+        const double nn = reduce_partials(part, j + 1, sh);
+        if (threadIdx.x == 0) arnoldi_finish(s, j, pythagoras(sqrt(nn), s->h2, j + 1), true, stop_mode);
         return;
     }
     double nn = reduce_partials(part, 0, sh);
     if (threadIdx.x != 0) return;
-    const double hn = sqrt(nn);
-    s->hn = hn;
-    double* Hj = s->H + j * (MAXM + 1);
-    for (int i = 0; i <= j; i++) Hj[i] = s->h[i] + s->h2[i];
-    Hj[j + 1] = hn;
-    for (int i = 0; i < j; i++) {
-        const double a = Hj[i], bb = Hj[i + 1];
-        Hj[i] = s->cs[i] * a + s->sn[i] * bb;
-        Hj[i + 1] = -s->sn[i] * a + s->cs[i] * bb;
+    arnoldi_finish(s, j, sqrt(nn), true, stop_mode);
+}
+
+// The projection left after a Pythagorean finish, fused with the
+// normalisation: w -= V(:, 0..j-1) hx (hx = h for one-reduction CGS, h2
+// for CGS2), then v_j = w / h_{j,j-1} (j was already advanced).
+__global__ void k_project_normalize(int n, double* __restrict__ w, double* __restrict__ V, int64_t ld, DevScal* s,
+                                    int use_h2) {
+    __shared__ double hc[MAXM + 1];
+    const int j = *(volatile int*)&s->j;   // advanced: columns 0..j-1 project, column j is new
+    const double hn = *(volatile double*)&s->hn;
+    const double* hsrc = use_h2 ? s->h2 : s->h;
+    for (int i = threadIdx.x; i < j; i += blockDim.x) hc[i] = ((volatile double*)hsrc)[i];
+    __syncthreads();
+    double* vn = V + (int64_t)j * ld;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = tid; t < n; t += stride) {
+        double wt = w[t];
+        for (int i = 0; i < j; i++) wt -= hc[i] * V[(int64_t)i * ld + t];
+        w[t] = wt;
+        vn[t] = hn > 0.0 ? wt / hn : 0.0;
     }
-    const double a = Hj[j], bb = Hj[j + 1];
-    const double rr = hypot(a, bb);
-    if (rr == 0.0) { s->cs[j] = 1.0; s->sn[j] = 0.0; }
-    else { s->cs[j] = a / rr; s->sn[j] = bb / rr; }
-    Hj[j] = rr;
-    Hj[j + 1] = 0.0;
-    s->g[j + 1] = -s->sn[j] * s->g[j];
-    s->g[j] = s->cs[j] * s->g[j];
-    s->iters += 1;
-    const double est = fabs(s->g[j + 1]);
-    const int met = (stop_mode == KKT_STOP_NRBE) ? (est <= s->thresh) : (est < s->thresh);
-    s->met = met;
-    s->j = j + 1;
 }
 
 // v_{j+1} = w / h_{j+1,j} (zero on breakdown); j was already advanced.

@@ -41,6 +41,7 @@ struct kkt_ctx {
     double *d_Ax = nullptr, *d_vals = nullptr;
     bool mixed = false;
     unsigned long long* solve_trace = nullptr;   // kkt_trace_solve only: 2n publish stamps
+    int32_t repivots = 0;                         // kkt_repivot calls that succeeded in analysis
     double *d_b = nullptr, *d_x = nullptr, *d_y = nullptr, *d_xp = nullptr, *d_r = nullptr, *d_w = nullptr;
     double *d_V = nullptr, *d_Z = nullptr, *d_part = nullptr;
     unsigned* d_done_f = nullptr;
@@ -374,6 +375,10 @@ void kkt_default_opts(kkt_opts* o) {
     o->create_stream = 1;
     o->stream = nullptr;
     o->spin_limit = 0;
+    o->method = KKT_METHOD_FGMRES;
+    o->ortho = KKT_ORTHO_CGS2;
+    o->inner_tol = 1e-6;
+    o->repivot = 0;
 }
 
 const char* kkt_strerror(int code) {
@@ -404,7 +409,10 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
         (c->o.stop_mode != KKT_STOP_NRBE && c->o.stop_mode != KKT_STOP_RR) || c->o.pivot_tol <= 0 ||
         c->o.pivot_tol > 1 || c->o.boost_eps < 0 ||
         (c->o.trisolve != KKT_TRSV_AUTO && c->o.trisolve != KKT_TRSV_GLOBAL) || c->o.tail_rows < 0 ||
-        (c->o.cluster_blocks != 0 && c->o.cluster_blocks != 8 && c->o.cluster_blocks != 16)) {
+        (c->o.cluster_blocks != 0 && c->o.cluster_blocks != 8 && c->o.cluster_blocks != 16) ||
+        c->o.method < KKT_METHOD_FGMRES || c->o.method > KKT_METHOD_FGMRES_EE ||
+        c->o.ortho < KKT_ORTHO_CGS2 || c->o.ortho > KKT_ORTHO_CGS1_PYTH ||
+        !(c->o.inner_tol > 0.0 && c->o.inner_tol <= 1.0) || (c->o.repivot != 0 && c->o.repivot != 1)) {
         delete c;
         return KKT_ERR_INVALID;
     }
@@ -483,6 +491,10 @@ int kkt_pivot(int32_t n, const int32_t* rowptr, const int32_t* colind, const dou
     return KKT_OK;
 }
 
+namespace {
+int setup_device(kkt_ctx* c, const kkt::ColStructure& S, std::chrono::steady_clock::time_point t0);
+}
+
 int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* colind, const double* values0,
                 const int32_t* Qin, const int32_t* Pin) {
     if (!c) return KKT_ERR_INVALID;
@@ -520,7 +532,15 @@ int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* col
         rc = kkt::pivot_lu(c->A, v.data(), c->Q, c->o.pivot_tol, &c->P, &S, &bad);
         if (rc) { c->detail = "pivoting factorization failed at column " + std::to_string(bad); return rc; }
     }
-    rc = kkt::build_layout(c->A, c->P, c->Q, S, &c->lay);
+    return setup_device(c, S, t0);
+}
+
+namespace {
+// Everything kkt_analyze does once P, Q and the factor structure are known:
+// the GPU layout, schedules and every device buffer.
+int setup_device(kkt_ctx* c, const kkt::ColStructure& S, std::chrono::steady_clock::time_point t0) {
+    const int32_t n = c->A.n;
+    int rc = kkt::build_layout(c->A, c->P, c->Q, S, &c->lay);
     if (rc) { c->detail = "factor layout failed"; return rc; }
     // composite gather map: factor slot -> caller value index
     std::vector<int64_t> fsrc(c->lay.Fsrc.size());
@@ -627,13 +647,47 @@ int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* col
     c->analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return KKT_OK;
 }
+}  // namespace
 
 namespace {
 int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsigned long long* trace);
 }
 
+int kkt_repivot(kkt_ctx* c, const double* values, int values_on_device) {
+    int rc = check_ctx(c, false);
+    if (rc) return rc;
+    if (!values) return KKT_ERR_INVALID;
+    auto t0 = std::chrono::steady_clock::now();
+    const int64_t nnz = c->nnz_a;
+    std::vector<double> hv((size_t)nnz);
+    if (values_on_device) {
+        CK(cudaMemcpyAsync(hv.data(), values, sizeof(double) * (size_t)nnz, cudaMemcpyDeviceToHost, c->stream));
+        c->d2h += (int64_t)sizeof(double) * nnz;
+    } else {
+        std::copy(values, values + nnz, hv.begin());
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<double> v((size_t)nnz);
+    for (int64_t e = 0; e < nnz; e++) v[e] = hv[c->A.src[e]];
+    kkt::ColStructure S;
+    std::vector<int32_t> P;
+    int32_t bad = -1;
+    rc = kkt::pivot_lu(c->A, v.data(), c->Q, c->o.pivot_tol, &P, &S, &bad);
+    if (rc) {   // the previous analysis stays in place
+        c->detail = "pivoting factorization failed at column " + std::to_string(bad);
+        return rc;
+    }
+    free_device(c);
+    c->P = P;
+    if ((rc = setup_device(c, S, t0))) return rc;
+    c->repivots++;
+    return refactor_impl(c, hv.data(), 0, nullptr);
+}
+
 int kkt_refactor(kkt_ctx* c, const double* values, int values_on_device) {
-    return refactor_impl(c, values, values_on_device, nullptr);
+    int rc = refactor_impl(c, values, values_on_device, nullptr);
+    if (rc == KKT_ERR_ZERO_PIVOT && c && c->o.repivot) rc = kkt_repivot(c, values, values_on_device);
+    return rc;
 }
 
 int kkt_trace_refactor(kkt_ctx* c, const double* values, int values_on_device, int64_t* t_start,
@@ -805,7 +859,59 @@ int kkt_matvec(kkt_ctx* c, const double* x, double* y, int on_device) {
     return KKT_OK;
 }
 
+namespace {
+// One Arnoldi step's orthogonalisation (w = K z_j against V(:, 0..j)), the
+// Hessenberg column, Givens rotation and v_{j+1}, by kkt_opts.ortho.
+void arnoldi_ortho(kkt_ctx* c, int rb, int stop) {
+    const int m = c->m;
+    switch (c->o.ortho) {
+        case KKT_ORTHO_CGS2_PYTH:
+            kkt::k_cgs_dots<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_V, c->ld, c->d_w, c->d_part, c->d_s,
+                                                                    0, stop);
+            kkt::k_cgs_update<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_V, c->ld, c->d_w, 0, c->d_part,
+                                                                      c->d_s, m, stop, 1);
+            kkt::k_project_normalize<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_w, c->d_V, c->ld, c->d_s, 1);
+            c->launches += 3;
+            break;
+        case KKT_ORTHO_CGS1_PYTH:
+            kkt::k_cgs_dots<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_V, c->ld, c->d_w, c->d_part, c->d_s,
+                                                                    1, stop);
+            kkt::k_project_normalize<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_w, c->d_V, c->ld, c->d_s, 0);
+            c->launches += 2;
+            break;
+        default:
+            kkt::k_cgs_dots<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_V, c->ld, c->d_w, c->d_part, c->d_s,
+                                                                    0, stop);
+            kkt::k_cgs_update<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_V, c->ld, c->d_w, 0, c->d_part,
+                                                                      c->d_s, m, stop, 0);
+            kkt::k_cgs_update<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_V, c->ld, c->d_w, 1, c->d_part,
+                                                                      c->d_s, m, stop, 0);
+            kkt::k_normalize<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_w, c->d_V, c->ld, c->d_s);
+            c->launches += 4;
+    }
+}
+
+int solve_impl(kkt_ctx* c, const double* b, double* x, int on_device, double tol, int* iters, double* nrbe);
+}  // namespace
+
 int kkt_solve(kkt_ctx* c, const double* b, double* x, int on_device, double tol, int* iters, double* nrbe) {
+    int rc = solve_impl(c, b, x, on_device, tol, iters, nrbe);
+    if (rc != KKT_ERR_NOT_CONVERGED || !c->o.repivot) return rc;
+    // re-pivot on the matrix in use (its canonical copy, back in the
+    // caller's entry order) and solve once more
+    const int64_t nnz = c->nnz_a;
+    std::vector<double> ax((size_t)nnz), hv((size_t)nnz);
+    CK(cudaMemcpyAsync(ax.data(), c->d_Ax, sizeof(double) * (size_t)nnz, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->d2h += (int64_t)sizeof(double) * nnz;
+    for (int64_t e = 0; e < nnz; e++) hv[c->A.src[e]] = ax[e];
+    const int rp = kkt_repivot(c, hv.data(), 0);
+    if (rp) return rp;
+    return solve_impl(c, b, x, on_device, tol, iters, nrbe);
+}
+
+namespace {
+int solve_impl(kkt_ctx* c, const double* b, double* x, int on_device, double tol, int* iters, double* nrbe) {
     int rc = check_ctx(c, true);
     if (rc) return rc;
     if (!b || !x || !(tol > 0)) return KKT_ERR_INVALID;
@@ -835,11 +941,33 @@ int kkt_solve(kkt_ctx* c, const double* b, double* x, int on_device, double tol,
     if ((rc = device_error(c))) { rearm(c); return rc; }
     int cycles = 0;
     int status = KKT_OK;
-    while (!c->h_s->done) {
+    const int method = c->o.method;
+    // classical iterative refinement: d = (LU)^{-1} rho, x += d, new residual
+    const int64_t max_steps = (int64_t)c->o.max_cycles * m;
+    int64_t steps = 0;
+    while (method == KKT_METHOD_RICHARDSON && !c->h_s->done) {
+        if (steps >= max_steps) { status = KKT_ERR_NOT_CONVERGED; break; }
+        steps++;
+        lu_apply(c, c->d_r, c->d_w);
+        t = phase_begin(c, KKT_PHASE_UPDATE);
+        kkt::k_axpy<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_w, xd);
+        phase_end(c, t);
+        t = phase_begin(c, KKT_PHASE_SPMV);
+        kkt::k_residual<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, bd, xd, c->d_r,
+                                                                c->d_part, c->d_s);
+        phase_end(c, t);
+        kkt::k_decide<<<1, 1, 0, c->stream>>>(c->d_s, 2, tol, stop, c->o.refine_delta);
+        c->launches += 3;
+        CK(cudaGetLastError());
+        if ((rc = read_scalars(c))) return rc;
+        if ((rc = device_error(c))) return rc;
+    }
+    const double inner_rel = method == KKT_METHOD_FGMRES_EE ? c->o.inner_tol : 0.0;
+    while (method != KKT_METHOD_RICHARDSON && !c->h_s->done) {
         if (cycles >= c->o.max_cycles) { status = KKT_ERR_NOT_CONVERGED; break; }
         cycles++;
         t = phase_begin(c, KKT_PHASE_UPDATE);
-        kkt::k_cycle_init<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_r, c->d_V, c->d_s, tol, stop);
+        kkt::k_cycle_init<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_r, c->d_V, c->d_s, tol, stop, inner_rel);
         phase_end(c, t);
         c->launches += 1;
         for (int j = 0; j < m; j++) {
@@ -850,14 +978,9 @@ int kkt_solve(kkt_ctx* c, const double* b, double* x, int on_device, double tol,
             kkt::k_spmv<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, zj, c->d_w);
             phase_end(c, t);
             t = phase_begin(c, KKT_PHASE_ORTHO);
-            kkt::k_cgs_dots<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_V, c->ld, c->d_w, c->d_part, c->d_s);
-            kkt::k_cgs_update<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_V, c->ld, c->d_w, 0, c->d_part,
-                                                                      c->d_s, m, stop);
-            kkt::k_cgs_update<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_V, c->ld, c->d_w, 1, c->d_part,
-                                                                      c->d_s, m, stop);
-            kkt::k_normalize<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_w, c->d_V, c->ld, c->d_s);
+            arnoldi_ortho(c, rb, stop);
             phase_end(c, t);
-            c->launches += 5;
+            c->launches += 1;
             CK(cudaGetLastError());
             if ((rc = read_scalars(c))) return rc;
             if ((rc = device_error(c))) { rearm(c); return rc; }
@@ -871,7 +994,8 @@ int kkt_solve(kkt_ctx* c, const double* b, double* x, int on_device, double tol,
         kkt::k_residual<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, bd, xd, c->d_r,
                                                                 c->d_part, c->d_s);
         phase_end(c, t);
-        kkt::k_decide<<<1, 1, 0, c->stream>>>(c->d_s, 1, tol, stop, c->o.refine_delta);
+        kkt::k_decide<<<1, 1, 0, c->stream>>>(c->d_s, method == KKT_METHOD_FGMRES_EE ? 3 : 1, tol, stop,
+                                              c->o.refine_delta);
         c->launches += 4;
         CK(cudaGetLastError());
         if ((rc = read_scalars(c))) return rc;
@@ -889,9 +1013,11 @@ int kkt_solve(kkt_ctx* c, const double* b, double* x, int on_device, double tol,
     c->last_rnorm0 = c->h_s->rnorm0;
     if (iters) *iters = c->h_s->iters;
     if (nrbe) *nrbe = c->h_s->nrbe;
-    if (status) c->detail = "max_cycles reached";
+    if (status) c->detail = method == KKT_METHOD_RICHARDSON ? "max_cycles * restart corrections reached"
+                                                             : "max_cycles reached";
     return status;
 }
+}  // namespace
 
 int kkt_get_perm(kkt_ctx* c, int32_t* P, int32_t* Q) {
     if (!c || !c->analyzed) return c ? KKT_ERR_STATE : KKT_ERR_INVALID;
@@ -961,6 +1087,7 @@ int kkt_query(kkt_ctx* c, kkt_info* info) {
     info->launches = c->launches;
     info->h2d_bytes = c->h2d;
     info->d2h_bytes = c->d2h;
+    info->repivots = c->repivots;
     return KKT_OK;
 }
 

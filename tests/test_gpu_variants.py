@@ -1,0 +1,218 @@
+"""Refinement variants on the GPU against the oracle (Section 2.1):
+classical iterative refinement, FGMRES on the error equation, the
+low-synchronisation Gram-Schmidt variants, and re-pivoting.
+
+The GPU's FP64 factors equal the oracle's bit for bit on the same P, Q, so
+both sides precondition with the same M; their dot products and triangular
+solves sum in different orders, so iteration counts may differ by one per
+restart cycle (one per run for classical refinement), and each side must meet
+the stopping rule on its own."""
+import numpy as np
+import pytest
+
+import paper_2401_13926_b300 as K
+from paper_2401_13926_b300.workload import KKTSequence, small_random_sparse
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def c1(oracle_mod):
+    seq = KKTSequence("kkt200")
+    P, Q, _ = oracle_mod.lu(seq.n, seq.rowptr, seq.colind, seq.values(0))
+    return seq, P, Q
+
+
+def _nrbe(oracle_mod, seq, v, b, x):
+    return oracle_mod.nrbe(seq.n, seq.rowptr, seq.colind, v, b, x)
+
+
+def test_richardson_matches_oracle_kkt200(oracle_mod, c1):
+    seq, P, Q = c1
+    s = K.KKTSolver(method="richardson")
+    s.analyze(seq.rowptr, seq.colind, Q=Q, P=P)
+    for k in range(seq.M):
+        v = seq.values(k)
+        b, _ = seq.rhs(k, v)
+        s.refactor(v)
+        x, it, nr = s.solve(b, tol=TOL)
+        F = oracle_mod.refactor(seq.n, seq.rowptr, seq.colind, v, P, Q)
+        o = oracle_mod.richardson(seq.n, seq.rowptr, seq.colind, v, F, P, Q, b, tol=TOL, max_steps=50 * 20)
+        assert o.status == 0
+        assert abs(it - o.iters) <= 1, (k, it, o.iters)
+        assert _nrbe(oracle_mod, seq, v, b, x) <= TOL * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("stop_mode", ["nrbe", "rr"])
+def test_richardson_with_fp32_factors_contracts_like_oracle(oracle_mod, stop_mode):
+    """Mixed precision + classical refinement on a well-conditioned system:
+    the FP32 factors are the oracle's bit for bit, so the contraction rate
+    |I - K M^{-1}| is the same and the correction counts agree closely
+    (NRBE rule, and the relative-residual rule with tol 1e-8).  The case is
+    chosen so that |I - K M^{-1}| < 1 with FP32 factors (several
+    corrections); with less diagonal dominance the oracle's classical
+    refinement diverges where FGMRES still converges, the contrast of Fig. 3."""
+    n = 2000
+    rp, ci, v = small_random_sparse(n, 4.0 / n, 21, diag_boost=1.5)
+    P, Q, _ = oracle_mod.lu(n, rp, ci, v)
+    tol = TOL if stop_mode == "nrbe" else 1e-8
+    s = K.KKTSolver(method="richardson", precision="mixed", stop_mode=stop_mode)
+    s.analyze(rp, ci, Q=Q, P=P)
+    s.refactor(v)
+    b = np.random.default_rng(8).standard_normal(n)
+    x, it, nr = s.solve(b, tol=tol)
+    F = oracle_mod.refactor_f32(n, rp, ci, v, P, Q)
+    o = oracle_mod.richardson(n, rp, ci, v, F, P, Q, b, tol=tol, max_steps=1000,
+                              stop_mode=0 if stop_mode == "nrbe" else 1)
+    assert o.status == 0 and it >= 1
+    assert abs(it - o.iters) <= 2, (it, o.iters)
+    if stop_mode == "nrbe":
+        assert oracle_mod.nrbe(n, rp, ci, v, b, x) <= TOL * (1 + 1e-6)
+    else:
+        r = np.linalg.norm(oracle_mod.residual(n, rp, ci, v, b, x))
+        assert r < tol * o.trace[0] * (1 + 1e-3)
+
+
+def _boosted_case(oracle_mod, seed=23, n=2000, boost=1e-3):
+    """FP64 factors made inexact by the static-pivot boost (pivots below
+    boost * ||K||_inf replaced; the same rule on both sides), so refinement
+    needs several iterations while GPU and oracle precondition with the same
+    M bit for bit."""
+    rp, ci, v = small_random_sparse(n, 4.0 / n, seed, diag_boost=1.0)
+    P, Q, _ = oracle_mod.lu(n, rp, ci, v)
+    F = oracle_mod.refactor(n, rp, ci, v, P, Q, boost_abs=boost * oracle_mod.norm_inf(n, rp, v))
+    b = np.random.default_rng(seed).standard_normal(n)
+    return n, rp, ci, v, P, Q, F, b
+
+
+def _gpu(n, rp, ci, v, P, Q, F, boost=1e-3, **kw):
+    s = K.KKTSolver(boost_eps=boost, **kw)
+    s.analyze(rp, ci, Q=Q, P=P)
+    s.refactor(v)
+    f = s.factors()
+    assert F.nboost > 0 and np.array_equal(f["Ux"], F.Ux) and np.array_equal(f["Lx"], F.Lx)
+    return s
+
+
+@pytest.mark.parametrize("inner_tol", [1e-2, 1e-6])
+def test_error_equation_fgmres_matches_oracle(oracle_mod, inner_tol):
+    n, rp, ci, v, P, Q, F, b = _boosted_case(oracle_mod, 24)
+    s = _gpu(n, rp, ci, v, P, Q, F, method="fgmres_ee", inner_tol=inner_tol)
+    x, it, nr = s.solve(b, tol=TOL)
+    o = oracle_mod.fgmres(n, rp, ci, v, F, P, Q, b, tol=TOL, error_equation=True, inner_tol=inner_tol)
+    assert o.status == 0 and o.cycles >= 2
+    cyc = s.info()["last_cycles"]
+    assert abs(cyc - o.cycles) <= 1, (cyc, o.cycles)
+    assert abs(it - o.iters) <= max(cyc, o.cycles), (it, o.iters)
+    assert oracle_mod.nrbe(n, rp, ci, v, b, x) <= TOL * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("ortho", ["cgs2", "cgs2_pythagoras", "cgs1_pythagoras"])
+def test_gram_schmidt_variants_match_oracle(oracle_mod, ortho):
+    n, rp, ci, v, P, Q, F, b = _boosted_case(oracle_mod, 23)
+    s = _gpu(n, rp, ci, v, P, Q, F, ortho=ortho)
+    x, it, nr = s.solve(b, tol=TOL)
+    o = oracle_mod.fgmres(n, rp, ci, v, F, P, Q, b, tol=TOL, ortho=ortho)
+    assert o.status == 0 and o.iters >= 5
+    cyc = s.info()["last_cycles"]
+    assert abs(it - o.iters) <= max(cyc, o.cycles), (it, o.iters)
+    assert oracle_mod.nrbe(n, rp, ci, v, b, x) <= TOL * (1 + 1e-6)
+
+
+def test_richardson_with_boosted_factors_matches_oracle(oracle_mod):
+    """A slowly contracting stationary iteration (hundreds of corrections):
+    the correction counts agree within two."""
+    n, rp, ci, v, P, Q, F, b = _boosted_case(oracle_mod, 23)
+    s = _gpu(n, rp, ci, v, P, Q, F, method="richardson")
+    x, it, nr = s.solve(b, tol=TOL)
+    o = oracle_mod.richardson(n, rp, ci, v, F, P, Q, b, tol=TOL, max_steps=1000)
+    assert o.status == 0 and o.iters >= 100
+    assert abs(it - o.iters) <= 2, (it, o.iters)
+    assert oracle_mod.nrbe(n, rp, ci, v, b, x) <= TOL * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("ortho", ["cgs2", "cgs2_pythagoras", "cgs1_pythagoras"])
+def test_gram_schmidt_variants_on_kkt_sequence(oracle_mod, c1, ortho):
+    """FP64 factors on the KKT sequence: every variant reaches the NRBE
+    tolerance (as the oracle evaluates it) like the oracle's same variant."""
+    seq, P, Q = c1
+    s = K.KKTSolver(ortho=ortho)
+    s.analyze(seq.rowptr, seq.colind, Q=Q, P=P)
+    for k in range(seq.M):
+        v = seq.values(k)
+        b, _ = seq.rhs(k, v)
+        s.refactor(v)
+        x, it, nr = s.solve(b, tol=TOL)
+        F = oracle_mod.refactor(seq.n, seq.rowptr, seq.colind, v, P, Q)
+        o = oracle_mod.fgmres(seq.n, seq.rowptr, seq.colind, v, F, P, Q, b, tol=TOL, ortho=ortho)
+        assert o.status == 0
+        assert abs(it - o.iters) <= max(1, o.cycles), (k, it, o.iters)
+        assert _nrbe(oracle_mod, seq, v, b, x) <= TOL * (1 + 1e-6)
+
+
+def _zero_first_pivot(rp, ci, v, P, Q):
+    """Values with the entry chosen as the first pivot, A(P[0], Q[0]), set to 0."""
+    w = v.copy()
+    row = P[0]
+    for e in range(rp[row], rp[row + 1]):
+        if ci[e] == Q[0]:
+            w[e] = 0.0
+    return w
+
+
+def test_repivot_after_zero_pivot(oracle_mod):
+    n = 600
+    rp, ci, v = small_random_sparse(n, 5.0 / n, 31, diag_boost=1.0)
+    s0 = K.KKTSolver()
+    s0.analyze(rp, ci, values0=v)
+    P0, Q0 = s0.perm()
+    w = _zero_first_pivot(rp, ci, v, P0, Q0)
+    with pytest.raises(K.KKTError) as e:
+        s0.refactor(w)
+    assert e.value.code == -4
+    # explicit re-pivot: the new P is the oracle's pivot choice on w with the same Q
+    s0.repivot(w)
+    P1, Q1 = s0.perm()
+    assert np.array_equal(Q1, Q0) and not np.array_equal(P1, P0)
+    Po, Qo, _ = oracle_mod.lu(n, rp, ci, w, Q=Q0)
+    assert np.array_equal(P1, Po)
+    f = s0.factors()
+    of = oracle_mod.refactor(n, rp, ci, w, Po, Qo)
+    assert np.array_equal(f["Lx"], of.Lx) and np.array_equal(f["Ux"], of.Ux)
+    assert s0.info()["repivots"] == 1
+    b = np.random.default_rng(0).standard_normal(n)
+    x, it, nr = s0.solve(b, tol=TOL)
+    assert oracle_mod.nrbe(n, rp, ci, w, b, x) <= TOL * (1 + 1e-6)
+    # automatic: kkt_refactor re-pivots by itself
+    s1 = K.KKTSolver(repivot=True)
+    s1.analyze(rp, ci, values0=v)
+    s1.refactor(w)
+    assert s1.info()["repivots"] == 1
+    assert np.array_equal(s1.perm()[0], Po)
+
+
+def test_repivot_when_refinement_fails(oracle_mod):
+    """Pivots that became tiny (not zero) make poor factors: refinement does
+    not converge within one short cycle; with repivot on, kkt_solve re-pivots
+    on the matrix in use and converges."""
+    n = 600
+    rp, ci, v = small_random_sparse(n, 5.0 / n, 32, diag_boost=1.0)
+    s = K.KKTSolver(repivot=True, max_cycles=1, restart=3)
+    s.analyze(rp, ci, values0=v)
+    P0, Q0 = s.perm()
+    w = v.copy()
+    for k in range(40):          # the first 40 pivots shrink by 1e-15
+        row = P0[k]
+        for e in range(rp[row], rp[row + 1]):
+            if ci[e] == Q0[k]:
+                w[e] = v[e] * 1e-15
+    s.refactor(w)
+    assert s.info()["repivots"] == 0
+    b = np.random.default_rng(1).standard_normal(n)
+    x, it, nr = s.solve(b, tol=TOL)
+    assert s.info()["repivots"] == 1
+    assert oracle_mod.nrbe(n, rp, ci, w, b, x) <= TOL * (1 + 1e-6)
+    Po, _, _ = oracle_mod.lu(n, rp, ci, w, Q=Q0)
+    assert np.array_equal(s.perm()[0], Po)
