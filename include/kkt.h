@@ -101,6 +101,12 @@ typedef struct {
     int repivot;          /* 1: when kkt_refactor meets a zero pivot, or kkt_solve does not
                              converge, re-run the pivoting factorization on the current
                              values (Q kept; kkt_repivot) and retry once; 0 = off (default) */
+    int graphs;           /* 1: kkt_refactor and kkt_solve replay CUDA graphs -- the
+                             refactorization's launches, and the whole refinement with
+                             device-side loop control (conditional WHILE/IF nodes: no host
+                             round trip per step); captured on first use, again when tol
+                             changes.  Same kernels in the same order, so the same results.
+                             0 = launch from the host (default) */
 } kkt_opts;
 
 /* Refinement methods (Section 2.1).  FGMRES: FGMRES(m) with M = LU as right
@@ -141,7 +147,9 @@ typedef struct {
 #define KKT_PHASE_ORTHO 5     /* CGS2 passes, normalisation, Givens */
 #define KKT_PHASE_UPDATE 6    /* cycle start and end (v_0, y = R^{-1} g, x += Z y) */
 #define KKT_PHASE_REFACTOR_TAIL 7  /* the part of the refactorization done one block per row */
-#define KKT_NUM_PHASES 8
+#define KKT_PHASE_GRAPH_REFACTOR 8 /* a whole refactorization replayed as a graph (kkt_opts.graphs) */
+#define KKT_PHASE_GRAPH_SOLVE 9    /* a whole solve replayed as a graph (kkt_opts.graphs) */
+#define KKT_NUM_PHASES 10
 
 typedef struct {
     int32_t n;

@@ -41,7 +41,8 @@ EXPORTS = [
     "kkt_trace_solve", "kkt_repivot",
 ]
 NOALLOC_MAX_N = 65536
-PHASES = ["gather", "refactor", "lsolve", "usolve", "spmv", "ortho", "update", "refactor_tail"]
+PHASES = ["gather", "refactor", "lsolve", "usolve", "spmv", "ortho", "update", "refactor_tail", "graph_refactor",
+          "graph_solve"]
 
 
 class _Opts(C.Structure):
@@ -51,6 +52,7 @@ class _Opts(C.Structure):
         ("device", C.c_int), ("create_stream", C.c_int), ("stream", C.c_void_p), ("spin_limit", C.c_int64),
         ("timing", C.c_int), ("trisolve", C.c_int), ("cluster_blocks", C.c_int), ("tail_rows", C.c_int),
         ("method", C.c_int), ("ortho", C.c_int), ("inner_tol", C.c_double), ("repivot", C.c_int),
+        ("graphs", C.c_int),
     ]
 
 
@@ -200,7 +202,7 @@ class KKTSolver:
     def __init__(self, restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3,
                  boost_eps=0.0, device=0, stream=None, spin_limit=0, timing=False, trisolve="auto",
                  tail_rows=0, cluster_blocks=0, precision="fp64", method="fgmres", ortho="cgs2",
-                 inner_tol=1e-6, repivot=False):
+                 inner_tol=1e-6, repivot=False, graphs=False):
         L = lib()
         o = _Opts()
         L.kkt_default_opts(C.byref(o))
@@ -213,6 +215,7 @@ class KKTSolver:
         o.precision = PRECISION[precision]
         o.method, o.ortho, o.inner_tol = METHOD[method], ORTHO[ortho], float(inner_tol)
         o.repivot = int(bool(repivot))
+        o.graphs = int(bool(graphs))
         if stream is None:
             stream = _torch_current_stream(device)
         if stream is None:

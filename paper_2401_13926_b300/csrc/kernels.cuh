@@ -50,6 +50,12 @@ struct DevScal {
     double h[MAXM + 1], h2[MAXM + 1];
     int j;                 // current Arnoldi column
     int iters;             // Arnoldi steps of this solve
+    int cycles;            // restart cycles of this solve (device-side loop control)
+    int not_converged;     // the device-side loop stopped at its cycle or step cap
+    // CUDA-graph loop control: the WHILE node's handle and one handle per
+    // Arnoldi-step IF node (a handle drives exactly one conditional node)
+    unsigned long long h_loop;
+    unsigned long long h_step[MAXM];
     int met;               // inner criterion met in this cycle
     int done;              // solve finished (converged or nothing to do)
     // sync-free scheduling
@@ -828,14 +834,40 @@ __global__ void k_residual(int n, const int32_t* __restrict__ Arp, const int32_t
 // mode 0: after x0; mode 1: after a cycle; mode 2: after a Richardson
 // correction (counted as an iteration); mode 3: after a cycle of FGMRES on
 // the error equation (RR is then tested on the true residual).
-__global__ void k_decide(DevScal* s, int mode, double tol, int stop_mode, double refine_delta) {
+__device__ void decide_rule(DevScal* s, int mode, double tol, int stop_mode, double refine_delta, double rn,
+                            double bn, double nrbe);
+
+// In a CUDA graph with device-side loop control (graph != 0) the decision
+// also sets the WHILE condition: continue while the solve is not done and
+// the cap (max_cycles cycles, or max_cycles * m Richardson corrections) is
+// not reached.
+__global__ void k_decide(DevScal* s, int mode, double tol, int stop_mode, double refine_delta,
+                         int cap, int graph) {
     const double rn = s->rnorm, xn = s->xnorm, bn = s->normb;
     const double nrbe = (rn == 0.0) ? 0.0 : rn / (s->normA * xn + bn);
     s->nrbe = nrbe;
-    if (!isfinite(rn) || !isfinite(xn)) { s->err = KKT_ERR_NONFINITE; s->done = 1; return; }
+    if (!isfinite(rn) || !isfinite(xn)) {
+        s->err = KKT_ERR_NONFINITE;
+        s->done = 1;
+        if (graph) cudaGraphSetConditional(s->h_loop, 0u);
+        return;
+    }
+    decide_rule(s, mode, tol, stop_mode, refine_delta, rn, bn, nrbe);
+    if (graph) {
+        const int used = (mode == 2) ? s->iters : s->cycles;
+        int cont = !s->done;
+        if (cont && used >= cap) { s->not_converged = 1; cont = 0; }
+        cudaGraphSetConditional(s->h_loop, (unsigned)cont);
+    }
+}
+
+__device__ void decide_rule(DevScal* s, int mode, double tol, int stop_mode, double refine_delta, double rn,
+                            double bn, double nrbe) {
     if (mode == 0) {
         s->rnorm0 = rn;
         s->iters = 0;
+        s->cycles = 0;
+        s->not_converged = 0;
         s->done = 0;
         if (rn == 0.0) s->done = 1;
         else if (refine_delta > 0.0 && rn < refine_delta * bn) s->done = 1;
@@ -859,8 +891,9 @@ __global__ void k_axpy(int n, const double* __restrict__ d, double* __restrict__
 // v_0 = r / ||r||, g = (||r||, 0, ...), threshold of the inner test.
 // inner_rel > 0 (FGMRES on the error equation): the cycle's inner test is
 // |g_{j+1}| <= inner_rel * beta.
+// In a graph, step 0's IF is armed and the other steps' IFs are cleared.
 __global__ void k_cycle_init(int n, const double* __restrict__ r, double* __restrict__ v0, DevScal* s,
-                             double tol, int stop_mode, double inner_rel) {
+                             double tol, int stop_mode, double inner_rel, int m, int graph) {
     const double beta = *(volatile double*)&s->rnorm;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -872,6 +905,9 @@ __global__ void k_cycle_init(int n, const double* __restrict__ r, double* __rest
                   : (stop_mode == KKT_STOP_NRBE) ? tol * (s->normA * s->xnorm + s->normb) : tol * s->rnorm0;
         s->j = 0;
         s->met = 0;
+        s->cycles += 1;
+        if (graph)
+            for (int i = 0; i < m; i++) cudaGraphSetConditional(s->h_step[i], i == 0 ? 1u : 0u);
     }
 }
 
@@ -888,7 +924,9 @@ __device__ __forceinline__ double pythagoras(double a, const double* h, int k) {
 // End of Arnoldi step j (one thread): H(:,j) = h (+ h2), h_{j+1,j} = hn,
 // previous Givens rotations applied, new rotation formed, g updated, the
 // inner stopping test sets s->met, j advances.
-__device__ void arnoldi_finish(DevScal* s, int j, double hn, bool add_h2, int stop_mode) {
+// In a graph, step j + 1's IF is armed only while the estimate has not met
+// the test and no breakdown occurred.
+__device__ void arnoldi_finish(DevScal* s, int j, double hn, bool add_h2, int stop_mode, int m, int graph) {
     s->hn = hn;
     double* Hj = s->H + j * (MAXM + 1);
     for (int i = 0; i <= j; i++) Hj[i] = add_h2 ? s->h[i] + s->h2[i] : s->h[i];
@@ -911,13 +949,14 @@ __device__ void arnoldi_finish(DevScal* s, int j, double hn, bool add_h2, int st
     const int met = (stop_mode == KKT_STOP_NRBE) ? (est <= s->thresh) : (est < s->thresh);
     s->met = met;
     s->j = j + 1;
+    if (graph && j + 1 < m) cudaGraphSetConditional(s->h_step[j + 1], (unsigned)(!met && hn > 0.0));
 }
 
 // Classical Gram-Schmidt, first projection: h_i = v_i . w for i <= j.
 // with_norm (one-reduction CGS): ||w||^2 is reduced with the h_i and the
 // last block finishes the Arnoldi step with h_{j+1,j} by Pythagoras.
 __global__ void k_cgs_dots(int n, const double* __restrict__ V, int64_t ld, const double* __restrict__ w,
-                           double* part, DevScal* s, int with_norm, int stop_mode) {
+                           double* part, DevScal* s, int with_norm, int stop_mode, int m, int graph) {
     __shared__ double sh[33];
     const int j = *(volatile int*)&s->j;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -942,7 +981,7 @@ __global__ void k_cgs_dots(int n, const double* __restrict__ V, int64_t ld, cons
     }
     if (!with_norm) return;
     const double nn = reduce_partials(part, j + 1, sh);
-    if (threadIdx.x == 0) arnoldi_finish(s, j, pythagoras(sqrt(nn), s->h, j + 1), false, stop_mode);
+    if (threadIdx.x == 0) arnoldi_finish(s, j, pythagoras(sqrt(nn), s->h, j + 1), false, stop_mode, m, graph);
 }
 
 // w -= V h (pass 0: h, then h2_i = v_i . w) or (pass 1: h2, then ||w||^2);
@@ -954,7 +993,7 @@ __global__ void k_cgs_dots(int n, const double* __restrict__ V, int64_t ld, cons
 // the Arnoldi step; the second projection then comes with the normalisation
 // (k_project_normalize).
 __global__ void k_cgs_update(int n, const double* __restrict__ V, int64_t ld, double* __restrict__ w, int pass,
-                             double* part, DevScal* s, int m, int stop_mode, int with_norm) {
+                             double* part, DevScal* s, int m, int stop_mode, int with_norm, int graph) {
     __shared__ double sh[33];
     __shared__ double hc[MAXM + 1];
     const int j = *(volatile int*)&s->j;
@@ -997,12 +1036,12 @@ __global__ void k_cgs_update(int n, const double* __restrict__ V, int64_t ld, do
         }
         if (!with_norm) return;
         const double nn = reduce_partials(part, j + 1, sh);
-        if (threadIdx.x == 0) arnoldi_finish(s, j, pythagoras(sqrt(nn), s->h2, j + 1), true, stop_mode);
+        if (threadIdx.x == 0) arnoldi_finish(s, j, pythagoras(sqrt(nn), s->h2, j + 1), true, stop_mode, m, graph);
         return;
     }
     double nn = reduce_partials(part, 0, sh);
     if (threadIdx.x != 0) return;
-    arnoldi_finish(s, j, sqrt(nn), true, stop_mode);
+    arnoldi_finish(s, j, sqrt(nn), true, stop_mode, m, graph);
 }
 
 // The projection left after a Pythagorean finish, fused with the

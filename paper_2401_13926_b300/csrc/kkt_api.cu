@@ -41,6 +41,14 @@ struct kkt_ctx {
     double *d_Ax = nullptr, *d_vals = nullptr;
     bool mixed = false;
     unsigned long long* solve_trace = nullptr;   // kkt_trace_solve only: 2n publish stamps
+    // CUDA graphs (kkt_opts.graphs): capture streams, the refactorization and
+    // solve graphs, and kernels per replayed part (for the launch count)
+    cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
+    bool capturing = false;
+    cudaGraph_t g_ref = nullptr, g_solve = nullptr;
+    cudaGraphExec_t gx_ref = nullptr, gx_solve = nullptr;
+    double g_solve_tol = 0.0;
+    int64_t gl_ref = 0, gl_pro = 0, gl_body = 0, gl_step = 0;
     int32_t repivots = 0;                         // kkt_repivot calls that succeeded in analysis
     double *d_b = nullptr, *d_x = nullptr, *d_y = nullptr, *d_xp = nullptr, *d_r = nullptr, *d_w = nullptr;
     double *d_V = nullptr, *d_Z = nullptr, *d_part = nullptr;
@@ -124,7 +132,56 @@ int cuda_fail(kkt_ctx* c, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
     } while (0)
 
+void drop_graph(cudaGraphExec_t* ex, cudaGraph_t* g) {
+    if (*ex) { cudaGraphExecDestroy(*ex); *ex = nullptr; }
+    if (*g) { cudaGraphDestroy(*g); *g = nullptr; }
+}
+
+thread_local const char* g_capture_where = "";   // the call that failed while building a graph
+
+// Captures `fill` (launches on c->stream, pointed at capture stream `level`
+// meanwhile) as a standalone graph.
+template <class F>
+cudaError_t capture_graph(kkt_ctx* c, int level, cudaGraph_t* out, F fill) {
+    cudaStream_t st = c->cap[level];
+    cudaStream_t saved = c->stream;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { g_capture_where = "cudaStreamBeginCapture"; return e; }
+    c->stream = st;
+    fill();
+    cudaError_t inner = cudaGetLastError();
+    c->stream = saved;
+    e = cudaStreamEndCapture(st, out);
+    if (inner != cudaSuccess) { g_capture_where = "a launch in the capture"; return inner; }
+    if (e != cudaSuccess) g_capture_where = "cudaStreamEndCapture";
+    return e;
+}
+
+// Adds `child` (copied, then destroyed) to g after `dep` (nullptr: none).
+cudaError_t add_child(cudaGraph_t g, const cudaGraphNode_t* dep, cudaGraph_t child, cudaGraphNode_t* node) {
+    cudaError_t e = cudaGraphAddChildGraphNode(node, g, dep, dep ? 1 : 0, child);
+    cudaGraphDestroy(child);
+    if (e != cudaSuccess) g_capture_where = "cudaGraphAddChildGraphNode";
+    return e;
+}
+
+// Adds a conditional node (WHILE or IF on h) to g after `dep`; its body in *body.
+cudaError_t add_conditional(cudaGraph_t g, const cudaGraphNode_t* dep, cudaGraphConditionalHandle h,
+                            cudaGraphConditionalNodeType type, cudaGraphNode_t* node, cudaGraph_t* body) {
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    cudaError_t e = cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &p);
+    if (e != cudaSuccess) { g_capture_where = "cudaGraphAddNode(conditional)"; return e; }
+    *body = p.conditional.phGraph_out[0];
+    return cudaSuccess;
+}
+
 void free_device(kkt_ctx* c) {
+    drop_graph(&c->gx_ref, &c->g_ref);
+    drop_graph(&c->gx_solve, &c->g_solve);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
     c->ev_used = 0;
@@ -179,7 +236,7 @@ constexpr size_t EV_PAIRS = 512;
 // Phase timer: a start event now, the matching end event from the returned
 // index after the launches of the phase.
 int phase_begin(kkt_ctx* c, int phase) {
-    if (!c->o.timing || c->ev_pool.empty()) return -1;
+    if (!c->o.timing || c->ev_pool.empty() || c->capturing) return -1;
     if (c->ev_used >= EV_PAIRS) return -1;   // pool full until the next drain
     size_t i = c->ev_used++;
     c->ev_phase[i] = phase;
@@ -379,6 +436,7 @@ void kkt_default_opts(kkt_opts* o) {
     o->ortho = KKT_ORTHO_CGS2;
     o->inner_tol = 1e-6;
     o->repivot = 0;
+    o->graphs = 0;
 }
 
 const char* kkt_strerror(int code) {
@@ -412,7 +470,8 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
         (c->o.cluster_blocks != 0 && c->o.cluster_blocks != 8 && c->o.cluster_blocks != 16) ||
         c->o.method < KKT_METHOD_FGMRES || c->o.method > KKT_METHOD_FGMRES_EE ||
         c->o.ortho < KKT_ORTHO_CGS2 || c->o.ortho > KKT_ORTHO_CGS1_PYTH ||
-        !(c->o.inner_tol > 0.0 && c->o.inner_tol <= 1.0) || (c->o.repivot != 0 && c->o.repivot != 1)) {
+        !(c->o.inner_tol > 0.0 && c->o.inner_tol <= 1.0) || (c->o.repivot != 0 && c->o.repivot != 1) ||
+        (c->o.graphs != 0 && c->o.graphs != 1)) {
         delete c;
         return KKT_ERR_INVALID;
     }
@@ -423,6 +482,8 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
     if (e == cudaSuccess) {
         if (!c->o.create_stream) c->stream = (cudaStream_t)c->o.stream;
         else { e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking); c->own_stream = true; }
+        for (int i = 0; i < 3 && e == cudaSuccess && c->o.graphs; i++)
+            e = cudaStreamCreateWithFlags(&c->cap[i], cudaStreamNonBlocking);
     }
     if (e != cudaSuccess) { delete c; return KKT_ERR_CUDA; }
     c->mixed = c->o.precision == KKT_PRECISION_MIXED;
@@ -452,6 +513,8 @@ void kkt_destroy(kkt_ctx* c) {
     cudaSetDevice(c->dev);
     cudaStreamSynchronize(c->stream);
     free_device(c);
+    for (cudaStream_t& st : c->cap)
+        if (st) { cudaStreamDestroy(st); st = nullptr; }
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -754,20 +817,52 @@ void refactor_launch(kkt_ctx* c, const double* vals, unsigned long long* trace) 
 }  // extern "C++"
 
 namespace {
+// The refactorization as one graph reading the values from d_vals.
+int build_refactor_graph(kkt_ctx* c) {
+    drop_graph(&c->gx_ref, &c->g_ref);
+    c->capturing = true;
+    g_capture_where = "";
+    const int64_t l0 = c->launches;
+    cudaError_t e = capture_graph(c, 0, &c->g_ref, [&] {
+        kkt::k_refactor_prep<<<1, 1, 0, c->stream>>>(c->d_s);
+        if (c->mixed) refactor_launch<float>(c, c->d_vals, nullptr);
+        else refactor_launch<double>(c, c->d_vals, nullptr);
+    });
+    c->capturing = false;
+    c->gl_ref = c->launches - l0 + 1;
+    c->launches = l0;
+    if (e != cudaSuccess) { drop_graph(&c->gx_ref, &c->g_ref); return cuda_fail(c, e, "refactor graph capture"); }
+    CK(cudaGraphInstantiate(&c->gx_ref, c->g_ref, 0));
+    return KKT_OK;
+}
+
 int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsigned long long* trace) {
     int rc = check_ctx(c, false);
     if (rc) return rc;
     if (!values) return KKT_ERR_INVALID;
     c->factored = false;
     const double* vals = values;
+    const bool graphs = c->o.graphs && !trace;
     if (!values_on_device) {
         CK(cudaMemcpyAsync(c->d_vals, values, sizeof(double) * (size_t)c->nnz_a, cudaMemcpyHostToDevice, c->stream));
         c->h2d += (int64_t)sizeof(double) * c->nnz_a;
         vals = c->d_vals;
+    } else if (graphs) {   // the graph reads its fixed buffer
+        CK(cudaMemcpyAsync(c->d_vals, values, sizeof(double) * (size_t)c->nnz_a, cudaMemcpyDeviceToDevice,
+                           c->stream));
+        vals = c->d_vals;
     }
-    kkt::k_refactor_prep<<<1, 1, 0, c->stream>>>(c->d_s);
-    if (c->mixed) refactor_launch<float>(c, vals, trace);
-    else refactor_launch<double>(c, vals, trace);
+    if (graphs) {
+        if (!c->gx_ref && (rc = build_refactor_graph(c))) return rc;
+        int t = phase_begin(c, KKT_PHASE_GRAPH_REFACTOR);
+        CK(cudaGraphLaunch(c->gx_ref, c->stream));
+        phase_end(c, t);
+        c->launches += c->gl_ref;
+    } else {
+        kkt::k_refactor_prep<<<1, 1, 0, c->stream>>>(c->d_s);
+        if (c->mixed) refactor_launch<float>(c, vals, trace);
+        else refactor_launch<double>(c, vals, trace);
+    }
     CK(cudaGetLastError());
     if ((rc = read_scalars(c))) return rc;
     c->nboost = c->h_s->nboost;
@@ -861,34 +956,191 @@ int kkt_matvec(kkt_ctx* c, const double* x, double* y, int on_device) {
 
 namespace {
 // One Arnoldi step's orthogonalisation (w = K z_j against V(:, 0..j)), the
-// Hessenberg column, Givens rotation and v_{j+1}, by kkt_opts.ortho.
-void arnoldi_ortho(kkt_ctx* c, int rb, int stop) {
+// Hessenberg column, Givens rotation and v_{j+1}, by kkt_opts.ortho.  `step`
+// != 0 inside a graph (the last kernel arms the next step's IF node).
+void arnoldi_ortho(kkt_ctx* c, int rb, int stop, int step) {
     const int m = c->m;
+    const int n = c->A.n;
     switch (c->o.ortho) {
         case KKT_ORTHO_CGS2_PYTH:
-            kkt::k_cgs_dots<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_V, c->ld, c->d_w, c->d_part, c->d_s,
-                                                                    0, stop);
-            kkt::k_cgs_update<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_V, c->ld, c->d_w, 0, c->d_part,
-                                                                      c->d_s, m, stop, 1);
-            kkt::k_project_normalize<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_w, c->d_V, c->ld, c->d_s, 1);
+            kkt::k_cgs_dots<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_V, c->ld, c->d_w, c->d_part, c->d_s, 0,
+                                                                    stop, m, step);
+            kkt::k_cgs_update<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_V, c->ld, c->d_w, 0, c->d_part,
+                                                                      c->d_s, m, stop, 1, step);
+            kkt::k_project_normalize<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_w, c->d_V, c->ld, c->d_s, 1);
             c->launches += 3;
             break;
         case KKT_ORTHO_CGS1_PYTH:
-            kkt::k_cgs_dots<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_V, c->ld, c->d_w, c->d_part, c->d_s,
-                                                                    1, stop);
-            kkt::k_project_normalize<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_w, c->d_V, c->ld, c->d_s, 0);
+            kkt::k_cgs_dots<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_V, c->ld, c->d_w, c->d_part, c->d_s, 1,
+                                                                    stop, m, step);
+            kkt::k_project_normalize<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_w, c->d_V, c->ld, c->d_s, 0);
             c->launches += 2;
             break;
         default:
-            kkt::k_cgs_dots<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_V, c->ld, c->d_w, c->d_part, c->d_s,
-                                                                    0, stop);
-            kkt::k_cgs_update<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_V, c->ld, c->d_w, 0, c->d_part,
-                                                                      c->d_s, m, stop, 0);
-            kkt::k_cgs_update<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_V, c->ld, c->d_w, 1, c->d_part,
-                                                                      c->d_s, m, stop, 0);
-            kkt::k_normalize<<<rb, kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_w, c->d_V, c->ld, c->d_s);
+            kkt::k_cgs_dots<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_V, c->ld, c->d_w, c->d_part, c->d_s, 0,
+                                                                    stop, m, 0);
+            kkt::k_cgs_update<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_V, c->ld, c->d_w, 0, c->d_part,
+                                                                      c->d_s, m, stop, 0, 0);
+            kkt::k_cgs_update<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_V, c->ld, c->d_w, 1, c->d_part,
+                                                                      c->d_s, m, stop, 0, step);
+            kkt::k_normalize<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_w, c->d_V, c->ld, c->d_s);
             c->launches += 4;
     }
+}
+
+// ---- launch sequences of a solve, shared by the host-driven loop and the
+// CUDA-graph capture (loop/step flags 0 outside graphs: inside, the kernels
+// set the graph's conditional handles held in DevScal).  None synchronises.
+int cap_of(const kkt_ctx* c) {   // the refinement's cap: cycles, or corrections
+    return c->o.method == KKT_METHOD_RICHARDSON ? c->o.max_cycles * c->m : c->o.max_cycles;
+}
+
+// x0 = (LU)^{-1} b, its residual and the refine-or-not decision
+void seq_prologue(kkt_ctx* c, const double* bd, double* xd, double tol, int loop) {
+    const int n = c->A.n, rb = red_blocks(c);
+    lu_apply(c, bd, xd);
+    int t = phase_begin(c, KKT_PHASE_SPMV);
+    kkt::k_residual<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, bd, xd, c->d_r,
+                                                            c->d_part, c->d_s);
+    phase_end(c, t);
+    kkt::k_decide<<<1, 1, 0, c->stream>>>(c->d_s, 0, tol, c->o.stop_mode, c->o.refine_delta, cap_of(c), loop);
+    c->launches += 2;
+}
+
+// classical iterative refinement: d = (LU)^{-1} rho, x += d, new residual
+void seq_richardson(kkt_ctx* c, const double* bd, double* xd, double tol, int loop) {
+    const int n = c->A.n, rb = red_blocks(c);
+    lu_apply(c, c->d_r, c->d_w);
+    int t = phase_begin(c, KKT_PHASE_UPDATE);
+    kkt::k_axpy<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_w, xd);
+    phase_end(c, t);
+    t = phase_begin(c, KKT_PHASE_SPMV);
+    kkt::k_residual<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, bd, xd, c->d_r,
+                                                            c->d_part, c->d_s);
+    phase_end(c, t);
+    kkt::k_decide<<<1, 1, 0, c->stream>>>(c->d_s, 2, tol, c->o.stop_mode, c->o.refine_delta, cap_of(c), loop);
+    c->launches += 3;
+}
+
+void seq_cycle_begin(kkt_ctx* c, double tol, int step) {
+    const double inner_rel = c->o.method == KKT_METHOD_FGMRES_EE ? c->o.inner_tol : 0.0;
+    int t = phase_begin(c, KKT_PHASE_UPDATE);
+    kkt::k_cycle_init<<<red_blocks(c), kkt::RED_THREADS, 0, c->stream>>>(c->A.n, c->d_r, c->d_V, c->d_s, tol,
+                                                                         c->o.stop_mode, inner_rel, c->m, step);
+    phase_end(c, t);
+    c->launches += 1;
+}
+
+// Arnoldi step j: z_j = M^{-1} v_j, w = K z_j, orthogonalisation
+void seq_arnoldi_step(kkt_ctx* c, int j, int step) {
+    const int n = c->A.n, rb = red_blocks(c);
+    double* vj = c->d_V + (int64_t)j * c->ld;
+    double* zj = c->d_Z + (int64_t)j * c->ld;
+    lu_apply(c, vj, zj);
+    int t = phase_begin(c, KKT_PHASE_SPMV);
+    kkt::k_spmv<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, zj, c->d_w);
+    phase_end(c, t);
+    t = phase_begin(c, KKT_PHASE_ORTHO);
+    arnoldi_ortho(c, rb, c->o.stop_mode, step);
+    phase_end(c, t);
+    c->launches += 1;
+}
+
+// cycle end: y = R^{-1} g, x += Z y, true residual, accept or restart
+void seq_cycle_end(kkt_ctx* c, const double* bd, double* xd, double tol, int loop) {
+    const int n = c->A.n, rb = red_blocks(c);
+    int t = phase_begin(c, KKT_PHASE_UPDATE);
+    kkt::k_hess_solve<<<1, 32, 0, c->stream>>>(c->d_s);
+    kkt::k_update_x<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Z, c->ld, xd, c->d_s);
+    phase_end(c, t);
+    t = phase_begin(c, KKT_PHASE_SPMV);
+    kkt::k_residual<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, bd, xd, c->d_r,
+                                                            c->d_part, c->d_s);
+    phase_end(c, t);
+    kkt::k_decide<<<1, 1, 0, c->stream>>>(c->d_s, c->o.method == KKT_METHOD_FGMRES_EE ? 3 : 1, tol,
+                                          c->o.stop_mode, c->o.refine_delta, cap_of(c), loop);
+    c->launches += 4;
+}
+
+// The whole solve as one graph: child(prologue) -> WHILE(loop) { child(cycle
+// begin) -> IF(step) { child(Arnoldi step 0) } -> ... -> IF(step) {
+// child(step m-1) } -> child(cycle end) } for FGMRES and FGMRES_EE, or
+// WHILE(loop) { child(correction) } for RICHARDSON.  Straight-line parts are
+// captured as standalone graphs; the conditional nodes are added with the
+// graph API (a conditional body cannot take nodes while its parent graph is
+// being captured).  Inputs d_b, iterate d_x.
+int build_solve_graph(kkt_ctx* c, double tol) {
+    drop_graph(&c->gx_solve, &c->g_solve);
+    CK(cudaGraphCreate(&c->g_solve, 0));
+    // a conditional node's handle belongs to the graph that holds the node,
+    // and drives that node only: one for the WHILE, one per Arnoldi-step IF
+    cudaGraphConditionalHandle loop = 0;
+    cudaGraphConditionalHandle steps[kkt::MAXM] = {};
+    CK(cudaGraphConditionalHandleCreate(&loop, c->g_solve, 0, 0));
+    c->capturing = true;
+    g_capture_where = "";
+    const int64_t l0 = c->launches;
+    int64_t l_pro = 0, l_body = 0, l_step = 0;
+    auto build = [&]() -> cudaError_t {
+        cudaGraph_t part;
+        cudaGraphNode_t pro, wn, prev;
+        cudaGraph_t body;
+        int64_t mark = c->launches;
+        cudaError_t e = capture_graph(c, 0, &part, [&] { seq_prologue(c, c->d_b, c->d_x, tol, 1); });
+        if (e != cudaSuccess || (e = add_child(c->g_solve, nullptr, part, &pro)) != cudaSuccess) return e;
+        l_pro = c->launches - mark;
+        if ((e = add_conditional(c->g_solve, &pro, loop, cudaGraphCondTypeWhile, &wn, &body)) != cudaSuccess) return e;
+        mark = c->launches;
+        if (c->o.method == KKT_METHOD_RICHARDSON) {
+            e = capture_graph(c, 0, &part, [&] { seq_richardson(c, c->d_b, c->d_x, tol, 1); });
+            if (e == cudaSuccess) e = add_child(body, nullptr, part, &prev);
+            l_body = c->launches - mark;
+            return e;
+        }
+        for (int j = 0; j < c->m; j++) {
+            if ((e = cudaGraphConditionalHandleCreate(&steps[j], body, 0, 0)) != cudaSuccess) {
+                g_capture_where = "cudaGraphConditionalHandleCreate(step)";
+                return e;
+            }
+        }
+        e = capture_graph(c, 0, &part, [&] { seq_cycle_begin(c, tol, 1); });
+        if (e != cudaSuccess || (e = add_child(body, nullptr, part, &prev)) != cudaSuccess) return e;
+        const int64_t begin_l = c->launches - mark;
+        for (int j = 0; j < c->m; j++) {
+            cudaGraphNode_t in, cn;
+            cudaGraph_t sb;
+            if ((e = add_conditional(body, &prev, steps[j], cudaGraphCondTypeIf, &in, &sb)) != cudaSuccess) return e;
+            const int64_t s0 = c->launches;
+            e = capture_graph(c, 0, &part, [&] { seq_arnoldi_step(c, j, 1); });
+            if (e != cudaSuccess || (e = add_child(sb, nullptr, part, &cn)) != cudaSuccess) return e;
+            l_step = c->launches - s0;
+            prev = in;
+        }
+        const int64_t s1 = c->launches;
+        e = capture_graph(c, 0, &part, [&] { seq_cycle_end(c, c->d_b, c->d_x, tol, 1); });
+        if (e != cudaSuccess || (e = add_child(body, &prev, part, &wn)) != cudaSuccess) return e;
+        l_body = begin_l + (c->launches - s1);
+        return cudaSuccess;
+    };
+    cudaError_t e = build();
+    c->capturing = false;
+    c->launches = l0;   // counted per replay instead
+    if (e != cudaSuccess) {
+        drop_graph(&c->gx_solve, &c->g_solve);
+        const int rc = cuda_fail(c, e, "solve graph");
+        c->detail += std::string(" (") + g_capture_where + ")";
+        return rc;
+    }
+    CK(cudaGraphInstantiate(&c->gx_solve, c->g_solve, 0));
+    // the kernels find the handles in the device scalars
+    CK(cudaMemcpyAsync(&c->d_s->h_loop, &loop, sizeof(loop), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(&c->d_s->h_step[0], steps, sizeof(steps), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->g_solve_tol = tol;
+    c->gl_pro = l_pro;
+    c->gl_body = l_body;
+    c->gl_step = l_step;
+    return KKT_OK;
 }
 
 int solve_impl(kkt_ctx* c, const double* b, double* x, int on_device, double tol, int* iters, double* nrbe);
@@ -917,93 +1169,70 @@ int solve_impl(kkt_ctx* c, const double* b, double* x, int on_device, double tol
     if (!b || !x || !(tol > 0)) return KKT_ERR_INVALID;
     const int n = c->A.n;
     const int m = c->m;
+    const bool graphs = c->o.graphs != 0;
     const double* bd = b;
     double* xd = x;
     if (!on_device) {
         CK(cudaMemcpyAsync(c->d_b, b, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
         c->h2d += (int64_t)sizeof(double) * n;
-        bd = c->d_b;
-        xd = c->d_x;
+    } else if (graphs) {   // the graph reads its fixed buffers
+        CK(cudaMemcpyAsync(c->d_b, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
     }
-    const int rb = red_blocks(c);
-    const int stop = c->o.stop_mode;
+    if (!on_device || graphs) { bd = c->d_b; xd = c->d_x; }
     CK(cudaMemsetAsync(&c->d_s->err, 0, sizeof(int) * 3, c->stream));
-    // x0 = (LU)^{-1} b, its residual and the refine-or-not decision
-    lu_apply(c, bd, xd);
-    int t = phase_begin(c, KKT_PHASE_SPMV);
-    kkt::k_residual<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, bd, xd, c->d_r,
-                                                            c->d_part, c->d_s);
-    phase_end(c, t);
-    kkt::k_decide<<<1, 1, 0, c->stream>>>(c->d_s, 0, tol, stop, c->o.refine_delta);
-    c->launches += 2;
-    CK(cudaGetLastError());
-    if ((rc = read_scalars(c))) return rc;
-    if ((rc = device_error(c))) { rearm(c); return rc; }
     int cycles = 0;
     int status = KKT_OK;
     const int method = c->o.method;
-    // classical iterative refinement: d = (LU)^{-1} rho, x += d, new residual
-    const int64_t max_steps = (int64_t)c->o.max_cycles * m;
-    int64_t steps = 0;
-    while (method == KKT_METHOD_RICHARDSON && !c->h_s->done) {
-        if (steps >= max_steps) { status = KKT_ERR_NOT_CONVERGED; break; }
-        steps++;
-        lu_apply(c, c->d_r, c->d_w);
-        t = phase_begin(c, KKT_PHASE_UPDATE);
-        kkt::k_axpy<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_w, xd);
+    if (graphs) {
+        if (!c->gx_solve || c->g_solve_tol != tol)
+            if ((rc = build_solve_graph(c, tol))) return rc;
+        int t = phase_begin(c, KKT_PHASE_GRAPH_SOLVE);
+        CK(cudaGraphLaunch(c->gx_solve, c->stream));
         phase_end(c, t);
-        t = phase_begin(c, KKT_PHASE_SPMV);
-        kkt::k_residual<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, bd, xd, c->d_r,
-                                                                c->d_part, c->d_s);
-        phase_end(c, t);
-        kkt::k_decide<<<1, 1, 0, c->stream>>>(c->d_s, 2, tol, stop, c->o.refine_delta);
-        c->launches += 3;
+        if ((rc = read_scalars(c))) return rc;
+        cycles = method == KKT_METHOD_RICHARDSON ? 0 : c->h_s->cycles;
+        c->launches += c->gl_pro + (method == KKT_METHOD_RICHARDSON ? (int64_t)c->h_s->iters * c->gl_body
+                                                                     : (int64_t)cycles * c->gl_body +
+                                                                           (int64_t)c->h_s->iters * c->gl_step);
+        if ((rc = device_error(c))) { rearm(c); return rc; }
+        if (c->h_s->not_converged) status = KKT_ERR_NOT_CONVERGED;
+    } else {
+        seq_prologue(c, bd, xd, tol, 0);
         CK(cudaGetLastError());
         if ((rc = read_scalars(c))) return rc;
-        if ((rc = device_error(c))) return rc;
-    }
-    const double inner_rel = method == KKT_METHOD_FGMRES_EE ? c->o.inner_tol : 0.0;
-    while (method != KKT_METHOD_RICHARDSON && !c->h_s->done) {
-        if (cycles >= c->o.max_cycles) { status = KKT_ERR_NOT_CONVERGED; break; }
-        cycles++;
-        t = phase_begin(c, KKT_PHASE_UPDATE);
-        kkt::k_cycle_init<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_r, c->d_V, c->d_s, tol, stop, inner_rel);
-        phase_end(c, t);
-        c->launches += 1;
-        for (int j = 0; j < m; j++) {
-            double* vj = c->d_V + (int64_t)j * c->ld;
-            double* zj = c->d_Z + (int64_t)j * c->ld;
-            lu_apply(c, vj, zj);
-            t = phase_begin(c, KKT_PHASE_SPMV);
-            kkt::k_spmv<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, zj, c->d_w);
-            phase_end(c, t);
-            t = phase_begin(c, KKT_PHASE_ORTHO);
-            arnoldi_ortho(c, rb, stop);
-            phase_end(c, t);
-            c->launches += 1;
+        if ((rc = device_error(c))) { rearm(c); return rc; }
+        const int64_t max_steps = (int64_t)c->o.max_cycles * m;
+        int64_t steps = 0;
+        while (method == KKT_METHOD_RICHARDSON && !c->h_s->done) {
+            if (steps >= max_steps) { status = KKT_ERR_NOT_CONVERGED; break; }
+            steps++;
+            seq_richardson(c, bd, xd, tol, 0);
             CK(cudaGetLastError());
             if ((rc = read_scalars(c))) return rc;
-            if ((rc = device_error(c))) { rearm(c); return rc; }
-            if (c->h_s->met || c->h_s->hn == 0.0) break;
+            if ((rc = device_error(c))) return rc;
         }
-        t = phase_begin(c, KKT_PHASE_UPDATE);
-        kkt::k_hess_solve<<<1, 32, 0, c->stream>>>(c->d_s);
-        kkt::k_update_x<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Z, c->ld, xd, c->d_s);
-        phase_end(c, t);
-        t = phase_begin(c, KKT_PHASE_SPMV);
-        kkt::k_residual<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, bd, xd, c->d_r,
-                                                                c->d_part, c->d_s);
-        phase_end(c, t);
-        kkt::k_decide<<<1, 1, 0, c->stream>>>(c->d_s, method == KKT_METHOD_FGMRES_EE ? 3 : 1, tol, stop,
-                                              c->o.refine_delta);
-        c->launches += 4;
-        CK(cudaGetLastError());
-        if ((rc = read_scalars(c))) return rc;
-        if ((rc = device_error(c))) return rc;
+        while (method != KKT_METHOD_RICHARDSON && !c->h_s->done) {
+            if (cycles >= c->o.max_cycles) { status = KKT_ERR_NOT_CONVERGED; break; }
+            cycles++;
+            seq_cycle_begin(c, tol, 0);
+            for (int j = 0; j < m; j++) {
+                seq_arnoldi_step(c, j, 0);
+                CK(cudaGetLastError());
+                if ((rc = read_scalars(c))) return rc;
+                if ((rc = device_error(c))) { rearm(c); return rc; }
+                if (c->h_s->met || c->h_s->hn == 0.0) break;
+            }
+            seq_cycle_end(c, bd, xd, tol, 0);
+            CK(cudaGetLastError());
+            if ((rc = read_scalars(c))) return rc;
+            if ((rc = device_error(c))) return rc;
+        }
     }
     if (!on_device) {
         CK(cudaMemcpyAsync(x, c->d_x, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
         c->d2h += (int64_t)sizeof(double) * n;
+    } else if (graphs) {
+        CK(cudaMemcpyAsync(x, c->d_x, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
     }
     CK(cudaStreamSynchronize(c->stream));
     phase_drain(c);
