@@ -334,6 +334,80 @@ int kkt_lu_solve_noalloc(int32_t n, const int64_t* Fp, const int32_t* Fj, const 
                          const double* Fx, const int32_t* P, const int32_t* Q, const double* b,
                          double* x, void* stream);
 
+/* ---- serving: many resident instances, steps in flight concurrently ----
+ *
+ * The paper solves one KKT sequence at a time and reuses the analysis,
+ * factor storage and Krylov space across the sequence (Sections 2.1, 3.1.1).
+ * A server holds many such sequences ("instances") resident on one GPU and
+ * keeps their refactor + solve steps in flight together: each instance is a
+ * context (kkt_create) with its own stream; a pool of host worker threads
+ * runs steps, one step per instance at a time, in each instance's submission
+ * order, so independent instances overlap on the GPU (continuous batching).
+ * Admission: an instance is admitted only if the device memory the admitted
+ * instances hold stays within the budget.  Results do not depend on the mix:
+ * each step runs the same kernels in the same order as alone.
+ */
+typedef struct kkt_server kkt_server;
+
+typedef struct {
+    int workers;          /* host threads = steps in flight at once (default 8, 1..256) */
+    int64_t hbm_budget;   /* device bytes the admitted instances may hold; 0 = 90% of the
+                             device memory free at kkt_server_create */
+    kkt_opts opts;        /* options of every instance's context (create_stream and
+                             stream are ignored: each instance makes its own stream) */
+} kkt_server_opts;
+
+typedef struct {
+    int status;           /* KKT_OK or the failing call's error (refactor or solve) */
+    int32_t iters;        /* refinement iterations */
+    double nrbe;          /* Eq. (nbre) of x */
+    double queue_ms;      /* submit -> a worker starts the step */
+    double run_ms;        /* refactor + solve, host wall time on the worker */
+} kkt_step_result;
+
+typedef struct {
+    int32_t instances;      /* admitted and open */
+    int64_t device_bytes;   /* held by the admitted instances */
+    int64_t hbm_budget;
+    int64_t submitted, completed;
+    int32_t in_flight;      /* steps running now */
+} kkt_server_info;
+
+/* Fill *o with the defaults above (kkt_default_opts for o->opts). */
+void kkt_server_default_opts(kkt_server_opts* o);
+
+int kkt_server_create(kkt_server** out, const kkt_server_opts* o);
+
+/*
+ * Admit a new instance: kkt_analyze of its pattern (values0 fixes the pivots,
+ * as in kkt_analyze) in a new context.  *instance gets its id.  Errors:
+ * KKT_ERR_OOM when its device memory would exceed the budget (nothing is
+ * kept; close an instance and retry), or kkt_create / kkt_analyze errors.
+ * The arrays are host memory and are not kept.
+ */
+int kkt_server_open(kkt_server* s, int32_t n, const int32_t* rowptr, const int32_t* colind,
+                    const double* values0, int64_t* instance);
+
+/*
+ * Queue one step of an instance: kkt_refactor(values) then kkt_solve(b)
+ * with tolerance tol, writing x (host, n doubles; written when the step
+ * completes -- keep it valid until kkt_server_wait returns).  values and b
+ * are copied at submit.  *ticket identifies the step for kkt_server_wait.
+ */
+int kkt_server_submit(kkt_server* s, int64_t instance, const double* values, const double* b,
+                      double* x, double tol, int64_t* ticket);
+
+/* Block until the step is done; its result in *r.  Each ticket is waited once. */
+int kkt_server_wait(kkt_server* s, int64_t ticket, kkt_step_result* r);
+
+/* Wait for the instance's queued steps, then free its context and memory. */
+int kkt_server_close(kkt_server* s, int64_t instance);
+
+int kkt_server_query(kkt_server* s, kkt_server_info* info);
+
+/* Wait for every queued step, close every instance, stop the workers. */
+void kkt_server_destroy(kkt_server* s);
+
 /* ---- host-only helpers (no GPU needed) ---- */
 
 /* Column order of kkt_analyze (approximate minimum degree on K^T K). */

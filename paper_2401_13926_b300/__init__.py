@@ -16,7 +16,7 @@ import os
 
 import numpy as np
 
-__all__ = ["KKTSolver", "KKTError", "order", "pivot", "lib", "LIB_PATH", "EXPORTS"]
+__all__ = ["KKTSolver", "KKTServer", "KKTError", "order", "pivot", "lib", "LIB_PATH", "EXPORTS"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libkkt_b300.so")
 
@@ -38,7 +38,8 @@ EXPORTS = [
     "kkt_matvec", "kkt_get_perm", "kkt_get_factor_sizes", "kkt_get_factors", "kkt_query",
     "kkt_destroy", "kkt_strerror", "kkt_last_error_detail", "kkt_order", "kkt_pivot",
     "kkt_get_phase_times", "kkt_lu_solve_noalloc", "kkt_selftest_wait", "kkt_trace_refactor",
-    "kkt_trace_solve", "kkt_repivot",
+    "kkt_trace_solve", "kkt_repivot", "kkt_server_default_opts", "kkt_server_create", "kkt_server_open",
+    "kkt_server_submit", "kkt_server_wait", "kkt_server_close", "kkt_server_query", "kkt_server_destroy",
 ]
 NOALLOC_MAX_N = 65536
 PHASES = ["gather", "refactor", "lsolve", "usolve", "spmv", "ortho", "update", "refactor_tail", "graph_refactor",
@@ -65,6 +66,20 @@ class _Info(C.Structure):
         ("norm_a_inf", C.c_double), ("analyze_ms", C.c_double), ("launches", C.c_int64),
         ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("repivots", C.c_int32),
     ]
+
+
+class _ServerOpts(C.Structure):
+    _fields_ = [("workers", C.c_int), ("hbm_budget", C.c_int64), ("opts", _Opts)]
+
+
+class _StepResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int32), ("nrbe", C.c_double), ("queue_ms", C.c_double),
+                ("run_ms", C.c_double)]
+
+
+class _ServerInfo(C.Structure):
+    _fields_ = [("instances", C.c_int32), ("device_bytes", C.c_int64), ("hbm_budget", C.c_int64),
+                ("submitted", C.c_int64), ("completed", C.c_int64), ("in_flight", C.c_int32)]
 
 
 class KKTError(RuntimeError):
@@ -111,8 +126,19 @@ def lib():
     L.kkt_trace_refactor.argtypes = [vp, vp, ip, vp, vp, C.POINTER(i32)]
     L.kkt_trace_solve.argtypes = [vp, vp, vp, ip, vp, vp, vp, vp]
     L.kkt_repivot.argtypes = [vp, vp, ip]
+    L.kkt_server_default_opts.argtypes = [C.POINTER(_ServerOpts)]
+    L.kkt_server_default_opts.restype = None
+    L.kkt_server_create.argtypes = [C.POINTER(vp), C.POINTER(_ServerOpts)]
+    L.kkt_server_open.argtypes = [vp, i32, vp, vp, vp, C.POINTER(i64)]
+    L.kkt_server_submit.argtypes = [vp, i64, vp, vp, vp, d, C.POINTER(i64)]
+    L.kkt_server_wait.argtypes = [vp, i64, C.POINTER(_StepResult)]
+    L.kkt_server_close.argtypes = [vp, i64]
+    L.kkt_server_query.argtypes = [vp, C.POINTER(_ServerInfo)]
+    L.kkt_server_destroy.argtypes = [vp]
+    L.kkt_server_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("kkt_default_opts", "kkt_destroy", "kkt_strerror", "kkt_last_error_detail"):
+        if name not in ("kkt_default_opts", "kkt_destroy", "kkt_strerror", "kkt_last_error_detail",
+                        "kkt_server_default_opts", "kkt_server_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -195,6 +221,25 @@ def lu_solve_noalloc(Fp, Fj, Fdiag, Fx, P, Q, b, x, stream=None):
     return x
 
 
+def _solver_opts(restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3, boost_eps=0.0,
+                 device=0, spin_limit=0, timing=False, trisolve="auto", tail_rows=0, cluster_blocks=0,
+                 precision="fp64", method="fgmres", ortho="cgs2", inner_tol=1e-6, repivot=False, graphs=False):
+    """kkt_opts from keyword arguments (defaults of kkt_default_opts)."""
+    o = _Opts()
+    lib().kkt_default_opts(C.byref(o))
+    o.restart, o.max_cycles, o.stop_mode = int(restart), int(max_cycles), STOP[stop_mode]
+    o.refine_delta, o.pivot_tol, o.boost_eps = float(refine_delta), float(pivot_tol), float(boost_eps)
+    o.device, o.spin_limit, o.timing = int(device), int(spin_limit), int(bool(timing))
+    o.trisolve = TRSV[trisolve]
+    o.tail_rows = int(tail_rows)
+    o.cluster_blocks = int(cluster_blocks)
+    o.precision = PRECISION[precision]
+    o.method, o.ortho, o.inner_tol = METHOD[method], ORTHO[ortho], float(inner_tol)
+    o.repivot = int(bool(repivot))
+    o.graphs = int(bool(graphs))
+    return o
+
+
 class KKTSolver:
     """One solver context: analyze once per pattern, then refactor + solve for
     every matrix of the sequence (Sections 1.3 and 2.1)."""
@@ -204,18 +249,9 @@ class KKTSolver:
                  tail_rows=0, cluster_blocks=0, precision="fp64", method="fgmres", ortho="cgs2",
                  inner_tol=1e-6, repivot=False, graphs=False):
         L = lib()
-        o = _Opts()
-        L.kkt_default_opts(C.byref(o))
-        o.restart, o.max_cycles, o.stop_mode = int(restart), int(max_cycles), STOP[stop_mode]
-        o.refine_delta, o.pivot_tol, o.boost_eps = float(refine_delta), float(pivot_tol), float(boost_eps)
-        o.device, o.spin_limit, o.timing = int(device), int(spin_limit), int(bool(timing))
-        o.trisolve = TRSV[trisolve]
-        o.tail_rows = int(tail_rows)
-        o.cluster_blocks = int(cluster_blocks)
-        o.precision = PRECISION[precision]
-        o.method, o.ortho, o.inner_tol = METHOD[method], ORTHO[ortho], float(inner_tol)
-        o.repivot = int(bool(repivot))
-        o.graphs = int(bool(graphs))
+        o = _solver_opts(restart, max_cycles, stop_mode, refine_delta, pivot_tol, boost_eps, device, spin_limit,
+                         timing, trisolve, tail_rows, cluster_blocks, precision, method, ortho, inner_tol, repivot,
+                         graphs)
         if stream is None:
             stream = _torch_current_stream(device)
         if stream is None:
@@ -357,3 +393,78 @@ class KKTSolver:
         inf = _Info()
         self._check(lib().kkt_query(self._h, C.byref(inf)), "kkt_query")
         return {k: getattr(inf, k) for k, _ in _Info._fields_}
+
+
+class KKTServer:
+    """Many resident KKT sequences on one GPU with their steps in flight
+    together (kkt_server_*): open() admits an instance (analysis + device
+    buffers, within the HBM budget), submit() queues a refactor + solve step
+    (host arrays; x is written when the step completes), wait() returns its
+    result.  Steps of one instance run in order; different instances overlap."""
+
+    def __init__(self, workers=8, hbm_budget=0, **solver_opts):
+        L = lib()
+        o = _ServerOpts()
+        L.kkt_server_default_opts(C.byref(o))
+        o.workers, o.hbm_budget = int(workers), int(hbm_budget)
+        o.opts = _solver_opts(**solver_opts)
+        h = C.c_void_p()
+        rc = L.kkt_server_create(C.byref(h), C.byref(o))
+        if rc:
+            raise KKTError(rc, "kkt_server_create")
+        self._h = h
+        self._n = {}
+        self._keep = {}
+
+    def open(self, rowptr, colind, values0):
+        rp, prp = _host(rowptr, np.int32)
+        ci, pci = _host(colind, np.int32)
+        v, pv = _host(values0, np.float64)
+        inst = C.c_int64()
+        rc = lib().kkt_server_open(self._h, len(rp) - 1, prp, pci, pv, C.byref(inst))
+        if rc:
+            raise KKTError(rc, "kkt_server_open")
+        self._n[inst.value] = len(rp) - 1
+        return inst.value
+
+    def submit(self, instance, values, b, tol=1e-12):
+        """Returns (ticket, x); x is filled when the step completes."""
+        v, pv = _host(values, np.float64)
+        bb, pb = _host(b, np.float64)
+        x = np.zeros(self._n[instance])
+        t = C.c_int64()
+        rc = lib().kkt_server_submit(self._h, int(instance), pv, pb, x.ctypes.data, float(tol), C.byref(t))
+        if rc:
+            raise KKTError(rc, "kkt_server_submit")
+        self._keep[t.value] = x
+        return t.value, x
+
+    def wait(self, ticket):
+        r = _StepResult()
+        rc = lib().kkt_server_wait(self._h, int(ticket), C.byref(r))
+        if rc:
+            raise KKTError(rc, "kkt_server_wait")
+        x = self._keep.pop(ticket)
+        return x, {k: getattr(r, k) for k, _ in _StepResult._fields_}
+
+    def close_instance(self, instance):
+        rc = lib().kkt_server_close(self._h, int(instance))
+        if rc:
+            raise KKTError(rc, "kkt_server_close")
+        self._n.pop(instance, None)
+
+    def info(self):
+        i = _ServerInfo()
+        lib().kkt_server_query(self._h, C.byref(i))
+        return {k: getattr(i, k) for k, _ in _ServerInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().kkt_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
