@@ -172,6 +172,7 @@ typedef struct {
     int64_t h2d_bytes;     /* host->device bytes copied by refactor/solve calls so far */
     int64_t d2h_bytes;     /* device->host bytes copied by refactor/solve calls so far */
     int32_t repivots;      /* pivoting refactorizations run by kkt_repivot so far */
+    int32_t tail_rows;     /* rows refactored one block per row (the rest: one warp per row) */
 } kkt_info;
 
 /* Fill *o with the defaults above. */
@@ -272,6 +273,20 @@ int kkt_get_phase_times(kkt_ctx* c, double* ms, int64_t* counts, int reset);
  */
 int kkt_trace_refactor(kkt_ctx* c, const double* values, int values_on_device, int64_t* t_start,
                        int64_t* t_publish, int32_t* t0_out);
+
+/*
+ * Autotuner: times kkt_refactor(values) + kkt_lu_solve(b) (median of `reps`
+ * runs after one warm-up) for each schedule of the refactorization and the
+ * solves -- the block-per-row part of the refactorization (the last 32767,
+ * 16384, 8192 or 4096 rows at most) times the solve schedule (cluster of 16
+ * or 8 blocks, or whole-GPU) -- and keeps the fastest in the context
+ * (kkt_query: tail_rows, trisolve_cluster).  Every schedule computes the
+ * same bits, so tuning changes only speed.  values, b as in kkt_refactor and
+ * kkt_lu_solve; with on_device != 0 one n-vector of device memory is added
+ * to the context.  *best_ms (may be NULL) gets the chosen time.  The factors
+ * must be recomputed afterwards (kkt_refactor).
+ */
+int kkt_tune(kkt_ctx* c, const double* values, const double* b, int on_device, int reps, double* best_ms);
 
 /*
  * Profiling: kkt_lu_solve (Section 1.3, the direct solve with the current

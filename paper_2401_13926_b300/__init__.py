@@ -38,7 +38,7 @@ EXPORTS = [
     "kkt_matvec", "kkt_get_perm", "kkt_get_factor_sizes", "kkt_get_factors", "kkt_query",
     "kkt_destroy", "kkt_strerror", "kkt_last_error_detail", "kkt_order", "kkt_pivot",
     "kkt_get_phase_times", "kkt_lu_solve_noalloc", "kkt_selftest_wait", "kkt_trace_refactor",
-    "kkt_trace_solve", "kkt_repivot", "kkt_server_default_opts", "kkt_server_create", "kkt_server_open",
+    "kkt_trace_solve", "kkt_repivot", "kkt_tune", "kkt_server_default_opts", "kkt_server_create", "kkt_server_open",
     "kkt_server_submit", "kkt_server_wait", "kkt_server_close", "kkt_server_query", "kkt_server_destroy",
 ]
 NOALLOC_MAX_N = 65536
@@ -64,7 +64,7 @@ class _Info(C.Structure):
         ("device_bytes", C.c_int64), ("nboost", C.c_int32), ("last_iters", C.c_int32),
         ("last_cycles", C.c_int32), ("trisolve_cluster", C.c_int32), ("last_nrbe", C.c_double), ("last_rnorm0", C.c_double),
         ("norm_a_inf", C.c_double), ("analyze_ms", C.c_double), ("launches", C.c_int64),
-        ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("repivots", C.c_int32),
+        ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("repivots", C.c_int32), ("tail_rows", C.c_int32),
     ]
 
 
@@ -126,6 +126,7 @@ def lib():
     L.kkt_trace_refactor.argtypes = [vp, vp, ip, vp, vp, C.POINTER(i32)]
     L.kkt_trace_solve.argtypes = [vp, vp, vp, ip, vp, vp, vp, vp]
     L.kkt_repivot.argtypes = [vp, vp, ip]
+    L.kkt_tune.argtypes = [vp, vp, vp, ip, ip, C.POINTER(d)]
     L.kkt_server_default_opts.argtypes = [C.POINTER(_ServerOpts)]
     L.kkt_server_default_opts.restype = None
     L.kkt_server_create.argtypes = [C.POINTER(vp), C.POINTER(_ServerOpts)]
@@ -297,6 +298,18 @@ class KKTSolver:
     def refactor(self, values):
         keep, p, dev = _ptr(values, np.float64)
         self._check(lib().kkt_refactor(self._h, p, dev), "kkt_refactor")
+
+    def tune(self, values, b, reps=3):
+        """kkt_tune: pick the fastest refactorization/solve schedule for this
+        matrix (same bits either way); returns the chosen ms of refactor +
+        lu_solve.  Refactor again afterwards."""
+        kv, pv, dev = _ptr(values, np.float64)
+        kb, pb, devb = _ptr(b, np.float64)
+        if dev != devb:
+            raise ValueError("values and b must both be host or both be device arrays")
+        best = C.c_double()
+        self._check(lib().kkt_tune(self._h, pv, pb, dev, int(reps), C.byref(best)), "kkt_tune")
+        return best.value
 
     def repivot(self, values):
         """kkt_repivot: pivoting factorization of `values` on the host (Q

@@ -555,6 +555,47 @@ int kkt_pivot(int32_t n, const int32_t* rowptr, const int32_t* colind, const dou
 }
 
 namespace {
+// The block-per-row part of the refactorization: the last rows (at most
+// kkt_opts.tail_rows, default 32767), as many as fit their longest row in
+// shared memory.
+int setup_tail(kkt_ctx* c) {
+    const int n = c->A.n;
+    int T = std::min<int>(n, c->o.tail_rows > 0 ? std::min(c->o.tail_rows, 32767) : TAIL_MAX_ROWS);
+    c->t0 = n;
+    c->tail_smem = 0;
+    while (T > 0) {
+        int t0 = n - T;
+        int64_t maxlen = 0, maxsteps = 0;
+        for (int32_t i = t0; i < n; i++) {
+            maxlen = std::max<int64_t>(maxlen, c->lay.Fp[i + 1] - c->lay.Fp[i]);
+            maxsteps = std::max<int64_t>(maxsteps, c->lay.Fdiag[i] - c->lay.Fp[i]);
+        }
+        // shared memory: step descriptors, row values and columns, and a
+        // position map for the last (at most TAIL_MAP_COLS) columns
+        const int mlo = std::max(t0, n - TAIL_MAP_COLS);
+        const size_t vsize = c->mixed ? sizeof(float) : sizeof(double);
+        size_t smem = 16 * (size_t)std::max<int64_t>(maxsteps, 1) + (vsize + 4) * (size_t)maxlen +
+                      2 * (size_t)(n - mlo);
+        if (smem <= TAIL_SMEM_MAX && maxlen <= 32767) {
+            c->t0 = t0;
+            c->tail_mlo = mlo;
+            c->tail_smem = smem;
+            c->tail_max_steps = (int)std::max<int64_t>(maxsteps, 1);
+            c->tail_max_len = (int)maxlen;
+            break;
+        }
+        T /= 2;
+    }
+    if (c->t0 < n) {
+        int per_sm = 0;
+        const void* fn = c->mixed ? (const void*)kkt::k_refactor_tail<float>
+                                  : (const void*)kkt::k_refactor_tail<double>;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kkt::TAIL_THREADS, c->tail_smem));
+        c->tail_blocks = std::max(1, per_sm) * c->num_sms;
+    }
+    return KKT_OK;
+}
+
 int setup_device(kkt_ctx* c, const kkt::ColStructure& S, std::chrono::steady_clock::time_point t0);
 }
 
@@ -661,41 +702,7 @@ int setup_device(kkt_ctx* c, const kkt::ColStructure& S, std::chrono::steady_clo
     fill_y_sentinel(c);
     if (c->o.trisolve == KKT_TRSV_AUTO) pick_cluster(c);
     else c->cluster = 0;
-    {   // refactorization tail: the last rows, if their longest row fits in shared memory
-        int T = std::min<int>(n, c->o.tail_rows > 0 ? std::min(c->o.tail_rows, 32767) : TAIL_MAX_ROWS);
-        c->t0 = n;
-        c->tail_smem = 0;
-        while (T > 0) {
-            int t0 = n - T;
-            int64_t maxlen = 0, maxsteps = 0;
-            for (int32_t i = t0; i < n; i++) {
-                maxlen = std::max<int64_t>(maxlen, c->lay.Fp[i + 1] - c->lay.Fp[i]);
-                maxsteps = std::max<int64_t>(maxsteps, c->lay.Fdiag[i] - c->lay.Fp[i]);
-            }
-            // shared memory: step descriptors, row values and columns, and a
-            // position map for the last (at most TAIL_MAP_COLS) columns
-            const int mlo = std::max(t0, n - TAIL_MAP_COLS);
-            const size_t vsize = c->mixed ? sizeof(float) : sizeof(double);
-            size_t smem = 16 * (size_t)std::max<int64_t>(maxsteps, 1) + (vsize + 4) * (size_t)maxlen +
-                          2 * (size_t)(n - mlo);
-            if (smem <= TAIL_SMEM_MAX && maxlen <= 32767) {
-                c->t0 = t0;
-                c->tail_mlo = mlo;
-                c->tail_smem = smem;
-                c->tail_max_steps = (int)std::max<int64_t>(maxsteps, 1);
-                c->tail_max_len = (int)maxlen;
-                break;
-            }
-            T /= 2;
-        }
-        if (c->t0 < n) {
-            int per_sm = 0;
-            const void* fn = c->mixed ? (const void*)kkt::k_refactor_tail<float>
-                                      : (const void*)kkt::k_refactor_tail<double>;
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kkt::TAIL_THREADS, c->tail_smem));
-            c->tail_blocks = std::max(1, per_sm) * c->num_sms;
-        }
-    }
+    if ((rc = setup_tail(c))) return rc;
     if ((rc = dalloc(c, &c->d_s, 1))) return rc;
     CK(cudaMemsetAsync(c->d_s, 0, sizeof(DevScal), c->stream));
     CK(cudaMallocHost(&c->h_s, sizeof(DevScal)));
@@ -896,6 +903,71 @@ int kkt_lu_solve(kkt_ctx* c, const double* b, double* x, int on_device) {
     if ((rc = read_scalars(c))) return rc;
     if ((rc = device_error(c))) rearm(c);
     return rc;
+}
+
+int kkt_tune(kkt_ctx* c, const double* values, const double* b, int on_device, int reps, double* best_ms) {
+    int rc = check_ctx(c, false);
+    if (rc) return rc;
+    if (!values || !b || reps < 1) return KKT_ERR_INVALID;
+    const int n = c->A.n;
+    double* x = nullptr;
+    std::vector<double> hx;
+    if (on_device) {
+        if ((rc = dalloc(c, &x, (size_t)n))) return rc;   // tuning buffer, freed with the context
+    } else {
+        hx.resize(n);
+        x = hx.data();
+    }
+    struct Cand { int trisolve, cluster_blocks, tail_rows; };
+    std::vector<Cand> cands;
+    for (int tr : {0, 16384, 8192, 4096}) {
+        for (int cb : {16, 8}) cands.push_back({KKT_TRSV_AUTO, cb, tr});
+        cands.push_back({KKT_TRSV_GLOBAL, 0, tr});
+    }
+    const kkt_opts saved = c->o;
+    double best = -1.0;
+    Cand pick{saved.trisolve, saved.cluster_blocks, saved.tail_rows};
+    auto apply = [&](const Cand& k) -> int {
+        c->o.trisolve = k.trisolve;
+        c->o.cluster_blocks = k.cluster_blocks;
+        c->o.tail_rows = k.tail_rows;
+        drop_graph(&c->gx_ref, &c->g_ref);
+        drop_graph(&c->gx_solve, &c->g_solve);
+        int r = setup_tail(c);
+        if (r) return r;
+        if (k.trisolve == KKT_TRSV_AUTO) {
+            pick_cluster(c);
+            if (c->cluster != k.cluster_blocks) return KKT_ERR_INVALID;   // does not fit or cannot be scheduled
+        } else {
+            c->cluster = 0;
+        }
+        return KKT_OK;
+    };
+    for (const Cand& k : cands) {
+        if (apply(k)) continue;
+        std::vector<double> t;
+        bool ok = true;
+        for (int r = 0; r <= reps && ok; r++) {   // the first run warms up
+            const auto t0 = std::chrono::steady_clock::now();
+            ok = kkt_refactor(c, values, on_device) == KKT_OK && kkt_lu_solve(c, b, x, on_device) == KKT_OK;
+            if (r > 0) t.push_back(std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+        }
+        if (!ok) continue;
+        std::sort(t.begin(), t.end());
+        const double med = t[t.size() / 2];
+        if (best < 0 || med < best) { best = med; pick = k; }
+    }
+    if (best < 0) {   // nothing ran: keep the previous configuration
+        c->o = saved;
+        apply(Cand{saved.trisolve, saved.cluster_blocks, saved.tail_rows});
+        c->detail = "kkt_tune: no configuration ran";
+        return KKT_ERR_STATE;
+    }
+    rc = apply(pick);
+    if (rc) return rc;
+    c->factored = false;   // factors must be recomputed by the caller's next kkt_refactor
+    if (best_ms) *best_ms = best;
+    return KKT_OK;
 }
 
 int kkt_trace_solve(kkt_ctx* c, const double* b, double* x, int on_device, int32_t* listL, int32_t* listU,
@@ -1317,6 +1389,7 @@ int kkt_query(kkt_ctx* c, kkt_info* info) {
     info->h2d_bytes = c->h2d;
     info->d2h_bytes = c->d2h;
     info->repivots = c->repivots;
+    info->tail_rows = c->A.n - c->t0;
     return KKT_OK;
 }
 
