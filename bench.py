@@ -229,11 +229,6 @@ def oracle_sample(seq, seconds, steps=None):
 
 def run_reference(args):
     rank, world, _ = dist_env()
-    # ---- serving: several independent sequences of the same workload resident
-    # at once, their steps in flight together (kkt_server_*)
-    serving = None
-    if args.serve_instances > 0:
-        serving = serve_measure(K, args, rank)
     if rank != 0:
         return
     from paper_2401_13926_b300.workload import KKTSequence
@@ -408,6 +403,11 @@ def run_ours(args):
                  "converged": ok2, "max_cycles": cyc2, "nrbe": [float(f"{v:.3g}") for v in nr2],
                  "phase_ms_per_step": {p: round(ph2[p][0] / seq.M, 4) for p in ph2}}
         s2.close()
+    # ---- serving: several independent sequences of the same workload resident
+    # at once, their steps in flight together (kkt_server_*)
+    serving = None
+    if args.serve_instances > 0:
+        serving = serve_measure(K, args, rank)
     if rank != 0:
         return
 

@@ -107,6 +107,10 @@ typedef struct {
                              round trip per step); captured on first use, again when tol
                              changes.  Same kernels in the same order, so the same results.
                              0 = launch from the host (default) */
+    int tail_warp_rows;   /* 1 (default): the leading short rows of the block-per-row part
+                             are refactored one per warp (eight per block) while they fit
+                             an eighth of the block's shared memory; 0: all of it one row
+                             per block.  Same arithmetic either way. */
 } kkt_opts;
 
 /* Refinement methods (Section 2.1).  FGMRES: FGMRES(m) with M = LU as right
@@ -172,7 +176,9 @@ typedef struct {
     int64_t h2d_bytes;     /* host->device bytes copied by refactor/solve calls so far */
     int64_t d2h_bytes;     /* device->host bytes copied by refactor/solve calls so far */
     int32_t repivots;      /* pivoting refactorizations run by kkt_repivot so far */
-    int32_t tail_rows;     /* rows refactored one block per row (the rest: one warp per row) */
+    int32_t tail_rows;     /* rows refactored in shared memory (the rest: one warp per row,
+                              values in global memory) */
+    int32_t tail_warp_rows; /* of those, rows refactored one per warp (the rest one per block) */
 } kkt_info;
 
 /* Fill *o with the defaults above. */
@@ -279,7 +285,8 @@ int kkt_trace_refactor(kkt_ctx* c, const double* values, int values_on_device, i
  * runs after one warm-up) for each schedule of the refactorization and the
  * solves -- the block-per-row part of the refactorization (the last 32767,
  * 16384, 8192 or 4096 rows at most) times the solve schedule (cluster of 16
- * or 8 blocks, or whole-GPU) -- and keeps the fastest in the context
+ * or 8 blocks, or whole-GPU), with and without the warp-per-row mode of the
+ * leading short rows -- and keeps the fastest in the context
  * (kkt_query: tail_rows, trisolve_cluster).  Every schedule computes the
  * same bits, so tuning changes only speed.  values, b as in kkt_refactor and
  * kkt_lu_solve; with on_device != 0 one n-vector of device memory is added

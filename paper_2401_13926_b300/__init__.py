@@ -53,7 +53,7 @@ class _Opts(C.Structure):
         ("device", C.c_int), ("create_stream", C.c_int), ("stream", C.c_void_p), ("spin_limit", C.c_int64),
         ("timing", C.c_int), ("trisolve", C.c_int), ("cluster_blocks", C.c_int), ("tail_rows", C.c_int),
         ("method", C.c_int), ("ortho", C.c_int), ("inner_tol", C.c_double), ("repivot", C.c_int),
-        ("graphs", C.c_int),
+        ("graphs", C.c_int), ("tail_warp_rows", C.c_int),
     ]
 
 
@@ -65,6 +65,7 @@ class _Info(C.Structure):
         ("last_cycles", C.c_int32), ("trisolve_cluster", C.c_int32), ("last_nrbe", C.c_double), ("last_rnorm0", C.c_double),
         ("norm_a_inf", C.c_double), ("analyze_ms", C.c_double), ("launches", C.c_int64),
         ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("repivots", C.c_int32), ("tail_rows", C.c_int32),
+        ("tail_warp_rows", C.c_int32),
     ]
 
 
@@ -224,7 +225,8 @@ def lu_solve_noalloc(Fp, Fj, Fdiag, Fx, P, Q, b, x, stream=None):
 
 def _solver_opts(restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3, boost_eps=0.0,
                  device=0, spin_limit=0, timing=False, trisolve="auto", tail_rows=0, cluster_blocks=0,
-                 precision="fp64", method="fgmres", ortho="cgs2", inner_tol=1e-6, repivot=False, graphs=False):
+                 precision="fp64", method="fgmres", ortho="cgs2", inner_tol=1e-6, repivot=False, graphs=False,
+                 tail_warp_rows=True):
     """kkt_opts from keyword arguments (defaults of kkt_default_opts)."""
     o = _Opts()
     lib().kkt_default_opts(C.byref(o))
@@ -238,6 +240,7 @@ def _solver_opts(restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, 
     o.method, o.ortho, o.inner_tol = METHOD[method], ORTHO[ortho], float(inner_tol)
     o.repivot = int(bool(repivot))
     o.graphs = int(bool(graphs))
+    o.tail_warp_rows = int(bool(tail_warp_rows))
     return o
 
 
@@ -248,11 +251,11 @@ class KKTSolver:
     def __init__(self, restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3,
                  boost_eps=0.0, device=0, stream=None, spin_limit=0, timing=False, trisolve="auto",
                  tail_rows=0, cluster_blocks=0, precision="fp64", method="fgmres", ortho="cgs2",
-                 inner_tol=1e-6, repivot=False, graphs=False):
+                 inner_tol=1e-6, repivot=False, graphs=False, tail_warp_rows=True):
         L = lib()
         o = _solver_opts(restart, max_cycles, stop_mode, refine_delta, pivot_tol, boost_eps, device, spin_limit,
                          timing, trisolve, tail_rows, cluster_blocks, precision, method, ortho, inner_tol, repivot,
-                         graphs)
+                         graphs, tail_warp_rows)
         if stream is None:
             stream = _torch_current_stream(device)
         if stream is None:

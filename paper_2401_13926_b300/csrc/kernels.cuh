@@ -61,6 +61,7 @@ struct DevScal {
     // sync-free scheduling
     unsigned gen_fact;
     unsigned ticket_fact, ticket_l, ticket_u;
+    unsigned ticket_mid;   // warp-per-row part of the refactorization tail
     unsigned red_count;
     // errors
     int err;               // first error code (0 = none)
@@ -290,7 +291,10 @@ __global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t*
 // (armed with SENTINEL by the gather) is the row's completion flag.
 constexpr int TAIL_THREADS = 256;
 
-__global__ void k_refactor_prep_tail(DevScal* s) { s->ticket_fact = 0; }
+__global__ void k_refactor_prep_tail(DevScal* s) {
+    s->ticket_fact = 0;
+    s->ticket_mid = 0;
+}
 
 // One step's worth of U(k,:) for one thread: up to TAIL_E entries
 // (columns and values) and the pivot reciprocal of row k, loaded two steps
@@ -351,10 +355,83 @@ __device__ __forceinline__ bool tail_wait(const T* p, T* v, DevScal* s, long lon
     return true;
 }
 
+// First position in cols[lo, len) holding column c, or -1.
+__device__ __forceinline__ int slice_pos(const int32_t* cols, int lo, int len, int c) {
+    int hi = len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cols[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    return (lo < len && cols[lo] == c) ? lo : -1;
+}
+
+// One short tail row by one warp, its values, columns and step descriptors
+// in the warp's slice of shared memory: the same steps, the same fused
+// multiply-add per entry in ascending k, and the same publication as a
+// block row.  Returns false if a wait gave up.
+template <typename T>
+__device__ bool tail_warp_row(int row, int t0, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
+                              const int64_t* __restrict__ Fdiag, T* Fx, T* rinv, const double* __restrict__ vals,
+                              const int64_t* __restrict__ fsrc, DevScal* s, T boost, long long limit,
+                              unsigned long long* trace, StepDesc* sd, T* w, int32_t* cols) {
+    const int lane = threadIdx.x & 31;
+    if (trace && lane == 0) trace[2 * (size_t)(row - t0)] = globaltimer_ns();
+    const int64_t b = Fp[row], d = Fdiag[row], e = Fp[row + 1];
+    const int len = (int)(e - b);
+    const int nsteps = (int)(d - b);
+    for (int q = lane; q < len; q += 32) {
+        const int64_t src = fsrc[b + q];
+        w[q] = src >= 0 ? (T)vals[src] : T(0);
+        const int c = Fj[b + q];
+        cols[q] = c;
+        if (q < nsteps) {
+            const int64_t dk = Fdiag[c];
+            sd[q] = StepDesc{dk, c, (int32_t)(Fp[c + 1] - dk - 1)};
+        }
+    }
+    __syncwarp();
+    for (int step = 0; step < nsteps; step++) {
+        const StepDesc dsc = sd[step];
+        T rk = ld_relaxed(&rinv[dsc.k]);
+        int ok = tail_wait(&rinv[dsc.k], &rk, s, limit, row);
+        const T l = w[step] * rk;   // l_ik = w_k * (1/u_kk)
+        for (int e2 = lane; e2 < dsc.cnt && ok; e2 += 32) {
+            const int64_t q = dsc.dk + 1 + e2;
+            T v = ld_relaxed(&Fx[q]);
+            if (!tail_wait(&Fx[q], &v, s, limit, row)) { ok = 0; break; }
+            const int pos = slice_pos(cols, step + 1, len, Fj[q]);
+            if (pos < 0) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
+            w[pos] = fma(-l, v, w[pos]);
+        }
+        if (!__all_sync(0xffffffffu, ok)) return false;
+        __syncwarp();
+        if (lane == 0) w[step] = l;   // nobody else touches position `step` any more
+        __syncwarp();
+    }
+    // publish: every value but the diagonal, then (lane 0) the pivot
+    for (int q = lane; q < len; q += 32)
+        if (b + q != d) st_relaxed(&Fx[b + q], w[q]);
+    if (lane == 0) {
+        T u = w[d - b];
+        int fail = 0;
+        if (!isfinite(u)) { raise_error(s, KKT_ERR_NONFINITE, row); fail = 1; }
+        else if (boost > 0.0) {
+            if (fabs(u) < boost) { u = (u < 0.0) ? -boost : boost; atomicAdd(&s->nboost, 1); }
+        } else if (u == 0.0) { raise_error(s, KKT_ERR_ZERO_PIVOT, row); fail = 1; }
+        if (!fail) {
+            st_relaxed(&Fx[d], u);
+            st_relaxed(&rinv[row], rcp_rn(u));
+            if (trace) trace[2 * (size_t)(row - t0) + 1] = globaltimer_ns();
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TAIL_THREADS)
-k_refactor_tail(int t0, int nrows, int mlo, int max_steps, int max_len, const int64_t* __restrict__ Fp,
-                const int32_t* __restrict__ Fj,
+k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, int wsteps, int wlen,
+                const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
                 const int64_t* __restrict__ Fdiag, T* Fx, T* rinv, const double* __restrict__ vals,
                 const int64_t* __restrict__ fsrc, DevScal* s, double boost_eps, long long limit,
                 unsigned long long* trace) {
@@ -362,15 +439,37 @@ k_refactor_tail(int t0, int nrows, int mlo, int max_steps, int max_len, const in
     __shared__ int s_row;
     const int M = nrows - mlo;   // columns [mlo, nrows) have an O(1) position map
     const int tid = threadIdx.x;
+    const T boost = (T)(boost_eps * *(volatile double*)&s->normA);
+    // Rows [t0, t1): short rows, one per warp (eight per block), from their
+    // own ticket, all of them dispensed before any block row below; each
+    // warp works in its own slice of shared memory.
+    if (t1 > t0) {
+        const int warp = tid >> 5;
+        const size_t slice = ((16 * (size_t)wsteps + (sizeof(T) + 4) * (size_t)wlen) + 15) & ~(size_t)15;
+        StepDesc* wsd = reinterpret_cast<StepDesc*>(tail_sh + warp * slice);
+        T* ww = reinterpret_cast<T*>(wsd + wsteps);
+        int32_t* wc = reinterpret_cast<int32_t*>(ww + wlen);
+        for (;;) {
+            if (tid == 0) s_row = t0 + (int)atomicAdd(&s->ticket_mid, (unsigned)(TAIL_THREADS / 32));
+            __syncthreads();
+            const int first = s_row;
+            if (__syncthreads_or(first >= t1 || ld_volatile_int(&s->abort))) break;
+            const int row = first + warp;
+            if (row < t1)
+                tail_warp_row<T>(row, t0, Fp, Fj, Fdiag, Fx, rinv, vals, fsrc, s, boost, limit, trace, wsd, ww, wc);
+            __syncthreads();   // the slices and s_row are reused
+        }
+        if (__syncthreads_or(ld_volatile_int(&s->abort))) return;   // uniform for the block
+    }
+    // Rows [t1, nrows): one per block.
     StepDesc* sd = reinterpret_cast<StepDesc*>(tail_sh);                          // max_steps
     T* w = reinterpret_cast<T*>(sd + max_steps);                                  // row values, max_len
     int32_t* cols = reinterpret_cast<int32_t*>(w + max_len);                      // row columns, max_len
     short* map = reinterpret_cast<short*>(cols + max_len);                        // M entries
     for (int c = tid; c < M; c += blockDim.x) map[c] = -1;
-    const T boost = (T)(boost_eps * *(volatile double*)&s->normA);
     __syncthreads();
     for (;;) {
-        if (tid == 0) s_row = t0 + (int)atomicAdd(&s->ticket_fact, 1u);
+        if (tid == 0) s_row = t1 + (int)atomicAdd(&s->ticket_fact, 1u);
         __syncthreads();
         const int row = s_row;
         const int stop = __syncthreads_or(row >= nrows || ld_volatile_int(&s->abort));

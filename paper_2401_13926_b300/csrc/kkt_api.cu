@@ -60,8 +60,11 @@ struct kkt_ctx {
     int nLc = 0, nUc = 0;
     int cluster = 0;            // blocks of the cluster solve (0: use the global schedule)
     size_t cluster_smem = 0;
-    // refactorization split: rows [0, t0) warp per row, [t0, n) block per row
-    int t0 = 0;
+    // refactorization split: rows [0, t0) warp per row with global values
+    // (k_refactor); [t0, t1) warp per row and [t1, n) block per row, both in
+    // shared memory (k_refactor_tail)
+    int t0 = 0, t1 = 0;
+    int tail_wsteps = 1, tail_wlen = 1;
     size_t tail_smem = 0;
     int tail_blocks = 0;
     int tail_max_steps = 1, tail_max_len = 1, tail_mlo = 0;
@@ -437,6 +440,7 @@ void kkt_default_opts(kkt_opts* o) {
     o->inner_tol = 1e-6;
     o->repivot = 0;
     o->graphs = 0;
+    o->tail_warp_rows = 1;
 }
 
 const char* kkt_strerror(int code) {
@@ -471,7 +475,7 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
         c->o.method < KKT_METHOD_FGMRES || c->o.method > KKT_METHOD_FGMRES_EE ||
         c->o.ortho < KKT_ORTHO_CGS2 || c->o.ortho > KKT_ORTHO_CGS1_PYTH ||
         !(c->o.inner_tol > 0.0 && c->o.inner_tol <= 1.0) || (c->o.repivot != 0 && c->o.repivot != 1) ||
-        (c->o.graphs != 0 && c->o.graphs != 1)) {
+        (c->o.graphs != 0 && c->o.graphs != 1) || (c->o.tail_warp_rows != 0 && c->o.tail_warp_rows != 1)) {
         delete c;
         return KKT_ERR_INVALID;
     }
@@ -585,6 +589,28 @@ int setup_tail(kkt_ctx* c) {
             break;
         }
         T /= 2;
+    }
+    // the short rows at the start of the tail go one per warp: [t0, t1), as
+    // long as every row so far fits a warp's slice (an eighth of the block's
+    // shared memory) with the running maxima of steps and length
+    c->t1 = c->t0;
+    c->tail_wsteps = 1;
+    c->tail_wlen = 1;
+    if (c->t0 < n && c->o.tail_warp_rows) {
+        const size_t vsize = c->mixed ? sizeof(float) : sizeof(double);
+        const size_t slice = (c->tail_smem / (kkt::TAIL_THREADS / 32)) & ~(size_t)15;
+        int64_t ms = 1, ml = 1;
+        int32_t i = c->t0;
+        for (; i < n; i++) {
+            const int64_t st = std::max<int64_t>(c->lay.Fdiag[i] - c->lay.Fp[i], ms);
+            const int64_t ln = std::max<int64_t>(c->lay.Fp[i + 1] - c->lay.Fp[i], ml);
+            if (((16 * (size_t)st + (vsize + 4) * (size_t)ln + 15) & ~(size_t)15) > slice) break;
+            ms = st;
+            ml = ln;
+        }
+        c->t1 = i;
+        c->tail_wsteps = (int)ms;
+        c->tail_wlen = (int)ml;
     }
     if (c->t0 < n) {
         int per_sm = 0;
@@ -814,8 +840,8 @@ void refactor_launch(kkt_ctx* c, const double* vals, unsigned long long* trace) 
         kkt::k_refactor_prep_tail<<<1, 1, 0, c->stream>>>(c->d_s);
         const int blocks = std::min(n - c->t0, c->tail_blocks);
         kkt::k_refactor_tail<T><<<blocks, kkt::TAIL_THREADS, c->tail_smem, c->stream>>>(
-            c->t0, n, c->tail_mlo, c->tail_max_steps, c->tail_max_len, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, vals,
-            c->d_fsrc, c->d_s, c->o.boost_eps, spin(c), trace);
+            c->t0, c->t1, n, c->tail_mlo, c->tail_max_steps, c->tail_max_len, c->tail_wsteps, c->tail_wlen,
+            c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, vals, c->d_fsrc, c->d_s, c->o.boost_eps, spin(c), trace);
         c->launches += 2;
     }
     phase_end(c, t);
@@ -918,19 +944,21 @@ int kkt_tune(kkt_ctx* c, const double* values, const double* b, int on_device, i
         hx.resize(n);
         x = hx.data();
     }
-    struct Cand { int trisolve, cluster_blocks, tail_rows; };
+    struct Cand { int trisolve, cluster_blocks, tail_rows, warp_rows; };
     std::vector<Cand> cands;
-    for (int tr : {0, 16384, 8192, 4096}) {
-        for (int cb : {16, 8}) cands.push_back({KKT_TRSV_AUTO, cb, tr});
-        cands.push_back({KKT_TRSV_GLOBAL, 0, tr});
-    }
+    for (int wr : {1, 0})
+        for (int tr : {0, 16384, 8192, 4096}) {
+            for (int cb : {16, 8}) cands.push_back({KKT_TRSV_AUTO, cb, tr, wr});
+            cands.push_back({KKT_TRSV_GLOBAL, 0, tr, wr});
+        }
     const kkt_opts saved = c->o;
     double best = -1.0;
-    Cand pick{saved.trisolve, saved.cluster_blocks, saved.tail_rows};
+    Cand pick{saved.trisolve, saved.cluster_blocks, saved.tail_rows, saved.tail_warp_rows};
     auto apply = [&](const Cand& k) -> int {
         c->o.trisolve = k.trisolve;
         c->o.cluster_blocks = k.cluster_blocks;
         c->o.tail_rows = k.tail_rows;
+        c->o.tail_warp_rows = k.warp_rows;
         drop_graph(&c->gx_ref, &c->g_ref);
         drop_graph(&c->gx_solve, &c->g_solve);
         int r = setup_tail(c);
@@ -959,7 +987,7 @@ int kkt_tune(kkt_ctx* c, const double* values, const double* b, int on_device, i
     }
     if (best < 0) {   // nothing ran: keep the previous configuration
         c->o = saved;
-        apply(Cand{saved.trisolve, saved.cluster_blocks, saved.tail_rows});
+        apply(Cand{saved.trisolve, saved.cluster_blocks, saved.tail_rows, saved.tail_warp_rows});
         c->detail = "kkt_tune: no configuration ran";
         return KKT_ERR_STATE;
     }
@@ -1390,6 +1418,7 @@ int kkt_query(kkt_ctx* c, kkt_info* info) {
     info->d2h_bytes = c->d2h;
     info->repivots = c->repivots;
     info->tail_rows = c->A.n - c->t0;
+    info->tail_warp_rows = c->t1 - c->t0;
     return KKT_OK;
 }
 

@@ -25,7 +25,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/kkt.h"
+#include "kkt.h"
 
 namespace {
 
