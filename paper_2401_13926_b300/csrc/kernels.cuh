@@ -195,7 +195,6 @@ __global__ void k_gather(const double* __restrict__ vals, const int64_t* __restr
     }
     const int lane = threadIdx.x & 31;
     const int64_t warp = tid >> 5, nwarps = stride >> 5;
-    double rmax = 0.0;
     bool bad = false;
     for (int64_t i = warp; i < n; i += nwarps) {
         for (int64_t e = Arp[i] + lane; e < Arp[i + 1]; e += 32) {
@@ -203,15 +202,19 @@ __global__ void k_gather(const double* __restrict__ vals, const int64_t* __restr
             Ax[e] = v;
             if (!isfinite(v)) bad = true;
         }
-        // the row's sum of |a_ij| in column order, as the definition reads
-        // (so the boost threshold boost_eps * ||K||_inf is reproducible)
-        if (lane == 0) {
-            double acc = 0.0;
-            for (int64_t e = Arp[i]; e < Arp[i + 1]; e++) acc += fabs(vals[asrc ? asrc[e] : e]);
-            rmax = fmax(rmax, acc);
-        }
     }
     if (bad) raise_error(s, KKT_ERR_NONFINITE, -1);
+    // each row's sum of |a_ij| in column order, as the definition reads (so
+    // the boost threshold boost_eps * ||K||_inf is reproducible): one thread
+    // per row
+    double rmax = 0.0;
+    for (int64_t i = tid; i < n; i += stride) {
+        double acc = 0.0;
+        for (int64_t e = Arp[i]; e < Arp[i + 1]; e++) acc += fabs(vals[asrc ? asrc[e] : e]);
+        rmax = fmax(rmax, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
     if (lane == 0 && rmax > 0.0)   // non-negative doubles order like their bit patterns
         atomicMax((unsigned long long*)&s->normA, (unsigned long long)__double_as_longlong(rmax));
 }
