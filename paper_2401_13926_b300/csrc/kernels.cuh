@@ -611,6 +611,7 @@ __global__ void k_fill_sentinel(T* a, int64_t n) {
 
 template <typename T>
 struct SrcGlobal {   // operand in a global vector, by column
+    static constexpr int kPollNs = 20;
     const int32_t* Fj;
     const T* x;
     __device__ const volatile T* operator()(int64_t p) const { return x + __ldg(&Fj[p]); }
@@ -650,6 +651,7 @@ __global__ void k_lsolve_bulk(int nrows, const int32_t* __restrict__ rows, const
 
 template <typename T>
 struct SrcChainL {   // dependency in the chain: shared memory; else y (final)
+    static constexpr int kPollNs = 0;
     const int32_t* Fj;
     const int32_t* Fpos;
     int cstart;
@@ -700,6 +702,7 @@ k_lsolve_chain(int nt, int cstart, const int32_t* __restrict__ rows, const int32
 
 template <typename T>
 struct SrcChainU {   // every dependency of a U-chain row is in the chain
+    static constexpr int kPollNs = 0;
     const int32_t* Fj;
     const int32_t* Fpos;
     int nt;
@@ -789,7 +792,8 @@ namespace cgx = cooperative_groups;
 constexpr int CLUSTER_THREADS = 1024;
 
 template <typename T>
-struct SrcCluster {
+struct SrcCluster {   // operand in the cluster's distributed shared memory
+    static constexpr int kPollNs = 0;
     const int32_t* Fpos;
     T* xs_local;
     int rank, sh, stride;
@@ -850,7 +854,7 @@ k_trsv_cluster(int n, const int32_t* __restrict__ list, const int32_t* __restric
 __global__ void k_selftest_wait(DevScal* s, const double* never, const unsigned* never_flag, long long limit) {
     double v = ld_relaxed_f64(never);
     const GiveUpGlobal gu{&s->abort};
-    const bool got_value = spin_value(never, &v, limit, gu);
+    const bool got_value = spin_value<20>(never, &v, limit, gu);
     const bool got_flag = wait_flag(never_flag, 0xffffffffu, s, limit, -1);
     if (threadIdx.x == 0 && (!got_value || !got_flag)) raise_error(s, KKT_ERR_TIMEOUT, -1);
 }

@@ -78,6 +78,7 @@ __global__ void k_na_clear(unsigned char* base, int n) {
 }
 
 struct NaSrc {
+    static constexpr int kPollNs = 20;
     const int32_t* Fj;
     const double* x;
     __device__ const volatile double* operator()(int64_t p) const { return x + __ldg(&Fj[p]); }

@@ -18,7 +18,8 @@
 //
 // Values are read through `Src`, which maps an entry p to the address of
 // its operand (shared, distributed shared or global memory, all accessed as
-// volatile); an operand that is not computed yet holds SENTINEL.
+// volatile) and names the sleep between polls (Src::kPollNs); an operand
+// that is not computed yet holds SENTINEL.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -54,14 +55,17 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Spin until *p is not SENTINEL.  `give_up()` is polled every 256 spins;
-// after `limit` spins the wait fails.  Returns false on failure.
-template <typename T, class GiveUp>
+// after `limit` spins the wait fails.  Returns false on failure.  POLL_NS:
+// sleep between polls -- 0 for operands in shared or distributed shared
+// memory (a tight spin measured ~10% faster sweeps), 20 ns for operands in
+// global memory (many warps polling L2).
+template <int POLL_NS, typename T, class GiveUp>
 __device__ __forceinline__ bool spin_value(const volatile T* p, T* v, long long limit, GiveUp give_up) {
     T x = *v;
     for (long long it = 0; is_sentinel(x); it++) {
         if ((it & 255) == 255 && give_up()) return false;
         if (it >= limit) return false;
-        __nanosleep(20);
+        if (POLL_NS > 0) __nanosleep(POLL_NS);
         x = *p;
     }
     *v = x;
@@ -116,7 +120,7 @@ __device__ __forceinline__ bool trsv_row(int64_t lo, int64_t hi, const T* __rest
 #pragma unroll
         for (int u = 0; u < ROW_BATCH; u++) {
             if (base + 32 * u >= ehi) continue;
-            if (!spin_value(s[u], &v[u], limit, give_up)) { ok = 0; break; }
+            if (!spin_value<Src::kPollNs>(s[u], &v[u], limit, give_up)) { ok = 0; break; }
             acc = fma(a[u], v[u], acc);
         }
     }
@@ -135,7 +139,7 @@ __device__ __forceinline__ bool trsv_row(int64_t lo, int64_t hi, const T* __rest
 #pragma unroll
         for (int j = 0; j < NLATE; j++) {
             if (j < nl && ok) {
-                if (!spin_value(ls[j], &lv[j], limit, give_up)) { ok = 0; break; }
+                if (!spin_value<Src::kPollNs>(ls[j], &lv[j], limit, give_up)) { ok = 0; break; }
                 r = fma(-la[j], lv[j], r);
             }
         }
