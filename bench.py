@@ -319,9 +319,11 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def step(k):
-        solver.refactor(vals[k % seq.M])
+        # one step of the sequence: kkt_step (refactor + solve, the forward
+        # sweep fused into the refactorization)
         # a mixed-precision headline reports unconverged solves instead of stopping
-        _, it, nr = solver.solve(rhs[k % seq.M], x=x, tol=TOL, allow_not_converged=args.precision == "mixed")
+        _, it, nr = solver.step(vals[k % seq.M], rhs[k % seq.M], x=x, tol=TOL,
+                                allow_not_converged=args.precision == "mixed")
         return it, nr
 
     for w in range(args.warmup):
@@ -362,8 +364,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     t = time.perf_counter()
     for k in range(n_e2e):
-        solver.refactor(hv[k])
-        solver.solve(hb[k], x=hx, tol=TOL)
+        solver.step(hv[k], hb[k], x=hx, tol=TOL)
     e2e_s = time.perf_counter() - t
     info_b = solver.info()
     e2e_units, e2e_secs = aggregate(float(n_e2e), e2e_s, world)
@@ -380,8 +381,7 @@ def run_ours(args):
                          max_cycles=cyc2)
         s2.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
         for w in range(args.warmup):
-            s2.refactor(vals[w % seq.M])
-            s2.solve(rhs[w % seq.M], x=x, tol=TOL, allow_not_converged=True)
+            s2.step(vals[w % seq.M], rhs[w % seq.M], x=x, tol=TOL, allow_not_converged=True)
         s2.phase_times(reset=True)
         ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(seq.M)]
         it2, nr2, ok2 = [], [], 0
@@ -389,8 +389,7 @@ def run_ours(args):
         for i in range(seq.M):
             flush.zero_()
             ev2[i][0].record(stream)
-            s2.refactor(vals[i])
-            _, it, nr = s2.solve(rhs[i], x=x, tol=TOL, allow_not_converged=True)
+            _, it, nr = s2.step(vals[i], rhs[i], x=x, tol=TOL, allow_not_converged=True)
             ev2[i][1].record(stream)
             it2.append(it)
             nr2.append(nr)

@@ -239,6 +239,21 @@ int kkt_repivot(kkt_ctx* c, const double* values, int values_on_device);
 int kkt_solve(kkt_ctx* c, const double* b, double* x, int on_device, double tol,
               int* iters, double* nrbe);
 
+/*
+ * One step of a sequence: kkt_refactor(values) then kkt_solve(b, tol), with
+ * the forward sweep y = L^{-1} P b fused into the refactorization: the warp
+ * or block that finishes a row of the factors computes that row of y at once,
+ * with the row arithmetic of the separate sweep (same bits), so the separate
+ * forward sweep of the initial solve disappears from the step.  values, b
+ * and x are all host arrays (on_device == 0) or all device arrays.  Returns
+ * and outputs as kkt_refactor then kkt_solve (including kkt_opts.repivot).
+ * With kkt_opts.graphs the two graphs are replayed unfused.  (A fused
+ * refactorization-solve pair is an implementation choice the paper's
+ * separate steps of Section 1.3 allow.)
+ */
+int kkt_step(kkt_ctx* c, const double* values, const double* b, double* x, int on_device, double tol,
+             int* iters, double* nrbe);
+
 /* x = Q U^{-1} L^{-1} P b only (Section 1.3 step 3), no refinement. */
 int kkt_lu_solve(kkt_ctx* c, const double* b, double* x, int on_device);
 
@@ -411,8 +426,8 @@ int kkt_server_open(kkt_server* s, int32_t n, const int32_t* rowptr, const int32
                     const double* values0, int64_t* instance);
 
 /*
- * Queue one step of an instance: kkt_refactor(values) then kkt_solve(b)
- * with tolerance tol, writing x (host, n doubles; written when the step
+ * Queue one step of an instance: kkt_step(values, b, tol) -- kkt_refactor
+ * then kkt_solve, the forward sweep fused -- writing x (host, n doubles; written when the step
  * completes -- keep it valid until kkt_server_wait returns).  values and b
  * are copied at submit.  *ticket identifies the step for kkt_server_wait.
  */

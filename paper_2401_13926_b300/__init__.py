@@ -38,7 +38,7 @@ EXPORTS = [
     "kkt_matvec", "kkt_get_perm", "kkt_get_factor_sizes", "kkt_get_factors", "kkt_query",
     "kkt_destroy", "kkt_strerror", "kkt_last_error_detail", "kkt_order", "kkt_pivot",
     "kkt_get_phase_times", "kkt_lu_solve_noalloc", "kkt_selftest_wait", "kkt_trace_refactor",
-    "kkt_trace_solve", "kkt_repivot", "kkt_tune", "kkt_server_default_opts", "kkt_server_create", "kkt_server_open",
+    "kkt_trace_solve", "kkt_repivot", "kkt_tune", "kkt_step", "kkt_server_default_opts", "kkt_server_create", "kkt_server_open",
     "kkt_server_submit", "kkt_server_wait", "kkt_server_close", "kkt_server_query", "kkt_server_destroy",
 ]
 NOALLOC_MAX_N = 65536
@@ -128,6 +128,7 @@ def lib():
     L.kkt_trace_solve.argtypes = [vp, vp, vp, ip, vp, vp, vp, vp]
     L.kkt_repivot.argtypes = [vp, vp, ip]
     L.kkt_tune.argtypes = [vp, vp, vp, ip, ip, C.POINTER(d)]
+    L.kkt_step.argtypes = [vp, vp, vp, vp, ip, d, C.POINTER(C.c_int), C.POINTER(d)]
     L.kkt_server_default_opts.argtypes = [C.POINTER(_ServerOpts)]
     L.kkt_server_default_opts.restype = None
     L.kkt_server_create.argtypes = [C.POINTER(vp), C.POINTER(_ServerOpts)]
@@ -331,6 +332,22 @@ class KKTSolver:
         it, nr = C.c_int(), C.c_double()
         ok = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
         rc = self._check(lib().kkt_solve(self._h, pb, px, dev, float(tol), C.byref(it), C.byref(nr)), "kkt_solve", ok)
+        self.last_status = rc
+        return x, it.value, nr.value
+
+    def step(self, values, b, x=None, tol=1e-12, allow_not_converged=False):
+        """kkt_step: refactor(values) + solve(b) with the forward sweep fused
+        into the refactorization.  Returns (x, iters, nrbe)."""
+        kv, pv, dv = _ptr(values, np.float64)
+        kb, pb, db = _ptr(b, np.float64)
+        if dv != db:
+            raise ValueError("values and b must both be host or both be device arrays")
+        if x is None:
+            x = b.new_empty(self.n) if db else np.zeros(self.n)
+        kx, px, _ = _ptr(x, np.float64)
+        it, nr = C.c_int(), C.c_double()
+        ok = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
+        rc = self._check(lib().kkt_step(self._h, pv, pb, px, db, float(tol), C.byref(it), C.byref(nr)), "kkt_step", ok)
         self.last_status = rc
         return x, it.value, nr.value
 

@@ -180,14 +180,77 @@ __global__ void k_refactor_prep(DevScal* s) {
 // gathers their values itself and publishes each row when it is final).
 // T is the factor type: double, or float in mixed precision (the caller's
 // FP64 values are rounded to nearest here).
+struct GiveUpGlobal {
+    const int* abort;
+    __device__ bool operator()() const { return *(volatile const int*)abort != 0; }
+};
+
+template <typename T>
+struct SrcGlobal {   // operand in a global vector, by column
+    static constexpr int kPollNs = 20;
+    const int32_t* Fj;
+    const T* x;
+    __device__ const volatile T* operator()(int64_t p) const { return x + __ldg(&Fj[p]); }
+};
+
+__device__ __forceinline__ void fail_row(DevScal* s, int row) {
+    if (!*(volatile int*)&s->abort) raise_error(s, KKT_ERR_TIMEOUT, row);
+}
+
+// The forward sweep y = L^{-1} P rhs fused into the refactorization: the
+// warp (or a warp of the block) that finished row i computes y_i at once
+// with the L-sweep's row arithmetic (trsv_row), so y has the same bits as
+// a separate sweep, and its chain trails the factorization's by one row.
+// rhs == nullptr: not fused.  y is armed with SENTINEL by the gather; xp
+// (the U-sweep's vector in the whole-GPU schedule) is armed per row.
+template <typename T>
+struct FwdArgs {
+    const double* rhs;
+    const int32_t* P;
+    T* y;
+    T* xp;
+};
+
+template <typename T>
+struct CgVals {   // row values this kernel wrote (read from L2)
+    const T* Fx;
+    __device__ T operator()(int64_t p) const { return __ldcg(&Fx[p]); }
+};
+
+template <typename T>
+struct SliceVals {   // row values in shared memory: entry p at w[p - b]
+    const T* w;
+    int64_t b;
+    __device__ T operator()(int64_t p) const { return w[p - b]; }
+};
+
+template <typename T, class Vals>
+__device__ bool fused_forward_row(int row, int64_t lo, int64_t hi, Vals vals, const int32_t* __restrict__ Fj,
+                                  const FwdArgs<T>& fw, DevScal* s, long long limit) {
+    const GiveUpGlobal gu{&s->abort};
+    T val;
+    if (!trsv_row_v<true>(lo, hi, vals, SrcGlobal<T>{Fj, fw.y}, (T)fw.rhs[fw.P[row]], T(1), limit, gu, &val)) {
+        if ((threadIdx.x & 31) == 0) fail_row(s, row);
+        return false;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        fw.xp[row] = sentinel_of<T>();
+        st_relaxed(&fw.y[row], val);
+    }
+    __syncwarp();
+    return true;
+}
+
 template <typename T>
 __global__ void k_gather(const double* __restrict__ vals, const int64_t* __restrict__ fsrc, int64_t nnzF,
                          int64_t tail_begin, T* __restrict__ Fx, const int32_t* __restrict__ Arp,
                          const int64_t* __restrict__ asrc, double* __restrict__ Ax, int n, int t0,
-                         T* __restrict__ rinv, DevScal* s) {
+                         T* __restrict__ rinv, DevScal* s, T* __restrict__ yarm) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = t0 + tid; i < n; i += stride) rinv[i] = sentinel_of<T>();   // tail rows publish 1/u_ii last
+    if (yarm)   // the fused forward sweep fills y
+        for (int64_t i = tid; i < n; i += stride) yarm[i] = sentinel_of<T>();
     for (int64_t t = tid; t < nnzF; t += stride) {
         if (t >= tail_begin) { Fx[t] = sentinel_of<T>(); continue; }
         int64_t q = fsrc[t];
@@ -236,7 +299,7 @@ __device__ __forceinline__ int64_t find_col(const int32_t* __restrict__ Fj, int6
 template <typename T>
 __global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
                            const int64_t* __restrict__ Fdiag, T* Fx, T* rinv, unsigned* done, DevScal* s,
-                           double boost_eps, long long limit) {
+                           double boost_eps, long long limit, FwdArgs<T> fw) {
     // rows [0, n) of the bulk: warp per row, factor values in global memory
     const int lane = threadIdx.x & 31;
     const unsigned gen = *(volatile unsigned*)&s->gen_fact;
@@ -282,6 +345,7 @@ __global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t*
             }
         }
         __syncwarp();
+        if (fw.rhs && !fused_forward_row<T>(row, b, d, CgVals<T>{Fx}, Fj, fw, s, limit)) return;
     }
 }
 
@@ -376,7 +440,7 @@ template <typename T>
 __device__ bool tail_warp_row(int row, int t0, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
                               const int64_t* __restrict__ Fdiag, T* Fx, T* rinv, const double* __restrict__ vals,
                               const int64_t* __restrict__ fsrc, DevScal* s, T boost, long long limit,
-                              unsigned long long* trace, StepDesc* sd, T* w, int32_t* cols) {
+                              unsigned long long* trace, StepDesc* sd, T* w, int32_t* cols, const FwdArgs<T>& fw) {
     const int lane = threadIdx.x & 31;
     if (trace && lane == 0) trace[2 * (size_t)(row - t0)] = globaltimer_ns();
     const int64_t b = Fp[row], d = Fdiag[row], e = Fp[row + 1];
@@ -428,6 +492,7 @@ __device__ bool tail_warp_row(int row, int t0, const int64_t* __restrict__ Fp, c
         }
     }
     __syncwarp();
+    if (fw.rhs) return fused_forward_row<T>(row, b, d, SliceVals<T>{w, b}, Fj, fw, s, limit);
     return true;
 }
 
@@ -437,7 +502,7 @@ k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, 
                 const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
                 const int64_t* __restrict__ Fdiag, T* Fx, T* rinv, const double* __restrict__ vals,
                 const int64_t* __restrict__ fsrc, DevScal* s, double boost_eps, long long limit,
-                unsigned long long* trace) {
+                unsigned long long* trace, FwdArgs<T> fw) {
     extern __shared__ __align__(16) unsigned char tail_sh[];
     __shared__ int s_row;
     const int M = nrows - mlo;   // columns [mlo, nrows) have an O(1) position map
@@ -459,7 +524,7 @@ k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, 
             if (__syncthreads_or(first >= t1 || ld_volatile_int(&s->abort))) break;
             const int row = first + warp;
             if (row < t1)
-                tail_warp_row<T>(row, t0, Fp, Fj, Fdiag, Fx, rinv, vals, fsrc, s, boost, limit, trace, wsd, ww, wc);
+                tail_warp_row<T>(row, t0, Fp, Fj, Fdiag, Fx, rinv, vals, fsrc, s, boost, limit, trace, wsd, ww, wc, fw);
             __syncthreads();   // the slices and s_row are reused
         }
         if (__syncthreads_or(ld_volatile_int(&s->abort))) return;   // uniform for the block
@@ -573,6 +638,9 @@ k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, 
                 if (trace) trace[2 * (size_t)(row - t0) + 1] = globaltimer_ns();
             }
         }
+        // the fused forward sweep's y_row, by warp 0 from the row in shared
+        // memory; the other warps wait at the next row's first barrier
+        if (fw.rhs && tid < 32) fused_forward_row<T>(row, b, d, SliceVals<T>{w, b}, Fj, fw, s, limit);
     }
 }
 
@@ -593,11 +661,6 @@ k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, 
 // sweep re-arms the other one's vector (L sets xp = SENTINEL, U sets
 // y = SENTINEL after reading it).
 
-struct GiveUpGlobal {
-    const int* abort;
-    __device__ bool operator()() const { return *(volatile const int*)abort != 0; }
-};
-
 __global__ void k_trsv_prep(DevScal* s) {
     s->ticket_l = 0;
     s->ticket_u = 0;
@@ -609,17 +672,6 @@ __global__ void k_fill_sentinel(T* a, int64_t n) {
         a[i] = sentinel_of<T>();
 }
 
-template <typename T>
-struct SrcGlobal {   // operand in a global vector, by column
-    static constexpr int kPollNs = 20;
-    const int32_t* Fj;
-    const T* x;
-    __device__ const volatile T* operator()(int64_t p) const { return x + __ldg(&Fj[p]); }
-};
-
-__device__ __forceinline__ void fail_row(DevScal* s, int row) {
-    if (!*(volatile int*)&s->abort) raise_error(s, KKT_ERR_TIMEOUT, row);
-}
 
 // T: factor and solve type (double, or float in mixed precision); the
 // right-hand side and the result of a sweep pair stay double.

@@ -50,6 +50,7 @@ struct kkt_ctx {
     double g_solve_tol = 0.0;
     int64_t gl_ref = 0, gl_pro = 0, gl_body = 0, gl_step = 0;
     int32_t repivots = 0;                         // kkt_repivot calls that succeeded in analysis
+    bool y_fused = false;                         // the last refactorization also computed y = L^{-1} P b
     double *d_b = nullptr, *d_x = nullptr, *d_y = nullptr, *d_xp = nullptr, *d_r = nullptr, *d_w = nullptr;
     double *d_V = nullptr, *d_Z = nullptr, *d_part = nullptr;
     unsigned* d_done_f = nullptr;
@@ -393,6 +394,41 @@ void lu_apply_t(kkt_ctx* c, const double* rhs, double* out) {
 void lu_apply(kkt_ctx* c, const double* rhs, double* out) {
     if (c->mixed) lu_apply_t<float>(c, rhs, out);
     else lu_apply_t<double>(c, rhs, out);
+}
+
+// x = Q U^{-1} y with y already in the context (the fused forward sweep)
+template <typename T>
+void u_apply_t(kkt_ctx* c, double* out) {
+    T* y = (T*)c->d_y;
+    T* xp = (T*)c->d_xp;
+    const T* Fx = (const T*)c->d_Fx;
+    int t = phase_begin(c, KKT_PHASE_USOLVE);
+    if (c->cluster) {
+        launch_cluster<false, T, T, double>(c, c->d_Q, y, out);
+        c->launches += 1;
+        phase_end(c, t);
+        return;
+    }
+    const int n = c->A.n;
+    const int nUb = n - c->nUc;
+    kkt::k_trsv_prep<<<1, 1, 0, c->stream>>>(c->d_s);
+    c->launches += 1;
+    if (c->nUc) {
+        kkt::k_usolve_chain<T><<<1, CHAIN_THREADS, sizeof(T) * c->nUc, c->stream>>>(
+            c->nUc, c->d_listU, c->d_Fpos, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, c->d_Q, y, xp, out, c->d_s, spin(c));
+        c->launches += 1;
+    }
+    if (nUb) {
+        kkt::k_usolve_bulk<T><<<grid_for(c, nUb), PERSIST_THREADS, 0, c->stream>>>(
+            nUb, c->d_listU + c->nUc, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, c->d_Q, y, xp, out, c->d_s, spin(c));
+        c->launches += 1;
+    }
+    phase_end(c, t);
+}
+
+void u_apply(kkt_ctx* c, double* out) {
+    if (c->mixed) u_apply_t<float>(c, out);
+    else u_apply_t<double>(c, out);
 }
 
 void fill_y_sentinel(kkt_ctx* c) {
@@ -746,7 +782,8 @@ int setup_device(kkt_ctx* c, const kkt::ColStructure& S, std::chrono::steady_clo
 }  // namespace
 
 namespace {
-int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsigned long long* trace);
+int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsigned long long* trace,
+                  const double* fused_rhs = nullptr);
 }
 
 int kkt_repivot(kkt_ctx* c, const double* values, int values_on_device) {
@@ -816,21 +853,23 @@ extern "C++" {
 namespace {
 // gather, bulk rows (warp per row), tail rows (block per row), in type T
 template <typename T>
-void refactor_launch(kkt_ctx* c, const double* vals, unsigned long long* trace) {
+void refactor_launch(kkt_ctx* c, const double* vals, unsigned long long* trace, const double* fused_rhs = nullptr) {
     const int n = c->A.n;
     const int64_t nnzF = (int64_t)c->lay.Fj.size();
     T* Fx = (T*)c->d_Fx;
     T* rinv = (T*)c->d_rinv;
+    const kkt::FwdArgs<T> fw{fused_rhs, c->d_P, (T*)c->d_y, (T*)c->d_xp};
     int t = phase_begin(c, KKT_PHASE_GATHER);
     const int64_t tail_begin = c->t0 < n ? c->lay.Fp[c->t0] : nnzF;
     kkt::k_gather<T><<<2 * c->num_sms, 256, 0, c->stream>>>(vals, c->d_fsrc, nnzF, tail_begin, Fx, c->d_Arp,
-                                                            c->d_asrc, c->d_Ax, n, c->t0, rinv, c->d_s);
+                                                            c->d_asrc, c->d_Ax, n, c->t0, rinv, c->d_s,
+                                                            fused_rhs ? (T*)c->d_y : nullptr);
     phase_end(c, t);
     t = phase_begin(c, KKT_PHASE_REFACTOR);
     c->launches += 2;
     if (c->t0 > 0) {
         kkt::k_refactor<T><<<grid_for(c, c->t0), PERSIST_THREADS, 0, c->stream>>>(
-            c->t0, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, c->d_done_f, c->d_s, c->o.boost_eps, spin(c));
+            c->t0, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, c->d_done_f, c->d_s, c->o.boost_eps, spin(c), fw);
         c->launches += 1;
     }
     phase_end(c, t);
@@ -841,7 +880,7 @@ void refactor_launch(kkt_ctx* c, const double* vals, unsigned long long* trace) 
         const int blocks = std::min(n - c->t0, c->tail_blocks);
         kkt::k_refactor_tail<T><<<blocks, kkt::TAIL_THREADS, c->tail_smem, c->stream>>>(
             c->t0, c->t1, n, c->tail_mlo, c->tail_max_steps, c->tail_max_len, c->tail_wsteps, c->tail_wlen,
-            c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, vals, c->d_fsrc, c->d_s, c->o.boost_eps, spin(c), trace);
+            c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, vals, c->d_fsrc, c->d_s, c->o.boost_eps, spin(c), trace, fw);
         c->launches += 2;
     }
     phase_end(c, t);
@@ -869,13 +908,15 @@ int build_refactor_graph(kkt_ctx* c) {
     return KKT_OK;
 }
 
-int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsigned long long* trace) {
+int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsigned long long* trace,
+                  const double* fused_rhs) {
     int rc = check_ctx(c, false);
     if (rc) return rc;
     if (!values) return KKT_ERR_INVALID;
     c->factored = false;
+    c->y_fused = false;
     const double* vals = values;
-    const bool graphs = c->o.graphs && !trace;
+    const bool graphs = c->o.graphs && !trace && !fused_rhs;
     if (!values_on_device) {
         CK(cudaMemcpyAsync(c->d_vals, values, sizeof(double) * (size_t)c->nnz_a, cudaMemcpyHostToDevice, c->stream));
         c->h2d += (int64_t)sizeof(double) * c->nnz_a;
@@ -893,8 +934,8 @@ int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsign
         c->launches += c->gl_ref;
     } else {
         kkt::k_refactor_prep<<<1, 1, 0, c->stream>>>(c->d_s);
-        if (c->mixed) refactor_launch<float>(c, vals, trace);
-        else refactor_launch<double>(c, vals, trace);
+        if (c->mixed) refactor_launch<float>(c, vals, trace, fused_rhs);
+        else refactor_launch<double>(c, vals, trace, fused_rhs);
     }
     CK(cudaGetLastError());
     if ((rc = read_scalars(c))) return rc;
@@ -902,6 +943,7 @@ int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsign
     c->norm_a = c->h_s->normA;
     if ((rc = device_error(c))) return rc;
     c->factored = true;
+    c->y_fused = fused_rhs != nullptr;
     return KKT_OK;
 }
 }  // namespace
@@ -1095,10 +1137,12 @@ int cap_of(const kkt_ctx* c) {   // the refinement's cap: cycles, or corrections
     return c->o.method == KKT_METHOD_RICHARDSON ? c->o.max_cycles * c->m : c->o.max_cycles;
 }
 
-// x0 = (LU)^{-1} b, its residual and the refine-or-not decision
-void seq_prologue(kkt_ctx* c, const double* bd, double* xd, double tol, int loop) {
+// x0 = (LU)^{-1} b, its residual and the refine-or-not decision; with
+// y_ready the refactorization already computed y = L^{-1} P b
+void seq_prologue(kkt_ctx* c, const double* bd, double* xd, double tol, int loop, bool y_ready = false) {
     const int n = c->A.n, rb = red_blocks(c);
-    lu_apply(c, bd, xd);
+    if (y_ready) u_apply(c, xd);
+    else lu_apply(c, bd, xd);
     int t = phase_begin(c, KKT_PHASE_SPMV);
     kkt::k_residual<<<rb, kkt::RED_THREADS, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, bd, xd, c->d_r,
                                                             c->d_part, c->d_s);
@@ -1243,11 +1287,45 @@ int build_solve_graph(kkt_ctx* c, double tol) {
     return KKT_OK;
 }
 
-int solve_impl(kkt_ctx* c, const double* b, double* x, int on_device, double tol, int* iters, double* nrbe);
+int solve_impl(kkt_ctx* c, const double* b, double* x, int on_device, double tol, int* iters, double* nrbe,
+               bool fused = false);
+int solve_with_fallback(kkt_ctx* c, const double* b, double* x, int on_device, double tol, int* iters,
+                        double* nrbe, bool fused);
 }  // namespace
 
 int kkt_solve(kkt_ctx* c, const double* b, double* x, int on_device, double tol, int* iters, double* nrbe) {
-    int rc = solve_impl(c, b, x, on_device, tol, iters, nrbe);
+    return solve_with_fallback(c, b, x, on_device, tol, iters, nrbe, false);
+}
+
+int kkt_step(kkt_ctx* c, const double* values, const double* b, double* x, int on_device, double tol, int* iters,
+             double* nrbe) {
+    int rc = check_ctx(c, false);
+    if (rc) return rc;
+    if (!values || !b || !x || !(tol > 0)) return KKT_ERR_INVALID;
+    if (c->o.graphs) {   // the graphs replay the separate refactorization and solve
+        if ((rc = kkt_refactor(c, values, on_device))) return rc;
+        return kkt_solve(c, b, x, on_device, tol, iters, nrbe);
+    }
+    const int n = c->A.n;
+    const double* bd = b;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(c->d_b, b, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        c->h2d += (int64_t)sizeof(double) * n;
+        bd = c->d_b;
+    }
+    rc = refactor_impl(c, values, on_device, nullptr, bd);
+    if (rc == KKT_ERR_ZERO_PIVOT && c->o.repivot) {
+        if ((rc = kkt_repivot(c, values, on_device))) return rc;
+        return kkt_solve(c, b, x, on_device, tol, iters, nrbe);
+    }
+    if (rc) return rc;
+    return solve_with_fallback(c, b, x, on_device, tol, iters, nrbe, true);
+}
+
+namespace {
+int solve_with_fallback(kkt_ctx* c, const double* b, double* x, int on_device, double tol, int* iters,
+                        double* nrbe, bool fused) {
+    int rc = solve_impl(c, b, x, on_device, tol, iters, nrbe, fused);
     if (rc != KKT_ERR_NOT_CONVERGED || !c->o.repivot) return rc;
     // re-pivot on the matrix in use (its canonical copy, back in the
     // caller's entry order) and solve once more
@@ -1261,18 +1339,26 @@ int kkt_solve(kkt_ctx* c, const double* b, double* x, int on_device, double tol,
     if (rp) return rp;
     return solve_impl(c, b, x, on_device, tol, iters, nrbe);
 }
+}  // namespace
 
 namespace {
-int solve_impl(kkt_ctx* c, const double* b, double* x, int on_device, double tol, int* iters, double* nrbe) {
+// fused: kkt_step -- b is already in d_b when it came from the host, and y =
+// L^{-1} P b was computed by the refactorization (c->y_fused)
+int solve_impl(kkt_ctx* c, const double* b, double* x, int on_device, double tol, int* iters, double* nrbe,
+               bool fused) {
     int rc = check_ctx(c, true);
     if (rc) return rc;
     if (!b || !x || !(tol > 0)) return KKT_ERR_INVALID;
     const int n = c->A.n;
     const int m = c->m;
     const bool graphs = c->o.graphs != 0;
+    const bool y_ready = fused && c->y_fused && !graphs;
+    c->y_fused = false;   // y is consumed by this solve
     const double* bd = b;
     double* xd = x;
-    if (!on_device) {
+    if (!on_device && y_ready) {
+        // b was copied to d_b by kkt_step
+    } else if (!on_device) {
         CK(cudaMemcpyAsync(c->d_b, b, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
         c->h2d += (int64_t)sizeof(double) * n;
     } else if (graphs) {   // the graph reads its fixed buffers
@@ -1297,7 +1383,7 @@ int solve_impl(kkt_ctx* c, const double* b, double* x, int on_device, double tol
         if ((rc = device_error(c))) { rearm(c); return rc; }
         if (c->h_s->not_converged) status = KKT_ERR_NOT_CONVERGED;
     } else {
-        seq_prologue(c, bd, xd, tol, 0);
+        seq_prologue(c, bd, xd, tol, 0, y_ready);
         CK(cudaGetLastError());
         if ((rc = read_scalars(c))) return rc;
         if ((rc = device_error(c))) { rearm(c); return rc; }

@@ -8,7 +8,7 @@
 // instances resident and lets their steps overlap: every instance is a
 // context with its own stream, and a pool of worker threads takes instances
 // that have a queued step and are not running one, runs that step (a
-// blocking kkt_refactor + kkt_solve on the instance's stream), and re-queues
+// blocking kkt_step -- refactor + solve -- on the instance's stream), and re-queues
 // the instance if more steps wait.  Steps of one instance run one at a time,
 // in submission order; steps of different instances run concurrently.
 // Admission holds the device memory of the admitted instances within a
@@ -82,18 +82,15 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
     return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
+// refactor + solve as one kkt_step (the forward sweep fused into the
+// refactorization; same results as the two calls)
 void run_step(kkt_server* s, Instance* in, Step& st, kkt_step_result* r) {
     cudaSetDevice(s->dev);
-    r->status = kkt_refactor(in->ctx, st.values.data(), 0);
-    r->iters = 0;
-    r->nrbe = 0.0;
-    if (r->status == KKT_OK) {
-        int it = 0;
-        double nr = 0.0;
-        r->status = kkt_solve(in->ctx, st.b.data(), st.x, 0, st.tol, &it, &nr);
-        r->iters = it;
-        r->nrbe = nr;
-    }
+    int it = 0;
+    double nr = 0.0;
+    r->status = kkt_step(in->ctx, st.values.data(), st.b.data(), st.x, 0, st.tol, &it, &nr);
+    r->iters = it;
+    r->nrbe = nr;
 }
 
 void worker_main(kkt_server* s) {

@@ -82,9 +82,12 @@ __device__ __forceinline__ bool spin_value(const volatile T* p, T* v, long long 
 // every lane if a wait failed.
 // T is the value type of the factors and of the solve (double, or float in
 // mixed precision); the arithmetic is the same in both.
-template <bool LOWER, typename T, class Src, class GiveUp>
-__device__ __forceinline__ bool trsv_row(int64_t lo, int64_t hi, const T* __restrict__ Fx, Src src,
-                                         T r0, T rinv, long long limit, GiveUp give_up, T* out) {
+// The factor values of the row come from `vals(p)`; trsv_row below reads
+// them through the read-only cache from a factor array no kernel of the
+// sweep writes.
+template <bool LOWER, typename T, class Vals, class Src, class GiveUp>
+__device__ __forceinline__ bool trsv_row_v(int64_t lo, int64_t hi, Vals vals, Src src,
+                                           T r0, T rinv, long long limit, GiveUp give_up, T* out) {
     constexpr int NLATE = LOWER ? NLATE_L : NLATE_U;
     const int lane = threadIdx.x & 31;
     const int64_t len = hi - lo;
@@ -99,7 +102,7 @@ __device__ __forceinline__ bool trsv_row(int64_t lo, int64_t hi, const T* __rest
         for (int j = 0; j < NLATE; j++) {
             if (j < nl) {
                 const int64_t p = LOWER ? hi - nl + j : lo + nl - 1 - j;   // completion order
-                la[j] = __ldg(&Fx[p]);
+                la[j] = vals(p);
                 ls[j] = src(p);
                 lv[j] = *ls[j];
             }
@@ -113,7 +116,7 @@ __device__ __forceinline__ bool trsv_row(int64_t lo, int64_t hi, const T* __rest
 #pragma unroll
         for (int u = 0; u < ROW_BATCH; u++) {
             const int64_t p = base + 32 * u;
-            if (p < ehi) { a[u] = __ldg(&Fx[p]); s[u] = src(p); }
+            if (p < ehi) { a[u] = vals(p); s[u] = src(p); }
         }
 #pragma unroll
         for (int u = 0; u < ROW_BATCH; u++)
@@ -149,6 +152,18 @@ __device__ __forceinline__ bool trsv_row(int64_t lo, int64_t hi, const T* __rest
     if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
     *out = r;
     return true;
+}
+
+template <typename T>
+struct LdgVals {   // factor values through the read-only cache
+    const T* Fx;
+    __device__ T operator()(int64_t p) const { return __ldg(&Fx[p]); }
+};
+
+template <bool LOWER, typename T, class Src, class GiveUp>
+__device__ __forceinline__ bool trsv_row(int64_t lo, int64_t hi, const T* __restrict__ Fx, Src src,
+                                         T r0, T rinv, long long limit, GiveUp give_up, T* out) {
+    return trsv_row_v<LOWER>(lo, hi, LdgVals<T>{Fx}, src, r0, rinv, limit, give_up, out);
 }
 
 }  // namespace kkt

@@ -1,0 +1,75 @@
+"""kkt_step: refactor + solve with the forward sweep fused into the
+refactorization.  The fused y is computed with the separate sweep's row
+arithmetic, so every result must equal refactor() followed by solve() bit
+for bit -- factors, solution, iteration count and NRBE -- on every schedule,
+in both precisions, with host and device arrays, and with refinement
+iterations after the fused initial solve."""
+import numpy as np
+import pytest
+
+import paper_2401_13926_b300 as K
+from paper_2401_13926_b300.workload import KKTSequence, small_random_sparse
+
+pytestmark = pytest.mark.gpu
+
+
+def _pair(rp, ci, v0=None, P=None, Q=None, **kw):
+    out = []
+    for _ in range(2):
+        s = K.KKTSolver(**kw)
+        if P is None:
+            s.analyze(rp, ci, values0=v0)
+        else:
+            s.analyze(rp, ci, Q=Q, P=P)
+        out.append(s)
+    return out
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(trisolve="global"), dict(precision="mixed", max_cycles=2),
+                                dict(tail_warp_rows=False), dict(tail_rows=1024)])
+def test_step_equals_refactor_then_solve_kkt200(kw):
+    seq = KKTSequence("kkt200")
+    a, f = _pair(seq.rowptr, seq.colind, seq.values(0), **kw)
+    for k in range(seq.M):
+        v = seq.values(k)
+        b, _ = seq.rhs(k, v)
+        a.refactor(v)
+        xa, ia, na = a.solve(b, tol=1e-12, allow_not_converged=True)
+        xf, i_f, nf = f.step(v, b, tol=1e-12, allow_not_converged=True)
+        assert a.last_status == f.last_status
+        assert np.array_equal(xa, xf), k
+        assert ia == i_f and na == nf
+        fa, ff = a.factors(), f.factors()
+        assert np.array_equal(fa["Ux"], ff["Ux"]) and np.array_equal(fa["Lx"], ff["Lx"])
+
+
+def test_step_with_refinement_iterations(oracle_mod):
+    n = 2000
+    rp, ci, v = small_random_sparse(n, 4.0 / n, 23, diag_boost=1.0)
+    P, Q, _ = oracle_mod.lu(n, rp, ci, v)
+    a, f = _pair(rp, ci, P=P, Q=Q, boost_eps=1e-3)
+    b = np.random.default_rng(3).standard_normal(n)
+    a.refactor(v)
+    xa, ia, na = a.solve(b, tol=1e-12)
+    xf, i_f, nf = f.step(v, b, tol=1e-12)
+    assert ia == i_f and ia >= 5 and np.array_equal(xa, xf)
+
+
+def test_step_device_arrays_and_full_size():
+    import torch
+    seq = KKTSequence("kkt2000", steps=4)
+    a, f = _pair(seq.rowptr, seq.colind, seq.values(0))
+    for k in range(seq.M):
+        v = torch.from_numpy(seq.values(k)).cuda()
+        b = torch.from_numpy(seq.rhs(k, seq.values(k))[0]).cuda()
+        xa, xf = torch.empty_like(b), torch.empty_like(b)
+        a.refactor(v)
+        _, ia, na = a.solve(b, x=xa, tol=1e-12)
+        _, i_f, nf = f.step(v, b, x=xf, tol=1e-12)
+        torch.cuda.synchronize()
+        assert torch.equal(xa, xf) and ia == i_f and na == nf
+    # a plain solve after a step recomputes y itself
+    xf2 = torch.empty_like(b)
+    f.solve(b, x=xf2, tol=1e-12)
+    torch.cuda.synchronize()
+    assert torch.equal(xf2, xf)
