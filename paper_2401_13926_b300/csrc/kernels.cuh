@@ -224,12 +224,16 @@ struct SliceVals {   // row values in shared memory: entry p at w[p - b]
     __device__ T operator()(int64_t p) const { return w[p - b]; }
 };
 
+// One load per lane in flight (same bits as the sweep's batched loads):
+// fewer registers in the refactorization kernels that carry it.
 template <typename T, class Vals>
-__device__ bool fused_forward_row(int row, int64_t lo, int64_t hi, Vals vals, const int32_t* __restrict__ Fj,
-                                  const FwdArgs<T>& fw, DevScal* s, long long limit) {
+__device__ __forceinline__ bool fused_forward_row(int row, int64_t lo, int64_t hi, Vals vals,
+                                                  const int32_t* __restrict__ Fj, const FwdArgs<T>& fw, DevScal* s,
+                                                  long long limit) {
     const GiveUpGlobal gu{&s->abort};
     T val;
-    if (!trsv_row_v<true>(lo, hi, vals, SrcGlobal<T>{Fj, fw.y}, (T)fw.rhs[fw.P[row]], T(1), limit, gu, &val)) {
+    if (!trsv_row_v<true, T, Vals, SrcGlobal<T>, GiveUpGlobal, 1>(lo, hi, vals, SrcGlobal<T>{Fj, fw.y},
+                                                                (T)fw.rhs[fw.P[row]], T(1), limit, gu, &val)) {
         if ((threadIdx.x & 31) == 0) fail_row(s, row);
         return false;
     }
@@ -296,7 +300,7 @@ __device__ __forceinline__ int64_t find_col(const int32_t* __restrict__ Fj, int6
     return lo;
 }
 
-template <typename T>
+template <typename T, bool FUSED>
 __global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
                            const int64_t* __restrict__ Fdiag, T* Fx, T* rinv, unsigned* done, DevScal* s,
                            double boost_eps, long long limit, FwdArgs<T> fw) {
@@ -345,7 +349,7 @@ __global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t*
             }
         }
         __syncwarp();
-        if (fw.rhs && !fused_forward_row<T>(row, b, d, CgVals<T>{Fx}, Fj, fw, s, limit)) return;
+        if (FUSED && !fused_forward_row<T>(row, b, d, CgVals<T>{Fx}, Fj, fw, s, limit)) return;
     }
 }
 
@@ -436,7 +440,7 @@ __device__ __forceinline__ int slice_pos(const int32_t* cols, int lo, int len, i
 // in the warp's slice of shared memory: the same steps, the same fused
 // multiply-add per entry in ascending k, and the same publication as a
 // block row.  Returns false if a wait gave up.
-template <typename T>
+template <typename T, bool FUSED>
 __device__ bool tail_warp_row(int row, int t0, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
                               const int64_t* __restrict__ Fdiag, T* Fx, T* rinv, const double* __restrict__ vals,
                               const int64_t* __restrict__ fsrc, DevScal* s, T boost, long long limit,
@@ -492,11 +496,11 @@ __device__ bool tail_warp_row(int row, int t0, const int64_t* __restrict__ Fp, c
         }
     }
     __syncwarp();
-    if (fw.rhs) return fused_forward_row<T>(row, b, d, SliceVals<T>{w, b}, Fj, fw, s, limit);
+    if (FUSED) return fused_forward_row<T>(row, b, d, SliceVals<T>{w, b}, Fj, fw, s, limit);
     return true;
 }
 
-template <typename T>
+template <typename T, bool FUSED>
 __global__ void __launch_bounds__(TAIL_THREADS)
 k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, int wsteps, int wlen,
                 const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
@@ -524,7 +528,8 @@ k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, 
             if (__syncthreads_or(first >= t1 || ld_volatile_int(&s->abort))) break;
             const int row = first + warp;
             if (row < t1)
-                tail_warp_row<T>(row, t0, Fp, Fj, Fdiag, Fx, rinv, vals, fsrc, s, boost, limit, trace, wsd, ww, wc, fw);
+                tail_warp_row<T, FUSED>(row, t0, Fp, Fj, Fdiag, Fx, rinv, vals, fsrc, s, boost, limit, trace, wsd,
+                                        ww, wc, fw);
             __syncthreads();   // the slices and s_row are reused
         }
         if (__syncthreads_or(ld_volatile_int(&s->abort))) return;   // uniform for the block
@@ -640,7 +645,7 @@ k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, 
         }
         // the fused forward sweep's y_row, by warp 0 from the row in shared
         // memory; the other warps wait at the next row's first barrier
-        if (fw.rhs && tid < 32) fused_forward_row<T>(row, b, d, SliceVals<T>{w, b}, Fj, fw, s, limit);
+        if (FUSED && tid < 32) fused_forward_row<T>(row, b, d, SliceVals<T>{w, b}, Fj, fw, s, limit);
     }
 }
 

@@ -527,22 +527,25 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
     }
     if (e != cudaSuccess) { delete c; return KKT_ERR_CUDA; }
     c->mixed = c->o.precision == KKT_PRECISION_MIXED;
-    int per_sm = 0, per_sm2 = 0, per_sm3 = 0;
+    int per_sm = 0, per_sm2 = 0, per_sm3 = 0, per_sm4 = 0;
     if (c->mixed) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kkt::k_lsolve_bulk<float>, PERSIST_THREADS, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kkt::k_refactor<float>, PERSIST_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kkt::k_refactor<float, false>, PERSIST_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm4, kkt::k_refactor<float, true>, PERSIST_THREADS, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, kkt::k_usolve_bulk<float>, PERSIST_THREADS, 0);
     } else {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kkt::k_lsolve_bulk<double>, PERSIST_THREADS, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kkt::k_refactor<double>, PERSIST_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kkt::k_refactor<double, false>, PERSIST_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm4, kkt::k_refactor<double, true>, PERSIST_THREADS, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, kkt::k_usolve_bulk<double>, PERSIST_THREADS, 0);
     }
     for (const void* fn : {(const void*)kkt::k_lsolve_chain<double>, (const void*)kkt::k_usolve_chain<double>,
                            (const void*)kkt::k_lsolve_chain<float>, (const void*)kkt::k_usolve_chain<float>})
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * CHAIN_MAX));
-    for (const void* fn : {(const void*)kkt::k_refactor_tail<double>, (const void*)kkt::k_refactor_tail<float>})
+    for (const void* fn : {(const void*)kkt::k_refactor_tail<double, false>, (const void*)kkt::k_refactor_tail<float, false>,
+                           (const void*)kkt::k_refactor_tail<double, true>, (const void*)kkt::k_refactor_tail<float, true>})
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TAIL_SMEM_MAX);
-    per_sm = std::max(1, std::min(per_sm, std::min(per_sm2, per_sm3)));
+    per_sm = std::max(1, std::min(std::min(per_sm, per_sm4), std::min(per_sm2, per_sm3)));
     c->persist_blocks = c->num_sms * per_sm;
     *out = c;
     return KKT_OK;
@@ -650,9 +653,17 @@ int setup_tail(kkt_ctx* c) {
     }
     if (c->t0 < n) {
         int per_sm = 0;
-        const void* fn = c->mixed ? (const void*)kkt::k_refactor_tail<float>
-                                  : (const void*)kkt::k_refactor_tail<double>;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kkt::TAIL_THREADS, c->tail_smem));
+        // both instantiations (plain, and with the fused forward sweep); the
+        // grid is sized for the one with fewer resident blocks
+        per_sm = 1 << 30;
+        for (const void* fn : {c->mixed ? (const void*)kkt::k_refactor_tail<float, false>
+                                        : (const void*)kkt::k_refactor_tail<double, false>,
+                               c->mixed ? (const void*)kkt::k_refactor_tail<float, true>
+                                        : (const void*)kkt::k_refactor_tail<double, true>}) {
+            int b = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kkt::TAIL_THREADS, c->tail_smem));
+            per_sm = std::min(per_sm, b);
+        }
         c->tail_blocks = std::max(1, per_sm) * c->num_sms;
     }
     return KKT_OK;
@@ -868,7 +879,8 @@ void refactor_launch(kkt_ctx* c, const double* vals, unsigned long long* trace, 
     t = phase_begin(c, KKT_PHASE_REFACTOR);
     c->launches += 2;
     if (c->t0 > 0) {
-        kkt::k_refactor<T><<<grid_for(c, c->t0), PERSIST_THREADS, 0, c->stream>>>(
+        auto kern = fused_rhs ? kkt::k_refactor<T, true> : kkt::k_refactor<T, false>;
+        kern<<<grid_for(c, c->t0), PERSIST_THREADS, 0, c->stream>>>(
             c->t0, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, c->d_done_f, c->d_s, c->o.boost_eps, spin(c), fw);
         c->launches += 1;
     }
@@ -878,7 +890,8 @@ void refactor_launch(kkt_ctx* c, const double* vals, unsigned long long* trace, 
         // the bulk kernel left ticket_fact at >= t0; restart it for the tail
         kkt::k_refactor_prep_tail<<<1, 1, 0, c->stream>>>(c->d_s);
         const int blocks = std::min(n - c->t0, c->tail_blocks);
-        kkt::k_refactor_tail<T><<<blocks, kkt::TAIL_THREADS, c->tail_smem, c->stream>>>(
+        auto kern = fused_rhs ? kkt::k_refactor_tail<T, true> : kkt::k_refactor_tail<T, false>;
+        kern<<<blocks, kkt::TAIL_THREADS, c->tail_smem, c->stream>>>(
             c->t0, c->t1, n, c->tail_mlo, c->tail_max_steps, c->tail_max_len, c->tail_wsteps, c->tail_wlen,
             c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, vals, c->d_fsrc, c->d_s, c->o.boost_eps, spin(c), trace, fw);
         c->launches += 2;

@@ -85,7 +85,10 @@ __device__ __forceinline__ bool spin_value(const volatile T* p, T* v, long long 
 // The factor values of the row come from `vals(p)`; trsv_row below reads
 // them through the read-only cache from a factor array no kernel of the
 // sweep writes.
-template <bool LOWER, typename T, class Vals, class Src, class GiveUp>
+// BATCH: early entries per lane whose loads are in flight together; it
+// changes no sum (each lane accumulates its entries in the same order), so
+// every BATCH gives the same bits -- a smaller one needs fewer registers.
+template <bool LOWER, typename T, class Vals, class Src, class GiveUp, int BATCH = ROW_BATCH>
 __device__ __forceinline__ bool trsv_row_v(int64_t lo, int64_t hi, Vals vals, Src src,
                                            T r0, T rinv, long long limit, GiveUp give_up, T* out) {
     constexpr int NLATE = LOWER ? NLATE_L : NLATE_U;
@@ -110,19 +113,19 @@ __device__ __forceinline__ bool trsv_row_v(int64_t lo, int64_t hi, Vals vals, Sr
     }
     int ok = 1;
     T acc = T(0);
-    for (int64_t base = elo + lane; base < ehi && ok; base += 32 * ROW_BATCH) {
-        T a[ROW_BATCH], v[ROW_BATCH];
-        const volatile T* s[ROW_BATCH];
+    for (int64_t base = elo + lane; base < ehi && ok; base += 32 * BATCH) {
+        T a[BATCH], v[BATCH];
+        const volatile T* s[BATCH];
 #pragma unroll
-        for (int u = 0; u < ROW_BATCH; u++) {
+        for (int u = 0; u < BATCH; u++) {
             const int64_t p = base + 32 * u;
             if (p < ehi) { a[u] = vals(p); s[u] = src(p); }
         }
 #pragma unroll
-        for (int u = 0; u < ROW_BATCH; u++)
+        for (int u = 0; u < BATCH; u++)
             if (base + 32 * u < ehi) v[u] = *s[u];
 #pragma unroll
-        for (int u = 0; u < ROW_BATCH; u++) {
+        for (int u = 0; u < BATCH; u++) {
             if (base + 32 * u >= ehi) continue;
             if (!spin_value<Src::kPollNs>(s[u], &v[u], limit, give_up)) { ok = 0; break; }
             acc = fma(a[u], v[u], acc);
