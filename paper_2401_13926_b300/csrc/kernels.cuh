@@ -890,7 +890,11 @@ k_trsv_cluster(int n, const int32_t* __restrict__ list, const int32_t* __restric
         const int orow = LOWER ? row : perm[row];
         T val;
         const bool ok = LOWER ? trsv_row<true>(Fp[row], d, Fx, src, r0, rinv, limit, gu, &val)
-                              : trsv_row<false>(d + 1, Fp[row + 1], Fx, src, r0, rinv, limit, gu, &val);
+                              // one early load per lane in flight: at the 64-register cap of
+                              // 1024-thread blocks the batched loads spilled (U-sweep 2.08 ->
+                              // 1.89 ms on kkt2000; same bits)
+                              : trsv_row_v<false, T, LdgVals<T>, SrcCluster<T>, GiveUpGlobal, 1>(
+                                    d + 1, Fp[row + 1], LdgVals<T>{Fx}, src, r0, rinv, limit, gu, &val);
         if (!ok) {
             if (lane == 0) fail_row(s, row);
             break;
