@@ -28,10 +28,11 @@ namespace kkt {
 
 constexpr unsigned long long SENTINEL_BITS = 0x7ff4dead5ca1ab1eull;
 constexpr unsigned SENTINEL_BITS_F32 = 0x7fa5ca1eu;   // the FP32 (mixed precision) counterpart
-// late entries per row, tuned per sweep on kkt2000 (L: 2 of 1..3; U: 6 of
-// 2..8 -- U rows are longer and take more of their dependencies late)
+// late entries per row, tuned per sweep on kkt2000 (L: 2 of 1..3; U: 8 of
+// 2..10 with one early load per lane -- U rows are longer and take more of
+// their dependencies late)
 constexpr int NLATE_L = 2;
-constexpr int NLATE_U = 6;
+constexpr int NLATE_U = 8;
 constexpr int ROW_BATCH = 4;    // early entries per lane with loads in flight together
 
 __device__ __forceinline__ double sentinel() { return __longlong_as_double((long long)SENTINEL_BITS); }
