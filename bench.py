@@ -51,6 +51,12 @@ def parse():
                     help="independent sequences of the serving measurement (0 = skip)")
     ap.add_argument("--serve-steps", type=int, default=10)
     ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-c4", type=int, default=0,
+                    help="mixed-size serving run: this many instances, bus counts uniform in "
+                         "[200, --serve-c4-buses], Poisson arrivals, each instance's steps closed-loop (0 = skip)")
+    ap.add_argument("--serve-c4-buses", type=int, default=2000)
+    ap.add_argument("--serve-c4-rate", type=float, default=50.0, help="instance arrivals per second")
+    ap.add_argument("--serve-c4-steps", type=int, default=10)
     return ap.parse_args()
 
 
@@ -204,10 +210,39 @@ def roofline(phases, info, seq, steps):
 
 
 # -------------------------------------------------------------------- oracle
+def host_cpu():
+    """CPU model and core count of the host (for the CPU-baseline record)."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
 def oracle_sample(seq, seconds, steps=None):
     """The CPU oracle as it stands: analysis once (not timed), then refactor +
-    FGMRES per matrix until `seconds` (or `steps`) are used."""
+    FGMRES per matrix until `seconds` (or `steps`) are used, on one core
+    (the calling thread is pinned to the first CPU it may use)."""
     from oracle import oracle as O
+    saved = None
+    try:
+        saved = os.sched_getaffinity(0)
+        os.sched_setaffinity(0, {min(saved)})
+    except (AttributeError, OSError):
+        saved = None
+    try:
+        return _oracle_sample(O, seq, seconds, steps)
+    finally:
+        if saved:
+            os.sched_setaffinity(0, saved)
+
+
+def _oracle_sample(O, seq, seconds, steps):
     v0 = seq.values(0)
     t0 = time.perf_counter()
     P, Q, _ = O.lu(seq.n, seq.rowptr, seq.colind, v0)
@@ -244,7 +279,7 @@ def run_reference(args):
         "ms_per_step": 1000 * t / done, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": workload_config(seq),
-        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", **host_cpu(),
                          "sample": f"{done} matrices of the {args.workload} sequence, oracle analysis "
                                    f"({t_an:.1f} s) excluded, single thread"},
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -291,6 +326,55 @@ def serve_measure(K, args, rank):
             "step_ms": {"p50": float(np.percentile(run, 50)), "p99": float(np.percentile(run, 99))},
             "timing": "host wall clock, submit of all steps to the last completion; includes host<->device "
                       "copies of values, b and x"}
+
+
+def serve_c4(K, args, rank):
+    """Mixed-size serving: instances with bus counts drawn uniformly from
+    [200, serve_c4_buses] arrive at Poisson times (rate serve_c4_rate per
+    second); each runs its own sequence closed-loop (step k+1 is submitted
+    when step k returns).  Instances are analysed before the clock starts
+    (the paper, too, excludes the one-time analysis).  Latency is from a
+    step's submission to its completion."""
+    import threading
+    from paper_2401_13926_b300.workload import KKTSequence
+    rng = np.random.default_rng(7000 + rank)
+    N, S = args.serve_c4, args.serve_c4_steps
+    buses = rng.integers(200, args.serve_c4_buses + 1, size=N)
+    seqs = [KKTSequence("kkt2000", instance=5000 + 100 * rank + i, buses=int(nb), steps=S)
+            for i, nb in enumerate(buses)]
+    data = [[(q.values(k), q.rhs(k, q.values(k))[0]) for k in range(S)] for q in seqs]
+    srv = K.KKTServer(workers=args.serve_workers, restart=RESTART)
+    t_open = time.perf_counter()
+    ids = [srv.open(q.rowptr, q.colind, q.values(0)) for q in seqs]
+    t_open = time.perf_counter() - t_open
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_c4_rate, size=N))
+    results = [[] for _ in range(N)]
+
+    def client(i, t_start):
+        delay = t_start + arrivals[i] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        for k in range(S):
+            t, _ = srv.submit(ids[i], *data[i][k], tol=TOL)
+            results[i].append(srv.wait(t)[1])
+
+    t0 = time.perf_counter()
+    threads = [threading.Thread(target=client, args=(i, t0)) for i in range(N)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    dt = time.perf_counter() - t0
+    srv.close()
+    res = [r for rr in results for r in rr]
+    lat = np.array([r["queue_ms"] + r["run_ms"] for r in res])
+    return {"value": len(res) / dt, "unit": "solves/s", "instances": N, "steps_per_instance": S,
+            "buses": [int(b) for b in buses], "n": [int(q.n) for q in seqs],
+            "arrival_rate_per_s": args.serve_c4_rate, "workers": args.serve_workers,
+            "converged": int(sum(r["status"] == 0 for r in res)), "max_nrbe": float(max(r["nrbe"] for r in res)),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "analysis_s_total": t_open,
+            "timing": "host wall clock from the first arrival to the last completion"}
 
 
 def run_ours(args):
@@ -409,6 +493,7 @@ def run_ours(args):
     serving = None
     if args.serve_instances > 0:
         serving = serve_measure(K, args, rank)
+    serving_c4 = serve_c4(K, args, rank) if args.serve_c4 > 0 else None
     if rank != 0:
         return
 
@@ -417,7 +502,7 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline:
         done, tcpu, t_an, _ = oracle_sample(KKTSequence(args.workload), args.cpu_seconds)
-        cpu = {"value": done / tcpu, "unit": "solves/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": done / tcpu, "unit": "solves/s", "cores": 1, "kind": "oracle", **host_cpu(),
                "sample": f"{done} matrices of the {args.workload} sequence (about {args.cpu_seconds:g} s), "
                          f"oracle analysis ({t_an:.1f} s) excluded, single thread"}
 
@@ -436,7 +521,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": (info_b["h2d_bytes"] - info_a["h2d_bytes"]) // n_e2e,
                 "d2h_bytes_per_step": (info_b["d2h_bytes"] - info_a["d2h_bytes"]) // n_e2e},
         "gpu_launches": launches, "clocks": clk, "wall_s": t_wall,
-        "precision": args.precision, "other_precision": other, "serving": serving,
+        "precision": args.precision, "other_precision": other, "serving": serving, "serving_mixed": serving_c4,
         "schedule": {"tail_rows": info0["tail_rows"], "trisolve_cluster": info0["trisolve_cluster"],
                      "chosen_by": "default" if args.no_tune else "kkt_tune at setup"},
         "analysis": {"analyze_ms": info0["analyze_ms"], "nnz_l": info0["nnz_l"], "nnz_u": info0["nnz_u"],
