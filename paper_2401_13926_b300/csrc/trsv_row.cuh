@@ -8,13 +8,16 @@
 // FP64 on B300 has a dependent-operation latency of about 64 cycles, so a
 // five-step warp reduction of doubles costs ~600 cycles -- more than the
 // rest of a dependency hand-off -- and the FP64 pipe is scarce (about 1.6
-// fused multiply-adds per clock per SM).  A row therefore splits its entries in two:
-// the EARLY ones are summed lane-parallel and warp-reduced while the LATE
-// ones -- the row's few most recent dependencies, which finish last -- are
-// still in flight; lane 0 then folds the late ones in one fused
-// multiply-add each, in a fixed order.  Only that last FMA (and, for U, one
-// multiply) sits on the dependency chain.  Which entries are late is fixed
-// by the row's structure, so the result does not depend on timing.
+// fused multiply-adds per clock per SM).  A row therefore splits its entries
+// in up to three tiers by how recently their dependencies finish: the EARLY
+// ones are summed lane-parallel and warp-reduced; the MIDDLE ones (U only)
+// go one per lane and are tree-reduced over only as many lanes as there are
+// of them; the LATE ones -- the few most recent -- are folded by lane 0 in
+// one fused multiply-add each, in a fixed order.  Only that last FMA (and,
+// for U, one multiply) sits on the dependency chain when the dependencies
+// arrive in order; a middle-tier dependency arriving last costs a short tree
+// instead of a string of serial FMAs.  The tiers are fixed by the row's
+// structure, so the result does not depend on timing.
 //
 // Values are read through `Src`, which maps an entry p to the address of
 // its operand (shared, distributed shared or global memory, all accessed as
@@ -28,11 +31,14 @@ namespace kkt {
 
 constexpr unsigned long long SENTINEL_BITS = 0x7ff4dead5ca1ab1eull;
 constexpr unsigned SENTINEL_BITS_F32 = 0x7fa5ca1eu;   // the FP32 (mixed precision) counterpart
-// late entries per row, tuned per sweep on kkt2000 (L: 2 of 1..3; U: 8 of
-// 2..10 with one early load per lane -- U rows are longer and take more of
-// their dependencies late)
+// Late and middle entries per row, tuned per sweep on kkt2000.  L: 2 late,
+// no middle tier (its kernel sits at the register cap).  U: 6 late and a
+// middle tier of 16 (swept late 2..10, middle 0..24): U rows are longer and
+// take more of their dependencies recently.
 constexpr int NLATE_L = 2;
-constexpr int NLATE_U = 8;
+constexpr int NMID_L = 0;
+constexpr int NLATE_U = 6;
+constexpr int NMID_U = 16;
 constexpr int ROW_BATCH = 4;    // early entries per lane with loads in flight together
 
 __device__ __forceinline__ double sentinel() { return __longlong_as_double((long long)SENTINEL_BITS); }
@@ -93,11 +99,25 @@ template <bool LOWER, typename T, class Vals, class Src, class GiveUp, int BATCH
 __device__ __forceinline__ bool trsv_row_v(int64_t lo, int64_t hi, Vals vals, Src src,
                                            T r0, T rinv, long long limit, GiveUp give_up, T* out) {
     constexpr int NLATE = LOWER ? NLATE_L : NLATE_U;
+    constexpr int NMID = LOWER ? NMID_L : NMID_U;
     const int lane = threadIdx.x & 31;
     const int64_t len = hi - lo;
     const int nl = (int)(len < NLATE ? len : NLATE);
-    const int64_t elo = LOWER ? lo : lo + nl;
-    const int64_t ehi = LOWER ? hi - nl : hi;
+    const int nm = NMID == 0 ? 0 : (int)((len - nl) < NMID ? (len - nl) : NMID);
+    // L: [lo .. early .. | middle | late .. hi); U: [lo late | middle | early .. hi)
+    const int64_t elo = LOWER ? lo : lo + nl + nm;
+    const int64_t ehi = LOWER ? hi - nl - nm : hi;
+    // the middle tier's loads start first: entry `lane` of the tier
+    T ma = T(0), mv = T(0);
+    const volatile T* ms = nullptr;
+    if constexpr (NMID > 0) {
+        if (lane < nm) {
+            const int64_t p = LOWER ? hi - nl - nm + lane : lo + nl + lane;
+            ma = vals(p);
+            ms = src(p);
+            mv = *ms;
+        }
+    }
     // lane 0 starts the loads of the late entries first
     T la[NLATE], lv[NLATE];
     const volatile T* ls[NLATE];
@@ -143,6 +163,20 @@ __device__ __forceinline__ bool trsv_row_v(int64_t lo, int64_t hi, Vals vals, Sr
         for (o >>= 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     }
     T r = r0 - acc;
+    if constexpr (NMID > 0) {
+        if (nm > 0) {
+            T prod = T(0);
+            if (lane < nm) {
+                if (!spin_value<Src::kPollNs>(ms, &mv, limit, give_up)) ok = 0;
+                else prod = ma * mv;
+            }
+            if (!__all_sync(0xffffffffu, ok)) return false;
+            int o = 1;
+            while (o < nm) o <<= 1;
+            for (o >>= 1; o > 0; o >>= 1) prod += __shfl_xor_sync(0xffffffffu, prod, o);
+            r -= prod;
+        }
+    }
     if (lane == 0) {
 #pragma unroll
         for (int j = 0; j < NLATE; j++) {
