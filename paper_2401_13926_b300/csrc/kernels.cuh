@@ -461,12 +461,36 @@ __device__ bool tail_warp_row(int row, int t0, const int64_t* __restrict__ Fp, c
         }
     }
     __syncwarp();
+    // the next step's pivot reciprocal and first entries of U(k,:) (one per
+    // lane) are loaded while the current step runs
+    T nrk = T(0), nv = T(0);
+    int ncol = 0;
+    auto prefetch = [&](int st) {
+        if (st >= nsteps) return;
+        const StepDesc ds = sd[st];
+        nrk = ld_relaxed(&rinv[ds.k]);
+        if (lane < ds.cnt) {
+            ncol = Fj[ds.dk + 1 + lane];
+            nv = ld_relaxed(&Fx[ds.dk + 1 + lane]);
+        }
+    };
+    prefetch(0);
     for (int step = 0; step < nsteps; step++) {
         const StepDesc dsc = sd[step];
-        T rk = ld_relaxed(&rinv[dsc.k]);
+        T rk = nrk, v0 = nv;
+        const int c0 = ncol;
+        prefetch(step + 1);
         int ok = tail_wait(&rinv[dsc.k], &rk, s, limit, row);
         const T l = w[step] * rk;   // l_ik = w_k * (1/u_kk)
-        for (int e2 = lane; e2 < dsc.cnt && ok; e2 += 32) {
+        if (ok && lane < dsc.cnt) {   // the prefetched entry
+            if (!tail_wait(&Fx[dsc.dk + 1 + lane], &v0, s, limit, row)) ok = 0;
+            else {
+                const int pos = slice_pos(cols, step + 1, len, c0);
+                if (pos < 0) raise_error(s, KKT_ERR_PATTERN, row);
+                else w[pos] = fma(-l, v0, w[pos]);
+            }
+        }
+        for (int e2 = lane + 32; e2 < dsc.cnt && ok; e2 += 32) {
             const int64_t q = dsc.dk + 1 + e2;
             T v = ld_relaxed(&Fx[q]);
             if (!tail_wait(&Fx[q], &v, s, limit, row)) { ok = 0; break; }
