@@ -107,10 +107,12 @@ typedef struct {
                              round trip per step); captured on first use, again when tol
                              changes.  Same kernels in the same order, so the same results.
                              0 = launch from the host (default) */
-    int tail_warp_rows;   /* 1 (default): the leading short rows of the block-per-row part
-                             are refactored one per warp (eight per block) while they fit
-                             an eighth of the block's shared memory; 0: all of it one row
-                             per block.  Same arithmetic either way. */
+    int tail_warp_rows;   /* 1 (default): the leading short rows of the block-per-row part,
+                             and the rows before it, are refactored one per warp (eight
+                             per block) in the same kernel while they fit an eighth of
+                             the block's shared memory; 0: the block-per-row part one row
+                             per block, the rows before it one warp per row with values in
+                             global memory.  Same arithmetic either way. */
 } kkt_opts;
 
 /* Refinement methods (Section 2.1).  FGMRES: FGMRES(m) with M = LU as right

@@ -633,6 +633,7 @@ k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, 
                     w[pos] = fma(-l, v, w[pos]);
                 }
             }
+            tail_load(st, step + 2, nsteps, sd, Fj, Fx, rinv);   // the stage's registers are free again
             const int any_fail = __syncthreads_or(!ok);   // uniform decision for the block
             if (tid == 0) w[step] = l;   // nobody else touches position `step` any more
             step++;
@@ -641,20 +642,21 @@ k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, 
         bool ok = true;
         while (step < nsteps && ok) {
             ok = run_step(A);
-            tail_load(A, step + 1, nsteps, sd, Fj, Fx, rinv);
             if (!ok || step >= nsteps) break;
             ok = run_step(B);
-            tail_load(B, step + 1, nsteps, sd, Fj, Fx, rinv);
         }
         if (!ok) return;
-        __syncthreads();   // the last L value written by thread 0 is visible
-        // publish: every value but the diagonal, then (thread 0) the pivot
+        // publish: thread 0 the pivot first (the row's U part is final
+        // after the last step's barrier), then every thread its share of
+        // the other values; the last step's l, which thread 0 wrote after
+        // that barrier, thread 0 stores itself
         for (int q = tid; q < len; q += blockDim.x) {
-            if (b + q != d) st_relaxed(&Fx[b + q], w[q]);
+            if (b + q != d && q != nsteps - 1) st_relaxed(&Fx[b + q], w[q]);
             const int c = cols[q];
             if (c >= mlo) map[c - mlo] = -1;
         }
         if (tid == 0) {
+            if (nsteps > 0) st_relaxed(&Fx[b + nsteps - 1], w[nsteps - 1]);
             T u = w[d - b];
             int fail = 0;
             if (!isfinite(u)) { raise_error(s, KKT_ERR_NONFINITE, row); fail = 1; }
@@ -669,7 +671,10 @@ k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, 
         }
         // the fused forward sweep's y_row, by warp 0 from the row in shared
         // memory; the other warps wait at the next row's first barrier
-        if (FUSED && tid < 32) fused_forward_row<T>(row, b, d, SliceVals<T>{w, b}, Fj, fw, s, limit);
+        if (FUSED && tid < 32) {
+            __syncwarp();   // thread 0's last L value
+            fused_forward_row<T>(row, b, d, SliceVals<T>{w, b}, Fj, fw, s, limit);
+        }
     }
 }
 

@@ -598,9 +598,10 @@ int kkt_pivot(int32_t n, const int32_t* rowptr, const int32_t* colind, const dou
 }
 
 namespace {
-// The block-per-row part of the refactorization: the last rows (at most
-// kkt_opts.tail_rows, default 32767), as many as fit their longest row in
-// shared memory.
+// The rows of the shared-memory refactorization kernel: the last rows (at
+// most kkt_opts.tail_rows, default 32767), as many as fit their longest row
+// in shared memory; with tail_warp_rows, the short rows at their start and
+// the rows before them, as far as they fit a warp's slice, go one per warp.
 int setup_tail(kkt_ctx* c) {
     const int n = c->A.n;
     int T = std::min<int>(n, c->o.tail_rows > 0 ? std::min(c->o.tail_rows, 32767) : TAIL_MAX_ROWS);
@@ -648,6 +649,19 @@ int setup_tail(kkt_ctx* c) {
             ml = ln;
         }
         c->t1 = i;
+        // and the rows before the tail as far as they fit the same slice:
+        // those leave the warp-per-row kernel for the tail kernel, so they
+        // run alongside the tail's rows instead of before all of them
+        int32_t lo = c->t0;
+        for (; lo > 0; lo--) {
+            const int32_t r = lo - 1;
+            const int64_t st = std::max<int64_t>(c->lay.Fdiag[r] - c->lay.Fp[r], ms);
+            const int64_t ln = std::max<int64_t>(c->lay.Fp[r + 1] - c->lay.Fp[r], ml);
+            if (((16 * (size_t)st + (vsize + 4) * (size_t)ln + 15) & ~(size_t)15) > slice) break;
+            ms = st;
+            ml = ln;
+        }
+        c->t0 = lo;
         c->tail_wsteps = (int)ms;
         c->tail_wlen = (int)ml;
     }
