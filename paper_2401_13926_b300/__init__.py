@@ -31,6 +31,7 @@ TRSV = {"auto": 0, "global": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 METHOD = {"fgmres": 0, "richardson": 1, "fgmres_ee": 2}
 ORTHO = {"cgs2": 0, "cgs2_pythagoras": 1, "cgs1_pythagoras": 2}
+TAIL_ORDER = {"row": 0, "level": 1}
 
 # every entry point declared in include/kkt.h
 EXPORTS = [
@@ -53,7 +54,7 @@ class _Opts(C.Structure):
         ("device", C.c_int), ("create_stream", C.c_int), ("stream", C.c_void_p), ("spin_limit", C.c_int64),
         ("timing", C.c_int), ("trisolve", C.c_int), ("cluster_blocks", C.c_int), ("tail_rows", C.c_int),
         ("method", C.c_int), ("ortho", C.c_int), ("inner_tol", C.c_double), ("repivot", C.c_int),
-        ("graphs", C.c_int), ("tail_warp_rows", C.c_int),
+        ("graphs", C.c_int), ("tail_warp_rows", C.c_int), ("tail_order", C.c_int),
     ]
 
 
@@ -227,7 +228,7 @@ def lu_solve_noalloc(Fp, Fj, Fdiag, Fx, P, Q, b, x, stream=None):
 def _solver_opts(restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3, boost_eps=0.0,
                  device=0, spin_limit=0, timing=False, trisolve="auto", tail_rows=0, cluster_blocks=0,
                  precision="fp64", method="fgmres", ortho="cgs2", inner_tol=1e-6, repivot=False, graphs=False,
-                 tail_warp_rows=True):
+                 tail_warp_rows=True, tail_order="level"):
     """kkt_opts from keyword arguments (defaults of kkt_default_opts)."""
     o = _Opts()
     lib().kkt_default_opts(C.byref(o))
@@ -242,6 +243,7 @@ def _solver_opts(restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, 
     o.repivot = int(bool(repivot))
     o.graphs = int(bool(graphs))
     o.tail_warp_rows = int(bool(tail_warp_rows))
+    o.tail_order = TAIL_ORDER[tail_order]
     return o
 
 
@@ -252,11 +254,11 @@ class KKTSolver:
     def __init__(self, restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3,
                  boost_eps=0.0, device=0, stream=None, spin_limit=0, timing=False, trisolve="auto",
                  tail_rows=0, cluster_blocks=0, precision="fp64", method="fgmres", ortho="cgs2",
-                 inner_tol=1e-6, repivot=False, graphs=False, tail_warp_rows=True):
+                 inner_tol=1e-6, repivot=False, graphs=False, tail_warp_rows=True, tail_order="level"):
         L = lib()
         o = _solver_opts(restart, max_cycles, stop_mode, refine_delta, pivot_tol, boost_eps, device, spin_limit,
                          timing, trisolve, tail_rows, cluster_blocks, precision, method, ortho, inner_tol, repivot,
-                         graphs, tail_warp_rows)
+                         graphs, tail_warp_rows, tail_order)
         if stream is None:
             stream = _torch_current_stream(device)
         if stream is None:

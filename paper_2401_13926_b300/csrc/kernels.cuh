@@ -527,7 +527,7 @@ __device__ bool tail_warp_row(int row, int t0, const int64_t* __restrict__ Fp, c
 template <typename T, bool FUSED>
 __global__ void __launch_bounds__(TAIL_THREADS)
 k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, int wsteps, int wlen,
-                const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
+                const int32_t* __restrict__ order, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
                 const int64_t* __restrict__ Fdiag, T* Fx, T* rinv, const double* __restrict__ vals,
                 const int64_t* __restrict__ fsrc, DevScal* s, double boost_eps, long long limit,
                 unsigned long long* trace, FwdArgs<T> fw) {
@@ -538,7 +538,8 @@ k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, 
     const T boost = (T)(boost_eps * *(volatile double*)&s->normA);
     // Rows [t0, t1): short rows, one per warp (eight per block), from their
     // own ticket, all of them dispensed before any block row below; each
-    // warp works in its own slice of shared memory.
+    // warp works in its own slice of shared memory.  order[] holds the rows
+    // in dispatch order: order[0, t1 - t0) this part, the rest the block rows.
     if (t1 > t0) {
         const int warp = tid >> 5;
         const size_t slice = ((16 * (size_t)wsteps + (sizeof(T) + 4) * (size_t)wlen) + 15) & ~(size_t)15;
@@ -546,13 +547,13 @@ k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, 
         T* ww = reinterpret_cast<T*>(wsd + wsteps);
         int32_t* wc = reinterpret_cast<int32_t*>(ww + wlen);
         for (;;) {
-            if (tid == 0) s_row = t0 + (int)atomicAdd(&s->ticket_mid, (unsigned)(TAIL_THREADS / 32));
+            if (tid == 0) s_row = (int)atomicAdd(&s->ticket_mid, (unsigned)(TAIL_THREADS / 32));
             __syncthreads();
             const int first = s_row;
-            if (__syncthreads_or(first >= t1 || ld_volatile_int(&s->abort))) break;
-            const int row = first + warp;
-            if (row < t1)
-                tail_warp_row<T, FUSED>(row, t0, Fp, Fj, Fdiag, Fx, rinv, vals, fsrc, s, boost, limit, trace, wsd,
+            if (__syncthreads_or(first >= t1 - t0 || ld_volatile_int(&s->abort))) break;
+            const int q = first + warp;
+            if (q < t1 - t0)
+                tail_warp_row<T, FUSED>(order[q], t0, Fp, Fj, Fdiag, Fx, rinv, vals, fsrc, s, boost, limit, trace, wsd,
                                         ww, wc, fw);
             __syncthreads();   // the slices and s_row are reused
         }
@@ -566,7 +567,10 @@ k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, 
     for (int c = tid; c < M; c += blockDim.x) map[c] = -1;
     __syncthreads();
     for (;;) {
-        if (tid == 0) s_row = t1 + (int)atomicAdd(&s->ticket_fact, 1u);
+        if (tid == 0) {
+            const int q = (int)atomicAdd(&s->ticket_fact, 1u);
+            s_row = q < nrows - t1 ? order[(t1 - t0) + q] : nrows;
+        }
         __syncthreads();
         const int row = s_row;
         const int stop = __syncthreads_or(row >= nrows || ld_volatile_int(&s->abort));

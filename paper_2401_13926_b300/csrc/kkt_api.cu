@@ -69,6 +69,7 @@ struct kkt_ctx {
     size_t tail_smem = 0;
     int tail_blocks = 0;
     int tail_max_steps = 1, tail_max_len = 1, tail_mlo = 0;
+    int32_t* d_tail_order = nullptr;   // rows [t0, n) in dispatch order: [t0, t1) part, then [t1, n) part
     DevScal* d_s = nullptr;
     DevScal* h_s = nullptr;   // pinned mirror
     int64_t ld = 0;
@@ -477,6 +478,7 @@ void kkt_default_opts(kkt_opts* o) {
     o->repivot = 0;
     o->graphs = 0;
     o->tail_warp_rows = 1;
+    o->tail_order = 1;
 }
 
 const char* kkt_strerror(int code) {
@@ -511,7 +513,8 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
         c->o.method < KKT_METHOD_FGMRES || c->o.method > KKT_METHOD_FGMRES_EE ||
         c->o.ortho < KKT_ORTHO_CGS2 || c->o.ortho > KKT_ORTHO_CGS1_PYTH ||
         !(c->o.inner_tol > 0.0 && c->o.inner_tol <= 1.0) || (c->o.repivot != 0 && c->o.repivot != 1) ||
-        (c->o.graphs != 0 && c->o.graphs != 1) || (c->o.tail_warp_rows != 0 && c->o.tail_warp_rows != 1)) {
+        (c->o.graphs != 0 && c->o.graphs != 1) || (c->o.tail_warp_rows != 0 && c->o.tail_warp_rows != 1) ||
+        (c->o.tail_order != 0 && c->o.tail_order != 1)) {
         delete c;
         return KKT_ERR_INVALID;
     }
@@ -666,6 +669,22 @@ int setup_tail(kkt_ctx* c) {
         c->tail_wlen = (int)ml;
     }
     if (c->t0 < n) {
+        // dispatch order: each part by level in the DAG of L (ties by row),
+        // so rows whose dependencies finish first start first; a row's
+        // dependencies are at lower levels, so they are dispatched before it
+        std::vector<int32_t> order((size_t)(n - c->t0));
+        std::iota(order.begin(), order.end(), c->t0);
+        if (c->o.tail_order) {
+            const std::vector<int32_t>& lev = c->lay.levL;
+            auto by_level = [&](int32_t a, int32_t b) { return lev[a] < lev[b] || (lev[a] == lev[b] && a < b); };
+            std::sort(order.begin(), order.begin() + (c->t1 - c->t0), by_level);
+            std::sort(order.begin() + (c->t1 - c->t0), order.end(), by_level);
+        }
+        CK(cudaMemcpyAsync(c->d_tail_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));   // `order` is a local
+    }
+    if (c->t0 < n) {
         int per_sm = 0;
         // both instantiations (plain, and with the fused forward sweep); the
         // grid is sized for the one with fewer resident blocks
@@ -789,6 +808,7 @@ int setup_device(kkt_ctx* c, const kkt::ColStructure& S, std::chrono::steady_clo
     fill_y_sentinel(c);
     if (c->o.trisolve == KKT_TRSV_AUTO) pick_cluster(c);
     else c->cluster = 0;
+    if ((rc = dalloc(c, &c->d_tail_order, (size_t)n))) return rc;
     if ((rc = setup_tail(c))) return rc;
     if ((rc = dalloc(c, &c->d_s, 1))) return rc;
     CK(cudaMemsetAsync(c->d_s, 0, sizeof(DevScal), c->stream));
@@ -907,7 +927,8 @@ void refactor_launch(kkt_ctx* c, const double* vals, unsigned long long* trace, 
         auto kern = fused_rhs ? kkt::k_refactor_tail<T, true> : kkt::k_refactor_tail<T, false>;
         kern<<<blocks, kkt::TAIL_THREADS, c->tail_smem, c->stream>>>(
             c->t0, c->t1, n, c->tail_mlo, c->tail_max_steps, c->tail_max_len, c->tail_wsteps, c->tail_wlen,
-            c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, vals, c->d_fsrc, c->d_s, c->o.boost_eps, spin(c), trace, fw);
+            c->d_tail_order, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, vals, c->d_fsrc, c->d_s, c->o.boost_eps,
+            spin(c), trace, fw);
         c->launches += 2;
     }
     phase_end(c, t);

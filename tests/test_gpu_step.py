@@ -73,3 +73,22 @@ def test_step_device_arrays_and_full_size():
     f.solve(b, x=xf2, tol=1e-12)
     torch.cuda.synchronize()
     assert torch.equal(xf2, xf)
+
+
+def test_tail_dispatch_order_same_bits():
+    """The shared-memory refactorization's rows dispatched by DAG level or by
+    row give the same factors, bit for bit (each row's arithmetic is fixed;
+    only when it runs changes)."""
+    seq = KKTSequence("kkt200", steps=2)
+    out = []
+    for order in ("row", "level"):
+        s = K.KKTSolver(tail_order=order)
+        s.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
+        v = seq.values(1)
+        b, _ = seq.rhs(1, v)
+        x, it, nr = s.step(v, b)
+        f = s.factors()
+        out.append((f["Lx"].copy(), f["Ux"].copy(), x.copy(), it, nr))
+        s.close()
+    for a, b_ in zip(out[0], out[1]):
+        assert np.array_equal(a, b_)
