@@ -426,14 +426,16 @@ __device__ __forceinline__ bool tail_wait(const T* p, T* v, DevScal* s, long lon
     return true;
 }
 
-// First position in cols[lo, len) holding column c, or -1.
-__device__ __forceinline__ int slice_pos(const int32_t* cols, int lo, int len, int c) {
-    int hi = len;
+// Position in cols[lo, hi) of column c, or -1.  Entry e of U(k,:) (cnt
+// entries, ascending columns, all of them in the row after position `step`)
+// lies in [step + 1 + e, len - (cnt - 1 - e)).
+__device__ __forceinline__ int slice_pos(const int32_t* cols, int lo, int hi, int c) {
+    const int end = hi;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (cols[mid] < c) lo = mid + 1; else hi = mid;
     }
-    return (lo < len && cols[lo] == c) ? lo : -1;
+    return (lo < end && cols[lo] == c) ? lo : -1;
 }
 
 // One short tail row by one warp, its values, columns and step descriptors
@@ -485,18 +487,28 @@ __device__ bool tail_warp_row(int row, int t0, const int64_t* __restrict__ Fp, c
         if (ok && lane < dsc.cnt) {   // the prefetched entry
             if (!tail_wait(&Fx[dsc.dk + 1 + lane], &v0, s, limit, row)) ok = 0;
             else {
-                const int pos = slice_pos(cols, step + 1, len, c0);
+                const int pos = slice_pos(cols, step + 1 + lane, len - (dsc.cnt - 1 - lane), c0);
                 if (pos < 0) raise_error(s, KKT_ERR_PATTERN, row);
                 else w[pos] = fma(-l, v0, w[pos]);
             }
         }
-        for (int e2 = lane + 32; e2 < dsc.cnt && ok; e2 += 32) {
+        // the other entries two per lane at a time, both loads issued first
+        for (int e2 = lane + 32; e2 < dsc.cnt && ok; e2 += 64) {
             const int64_t q = dsc.dk + 1 + e2;
-            T v = ld_relaxed(&Fx[q]);
+            const bool two = e2 + 32 < dsc.cnt;
+            T v = ld_relaxed(&Fx[q]), v2 = T(0);
+            const int c = Fj[q];
+            int c2 = 0;
+            if (two) { v2 = ld_relaxed(&Fx[q + 32]); c2 = Fj[q + 32]; }
             if (!tail_wait(&Fx[q], &v, s, limit, row)) { ok = 0; break; }
-            const int pos = slice_pos(cols, step + 1, len, Fj[q]);
-            if (pos < 0) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
-            w[pos] = fma(-l, v, w[pos]);
+            const int pos = slice_pos(cols, step + 1 + e2, len - (dsc.cnt - 1 - e2), c);
+            if (pos < 0) raise_error(s, KKT_ERR_PATTERN, row);
+            else w[pos] = fma(-l, v, w[pos]);
+            if (!two) break;
+            if (!tail_wait(&Fx[q + 32], &v2, s, limit, row)) { ok = 0; break; }
+            const int pos2 = slice_pos(cols, step + 33 + e2, len - (dsc.cnt - 33 - e2), c2);
+            if (pos2 < 0) raise_error(s, KKT_ERR_PATTERN, row);
+            else w[pos2] = fma(-l, v2, w[pos2]);
         }
         if (!__all_sync(0xffffffffu, ok)) return false;
         __syncwarp();
@@ -808,8 +820,8 @@ template <typename T>
 __global__ void __launch_bounds__(1024)
 k_usolve_chain(int nt, const int32_t* __restrict__ rows, const int32_t* __restrict__ Fpos,
                const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj, const int64_t* __restrict__ Fdiag,
-               const T* __restrict__ Fx, const int32_t* __restrict__ Q, T* y, T* xp, double* __restrict__ out,
-               DevScal* s, long long limit) {
+               const T* __restrict__ Fx, const T* __restrict__ rinv_u, const int32_t* __restrict__ Q, T* y, T* xp,
+               double* __restrict__ out, DevScal* s, long long limit) {
     extern __shared__ __align__(16) unsigned char chain_sh[];
     volatile T* xs = reinterpret_cast<T*>(chain_sh);
     for (int t = threadIdx.x; t < nt; t += blockDim.x) xs[t] = sentinel_of<T>();
@@ -820,7 +832,7 @@ k_usolve_chain(int nt, const int32_t* __restrict__ rows, const int32_t* __restri
         const int row = rows[t];
         const int64_t d = Fdiag[row];
         const T r0 = __ldcg(&y[row]);
-        const T rinv = rcp_rn(__ldg(&Fx[d]));
+        const T rinv = __ldg(&rinv_u[row]);   // 1/u_ii as the refactorization formed it
         const int qrow = Q[row];
         T val;
         if (!trsv_row<false>(d + 1, Fp[row + 1], Fx, SrcChainU<T>{Fj, Fpos, nt, xs, xp}, r0, rinv, 4 * limit, gu,
@@ -841,8 +853,8 @@ k_usolve_chain(int nt, const int32_t* __restrict__ rows, const int32_t* __restri
 template <typename T>
 __global__ void k_usolve_bulk(int nrows, const int32_t* __restrict__ rows, const int64_t* __restrict__ Fp,
                               const int32_t* __restrict__ Fj, const int64_t* __restrict__ Fdiag,
-                              const T* __restrict__ Fx, const int32_t* __restrict__ Q, T* y, T* xp,
-                              double* __restrict__ out, DevScal* s, long long limit) {
+                              const T* __restrict__ Fx, const T* __restrict__ rinv_u, const int32_t* __restrict__ Q,
+                              T* y, T* xp, double* __restrict__ out, DevScal* s, long long limit) {
     const int lane = threadIdx.x & 31;
     const GiveUpGlobal gu{&s->abort};
     for (;;) {
@@ -853,7 +865,7 @@ __global__ void k_usolve_bulk(int nrows, const int32_t* __restrict__ rows, const
         const int row = rows[t];
         const int64_t d = Fdiag[row];
         const T r0 = __ldcg(&y[row]);
-        const T rinv = rcp_rn(__ldg(&Fx[d]));
+        const T rinv = __ldg(&rinv_u[row]);   // 1/u_ii as the refactorization formed it
         const int qrow = Q[row];
         T val;
         if (!trsv_row<false>(d + 1, Fp[row + 1], Fx, SrcGlobal<T>{Fj, xp}, r0, rinv, limit, gu, &val)) {
@@ -900,8 +912,8 @@ template <bool LOWER, typename T, typename TIN, typename TOUT>
 __global__ void __launch_bounds__(CLUSTER_THREADS)
 k_trsv_cluster(int n, const int32_t* __restrict__ list, const int32_t* __restrict__ Fpos,
                const int64_t* __restrict__ Fp, const int64_t* __restrict__ Fdiag, const T* __restrict__ Fx,
-               const int32_t* __restrict__ perm, const TIN* __restrict__ rhs, TOUT* __restrict__ out,
-               DevScal* s, long long limit, unsigned long long* __restrict__ trace) {
+               const T* __restrict__ rinv_u, const int32_t* __restrict__ perm, const TIN* __restrict__ rhs,
+               TOUT* __restrict__ out, DevScal* s, long long limit, unsigned long long* __restrict__ trace) {
     extern __shared__ __align__(16) unsigned char cl_sh[];
     T* xs_cl = reinterpret_cast<T*>(cl_sh);
     cgx::cluster_group cluster = cgx::this_cluster();
@@ -919,7 +931,7 @@ k_trsv_cluster(int n, const int32_t* __restrict__ list, const int32_t* __restric
         const int row = list[t];
         const int64_t d = Fdiag[row];
         const T r0 = LOWER ? (T)rhs[perm[row]] : (T)rhs[row];
-        const T rinv = LOWER ? T(1) : rcp_rn(__ldg(&Fx[d]));
+        const T rinv = LOWER ? T(1) : __ldg(&rinv_u[row]);   // 1/u_ii as the refactorization formed it
         const int orow = LOWER ? row : perm[row];
         T val;
         const bool ok = LOWER ? trsv_row<true>(Fp[row], d, Fx, src, r0, rinv, limit, gu, &val)

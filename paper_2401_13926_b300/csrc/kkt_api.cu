@@ -293,8 +293,8 @@ cudaError_t launch_cluster(kkt_ctx* c, const int32_t* perm, const TIN* rhs, TOUT
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kkt::k_trsv_cluster<LOWER, T, TIN, TOUT>, c->A.n,
                               (const int32_t*)(LOWER ? c->d_listL : c->d_listU), (const int32_t*)c->d_Fpos,
-                              (const int64_t*)c->d_Fp, (const int64_t*)c->d_Fdiag, (const T*)c->d_Fx, perm,
-                              rhs, out, c->d_s, spin(c),
+                              (const int64_t*)c->d_Fp, (const int64_t*)c->d_Fdiag, (const T*)c->d_Fx,
+                              (const T*)c->d_rinv, perm, rhs, out, c->d_s, spin(c),
                               c->solve_trace ? c->solve_trace + (LOWER ? 0 : c->A.n) : nullptr);
 }
 
@@ -381,12 +381,14 @@ void lu_apply_t(kkt_ctx* c, const double* rhs, double* out) {
     t = phase_begin(c, KKT_PHASE_USOLVE);
     if (c->nUc) {
         kkt::k_usolve_chain<T><<<1, CHAIN_THREADS, sizeof(T) * c->nUc, c->stream>>>(
-            c->nUc, c->d_listU, c->d_Fpos, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, c->d_Q, y, xp, out, c->d_s, spin(c));
+            c->nUc, c->d_listU, c->d_Fpos, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, (const T*)c->d_rinv, c->d_Q, y, xp, out,
+            c->d_s, spin(c));
         c->launches += 1;
     }
     if (nUb) {
         kkt::k_usolve_bulk<T><<<grid_for(c, nUb), PERSIST_THREADS, 0, c->stream>>>(
-            nUb, c->d_listU + c->nUc, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, c->d_Q, y, xp, out, c->d_s, spin(c));
+            nUb, c->d_listU + c->nUc, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, (const T*)c->d_rinv, c->d_Q, y, xp, out,
+            c->d_s, spin(c));
         c->launches += 1;
     }
     phase_end(c, t);
@@ -416,12 +418,14 @@ void u_apply_t(kkt_ctx* c, double* out) {
     c->launches += 1;
     if (c->nUc) {
         kkt::k_usolve_chain<T><<<1, CHAIN_THREADS, sizeof(T) * c->nUc, c->stream>>>(
-            c->nUc, c->d_listU, c->d_Fpos, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, c->d_Q, y, xp, out, c->d_s, spin(c));
+            c->nUc, c->d_listU, c->d_Fpos, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, (const T*)c->d_rinv, c->d_Q, y, xp, out,
+            c->d_s, spin(c));
         c->launches += 1;
     }
     if (nUb) {
         kkt::k_usolve_bulk<T><<<grid_for(c, nUb), PERSIST_THREADS, 0, c->stream>>>(
-            nUb, c->d_listU + c->nUc, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, c->d_Q, y, xp, out, c->d_s, spin(c));
+            nUb, c->d_listU + c->nUc, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, (const T*)c->d_rinv, c->d_Q, y, xp, out,
+            c->d_s, spin(c));
         c->launches += 1;
     }
     phase_end(c, t);
