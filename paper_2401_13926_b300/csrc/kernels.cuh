@@ -367,6 +367,37 @@ __global__ void k_refactor_prep_tail(DevScal* s) {
     s->ticket_mid = 0;
 }
 
+// Publish a tail row's pivot u_ii and its reciprocal.  The reciprocal is
+// on the dependency chain, so it is formed first; the checks (non-finite,
+// zero, below the boost threshold) read the bits or run beside it.
+__device__ __forceinline__ bool finite_bits(double v) {
+    return (__double_as_longlong(v) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool finite_bits(float v) { return (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u; }
+__device__ __forceinline__ bool zero_bits(double v) { return (__double_as_longlong(v) << 1) == 0; }
+__device__ __forceinline__ bool zero_bits(float v) { return (__float_as_uint(v) << 1) == 0u; }
+__device__ __forceinline__ bool sign_bit(double v) { return __double_as_longlong(v) < 0; }
+__device__ __forceinline__ bool sign_bit(float v) { return (int)__float_as_uint(v) < 0; }
+
+template <typename T>
+__device__ __forceinline__ bool tail_pivot(T u, T boost, bool use_boost, DevScal* s, int row, T* Fx_d, T* rinv_row) {
+    T ri = rcp_rn(u);
+    if (!finite_bits(u)) { raise_error(s, KKT_ERR_NONFINITE, row); return false; }
+    if (use_boost) {
+        if (fabs(u) < boost) {
+            u = sign_bit(u) ? -boost : boost;
+            ri = rcp_rn(u);
+            atomicAdd(&s->nboost, 1);
+        }
+    } else if (zero_bits(u)) {
+        raise_error(s, KKT_ERR_ZERO_PIVOT, row);
+        return false;
+    }
+    st_relaxed(Fx_d, u);
+    st_relaxed(rinv_row, ri);
+    return true;
+}
+
 // One step's worth of U(k,:) for one thread: up to TAIL_E entries
 // (columns and values) and the pivot reciprocal of row k, loaded two steps
 // ahead from addresses staged in shared memory, so issuing the loads never
@@ -519,17 +550,8 @@ __device__ bool tail_warp_row(int row, int t0, const int64_t* __restrict__ Fp, c
     for (int q = lane; q < len; q += 32)
         if (b + q != d) st_relaxed(&Fx[b + q], w[q]);
     if (lane == 0) {
-        T u = w[d - b];
-        int fail = 0;
-        if (!isfinite(u)) { raise_error(s, KKT_ERR_NONFINITE, row); fail = 1; }
-        else if (boost > 0.0) {
-            if (fabs(u) < boost) { u = (u < 0.0) ? -boost : boost; atomicAdd(&s->nboost, 1); }
-        } else if (u == 0.0) { raise_error(s, KKT_ERR_ZERO_PIVOT, row); fail = 1; }
-        if (!fail) {
-            st_relaxed(&Fx[d], u);
-            st_relaxed(&rinv[row], rcp_rn(u));
-            if (trace) trace[2 * (size_t)(row - t0) + 1] = globaltimer_ns();
-        }
+        if (tail_pivot<T>(w[d - b], boost, boost > T(0), s, row, &Fx[d], &rinv[row]) && trace)
+            trace[2 * (size_t)(row - t0) + 1] = globaltimer_ns();
     }
     __syncwarp();
     if (FUSED) return fused_forward_row<T>(row, b, d, SliceVals<T>{w, b}, Fj, fw, s, limit);
@@ -673,17 +695,8 @@ k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, 
         }
         if (tid == 0) {
             if (nsteps > 0) st_relaxed(&Fx[b + nsteps - 1], w[nsteps - 1]);
-            T u = w[d - b];
-            int fail = 0;
-            if (!isfinite(u)) { raise_error(s, KKT_ERR_NONFINITE, row); fail = 1; }
-            else if (boost > 0.0) {
-                if (fabs(u) < boost) { u = (u < 0.0) ? -boost : boost; atomicAdd(&s->nboost, 1); }
-            } else if (u == 0.0) { raise_error(s, KKT_ERR_ZERO_PIVOT, row); fail = 1; }
-            if (!fail) {
-                st_relaxed(&Fx[d], u);
-                st_relaxed(&rinv[row], rcp_rn(u));
-                if (trace) trace[2 * (size_t)(row - t0) + 1] = globaltimer_ns();
-            }
+            if (tail_pivot<T>(w[d - b], boost, boost > T(0), s, row, &Fx[d], &rinv[row]) && trace)
+                trace[2 * (size_t)(row - t0) + 1] = globaltimer_ns();
         }
         // the fused forward sweep's y_row, by warp 0 from the row in shared
         // memory; the other warps wait at the next row's first barrier

@@ -5,18 +5,20 @@
 //   L row i:  y_i = r0 - sum_k L_ik y_k            (unit diagonal)
 //   U row i:  x_i = (r0 - sum_j U_ij x_j) * (1/U_ii)
 //
-// FP64 on B300 has a dependent-operation latency of about 64 cycles, so a
-// five-step warp reduction of doubles costs ~600 cycles -- more than the
-// rest of a dependency hand-off -- and the FP64 pipe is scarce (about 1.6
-// fused multiply-adds per clock per SM).  A row therefore splits its entries
-// in up to three tiers by how recently their dependencies finish: the EARLY
-// ones are summed lane-parallel and warp-reduced; the MIDDLE ones (U only)
-// go one per lane and are tree-reduced over only as many lanes as there are
-// of them; the LATE ones -- the few most recent -- are folded by lane 0 in
-// one fused multiply-add each, in a fixed order.  Only that last FMA (and,
-// for U, one multiply) sits on the dependency chain when the dependencies
-// arrive in order; a middle-tier dependency arriving last costs a short tree
-// instead of a string of serial FMAs.  The tiers are fixed by the row's
+// FP64 on B300 is scarce in a way that shapes this code: a dependent FP64
+// operation takes about 64 cycles, and every FP64 warp instruction holds
+// the SM's FP64 pipe for about 20 cycles however many lanes are active
+// (measured: 0.05 warp instructions per SM-cycle with 1, 8, 16 or 32 active
+// lanes), so the cost of a row is its count of FP64 warp instructions, and
+// a fold by one lane costs as much as a 32-lane FMA.  A row therefore
+// splits its entries in up to three tiers by how recently their
+// dependencies finish: the EARLY ones are summed lane-parallel; the MIDDLE
+// ones (U only) go one per lane, each multiplied into its lane's early sum
+// as it arrives, and one warp reduction then sums both tiers; the LATE ones
+// -- the few most recent -- are folded by lane 0 in one fused multiply-add
+// each, in a fixed order.  Only that last FMA (and, for U, one multiply by
+// the pivot's reciprocal) sits on the dependency chain when the
+// dependencies arrive in order.  The tiers are fixed by the row's
 // structure, so the result does not depend on timing.
 //
 // Values are read through `Src`, which maps an entry p to the address of
@@ -31,14 +33,15 @@ namespace kkt {
 
 constexpr unsigned long long SENTINEL_BITS = 0x7ff4dead5ca1ab1eull;
 constexpr unsigned SENTINEL_BITS_F32 = 0x7fa5ca1eu;   // the FP32 (mixed precision) counterpart
-// Late and middle entries per row, tuned per sweep on kkt2000.  L: 2 late,
-// no middle tier (its kernel sits at the register cap).  U: 6 late and a
-// middle tier of 16 (swept late 2..10, middle 0..24): U rows are longer and
-// take more of their dependencies recently.
+// Late and middle entries per row, tuned per sweep.  L: 2 late, no middle
+// tier (its kernel sits at the register cap).  U: 3 late and a middle tier
+// of 24 (swept late 1..6, middle 16..30 on kkt2000, checked on kkt200 and
+// kkt10000): U rows are longer and take more of their dependencies
+// recently; each late entry costs a whole FP64 warp instruction.
 constexpr int NLATE_L = 2;
 constexpr int NMID_L = 0;
-constexpr int NLATE_U = 6;
-constexpr int NMID_U = 16;
+constexpr int NLATE_U = 3;
+constexpr int NMID_U = 24;
 constexpr int ROW_BATCH = 4;    // early entries per lane with loads in flight together
 
 __device__ __forceinline__ double sentinel() { return __longlong_as_double((long long)SENTINEL_BITS); }
@@ -152,30 +155,24 @@ __device__ __forceinline__ bool trsv_row_v(int64_t lo, int64_t hi, Vals vals, Sr
             acc = fma(a[u], v[u], acc);
         }
     }
+    // the middle tier's entry joins its lane's early sum
+    if constexpr (NMID > 0) {
+        if (lane < nm && ok) {
+            if (!spin_value<Src::kPollNs>(ms, &mv, limit, give_up)) ok = 0;
+            else acc = fma(ma, mv, acc);
+        }
+    }
     if (!__all_sync(0xffffffffu, ok)) return false;
-    // lanes past the m-th early entry hold exact zeros: reduce over the
-    // first 2^ceil(log2 m) lanes only (same sum, fewer FP64 steps)
-    const int64_t m = ehi - elo;
+    // lanes past the m-th early (or middle) entry hold exact zeros: reduce
+    // over the first 2^ceil(log2 m) lanes only (same sum, fewer FP64 steps)
+    const int64_t m = (ehi - elo) > nm ? (ehi - elo) : nm;
+    T r = r0;
     if (m > 0) {
         const int span = m >= 32 ? 32 : (int)m;
         int o = 1;
         while (o < span) o <<= 1;
         for (o >>= 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    }
-    T r = r0 - acc;
-    if constexpr (NMID > 0) {
-        if (nm > 0) {
-            T prod = T(0);
-            if (lane < nm) {
-                if (!spin_value<Src::kPollNs>(ms, &mv, limit, give_up)) ok = 0;
-                else prod = ma * mv;
-            }
-            if (!__all_sync(0xffffffffu, ok)) return false;
-            int o = 1;
-            while (o < nm) o <<= 1;
-            for (o >>= 1; o > 0; o >>= 1) prod += __shfl_xor_sync(0xffffffffu, prod, o);
-            r -= prod;
-        }
+        r = r0 - acc;
     }
     if (lane == 0) {
 #pragma unroll
