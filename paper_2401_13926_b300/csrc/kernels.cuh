@@ -684,10 +684,10 @@ k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, 
             ok = run_step(B);
         }
         if (!ok) return;
-        // publish: thread 0 the pivot first (the row's U part is final
-        // after the last step's barrier), then every thread its share of
-        // the other values; the last step's l, which thread 0 wrote after
-        // that barrier, thread 0 stores itself
+        // publish (the row is final after the last step's barrier): every
+        // thread its share of the values but the diagonal, then thread 0 the
+        // pivot; the last step's l, which thread 0 wrote after that barrier,
+        // thread 0 stores itself
         for (int q = tid; q < len; q += blockDim.x) {
             if (b + q != d && q != nsteps - 1) st_relaxed(&Fx[b + q], w[q]);
             const int c = cols[q];
