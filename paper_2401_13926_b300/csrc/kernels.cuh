@@ -301,19 +301,22 @@ __device__ __forceinline__ int64_t find_col(const int32_t* __restrict__ Fj, int6
 }
 
 template <typename T, bool FUSED>
-__global__ void k_refactor(int n, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
+__global__ void k_refactor(int n, const int32_t* __restrict__ order, const int64_t* __restrict__ Fp,
+                           const int32_t* __restrict__ Fj,
                            const int64_t* __restrict__ Fdiag, T* Fx, T* rinv, unsigned* done, DevScal* s,
                            double boost_eps, long long limit, FwdArgs<T> fw) {
-    // rows [0, n) of the bulk: warp per row, factor values in global memory
+    // rows [0, n) of the bulk: warp per row, factor values in global memory,
+    // taken in the dispatch order order[0, n)
     const int lane = threadIdx.x & 31;
     const unsigned gen = *(volatile unsigned*)&s->gen_fact;
     const T boost = (T)(boost_eps * *(volatile double*)&s->normA);
     for (;;) {
-        int row = 0;
-        if (lane == 0) row = (int)atomicAdd(&s->ticket_fact, 1u);
-        row = __shfl_sync(0xffffffffu, row, 0);
-        if (row >= n) return;
+        int q = 0;
+        if (lane == 0) q = (int)atomicAdd(&s->ticket_fact, 1u);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= n) return;
         if (ld_volatile_int(&s->abort)) return;
+        const int row = order[q];
         const int64_t b = Fp[row], d = Fdiag[row], e = Fp[row + 1];
         for (int64_t p = b; p < d; p++) {
             const int32_t k = __ldg(&Fj[p]);

@@ -69,7 +69,7 @@ struct kkt_ctx {
     size_t tail_smem = 0;
     int tail_blocks = 0;
     int tail_max_steps = 1, tail_max_len = 1, tail_mlo = 0;
-    int32_t* d_tail_order = nullptr;   // rows [t0, n) in dispatch order: [t0, t1) part, then [t1, n) part
+    int32_t* d_order = nullptr;   // rows in dispatch order: the [0, t0), [t0, t1) and [t1, n) parts
     DevScal* d_s = nullptr;
     DevScal* h_s = nullptr;   // pinned mirror
     int64_t ld = 0;
@@ -672,19 +672,22 @@ int setup_tail(kkt_ctx* c) {
         c->tail_wsteps = (int)ms;
         c->tail_wlen = (int)ml;
     }
-    if (c->t0 < n) {
-        // dispatch order: each part by level in the DAG of L (ties by row),
-        // so rows whose dependencies finish first start first; a row's
-        // dependencies are at lower levels, so they are dispatched before it
-        std::vector<int32_t> order((size_t)(n - c->t0));
-        std::iota(order.begin(), order.end(), c->t0);
+    {
+        // dispatch order: each part -- [0, t0) warp per row in global memory,
+        // [t0, t1) warp per row and [t1, n) block per row in shared memory --
+        // by level in the DAG of L (ties by row), so rows whose dependencies
+        // finish first start first; a row's dependencies are at lower
+        // levels, so they are dispatched before it
+        std::vector<int32_t> order((size_t)n);
+        std::iota(order.begin(), order.end(), 0);
         if (c->o.tail_order) {
             const std::vector<int32_t>& lev = c->lay.levL;
             auto by_level = [&](int32_t a, int32_t b) { return lev[a] < lev[b] || (lev[a] == lev[b] && a < b); };
-            std::sort(order.begin(), order.begin() + (c->t1 - c->t0), by_level);
-            std::sort(order.begin() + (c->t1 - c->t0), order.end(), by_level);
+            std::sort(order.begin(), order.begin() + c->t0, by_level);
+            std::sort(order.begin() + c->t0, order.begin() + c->t1, by_level);
+            std::sort(order.begin() + c->t1, order.end(), by_level);
         }
-        CK(cudaMemcpyAsync(c->d_tail_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice,
+        CK(cudaMemcpyAsync(c->d_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice,
                            c->stream));
         CK(cudaStreamSynchronize(c->stream));   // `order` is a local
     }
@@ -812,7 +815,7 @@ int setup_device(kkt_ctx* c, const kkt::ColStructure& S, std::chrono::steady_clo
     fill_y_sentinel(c);
     if (c->o.trisolve == KKT_TRSV_AUTO) pick_cluster(c);
     else c->cluster = 0;
-    if ((rc = dalloc(c, &c->d_tail_order, (size_t)n))) return rc;
+    if ((rc = dalloc(c, &c->d_order, (size_t)n))) return rc;
     if ((rc = setup_tail(c))) return rc;
     if ((rc = dalloc(c, &c->d_s, 1))) return rc;
     CK(cudaMemsetAsync(c->d_s, 0, sizeof(DevScal), c->stream));
@@ -919,7 +922,8 @@ void refactor_launch(kkt_ctx* c, const double* vals, unsigned long long* trace, 
     if (c->t0 > 0) {
         auto kern = fused_rhs ? kkt::k_refactor<T, true> : kkt::k_refactor<T, false>;
         kern<<<grid_for(c, c->t0), PERSIST_THREADS, 0, c->stream>>>(
-            c->t0, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, c->d_done_f, c->d_s, c->o.boost_eps, spin(c), fw);
+            c->t0, c->d_order, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, c->d_done_f, c->d_s, c->o.boost_eps, spin(c),
+            fw);
         c->launches += 1;
     }
     phase_end(c, t);
@@ -931,7 +935,7 @@ void refactor_launch(kkt_ctx* c, const double* vals, unsigned long long* trace, 
         auto kern = fused_rhs ? kkt::k_refactor_tail<T, true> : kkt::k_refactor_tail<T, false>;
         kern<<<blocks, kkt::TAIL_THREADS, c->tail_smem, c->stream>>>(
             c->t0, c->t1, n, c->tail_mlo, c->tail_max_steps, c->tail_max_len, c->tail_wsteps, c->tail_wlen,
-            c->d_tail_order, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, vals, c->d_fsrc, c->d_s, c->o.boost_eps,
+            c->d_order + c->t0, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, vals, c->d_fsrc, c->d_s, c->o.boost_eps,
             spin(c), trace, fw);
         c->launches += 2;
     }
