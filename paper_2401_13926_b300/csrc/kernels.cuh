@@ -331,8 +331,11 @@ __global__ void k_refactor(int n, const int32_t* __restrict__ order, const int64
             if (lane == 0) __stcg(&Fx[p], lik);
             for (int64_t q = dk + 1 + lane; q < ek; q += 32) {
                 const int32_t c = __ldg(&Fj[q]);
-                const int64_t pos = find_col(Fj, p + 1, e, c);
-                if (pos >= e || __ldg(&Fj[pos]) != c) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
+                // entry q of U(k,:) lies after its predecessors and before its
+                // successors among row i's columns past k
+                const int64_t hi = e - (ek - 1 - q);
+                const int64_t pos = find_col(Fj, p + 1 + (q - dk - 1), hi, c);
+                if (pos >= hi || __ldg(&Fj[pos]) != c) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
                 __stcg(&Fx[pos], fma(-lik, __ldcg(&Fx[q]), __ldcg(&Fx[pos])));
             }
             __threadfence();
