@@ -75,20 +75,24 @@ def test_step_device_arrays_and_full_size():
     assert torch.equal(xf2, xf)
 
 
-def test_tail_dispatch_order_same_bits():
-    """The shared-memory refactorization's rows dispatched by DAG level or by
-    row give the same factors, bit for bit (each row's arithmetic is fixed;
-    only when it runs changes)."""
+@pytest.mark.parametrize("warp_rows", [True, False])
+def test_tail_dispatch_order_same_bits(warp_rows):
+    """The refactorization's rows dispatched by DAG level or by row give the
+    same factors, bit for bit (each row's arithmetic is fixed; only when it
+    runs changes).  Without warp rows the rows before the block rows go to
+    the warp-per-row kernel in global memory, which follows the same order."""
     seq = KKTSequence("kkt200", steps=2)
     out = []
     for order in ("row", "level"):
-        s = K.KKTSolver(tail_order=order)
+        s = K.KKTSolver(tail_order=order, tail_warp_rows=warp_rows, tail_rows=0 if warp_rows else 1024)
         s.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
         v = seq.values(1)
         b, _ = seq.rhs(1, v)
         x, it, nr = s.step(v, b)
         f = s.factors()
         out.append((f["Lx"].copy(), f["Ux"].copy(), x.copy(), it, nr))
+        if not warp_rows:
+            assert s.info()["tail_rows"] < seq.n   # the warp-per-row kernel ran
         s.close()
     for a, b_ in zip(out[0], out[1]):
         assert np.array_equal(a, b_)
