@@ -113,11 +113,12 @@ typedef struct {
                              the block's shared memory; 0: the block-per-row part one row
                              per block, the rows before it one warp per row with values in
                              global memory.  Same arithmetic either way. */
-    int tail_order;       /* dispatch order of the shared-memory refactorization's rows:
-                             1 (default) by level in the dependency DAG of L (ties by
-                             row), each part -- rows one per warp, then rows one per
-                             block -- on its own; 0 by row.  A row's dependencies are
-                             always dispatched before it.  Same arithmetic either way. */
+    int tail_order;       /* dispatch order of the refactorization's rows: 1 (default)
+                             by level in the dependency DAG of L (ties by row), each
+                             part -- rows in global memory one per warp, rows in shared
+                             memory one per warp, rows one per block -- on its own;
+                             0 by row.  A row's dependencies are always dispatched
+                             before it.  Same arithmetic either way. */
 } kkt_opts;
 
 /* Refinement methods (Section 2.1).  FGMRES: FGMRES(m) with M = LU as right
