@@ -96,3 +96,25 @@ def test_tail_dispatch_order_same_bits(warp_rows):
         s.close()
     for a, b_ in zip(out[0], out[1]):
         assert np.array_equal(a, b_)
+
+
+def test_step_factors_bitwise_oracle_full_size_kkt2000(oracle_mod):
+    """The benchmark's timed call at its size: kkt_step on the library's own
+    ordering and pivots gives factors equal, bit for bit, to the oracle's
+    refactorization on the same P and Q (first and last matrix), whatever
+    the dispatch order of the rows."""
+    seq = KKTSequence("kkt2000")
+    for order in ("level", "row"):
+        s = K.KKTSolver(tail_order=order)
+        s.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
+        P, Q = s.perm()
+        for k in (0, seq.M - 1):
+            v = seq.values(k)
+            b, _ = seq.rhs(k, v)
+            s.step(v, b, allow_not_converged=True)
+            f = s.factors()
+            of = oracle_mod.refactor(seq.n, seq.rowptr, seq.colind, v, P, Q)
+            assert np.array_equal(f["Li"], of.Li) and np.array_equal(f["Ui"], of.Ui)
+            assert np.array_equal(f["Lx"], of.Lx), (order, k)
+            assert np.array_equal(f["Ux"], of.Ux), (order, k)
+        s.close()
