@@ -295,10 +295,11 @@ int kkt_get_phase_times(kkt_ctx* c, double* ms, int64_t* counts, int reset);
 
 /*
  * Profiling: kkt_refactor, with the GPU's global timer (ns) recorded when
- * each row of the block-per-row part starts and when it publishes its
- * pivot.  t_start[n], t_publish[n] (host) get the stamps (-1 for rows of
- * the other part); *t0_out = first row of the block-per-row part.  Makes
- * one temporary device allocation for the stamps.
+ * each row of the shared-memory kernel (rows one per warp and one per
+ * block) starts and when it publishes its pivot.  t_start[n], t_publish[n]
+ * (host) get the stamps (-1 for rows of the warp-per-row kernel in global
+ * memory); *t0_out = first row of the shared-memory kernel.  Makes one
+ * temporary device allocation for the stamps.
  */
 int kkt_trace_refactor(kkt_ctx* c, const double* values, int values_on_device, int64_t* t_start,
                        int64_t* t_publish, int32_t* t0_out);
