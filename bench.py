@@ -144,9 +144,6 @@ def peaks():
         return 6400.0, "fallback"
 
 
-# FP64 peak of a B300 from the profiling recipe's nominal table (1.25 TFLOP/s
-# dense FP64); the DFMA probe in the design doc measured 0.95 TFLOP/s.
-FP64_PEAK_TFLOPS = 1.25
 
 
 def kernel_source_hash():

@@ -364,18 +364,23 @@ int kkt_selftest_wait(kkt_ctx* c, int64_t limit);
  *   stream   cudaStream_t (NULL = the legacy default stream); the call
  *            returns after the solve has finished on it.
  * Working memory is one static device array of KKT_NOALLOC_SCRATCH_BYTES in
- * the library image, held by every GPU that loads the library until the
- * process exits; the call makes no cudaMalloc or cudaFree.  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress)
- * with the device current and caches it: make that first call before any
- * stream capture.  All calls on a device share the array, so calls that
- * overlap on the GPU (other streams, other threads) race and give wrong
- * results: serialise them.  Each call clears the flags and counters it uses.
+ * the library image -- 256 bytes of tickets and error words, then the two
+ * intermediate vectors (y = L^{-1} P b and U^{-1} y, 8 bytes per row each) --
+ * held by every GPU that loads the library until the process exits; the
+ * call makes no cudaMalloc or cudaFree.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) with the device current
+ * and caches it.  Every call reads its error status back and synchronises
+ * the stream before it returns.  All calls on a device share the array, so
+ * calls that overlap on the GPU (other streams, other threads) race and give
+ * wrong results: serialise them.  Each call re-arms the parts of the array
+ * it uses (the vectors' first n entries, the tickets, the error words).
+ * Result: the same bits as kkt_lu_solve on the same factors (the same row
+ * arithmetic and summation order).
  * Errors: KKT_ERR_INVALID, KKT_ERR_TIMEOUT (a bounded wait ran out),
  * KKT_ERR_CUDA.
  */
 #define KKT_NOALLOC_MAX_N 65536
-#define KKT_NOALLOC_SCRATCH_BYTES (256 + (KKT_NOALLOC_MAX_N) * 24)
+#define KKT_NOALLOC_SCRATCH_BYTES (256 + (KKT_NOALLOC_MAX_N) * 16)
 int kkt_lu_solve_noalloc(int32_t n, const int64_t* Fp, const int32_t* Fj, const int64_t* Fdiag,
                          const double* Fx, const int32_t* P, const int32_t* Q, const double* b,
                          double* x, void* stream);

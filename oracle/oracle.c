@@ -63,9 +63,11 @@
  * Matrices enter in CSC (Ap, Ai, Ax) for the factorization and CSR for the
  * matrix-vector product; both describe the same K.
  */
+#define _POSIX_C_SOURCE 199309L
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 
 #define OR_OK 0
 #define OR_ERR_SINGULAR (-4)
@@ -296,8 +298,22 @@ fail:
 /* boost_abs > 0 turns on the static-pivot boost: |u_jj| < boost_abs is */
 /* replaced by sign(u_jj) * boost_abs (sign(0) = +1) and counted.       */
 /* boost_abs == 0: an exact zero pivot is an error.                     */
-void *or_refactor(int n, const int *Ap, const int *Ai, const double *Ax,
-                  const int *P, const int *Q, double boost_abs, int *status) {
+/* budget_s > 0 (the bounded CPU-baseline sample only): stop at the first  */
+/* column reached after budget_s seconds; *cols_done and                    */
+/* *madds get the columns finished and the multiply-adds they took.  The   */
+/* arithmetic of every finished column is the same either way.             */
+static double wall_seconds(void) {
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+static void *refactor_run(int n, const int *Ap, const int *Ai, const double *Ax,
+                          const int *P, const int *Q, double boost_abs, double budget_s,
+                          int *cols_done, double *madds, double *marks, int nmarks, int *status) {
+    const double t_start = budget_s > 0.0 ? wall_seconds() : 0.0;
+    double nmadd = 0.0;
+    int jend = n;
     *status = OR_ERR_OOM;
     or_factors *F = (or_factors *)calloc(1, sizeof(or_factors));
     int *pinv = (int *)malloc(sizeof(int) * (size_t)n);
@@ -322,6 +338,16 @@ void *or_refactor(int n, const int *Ap, const int *Ai, const double *Ax,
     }
     F->Lp[0] = 0; F->Up[0] = 0;
     for (int j = 0; j < n; j++) {
+        if (budget_s > 0.0 && j > 0) {
+            const double el = wall_seconds() - t_start;
+            /* checkpoint every 256 columns: columns, multiply-adds, stored
+             * factor entries, seconds (the sample's cost profile) */
+            if (marks && (j & 255) == 0 && (j >> 8) <= nmarks) {
+                double *mk = marks + 4 * ((j >> 8) - 1);
+                mk[0] = (double)j; mk[1] = nmadd; mk[2] = (double)(Li.n + Ui.n); mk[3] = el;
+            }
+            if (el >= budget_s) { jend = j; break; }
+        }
         int c = Q[j];
         int ns = 0;
         for (int p = Ap[c]; p < Ap[c + 1]; p++) seeds[ns++] = pinv[Ai[p]];
@@ -337,6 +363,7 @@ void *or_refactor(int n, const int *Ap, const int *Ai, const double *Ax,
             if (i >= j) break;
             double xi = x[i];
             for (int p = F->Lp[i]; p < F->Lp[i + 1]; p++) x[Li.a[p]] = fma(-Lx.a[p], xi, x[Li.a[p]]);
+            nmadd += (double)(F->Lp[i + 1] - F->Lp[i]);
         }
         if (mark[j] != j) { *status = OR_ERR_SINGULAR; goto fail; }
         double d = x[j];
@@ -365,6 +392,16 @@ void *or_refactor(int n, const int *Ap, const int *Ai, const double *Ax,
         F->Lp[j + 1] = (int)Li.n;
         F->Up[j + 1] = (int)Ui.n;
     }
+    if (cols_done) *cols_done = jend;
+    if (madds) *madds = nmadd;
+    if (jend < n) {   /* a bounded sample stopped early: no factors to return */
+        free(pinv); free(colof); free(mark); free(stack); free(pos); free(out); free(seeds); free(x);
+        free(Li.a); free(Lx.a); free(Ui.a); free(Ux.a);
+        F->Li = NULL; F->Lx = NULL; F->Ui = NULL; F->Ux = NULL;
+        or_factor_free(F);
+        *status = OR_OK;
+        return NULL;
+    }
     F->Li = Li.a; F->Lx = Lx.a; F->Ui = Ui.a; F->Ux = Ux.a;
     if (!F->Li) { F->Li = (int *)malloc(sizeof(int)); F->Lx = (double *)malloc(sizeof(double)); }
     sort_columns(n, F->Lp, F->Li, F->Lx);
@@ -377,6 +414,24 @@ fail:
     free(Li.a); free(Lx.a); free(Ui.a); free(Ux.a);
     if (F) { F->Li = NULL; F->Lx = NULL; F->Ui = NULL; F->Ux = NULL; or_factor_free(F); }
     return NULL;
+}
+
+void *or_refactor(int n, const int *Ap, const int *Ai, const double *Ax,
+                  const int *P, const int *Q, double boost_abs, int *status) {
+    return refactor_run(n, Ap, Ai, Ax, P, Q, boost_abs, 0.0, NULL, NULL, NULL, 0, status);
+}
+
+/* CPU-baseline sample: the refactorization above, stopped after about     */
+/* budget_s seconds (all columns if it finishes first).  Returns the       */
+/* status; *cols_done and *madds as in refactor_run; marks[4 k .. 4 k + 3] */
+/* (k < nmarks) the checkpoint after 256 (k + 1) columns.                  */
+int or_refactor_sample(int n, const int *Ap, const int *Ai, const double *Ax,
+                       const int *P, const int *Q, double budget_s, int *cols_done, double *madds,
+                       double *marks, int nmarks) {
+    int st = OR_OK;
+    void *h = refactor_run(n, Ap, Ai, Ax, P, Q, 0.0, budget_s, cols_done, madds, marks, nmarks, &st);
+    or_factor_free(h);
+    return st;
 }
 
 /* ------------------------------------------------------------------ */

@@ -35,6 +35,9 @@ def lib():
         L.or_lu.argtypes = [C.c_int, _i32, _i32, _f64, _i32, C.c_double, _i32, C.POINTER(C.c_int)]
         L.or_refactor.restype = C.c_void_p
         L.or_refactor.argtypes = [C.c_int, _i32, _i32, _f64, _i32, _i32, C.c_double, C.POINTER(C.c_int)]
+        L.or_refactor_sample.restype = C.c_int
+        L.or_refactor_sample.argtypes = [C.c_int, _i32, _i32, _f64, _i32, _i32, C.c_double, C.POINTER(C.c_int),
+                                         C.POINTER(C.c_double), _f64, C.c_int]
         L.or_refactor_f32.restype = C.c_void_p
         L.or_refactor_f32.argtypes = [C.c_int, _i32, _i32, _f64, _i32, _i32, C.c_double, C.POINTER(C.c_int)]
         L.or_factor_free.argtypes = [C.c_void_p]
@@ -172,6 +175,28 @@ def refactor(n, rowptr, colind, values, P, Q, boost_abs=0.0):
     if not h:
         raise OracleError(st.value, "refactor")
     return _factors_from_handle(n, h)
+
+
+def refactor_sample(n, rowptr, colind, values, P, Q, seconds):
+    """The refactorization run for about `seconds` (the bounded CPU-baseline
+    sample).  Returns (columns finished, multiply-adds they took, seconds
+    spent in the call, checkpoints): the checkpoints are rows (columns,
+    multiply-adds, stored factor entries, seconds) every 256 columns; no
+    factors are kept."""
+    import time
+    Ap, Ai, Ax = csr_to_csc(n, rowptr, colind, values)
+    cols, madds = C.c_int(), C.c_double()
+    nmarks = n // 256
+    marks = np.zeros(4 * max(nmarks, 1))
+    t = time.perf_counter()
+    st = lib().or_refactor_sample(n, Ap, Ai, Ax, np.ascontiguousarray(P, np.int32), np.ascontiguousarray(Q, np.int32),
+                                  float(seconds), C.byref(cols), C.byref(madds), marks, nmarks)
+    dt = time.perf_counter() - t
+    if st != OK:
+        raise OracleError(st, "refactor_sample")
+    marks = marks.reshape(-1, 4)
+    marks = marks[marks[:, 0] > 0]
+    return cols.value, madds.value, dt, marks
 
 
 def refactor_f32(n, rowptr, colind, values, P, Q, boost_abs=0.0):

@@ -233,7 +233,7 @@ __device__ __forceinline__ bool fused_forward_row(int row, int64_t lo, int64_t h
     const GiveUpGlobal gu{&s->abort};
     T val;
     if (!trsv_row_v<true, T, Vals, SrcGlobal<T>, GiveUpGlobal, 1>(lo, hi, vals, SrcGlobal<T>{Fj, fw.y},
-                                                                (T)fw.rhs[fw.P[row]], T(1), limit, gu, &val)) {
+                                                                rhs_value<T>(fw.rhs[fw.P[row]]), T(1), limit, gu, &val)) {
         if ((threadIdx.x & 31) == 0) fail_row(s, row);
         return false;
     }
@@ -757,7 +757,7 @@ __global__ void k_lsolve_bulk(int nrows, const int32_t* __restrict__ rows, const
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= nrows) return;
         const int row = rows[t];
-        const T r0 = (T)rhs[P[row]];
+        const T r0 = rhs_value<T>(rhs[P[row]]);
         T val;
         if (!trsv_row<true>(Fp[row], Fdiag[row], Fx, SrcGlobal<T>{Fj, y}, r0, T(1), limit, gu, &val)) {
             if (lane == 0) fail_row(s, row);
@@ -805,7 +805,7 @@ k_lsolve_chain(int nt, int cstart, const int32_t* __restrict__ rows, const int32
     const GiveUpShared gu{&s->abort};
     for (int t = warp; t < nt; t += nw) {
         const int row = rows[cstart + t];
-        const T r0 = (T)rhs[P[row]];
+        const T r0 = rhs_value<T>(rhs[P[row]]);
         T val;
         if (!trsv_row<true>(Fp[row], Fdiag[row], Fx, SrcChainL<T>{Fj, Fpos, cstart, xs, y}, r0, T(1), 4 * limit,
                             gu, &val)) {
@@ -949,7 +949,7 @@ k_trsv_cluster(int n, const int32_t* __restrict__ list, const int32_t* __restric
     for (int t = rank * 32 + warp; t < n; t += stride) {
         const int row = list[t];
         const int64_t d = Fdiag[row];
-        const T r0 = LOWER ? (T)rhs[perm[row]] : (T)rhs[row];
+        const T r0 = LOWER ? rhs_value<T>(rhs[perm[row]]) : (T)rhs[row];
         const T rinv = LOWER ? T(1) : __ldg(&rinv_u[row]);   // 1/u_ii as the refactorization formed it
         const int orow = LOWER ? row : perm[row];
         T val;

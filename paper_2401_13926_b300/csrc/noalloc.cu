@@ -7,15 +7,18 @@
 // a controller that solves one KKT system per control period) where
 // cudaMalloc/cudaFree may synchronise the device and stall the loop.  This
 // entry point takes the factors, b and x from the caller and keeps its
-// working memory -- the intermediate vectors, per-row completion flags and
-// the row tickets -- in one file-scope device array of fixed size that the
+// working memory -- the two intermediate vectors (each entry doubles as its
+// row's completion flag: it holds SENTINEL until the row is solved) and the
+// row tickets -- in one file-scope device array of fixed size that the
 // library image carries.  Every GPU that loads the library holds that array
 // (KKT_NOALLOC_SCRATCH_BYTES) until the process exits.
 //
 // The kernels take rows from an atomic ticket in dependency order and
-// evaluate each row with the same arithmetic as the context's solves
-// (trsv_row.cuh), so the two entry points return the same bits; every wait
-// on a value another warp produces is bounded.
+// evaluate each row with the row arithmetic of the context's solves
+// (trsv_row.cuh): the same tiers, the same summation order and the same
+// correctly rounded pivot reciprocal, so on the same factors the two entry
+// points return the same bits.  Every wait on a value another warp
+// produces is bounded.
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -34,14 +37,14 @@ struct NoallocHeader {
 
 constexpr int64_t kMaxN = KKT_NOALLOC_MAX_N;
 constexpr size_t kHeaderBytes = 256;
-constexpr size_t kScratchBytes = kHeaderBytes + (size_t)kMaxN * (2 * sizeof(double) + 2 * sizeof(unsigned));
+constexpr size_t kScratchBytes = kHeaderBytes + (size_t)kMaxN * 2 * sizeof(double);
 static_assert(kScratchBytes == KKT_NOALLOC_SCRATCH_BYTES, "header and implementation disagree on the size");
 
 // The scratch.  Host code must never pass `g_noalloc_scratch` itself to a
 // kernel: in host code it names a host-side stand-in, not device memory.
 // Its device address comes from cudaGetSymbolAddress (scratch_on_device).
-// Layout: header, y[kMaxN], xp[kMaxN] (doubles), then 2 kMaxN words kept
-// for the layout's stated size.
+// Layout: the header (tickets and error words) in the first 256 bytes, then
+// y[kMaxN] and xp[kMaxN] (doubles).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 struct Scratch {
@@ -107,7 +110,7 @@ __global__ void k_na_lsolve(unsigned char* base, int n, const int64_t* __restric
         if (lane == 0) row = (int)atomicAdd(&s.h->ticket_l, 1u);
         row = __shfl_sync(0xffffffffu, row, 0);
         if (row >= n) return;
-        const double r0 = b[P[row]];
+        const double r0 = kkt::rhs_value<double>(b[P[row]]);
         double val;
         if (!kkt::trsv_row<true>(Fp[row], Fdiag[row], Fx, NaSrc{Fj, s.y}, r0, 1.0, limit, gu, &val)) {
             if (lane == 0) na_fail(s.h);

@@ -50,10 +50,24 @@ __device__ __forceinline__ bool is_sentinel(double v) {
 }
 __device__ __forceinline__ bool is_sentinel(float v) { return __float_as_uint(v) == SENTINEL_BITS_F32; }
 
+template <typename T> __device__ __forceinline__ T quiet_nan();
+template <> __device__ __forceinline__ double quiet_nan<double>() { return __longlong_as_double(0x7ff8000000000000ll); }
+template <> __device__ __forceinline__ float quiet_nan<float>() { return __int_as_float(0x7fc00000); }
+
 // SENTINEL of the value type T (double for FP64 factors, float for FP32)
 template <typename T> __device__ __forceinline__ T sentinel_of();
 template <> __device__ __forceinline__ double sentinel_of<double>() { return sentinel(); }
 template <> __device__ __forceinline__ float sentinel_of<float>() { return __uint_as_float(SENTINEL_BITS_F32); }
+
+// A right-hand-side entry as the forward sweep's first operand.  A value
+// with SENTINEL's bits (a NaN payload a caller could pass in b) would read
+// as "not computed yet" to every row that depends on it, so it enters as
+// the canonical quiet NaN instead and propagates like any other NaN.
+template <typename T>
+__device__ __forceinline__ T rhs_value(double b) {
+    const T r = (T)b;
+    return is_sentinel(r) ? quiet_nan<T>() : r;
+}
 
 // correctly rounded reciprocal (same bits as 1/x)
 __device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
