@@ -1,9 +1,16 @@
 """Benchmark: KKT solves/sec on a same-pattern synthetic power-grid KKT sequence.
 
 One step = one pass of the hot path over one matrix of the sequence:
-kkt_refactor (value gather, numeric LU on the fixed pattern and pivots) then
-kkt_solve (triangular solves, residual, FGMRES(20) with CGS2 until
-NRBE <= 1e-12).  Matrices cycle k = 0..M-1 over the sequence.
+kkt_step -- the value gather, the numeric LU refactorization on the fixed
+pattern and pivots with the forward sweep fused into it, the backward sweep,
+the residual and FGMRES(20) with CGS2 until NRBE <= 1e-12.  Matrices cycle
+k = 0..M-1 over the sequence.
+
+The headline workload is the largest single-GPU configuration (kkt70000:
+70,000 buses, n = 1.76M, nnz = 20.4M, 20 matrices).  The smaller
+configurations (kkt200, kkt2000, kkt10000) are measured with the same
+protocol and reported under `per_config`; their host analysis runs while
+the headline's (minutes on one core) proceeds on another thread.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -19,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 import numpy as np
@@ -26,29 +34,35 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "kkt2000"
+WORKLOAD = "kkt70000"
+PER_CONFIG = "kkt200,kkt2000,kkt10000"
 TOL = 1e-12
 RESTART = 20
-ALT_MAX_CYCLES = 2      # cycle cap of the side-by-side mixed-precision run
 L2_FLUSH_BYTES = 256 << 20   # larger than the 126 MB L2
+METRIC = "KKT solves/sec (refactor+FGMRES to NRBE<=1e-12)"
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--per-config", default=PER_CONFIG, help="comma-separated smaller configs ('' = none)")
+    ap.add_argument("--per-config-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample for cpu_baseline")
+    ap.add_argument("--ref-seconds", type=float, default=4.0, help="oracle sample per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="factor precision of the headline line")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the side-by-side mixed-precision run")
-    ap.add_argument("--no-tune", action="store_true", help="skip the schedule autotuning at setup")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the side-by-side other-precision run")
+    ap.add_argument("--mixed-steps", type=int, default=6)
+    ap.add_argument("--mixed-cycles", type=int, default=3, help="FGMRES cycle cap of the other-precision leg")
+    ap.add_argument("--no-trace", action="store_true", help="skip the refactorization trace (critical path)")
     ap.add_argument("--serve-instances", type=int, default=4,
-                    help="independent sequences of the serving measurement (0 = skip)")
+                    help="independent kkt2000 sequences of the serving measurement (0 = skip)")
     ap.add_argument("--serve-steps", type=int, default=10)
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-c4", type=int, default=0,
@@ -144,8 +158,6 @@ def peaks():
         return 6400.0, "fallback"
 
 
-
-
 def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
@@ -155,10 +167,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None when the kernel source changed since that capture."""
-    path = os.path.join(ROOT, "profiles", "traffic_kkt2000.txt")
+def measured_traffic(workload, kernel):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary, or None when the kernel sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")
     try:
         rows = {}
         for line in open(path):
@@ -172,38 +184,83 @@ def measured_traffic(kernel):
         return None
 
 
-def roofline(phases, info, seq, steps):
-    """Roofline of the dominant kernel group, from the library's own CUDA
-    event timers over the timed region.
+# ------------------------------------------------------------ algorithmic bytes
+# Per unit of work, FP64 factors (8-byte values, 4-byte indices); l = nnz of
+# strict L, u = nnz of U with its diagonal, a = nnz(K), n rows.
+def bytes_refactor(a, l, u, n, fused=True, vsize=8):
+    """Gather + refactorization: A values (8a) and the gather map (4a) read,
+    factor values written (vsize (l+u)), the factor pattern (4 (l+u)) and
+    row pointers (8n) read; with the forward sweep fused in, that sweep's
+    factor reads (vsize+4) l and its vectors (b, P, y, re-arm: 36n)."""
+    b = 12 * a + (vsize + 4) * (l + u) + 8 * n
+    if fused:
+        b += (vsize + 4) * l + 36 * n
+    return b
 
-    refactorization (gather + bulk + block-per-row kernels): FP64 ALU bound,
-      2 x multiply-adds of one refactorization per launch;
-    triangular solves: HBM, 12 bytes per factor entry + 36 (L) / 44 (U)
-      bytes per row per launch."""
+
+def bytes_usolve(u, n, vsize=8):
+    return (vsize + 4) * u + 44 * n
+
+
+def bytes_lsolve(l, n, vsize=8):
+    return (vsize + 4) * l + 36 * n
+
+
+def bytes_spmv(a, n):
+    return 12 * a + 20 * n
+
+
+def bytes_solve_step(a, l, u, n, iters, vsize=8):
+    """Everything after the refactorization in one kkt_step with `iters`
+    Arnoldi steps in one cycle: the backward sweep, the residual of x0, and
+    per Arnoldi step j both sweeps, a product with K, CGS2 (two projections:
+    32 (j+1) n + 32 n) and the normalisation (24 n) and the stored z (8 n);
+    at the cycle end x += Z y (8 iters n + 16 n) and the true residual."""
+    b = bytes_usolve(u, n, vsize) + bytes_spmv(a, n)
+    for j in range(iters):
+        b += bytes_lsolve(l, n, vsize) + bytes_usolve(u, n, vsize) + bytes_spmv(a, n)
+        b += 32 * (j + 1) * n + 32 * n + 24 * n + 8 * n
+    if iters:
+        b += 8 * iters * n + 16 * n + bytes_spmv(a, n)
+    return b
+
+
+def step_bytes(info, n, nnz, iters, vsize=8):
+    l, u = info["nnz_l"], info["nnz_u"]
+    return bytes_refactor(nnz, l, u, n, True, vsize) + bytes_solve_step(nnz, l, u, n, iters, vsize)
+
+
+def roofline(phases, info, n, nnz, steps, workload):
+    """Roofline of the dominant kernel group over the timed region, from the
+    library's own CUDA events (on the context's stream).  Bound: HBM (the
+    path is sparse; no tensor cores), algorithmic bytes per launch as above
+    divided by the group's average launch time."""
     hbm, peak_kind = peaks()
-    n = seq.n
-    ref_ms = phases["gather"][0] + phases["refactor"][0] + phases["refactor_tail"][0]
-    ref_n = max(phases["refactor_tail"][1], phases["refactor"][1], 1)
-    groups = {"refactor": (ref_ms, ref_n), "lsolve": phases["lsolve"], "usolve": phases["usolve"]}
+    l, u = info["nnz_l"], info["nnz_u"]
+    ref_ms = phases["gather"][0] + phases["refactor"][0]
+    ref_n = max(phases["gather"][1], 1)
+    groups = {"refactorization": (ref_ms, ref_n), "lsolve": phases["lsolve"], "usolve": phases["usolve"]}
     dom = max(groups, key=lambda g: groups[g][0])
     ms, cnt = groups[dom]
     per_ms = ms / max(cnt, 1)
-    extra = {"kernel_group": dom, "ms_per_launch": per_ms,
-             "phase_ms_per_step": {p: round(phases[p][0] / steps, 4) for p in phases},
-             "phase_launches": {p: phases[p][1] for p in phases}}
-    if dom == "refactor":
-        flops = 2.0 * info["refactor_updates"]
-        ach = flops / (per_ms * 1e-3) / 1e12
-        return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": measured_traffic("k_refactor_tail"),
-                "peak_kind": "nominal FP64 (recipe table)", "flops_per_launch": flops, **extra}
-    nnz = info["nnz_l"] if dom == "lsolve" else info["nnz_u"]
-    bytes_ = 12 * nnz + (36 if dom == "lsolve" else 44) * n
+    if dom == "refactorization":
+        bytes_ = bytes_refactor(nnz, l, u, n, True)
+        kern = "k_refactor_rows<double,1>"
+        names = "k_gather + k_refactor_rows (forward sweep fused)"
+    elif dom == "usolve":
+        bytes_, kern, names = bytes_usolve(u, n), "k_trsv_cluster<0>", "backward sweep"
+    else:
+        bytes_, kern, names = bytes_lsolve(l, n), "k_trsv_cluster<1>", "forward sweep"
     ach = bytes_ / (per_ms * 1e-3) / 1e9
-    kern = "k_trsv_cluster<1>" if dom == "lsolve" else "k_trsv_cluster<0>"
-    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "traffic": measured_traffic(kern), "peak_kind": peak_kind + " hbm_gbs", "bytes_per_launch": bytes_,
-            **extra}
+    out = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+           "traffic": measured_traffic(workload, kern), "peak_kind": f"{peak_kind} hbm_gbs",
+           "kernel_group": dom, "kernels": names, "dominant_kernel": kern, "bytes_per_launch": bytes_,
+           "ms_per_launch": per_ms,
+           "phase_ms_per_step": {p: round(phases[p][0] / steps, 4) for p in phases},
+           "phase_launches": {p: phases[p][1] for p in phases}}
+    if dom == "refactorization":
+        out["fp64_gflops"] = 2.0 * info["refactor_updates"] / (per_ms * 1e-3) / 1e9
+    return out
 
 
 # -------------------------------------------------------------------- oracle
@@ -221,68 +278,42 @@ def host_cpu():
     return {"cpu_model": model, "nproc": os.cpu_count()}
 
 
-def oracle_sample(seq, seconds, steps=None):
-    """The CPU oracle as it stands: analysis once (not timed), then refactor +
-    FGMRES per matrix until `seconds` (or `steps`) are used, on one core
-    (the calling thread is pinned to the first CPU it may use)."""
-    from oracle import oracle as O
-    saved = None
-    try:
-        saved = os.sched_getaffinity(0)
-        os.sched_setaffinity(0, {min(saved)})
-    except (AttributeError, OSError):
-        saved = None
-    try:
-        return _oracle_sample(O, seq, seconds, steps)
-    finally:
-        if saved:
-            os.sched_setaffinity(0, saved)
+class pinned_core:
+    """Run the calling thread on one CPU (the oracle is single-threaded)."""
+
+    def __enter__(self):
+        self.saved = None
+        try:
+            self.saved = os.sched_getaffinity(0)
+            os.sched_setaffinity(0, {min(self.saved)})
+        except (AttributeError, OSError):
+            self.saved = None
+
+    def __exit__(self, *a):
+        if self.saved:
+            os.sched_setaffinity(0, self.saved)
 
 
-def _oracle_sample(O, seq, seconds, steps):
-    v0 = seq.values(0)
-    t0 = time.perf_counter()
-    P, Q, _ = O.lu(seq.n, seq.rowptr, seq.colind, v0)
-    t_an = time.perf_counter() - t0
-    done, t_solve, k = 0, 0.0, 0
-    nrbe = []
-    while True:
-        v = seq.values(k % seq.M)
-        b, _ = seq.rhs(k % seq.M, v)
-        t = time.perf_counter()
-        _, res = O.solve_sequence_step(seq.n, seq.rowptr, seq.colind, v, P, Q, b, tol=TOL, restart=RESTART)
-        t_solve += time.perf_counter() - t
-        nrbe.append(res.nrbe)
-        done += 1
-        k += 1
-        if (steps is not None and done >= steps) or (steps is None and t_solve >= seconds):
-            break
-    return done, t_solve, t_an, max(nrbe)
-
-
-def run_reference(args):
-    rank, world, _ = dist_env()
-    if rank != 0:
-        return
-    from paper_2401_13926_b300.workload import KKTSequence
-    seq = KKTSequence(args.workload)
-    # warmup steps, then the timed ones
-    oracle_sample(seq, 0, steps=max(args.warmup, 0) or 1)
-    done, t, t_an, worst = oracle_sample(seq, 0, steps=args.steps)
-    v = done / t
-    line = {
-        "impl": "reference", "metric": "KKT solves/sec (refactor+FGMRES to NRBE<=1e-12)", "value": v,
-        "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000 * t / done, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
-        "config": workload_config(seq),
-        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", **host_cpu(),
-                         "sample": f"{done} matrices of the {args.workload} sequence, oracle analysis "
-                                   f"({t_an:.1f} s) excluded, single thread"},
-        "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "max_nrbe": worst,
-    }
-    print(json.dumps(line), flush=True)
+def oracle_solve_estimate(O, seq, k, P, Q, totals, seconds):
+    """Seconds the oracle takes for one solve of matrix k, from a bounded
+    sample: the oracle's refactorization (on P, Q) runs for `seconds`; if it
+    finishes, that is the time; otherwise its cost profile (checkpoints every
+    256 columns) is fitted as time = a cols + b multiply-adds + c stored
+    entries (non-negative least squares) and extrapolated to the whole
+    refactorization (totals: n, multiply-adds, entries).  The oracle's
+    triangular solves and FGMRES are not sampled (about 2% of its solve time
+    on kkt2000).  Returns (seconds per solve, sample description)."""
+    from scipy.optimize import nnls
+    v = seq.values(k % seq.M)
+    cols, madds, dt, marks = O.refactor_sample(seq.n, seq.rowptr, seq.colind, v, P, Q, seconds)
+    if cols >= seq.n:
+        return dt, {"cols": cols, "madds": madds, "seconds": dt, "extrapolated": False}
+    d = np.diff(np.vstack([np.zeros((1, 4)), marks]), axis=0)
+    coef, _ = nnls(d[:, :3], d[:, 3])
+    est = float(coef @ np.array(totals, dtype=np.float64))
+    est = max(est, dt)
+    return est, {"cols": cols, "madds": madds, "seconds": dt, "extrapolated": True,
+                 "frac_madds": madds / totals[1]}
 
 
 def workload_config(seq):
@@ -293,17 +324,128 @@ def workload_config(seq):
                     f"FGMRES({RESTART}) to NRBE<={TOL:g}, FP64",
         "n": seq.n, "nnz": seq.nnz, "sequence": seq.M, "restart": RESTART, "tol": TOL,
         "l2": "flushed between timed steps (256 MiB write, outside the per-step events)",
+        "call": "kkt_step: refactor + solve, forward sweep fused into the refactorization",
     }
 
 
+def run_reference(args):
+    """The oracle as it stands, single thread, on the headline workload:
+    each step is a bounded sample of one matrix's solve (oracle_solve_estimate),
+    on the ordering and pivots of the library's host analysis (kkt_host_analyze,
+    no GPU; the oracle's own exact minimum-degree ordering does not finish on
+    the largest configuration in hours)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import paper_2401_13926_b300 as K
+    from oracle import oracle as O
+    from paper_2401_13926_b300.workload import KKTSequence
+    seq = KKTSequence(args.workload)
+    t = time.perf_counter()
+    P, Q, st = K.host_analyze(seq.rowptr, seq.colind, seq.values(0))
+    t_an = time.perf_counter() - t
+    totals = (seq.n, st["refactor_updates"], st["nnz_l"] + st["nnz_u"])
+    est, samples = [], []
+    with pinned_core():
+        for i in range(args.warmup + args.steps):
+            e, smp = oracle_solve_estimate(O, seq, i, P, Q, totals, args.ref_seconds)
+            if i >= args.warmup:
+                est.append(e)
+                samples.append(smp)
+    tot = sum(est)
+    v = len(est) / tot
+    ext = any(s["extrapolated"] for s in samples)
+    desc = (f"{len(est)} matrices of the {args.workload} sequence, each a ~{args.ref_seconds:g} s run of the oracle "
+            f"refactorization on the library host analysis' P, Q"
+            + (f" (median {100 * np.median([s.get('frac_madds', 1) for s in samples]):.2g}% of its multiply-adds), "
+               f"extrapolated to the whole refactorization by a fitted cost model" if ext else ", run to completion")
+            + f"; triangular solves and FGMRES not sampled; analysis ({t_an:.0f} s) excluded; single thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(est), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(seq),
+        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", **host_cpu(), "sample": desc},
+        "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # -------------------------------------------------------------------- ours
+def timed_steps(solver, vals, rhs, x, steps, M, flush, stream, allow_nc=False):
+    """`steps` kkt_step calls cycling over the M matrices, CUDA events on the
+    solver's stream around each, the L2 flushed before each (outside the
+    events).  Returns (per-step ms, iterations, NRBE, statuses)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    iters, nrbes, st = [], [], []
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[i][0].record(stream)
+        try:
+            _, it, nr = solver.step(vals[i % M], rhs[i % M], x=x, tol=TOL, allow_not_converged=allow_nc)
+            code = solver.last_status
+        except Exception as e:   # a failed step of a leg that reports failures (allow_nc)
+            if not allow_nc or not hasattr(e, "code"):
+                raise
+            it, nr, code = -1, float("nan"), e.code
+        ev[i][1].record(stream)
+        iters.append(it)
+        nrbes.append(nr)
+        st.append(code)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], iters, nrbes, st
+
+
+def measure_config(K, name, steps, warmup, flush, device, rank):
+    """The headline protocol on a smaller configuration: analysis (not
+    timed), `warmup` steps, `steps` timed kkt_step calls; solves/s,
+    latency percentiles, NRBE, and the HBM fraction of the algorithmic bytes
+    per solve (refactorization + everything the solve touches)."""
+    import torch
+    from paper_2401_13926_b300.workload import KKTSequence
+    seq = KKTSequence(name, instance=rank)
+    stream = torch.cuda.Stream(device=device)
+    s = K.KKTSolver(restart=RESTART, device=device, stream=stream, timing=True)
+    t = time.perf_counter()
+    s.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
+    t_an = time.perf_counter() - t
+    info = s.info()
+    with torch.cuda.stream(stream):
+        vals = [torch.from_numpy(seq.values(k)).cuda() for k in range(seq.M)]
+        rhs = [torch.from_numpy(seq.rhs(k, vals[k].cpu().numpy())[0]).cuda() for k in range(seq.M)]
+        x = torch.empty(seq.n, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    timed_steps(s, vals, rhs, x, warmup, seq.M, flush, stream)
+    s.phase_times(reset=True)
+    ms, iters, nrbes, _ = timed_steps(s, vals, rhs, x, steps, seq.M, flush, stream)
+    phases = s.phase_times(reset=True)
+    hbm, _ = peaks()
+    tot_bytes = sum(step_bytes(info, seq.n, seq.nnz, it) for it in iters)
+    tot_s = sum(ms) / 1000.0
+    out = {"value": steps / tot_s, "unit": "solves/s", "steps": steps, "n": seq.n, "nnz": seq.nnz,
+           "ms_per_step": 1000 * tot_s / steps,
+           "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+           "max_nrbe": float(max(nrbes)), "iters_mean": float(np.mean(iters)),
+           "hbm": {"achieved_gbs": tot_bytes / tot_s / 1e9, "frac": tot_bytes / tot_s / 1e9 / hbm,
+                   "bytes_per_solve": tot_bytes / steps},
+           "refactorization_ms": (phases["gather"][0] + phases["refactor"][0]) / steps,
+           "usolve_ms": phases["usolve"][0] / steps,
+           "analyze_s": t_an, "nnz_l": info["nnz_l"], "nnz_u": info["nnz_u"],
+           "levels_l": info["levels_l"], "levels_u": info["levels_u"],
+           "refactor_updates": info["refactor_updates"]}
+    s.close()
+    return out
+
+
 def serve_measure(K, args, rank):
-    """Throughput and latency of several sequences of the workload served
+    """Throughput and latency of several sequences of kkt2000 served
     together: every instance's steps are submitted at once (closed loop, the
     server runs one step per instance at a time), host arrays in and out."""
     from paper_2401_13926_b300.workload import KKTSequence
     N, S = args.serve_instances, args.serve_steps
-    seqs = [KKTSequence(args.workload, instance=1000 * (rank + 1) + i, steps=S) for i in range(N)]
+    seqs = [KKTSequence("kkt2000", instance=1000 * (rank + 1) + i, steps=S) for i in range(N)]
     data = [[(q.values(k), q.rhs(k, q.values(k))[0]) for k in range(S)] for q in seqs]
     srv = K.KKTServer(workers=args.serve_workers, restart=RESTART)
     ids = [srv.open(q.rowptr, q.colind, q.values(0)) for q in seqs]
@@ -316,7 +458,7 @@ def serve_measure(K, args, rank):
     srv.close()
     lat = np.array([r["queue_ms"] + r["run_ms"] for r in res])
     run = np.array([r["run_ms"] for r in res])
-    return {"value": N * S / dt, "unit": "solves/s", "instances": N, "steps_per_instance": S,
+    return {"workload": "kkt2000", "value": N * S / dt, "unit": "solves/s", "instances": N, "steps_per_instance": S,
             "workers": args.serve_workers, "converged": int(sum(r["status"] == 0 for r in res)),
             "max_nrbe": float(max(r["nrbe"] for r in res)),
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
@@ -332,7 +474,6 @@ def serve_c4(K, args, rank):
     when step k returns).  Instances are analysed before the clock starts
     (the paper, too, excludes the one-time analysis).  Latency is from a
     step's submission to its completion."""
-    import threading
     from paper_2401_13926_b300.workload import KKTSequence
     rng = np.random.default_rng(7000 + rank)
     N, S = args.serve_c4, args.serve_c4_steps
@@ -384,128 +525,154 @@ def run_ours(args):
     import paper_2401_13926_b300 as K
     from paper_2401_13926_b300.workload import KKTSequence
 
+    t_job = time.perf_counter()
     seq = KKTSequence(args.workload, instance=rank)
     stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
     solver = K.KKTSolver(restart=RESTART, device=local, stream=stream, timing=True, precision=args.precision)
-    solver.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
-    # schedule autotuning once at setup (kkt_tune; same bits, speed only)
-    if not args.no_tune:
-        solver.tune(seq.values(0), seq.rhs(0, seq.values(0))[0], reps=3)
-    info0 = solver.info()
-    # inputs resident in HBM before the timed region
-    vals = [torch.from_numpy(seq.values(k)).cuda() for k in range(seq.M)]
-    rhs = [torch.from_numpy(seq.rhs(k, vals[k].cpu().numpy())[0]).cuda() for k in range(seq.M)]
-    x = torch.empty(seq.n, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def step(k):
-        # one step of the sequence: kkt_step (refactor + solve, the forward
-        # sweep fused into the refactorization)
-        # a mixed-precision headline reports unconverged solves instead of stopping
-        _, it, nr = solver.step(vals[k % seq.M], rhs[k % seq.M], x=x, tol=TOL,
-                                allow_not_converged=args.precision == "mixed")
-        return it, nr
+    # the headline's host analysis (ordering + pivoting factorization, one
+    # core, minutes at kkt70000) on its own thread; the smaller
+    # configurations are measured on the GPU meanwhile
+    an_err = []
 
-    for w in range(args.warmup):
-        step(w)
+    def analyse():
+        try:
+            solver.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
+        except Exception as e:   # re-raised on the main thread
+            an_err.append(e)
+
+    th = threading.Thread(target=analyse)
+    th.start()
+    per_config = {}
+    for name in [c for c in args.per_config.split(",") if c and c != args.workload]:
+        per_config[name] = measure_config(K, name, args.per_config_steps, 3, flush, local, rank)
+    th.join()
+    if an_err:
+        raise an_err[0]
+    info0 = solver.info()
+
+    # inputs resident in HBM before the timed region
+    with torch.cuda.stream(stream):
+        vals = [torch.from_numpy(seq.values(k)).cuda() for k in range(seq.M)]
+        rhs = [torch.from_numpy(seq.rhs(k, vals[k].cpu().numpy())[0]).cuda() for k in range(seq.M)]
+        x = torch.empty(seq.n, dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
+    allow_nc = args.precision == "mixed"
+    timed_steps(solver, vals, rhs, x, args.warmup, seq.M, flush, stream, allow_nc)
     solver.phase_times(reset=True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = Clocks(local)
     launches0 = solver.info()["launches"]
-    iters, nrbes = [], []
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
     t_wall = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        it, nr = step(i)
-        ev[i][1].record(stream)
-        iters.append(it)
-        nrbes.append(nr)
-    torch.cuda.synchronize()
+    per_step, iters, nrbes, _ = timed_steps(solver, vals, rhs, x, args.steps, seq.M, flush, stream, allow_nc)
     t_wall = time.perf_counter() - t_wall
     barrier(world)
     clk = clocks.stop()
     launches = solver.info()["launches"] - launches0
-    per_step = [a.elapsed_time(b) for a, b in ev]
     dev_s = sum(per_step) / 1000.0
     phases = solver.phase_times(reset=True)
     units, secs = aggregate(float(args.steps), dev_s, world)
 
-    # ---- end to end through the C ABI with pinned host buffers
+    # ---- the same steps unfused: kkt_refactor then kkt_solve
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+    for i in range(3):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[i][0].record(stream)
+        solver.refactor(vals[i % seq.M])
+        solver.solve(rhs[i % seq.M], x=x, tol=TOL, allow_not_converged=allow_nc)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    unfused_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    # ---- end to end through the C ABI with pinned host buffers; the
+    # returned x is checked against Eq. (nbre) as the oracle evaluates it
+    from oracle import oracle as O
     n_e2e = min(args.e2e_steps, seq.M)
     hv = [torch.from_numpy(seq.values(k)).pin_memory().numpy() for k in range(n_e2e)]
     hb = [torch.from_numpy(seq.rhs(k)[0]).pin_memory().numpy() for k in range(n_e2e)]
-    hx = torch.empty(seq.n, dtype=torch.float64).pin_memory().numpy()
+    hx = [torch.empty(seq.n, dtype=torch.float64).pin_memory().numpy() for _ in range(n_e2e)]
     info_a = solver.info()
     torch.cuda.synchronize()
     t = time.perf_counter()
+    e2e_nr = []
     for k in range(n_e2e):
-        solver.step(hv[k], hb[k], x=hx, tol=TOL)
+        _, _, nr = solver.step(hv[k], hb[k], x=hx[k], tol=TOL, allow_not_converged=allow_nc)
+        e2e_nr.append(nr)
     e2e_s = time.perf_counter() - t
     info_b = solver.info()
     e2e_units, e2e_secs = aggregate(float(n_e2e), e2e_s, world)
+    or_nr = [O.nrbe(seq.n, seq.rowptr, seq.colind, hv[k], hb[k], hx[k]) for k in range(n_e2e)]
+    eps_terms = 2 * (int(np.diff(seq.rowptr).max()) + 2) * 2.0 ** -53
+    nrbe_check = {"steps": n_e2e, "max_oracle_nrbe": float(max(or_nr)),
+                  "max_abs_diff": float(max(abs(a - b) for a, b in zip(e2e_nr, or_nr))),
+                  "bound": "|gpu - oracle| <= 1e-6 oracle + 2 (max row nnz + 2) eps (two residual roundings)",
+                  "within_bound": bool(all(abs(a - b) <= 1e-6 * b + eps_terms for a, b in zip(e2e_nr, or_nr)))}
 
-    # ---- the other precision on the same workload, same protocol (device time)
+    # ---- the refactorization's critical path (trace stamps of one call)
+    crit = None
+    if not args.no_trace:
+        ts, tp, t0 = solver.trace_refactor(vals[0])
+        crit = solver.critical_path(ts, tp)
+        crit["first_traced_row"] = t0
+
+    # ---- the other precision on the same workload, same protocol
     other = None
     if not args.no_mixed:
         alt = "mixed" if args.precision == "fp64" else "fp64"
         # FP32-preconditioned refinement stalls above 1e-12 on some of these
-        # ill-conditioned matrices, so this run caps the cycles and reports
-        # how many solves reached the tolerance
-        cyc2 = ALT_MAX_CYCLES if alt == "mixed" else 50
+        # matrices: the cycle cap keeps this leg bounded, and it reports how
+        # many solves reached the tolerance
         s2 = K.KKTSolver(restart=RESTART, device=local, stream=stream, timing=True, precision=alt,
-                         max_cycles=cyc2)
-        s2.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
-        for w in range(args.warmup):
-            s2.step(vals[w % seq.M], rhs[w % seq.M], x=x, tol=TOL, allow_not_converged=True)
+                         max_cycles=args.mixed_cycles)
+        s2.analyze_like(solver)
+        nm = min(args.mixed_steps, seq.M)
+        idx = [int(round(i * (seq.M - 1) / max(nm - 1, 1))) for i in range(nm)]
+        timed_steps(s2, [vals[idx[0]]], [rhs[idx[0]]], x, 1, 1, flush, stream, True)
         s2.phase_times(reset=True)
-        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(seq.M)]
-        it2, nr2, ok2 = [], [], 0
-        torch.cuda.synchronize()
-        for i in range(seq.M):
-            flush.zero_()
-            ev2[i][0].record(stream)
-            _, it, nr = s2.step(vals[i], rhs[i], x=x, tol=TOL, allow_not_converged=True)
-            ev2[i][1].record(stream)
-            it2.append(it)
-            nr2.append(nr)
-            ok2 += s2.last_status == K.OK
-        torch.cuda.synchronize()
-        ms2 = [a.elapsed_time(b) for a, b in ev2]
+        ms2, it2, nr2, st2 = timed_steps(s2, [vals[i] for i in idx], [rhs[i] for i in idx], x, nm, nm, flush,
+                                         stream, True)
         ph2 = s2.phase_times(reset=True)
-        other = {"precision": alt, "value": seq.M / (sum(ms2) / 1000.0), "unit": "solves/s",
-                 "steps": seq.M, "latency_ms": {"p50": float(np.percentile(ms2, 50)),
-                                                "p99": float(np.percentile(ms2, 99))},
-                 "iters_mean": float(np.mean(it2)), "max_nrbe": float(np.max(nr2)),
-                 "converged": ok2, "max_cycles": cyc2, "nrbe": [float(f"{v:.3g}") for v in nr2],
-                 "phase_ms_per_step": {p: round(ph2[p][0] / seq.M, 4) for p in ph2}}
+        other = {"precision": alt, "value": nm / (sum(ms2) / 1000.0), "unit": "solves/s", "steps": nm,
+                 "matrices": idx, "latency_ms": {"p50": float(np.percentile(ms2, 50)),
+                                                 "p99": float(np.percentile(ms2, 99))},
+                 "iters": it2, "nrbe": [float(f"{v:.3g}") for v in nr2], "status": st2,
+                 "converged": int(sum(s_ == K.OK for s_ in st2)), "max_nrbe": float(np.nanmax(nr2 + [0.0])),
+                 "phase_ms_per_step": {p: round(ph2[p][0] / nm, 4) for p in ph2}}
         s2.close()
-    # ---- serving: several independent sequences of the same workload resident
-    # at once, their steps in flight together (kkt_server_*)
-    serving = None
-    if args.serve_instances > 0:
-        serving = serve_measure(K, args, rank)
+    # ---- serving: several independent sequences resident at once, their
+    # steps in flight together (kkt_server_*)
+    serving = serve_measure(K, args, rank) if args.serve_instances > 0 else None
     serving_c4 = serve_c4(K, args, rank) if args.serve_c4 > 0 else None
     if rank != 0:
         return
 
-    # ---- roofline of the dominant kernel group
-    roof = roofline(phases, info0, seq, args.steps)
+    roof = roofline(phases, info0, seq.n, seq.nnz, args.steps, args.workload)
+    if crit is not None:
+        crit["kernel_ms_per_launch"] = roof["ms_per_launch"] if roof["kernel_group"] == "refactorization" else None
+        roof["critical_path"] = crit
     cpu = None
     if not args.no_cpu_baseline:
-        done, tcpu, t_an, _ = oracle_sample(KKTSequence(args.workload), args.cpu_seconds)
-        cpu = {"value": done / tcpu, "unit": "solves/s", "cores": 1, "kind": "oracle", **host_cpu(),
-               "sample": f"{done} matrices of the {args.workload} sequence (about {args.cpu_seconds:g} s), "
-                         f"oracle analysis ({t_an:.1f} s) excluded, single thread"}
+        P, Q = solver.perm()
+        totals = (seq.n, info0["refactor_updates"], info0["nnz_l"] + info0["nnz_u"])
+        with pinned_core():
+            est, smp = oracle_solve_estimate(O, seq, 1, P, Q, totals, args.cpu_seconds)
+        cpu = {"value": 1.0 / est, "unit": "solves/s", "cores": 1, "kind": "oracle", **host_cpu(),
+               "sample": (f"matrix 1 of the {args.workload} sequence: the oracle refactorization on the library's "
+                          f"P, Q for {smp['seconds']:.1f} s ({smp['cols']} of {seq.n} columns, "
+                          f"{100 * smp['madds'] / totals[1]:.2g}% of the multiply-adds)"
+                          + (", extrapolated to the whole refactorization by a fitted cost model"
+                             if smp["extrapolated"] else "")
+                          + "; triangular solves and FGMRES not sampled; single thread")}
 
     lat = sorted(per_step)
+    hbm, _ = peaks()
+    tot_bytes = sum(step_bytes(info0, seq.n, seq.nnz, it) for it in iters)
     line = {
-        "metric": "KKT solves/sec (refactor+FGMRES to NRBE<=1e-12)",
+        "metric": METRIC,
         "value": units / secs, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32-factors/f64",
@@ -513,17 +680,22 @@ def run_ours(args):
         "config": {**workload_config(seq), "parallelism": f"replicas{world}", "precision": args.precision},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "iters_mean": float(np.mean(iters)), "max_nrbe": float(np.max(nrbes)),
+        "nrbe_check": nrbe_check,
+        "hbm_per_solve": {"achieved_gbs": tot_bytes / dev_s / 1e9, "frac": tot_bytes / dev_s / 1e9 / hbm,
+                          "bytes_per_solve": tot_bytes / args.steps},
+        "unfused_ms_per_step": unfused_ms,
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": e2e_units / e2e_secs, "unit": "solves/s",
                 "h2d_bytes_per_step": (info_b["h2d_bytes"] - info_a["h2d_bytes"]) // n_e2e,
                 "d2h_bytes_per_step": (info_b["d2h_bytes"] - info_a["d2h_bytes"]) // n_e2e},
-        "gpu_launches": launches, "clocks": clk, "wall_s": t_wall,
-        "precision": args.precision, "other_precision": other, "serving": serving, "serving_mixed": serving_c4,
-        "schedule": {"tail_rows": info0["tail_rows"], "trisolve_cluster": info0["trisolve_cluster"],
-                     "chosen_by": "default" if args.no_tune else "kkt_tune at setup"},
+        "gpu_launches": launches, "clocks": clk, "wall_s": t_wall, "job_s": time.perf_counter() - t_job,
+        "precision": args.precision, "other_precision": other, "per_config": per_config,
+        "serving": serving, "serving_mixed": serving_c4,
+        "schedule": {k: info0[k] for k in ("rows_warp", "rows_block", "rows_global", "refactor_smem",
+                                           "refactor_threads", "refactor_blocks", "trisolve_cluster")},
         "analysis": {"analyze_ms": info0["analyze_ms"], "nnz_l": info0["nnz_l"], "nnz_u": info0["nnz_u"],
                      "levels_l": info0["levels_l"], "levels_u": info0["levels_u"],
-                     "refactor_updates": info0["refactor_updates"]},
+                     "refactor_updates": info0["refactor_updates"], "device_bytes": info0["device_bytes"]},
     }
     print(json.dumps(line), flush=True)
 

@@ -88,9 +88,13 @@ typedef struct {
     int trisolve;         /* triangular-solve schedule: KKT_TRSV_AUTO (default), KKT_TRSV_GLOBAL */
     int cluster_blocks;   /* blocks of the cluster solve: 0 = 16 if it fits and can be
                              scheduled, else 8; 8 or 16 to force one */
-    int tail_rows;        /* rows refactored one block per row at the end of the order
-                             (0 = default 32767, the most; fewer if a row does not fit
-                             in shared memory) */
+    int block_smem;       /* shared memory (bytes) of each block of the refactorization
+                             kernel: 0 (default) = sized by the longest row of the
+                             factors, up to the device's limit; rows whose working set
+                             fits a warp's slice of it go one per warp, longer rows
+                             that fit it one per block, the rest one per block with
+                             their values in global memory.  Blocks of more than
+                             ~113 KB run 512 threads, else 256. */
     int method;           /* refinement after x0 = (LU)^{-1} b: KKT_METHOD_FGMRES (default),
                              KKT_METHOD_RICHARDSON, KKT_METHOD_FGMRES_EE */
     int ortho;            /* Arnoldi orthogonalisation: KKT_ORTHO_CGS2 (default),
@@ -107,18 +111,14 @@ typedef struct {
                              round trip per step); captured on first use, again when tol
                              changes.  Same kernels in the same order, so the same results.
                              0 = launch from the host (default) */
-    int tail_warp_rows;   /* 1 (default): the leading short rows of the block-per-row part,
-                             and the rows before it, are refactored one per warp (eight
-                             per block) in the same kernel while they fit an eighth of
-                             the block's shared memory; 0: the block-per-row part one row
-                             per block, the rows before it one warp per row with values in
-                             global memory.  Same arithmetic either way. */
-    int tail_order;       /* dispatch order of the refactorization's rows: 1 (default)
-                             by level in the dependency DAG of L (ties by row), each
-                             part -- rows in global memory one per warp, rows in shared
-                             memory one per warp, rows one per block -- on its own;
-                             0 by row.  A row's dependencies are always dispatched
-                             before it.  Same arithmetic either way. */
+    int warp_rows;        /* 1 (default): rows whose working set (values, columns, step
+                             descriptors) fits a warp's slice of the block's shared
+                             memory are refactored one per warp; 0: every row one per
+                             block.  Same arithmetic either way. */
+    int row_order;        /* dispatch order of the refactorization's rows: 1 (default)
+                             by level in the dependency DAG of L (ties by row); 0 by
+                             row.  A row's dependencies are always dispatched before
+                             it.  Same arithmetic either way. */
 } kkt_opts;
 
 /* Refinement methods (Section 2.1).  FGMRES: FGMRES(m) with M = LU as right
@@ -158,7 +158,7 @@ typedef struct {
 #define KKT_PHASE_SPMV 4      /* products with K and residuals */
 #define KKT_PHASE_ORTHO 5     /* CGS2 passes, normalisation, Givens */
 #define KKT_PHASE_UPDATE 6    /* cycle start and end (v_0, y = R^{-1} g, x += Z y) */
-#define KKT_PHASE_REFACTOR_TAIL 7  /* the part of the refactorization done one block per row */
+#define KKT_PHASE_REFACTOR_TAIL 7  /* reserved (the refactorization is one kernel: KKT_PHASE_REFACTOR) */
 #define KKT_PHASE_GRAPH_REFACTOR 8 /* a whole refactorization replayed as a graph (kkt_opts.graphs) */
 #define KKT_PHASE_GRAPH_SOLVE 9    /* a whole solve replayed as a graph (kkt_opts.graphs) */
 #define KKT_NUM_PHASES 10
@@ -184,9 +184,12 @@ typedef struct {
     int64_t h2d_bytes;     /* host->device bytes copied by refactor/solve calls so far */
     int64_t d2h_bytes;     /* device->host bytes copied by refactor/solve calls so far */
     int32_t repivots;      /* pivoting refactorizations run by kkt_repivot so far */
-    int32_t tail_rows;     /* rows refactored in shared memory (the rest: one warp per row,
-                              values in global memory) */
-    int32_t tail_warp_rows; /* of those, rows refactored one per warp (the rest one per block) */
+    int32_t rows_warp;     /* rows refactored one per warp in shared memory */
+    int32_t rows_block;    /* rows refactored one per block in shared memory */
+    int32_t rows_global;   /* rows refactored one per block with values in global memory */
+    int32_t refactor_smem; /* shared memory per block of the refactorization kernel (bytes) */
+    int32_t refactor_threads; /* threads per block of the refactorization kernel */
+    int32_t refactor_blocks;  /* blocks of the refactorization kernel */
 } kkt_info;
 
 /* Fill *o with the defaults above. */
@@ -295,11 +298,9 @@ int kkt_get_phase_times(kkt_ctx* c, double* ms, int64_t* counts, int reset);
 
 /*
  * Profiling: kkt_refactor, with the GPU's global timer (ns) recorded when
- * each row of the shared-memory kernel (rows one per warp and one per
- * block) starts and when it publishes its pivot.  t_start[n], t_publish[n]
- * (host) get the stamps (-1 for rows of the warp-per-row kernel in global
- * memory); *t0_out = first row of the shared-memory kernel.  Makes one
- * temporary device allocation for the stamps.
+ * each row starts and when it publishes its pivot.  t_start[n],
+ * t_publish[n] (host) get the stamps; *t0_out = 0 (the first traced row).
+ * Makes one temporary device allocation for the stamps.
  */
 int kkt_trace_refactor(kkt_ctx* c, const double* values, int values_on_device, int64_t* t_start,
                        int64_t* t_publish, int32_t* t0_out);
@@ -307,11 +308,11 @@ int kkt_trace_refactor(kkt_ctx* c, const double* values, int values_on_device, i
 /*
  * Autotuner: times kkt_refactor(values) + kkt_lu_solve(b) (median of `reps`
  * runs after one warm-up) for each schedule of the refactorization and the
- * solves -- the block-per-row part of the refactorization (the last 32767,
- * 16384, 8192 or 4096 rows at most) times the solve schedule (cluster of 16
- * or 8 blocks, or whole-GPU), with and without the warp-per-row mode of the
- * leading short rows -- and keeps the fastest in the context
- * (kkt_query: tail_rows, trisolve_cluster).  Every schedule computes the
+ * solves -- the refactorization kernel's shared memory per block (sized by
+ * the longest row, 72 KB, 110 KB or the device's limit), with and without
+ * warp rows, times the solve schedule (cluster of 16 or 8 blocks, or
+ * whole-GPU) -- and keeps the fastest in the context (kkt_query:
+ * refactor_smem, rows_warp, trisolve_cluster).  Every schedule computes the
  * same bits, so tuning changes only speed.  values, b as in kkt_refactor and
  * kkt_lu_solve; with on_device != 0 one n-vector of device memory is added
  * to the context.  *best_ms (may be NULL) gets the chosen time.  The factors
@@ -459,7 +460,52 @@ int kkt_server_query(kkt_server* s, kkt_server_info* info);
 /* Wait for every queued step, close every instance, stop the workers. */
 void kkt_server_destroy(kkt_server* s);
 
+/*
+ * Profiling: the critical path of the last traced refactorization
+ * (kkt_trace_refactor's stamps, passed back in).  Rows in index order are a
+ * topological order of the dependency DAG of L (row i waits for every row k
+ * with L(i,k) != 0); a row's link is t_publish[i] - max(t_start[i], the
+ * latest t_publish of its dependencies), the time from when it could take
+ * its last step to its publication.  *path_ns gets the longest path of
+ * links through the DAG (rows without stamps count 0), *levels the depth of
+ * the DAG, *median_link_ns the median link of the stamped rows, *rows the
+ * rows with stamps.  Host only (no device work).
+ */
+int kkt_trace_critical_path(kkt_ctx* c, const int64_t* t_start, const int64_t* t_publish, double* path_ns,
+                            int32_t* levels, double* median_link_ns, int32_t* rows);
+
+/*
+ * A second context on the same pattern: copies src's analysis (canonical
+ * pattern, P, Q, factor structure, schedules) into c, which must have been
+ * created (kkt_create) with its own options (for example another
+ * precision), and makes c's device buffers.  Costs no host factorization.
+ * Errors: KKT_ERR_STATE (src not analysed), kkt_analyze's device errors.
+ */
+int kkt_analyze_like(kkt_ctx* c, const kkt_ctx* src);
+
 /* ---- host-only helpers (no GPU needed) ---- */
+
+/* Statistics of a host analysis (kkt_host_analyze). */
+typedef struct {
+    int64_t nnz_l;           /* strictly lower entries of L */
+    int64_t nnz_u;           /* entries of U including the diagonal */
+    int32_t levels_l;        /* depth of the L-solve dependency DAG */
+    int32_t levels_u;        /* depth of the U-solve dependency DAG */
+    double refactor_updates; /* multiply-adds of one refactorization */
+    double order_ms;         /* host time of the column ordering */
+    double pivot_ms;         /* host time of the pivoting factorization */
+} kkt_host_stats;
+
+/*
+ * The one-time analysis of kkt_analyze without a GPU (Section 3.1.1: the
+ * first factorization runs on the CPU): the column order Q (approximate
+ * minimum degree on the pattern of K^T K) and the pivot sequence P
+ * (threshold partial pivoting with pivot_tol on values0), both written to
+ * host arrays of n, and the structure's statistics in *st (may be NULL).
+ * kkt_analyze(…, Q, P) on another thread or later reuses them.  Thread safe.
+ */
+int kkt_host_analyze(int32_t n, const int32_t* rowptr, const int32_t* colind, const double* values0,
+                     double pivot_tol, int32_t* P, int32_t* Q, kkt_host_stats* st);
 
 /* Column order of kkt_analyze (approximate minimum degree on K^T K). */
 int kkt_order(int32_t n, const int32_t* rowptr, const int32_t* colind, int32_t* Q);

@@ -16,7 +16,7 @@ import os
 
 import numpy as np
 
-__all__ = ["KKTSolver", "KKTServer", "KKTError", "order", "pivot", "lib", "LIB_PATH", "EXPORTS"]
+__all__ = ["KKTSolver", "KKTServer", "KKTError", "order", "pivot", "host_analyze", "lib", "LIB_PATH", "EXPORTS"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libkkt_b300.so")
 
@@ -31,7 +31,7 @@ TRSV = {"auto": 0, "global": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 METHOD = {"fgmres": 0, "richardson": 1, "fgmres_ee": 2}
 ORTHO = {"cgs2": 0, "cgs2_pythagoras": 1, "cgs1_pythagoras": 2}
-TAIL_ORDER = {"row": 0, "level": 1}
+ROW_ORDER = {"row": 0, "level": 1}
 
 # every entry point declared in include/kkt.h
 EXPORTS = [
@@ -41,6 +41,7 @@ EXPORTS = [
     "kkt_get_phase_times", "kkt_lu_solve_noalloc", "kkt_selftest_wait", "kkt_trace_refactor",
     "kkt_trace_solve", "kkt_repivot", "kkt_tune", "kkt_step", "kkt_server_default_opts", "kkt_server_create", "kkt_server_open",
     "kkt_server_submit", "kkt_server_wait", "kkt_server_close", "kkt_server_query", "kkt_server_destroy",
+    "kkt_host_analyze", "kkt_analyze_like", "kkt_trace_critical_path",
 ]
 NOALLOC_MAX_N = 65536
 PHASES = ["gather", "refactor", "lsolve", "usolve", "spmv", "ortho", "update", "refactor_tail", "graph_refactor",
@@ -52,9 +53,9 @@ class _Opts(C.Structure):
         ("restart", C.c_int), ("max_cycles", C.c_int), ("stop_mode", C.c_int), ("precision", C.c_int),
         ("refine_delta", C.c_double), ("pivot_tol", C.c_double), ("boost_eps", C.c_double),
         ("device", C.c_int), ("create_stream", C.c_int), ("stream", C.c_void_p), ("spin_limit", C.c_int64),
-        ("timing", C.c_int), ("trisolve", C.c_int), ("cluster_blocks", C.c_int), ("tail_rows", C.c_int),
+        ("timing", C.c_int), ("trisolve", C.c_int), ("cluster_blocks", C.c_int), ("block_smem", C.c_int),
         ("method", C.c_int), ("ortho", C.c_int), ("inner_tol", C.c_double), ("repivot", C.c_int),
-        ("graphs", C.c_int), ("tail_warp_rows", C.c_int), ("tail_order", C.c_int),
+        ("graphs", C.c_int), ("warp_rows", C.c_int), ("row_order", C.c_int),
     ]
 
 
@@ -65,8 +66,9 @@ class _Info(C.Structure):
         ("device_bytes", C.c_int64), ("nboost", C.c_int32), ("last_iters", C.c_int32),
         ("last_cycles", C.c_int32), ("trisolve_cluster", C.c_int32), ("last_nrbe", C.c_double), ("last_rnorm0", C.c_double),
         ("norm_a_inf", C.c_double), ("analyze_ms", C.c_double), ("launches", C.c_int64),
-        ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("repivots", C.c_int32), ("tail_rows", C.c_int32),
-        ("tail_warp_rows", C.c_int32),
+        ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("repivots", C.c_int32), ("rows_warp", C.c_int32),
+        ("rows_block", C.c_int32), ("rows_global", C.c_int32), ("refactor_smem", C.c_int32),
+        ("refactor_threads", C.c_int32), ("refactor_blocks", C.c_int32),
     ]
 
 
@@ -82,6 +84,11 @@ class _StepResult(C.Structure):
 class _ServerInfo(C.Structure):
     _fields_ = [("instances", C.c_int32), ("device_bytes", C.c_int64), ("hbm_budget", C.c_int64),
                 ("submitted", C.c_int64), ("completed", C.c_int64), ("in_flight", C.c_int32)]
+
+
+class _HostStats(C.Structure):
+    _fields_ = [("nnz_l", C.c_int64), ("nnz_u", C.c_int64), ("levels_l", C.c_int32), ("levels_u", C.c_int32),
+                ("refactor_updates", C.c_double), ("order_ms", C.c_double), ("pivot_ms", C.c_double)]
 
 
 class KKTError(RuntimeError):
@@ -140,6 +147,9 @@ def lib():
     L.kkt_server_query.argtypes = [vp, C.POINTER(_ServerInfo)]
     L.kkt_server_destroy.argtypes = [vp]
     L.kkt_server_destroy.restype = None
+    L.kkt_host_analyze.argtypes = [i32, vp, vp, vp, d, vp, vp, C.POINTER(_HostStats)]
+    L.kkt_analyze_like.argtypes = [vp, vp]
+    L.kkt_trace_critical_path.argtypes = [vp, vp, vp, C.POINTER(d), C.POINTER(i32), C.POINTER(d), C.POINTER(i32)]
     for name in EXPORTS:
         if name not in ("kkt_default_opts", "kkt_destroy", "kkt_strerror", "kkt_last_error_detail",
                         "kkt_server_default_opts", "kkt_server_destroy"):
@@ -209,6 +219,23 @@ def pivot(rowptr, colind, values, Q=None, tol=1e-3):
     return P, nl.value, nu.value
 
 
+def host_analyze(rowptr, colind, values0, pivot_tol=1e-3):
+    """kkt_host_analyze: the analysis of kkt_analyze on the host only (no
+    GPU) -- returns (P, Q, stats) with stats the structure's statistics."""
+    L = lib()
+    rp, prp = _host(rowptr, np.int32)
+    ci, pci = _host(colind, np.int32)
+    v, pv = _host(values0, np.float64)
+    n = len(rp) - 1
+    P = np.zeros(n, np.int32)
+    Q = np.zeros(n, np.int32)
+    st = _HostStats()
+    rc = L.kkt_host_analyze(n, prp, pci, pv, float(pivot_tol), P.ctypes.data, Q.ctypes.data, C.byref(st))
+    if rc:
+        raise KKTError(rc, "kkt_host_analyze")
+    return P, Q, {k: getattr(st, k) for k, _ in _HostStats._fields_}
+
+
 def lu_solve_noalloc(Fp, Fj, Fdiag, Fx, P, Q, b, x, stream=None):
     """kkt_lu_solve_noalloc: x = Q U^{-1} L^{-1} P b from caller-held device
     factors in the combined row layout, with no device allocation (for
@@ -226,9 +253,9 @@ def lu_solve_noalloc(Fp, Fj, Fdiag, Fx, P, Q, b, x, stream=None):
 
 
 def _solver_opts(restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3, boost_eps=0.0,
-                 device=0, spin_limit=0, timing=False, trisolve="auto", tail_rows=0, cluster_blocks=0,
+                 device=0, spin_limit=0, timing=False, trisolve="auto", block_smem=0, cluster_blocks=0,
                  precision="fp64", method="fgmres", ortho="cgs2", inner_tol=1e-6, repivot=False, graphs=False,
-                 tail_warp_rows=True, tail_order="level"):
+                 warp_rows=True, row_order="level"):
     """kkt_opts from keyword arguments (defaults of kkt_default_opts)."""
     o = _Opts()
     lib().kkt_default_opts(C.byref(o))
@@ -236,14 +263,14 @@ def _solver_opts(restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, 
     o.refine_delta, o.pivot_tol, o.boost_eps = float(refine_delta), float(pivot_tol), float(boost_eps)
     o.device, o.spin_limit, o.timing = int(device), int(spin_limit), int(bool(timing))
     o.trisolve = TRSV[trisolve]
-    o.tail_rows = int(tail_rows)
+    o.block_smem = int(block_smem)
     o.cluster_blocks = int(cluster_blocks)
     o.precision = PRECISION[precision]
     o.method, o.ortho, o.inner_tol = METHOD[method], ORTHO[ortho], float(inner_tol)
     o.repivot = int(bool(repivot))
     o.graphs = int(bool(graphs))
-    o.tail_warp_rows = int(bool(tail_warp_rows))
-    o.tail_order = TAIL_ORDER[tail_order]
+    o.warp_rows = int(bool(warp_rows))
+    o.row_order = ROW_ORDER[row_order]
     return o
 
 
@@ -253,12 +280,12 @@ class KKTSolver:
 
     def __init__(self, restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3,
                  boost_eps=0.0, device=0, stream=None, spin_limit=0, timing=False, trisolve="auto",
-                 tail_rows=0, cluster_blocks=0, precision="fp64", method="fgmres", ortho="cgs2",
-                 inner_tol=1e-6, repivot=False, graphs=False, tail_warp_rows=True, tail_order="level"):
+                 block_smem=0, cluster_blocks=0, precision="fp64", method="fgmres", ortho="cgs2",
+                 inner_tol=1e-6, repivot=False, graphs=False, warp_rows=True, row_order="level"):
         L = lib()
         o = _solver_opts(restart, max_cycles, stop_mode, refine_delta, pivot_tol, boost_eps, device, spin_limit,
-                         timing, trisolve, tail_rows, cluster_blocks, precision, method, ortho, inner_tol, repivot,
-                         graphs, tail_warp_rows, tail_order)
+                         timing, trisolve, block_smem, cluster_blocks, precision, method, ortho, inner_tol, repivot,
+                         graphs, warp_rows, row_order)
         if stream is None:
             stream = _torch_current_stream(device)
         if stream is None:
@@ -299,6 +326,13 @@ class KKTSolver:
         self._check(lib().kkt_analyze(self._h, n, prp, pci, v[1] if v else None, q[1] if q else None,
                                       p[1] if p else None), "kkt_analyze")
         self.n, self.nnz = n, int(rp[-1])
+        return self
+
+    def analyze_like(self, other):
+        """kkt_analyze_like: reuse another context's analysis (same pattern,
+        P, Q and structure) for this context's options."""
+        self._check(lib().kkt_analyze_like(self._h, other._h), "kkt_analyze_like")
+        self.n, self.nnz = other.n, other.nnz
         return self
 
     def refactor(self, values):
@@ -410,8 +444,8 @@ class KKTSolver:
         return x, lL, tL, lU, tU
 
     def trace_refactor(self, values):
-        """kkt_refactor with per-row start/publish stamps (ns) of the
-        block-per-row part: (t_start, t_publish, t0)."""
+        """kkt_refactor with per-row start/publish stamps (ns) of every row:
+        (t_start, t_publish, t0 = 0)."""
         keep, p, dev = _ptr(values, np.float64)
         ts = np.zeros(self.n, np.int64)
         tp = np.zeros(self.n, np.int64)
@@ -419,6 +453,20 @@ class KKTSolver:
         self._check(lib().kkt_trace_refactor(self._h, p, dev, ts.ctypes.data, tp.ctypes.data, C.byref(t0)),
                     "kkt_trace_refactor")
         return ts, tp, t0.value
+
+    def critical_path(self, t_start, t_publish):
+        """kkt_trace_critical_path on trace_refactor's stamps: dict with the
+        longest path of per-row links (ms), the DAG depth, the median link
+        (us) and the stamped rows."""
+        ts = np.ascontiguousarray(t_start, np.int64)
+        tp = np.ascontiguousarray(t_publish, np.int64)
+        path, med = C.c_double(), C.c_double()
+        lev, rows = C.c_int32(), C.c_int32()
+        self._check(lib().kkt_trace_critical_path(self._h, ts.ctypes.data, tp.ctypes.data, C.byref(path),
+                                                  C.byref(lev), C.byref(med), C.byref(rows)),
+                    "kkt_trace_critical_path")
+        return {"path_ms": path.value * 1e-6, "levels": lev.value, "median_link_us": med.value * 1e-3,
+                "rows_stamped": rows.value}
 
     def selftest_wait(self, limit):
         """Return code of kkt_selftest_wait (KKT_ERR_TIMEOUT = -7 expected)."""

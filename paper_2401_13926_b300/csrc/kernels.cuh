@@ -61,7 +61,6 @@ struct DevScal {
     // sync-free scheduling
     unsigned gen_fact;
     unsigned ticket_fact, ticket_l, ticket_u;
-    unsigned ticket_mid;   // warp-per-row part of the refactorization tail
     unsigned red_count;
     // errors
     int err;               // first error code (0 = none)
@@ -173,13 +172,6 @@ __global__ void k_refactor_prep(DevScal* s) {
     s->normA = 0.0;
 }
 
-// Fx[t] = caller value of the entry of A that lands in factor slot t (0 for
-// fill); Ax[e] = caller value of canonical entry e; ||K||_inf from row sums.
-// Slots from tail_begin on belong to the rows the tail kernel factors in
-// shared memory; they are armed with SENTINEL instead (the tail kernel
-// gathers their values itself and publishes each row when it is final).
-// T is the factor type: double, or float in mixed precision (the caller's
-// FP64 values are rounded to nearest here).
 struct GiveUpGlobal {
     const int* abort;
     __device__ bool operator()() const { return *(volatile const int*)abort != 0; }
@@ -212,20 +204,14 @@ struct FwdArgs {
 };
 
 template <typename T>
-struct CgVals {   // row values this kernel wrote (read from L2)
-    const T* Fx;
-    __device__ T operator()(int64_t p) const { return __ldcg(&Fx[p]); }
-};
-
-template <typename T>
-struct SliceVals {   // row values in shared memory: entry p at w[p - b]
+struct SliceVals {   // the row's values as the refactorization left them: entry p at w[p - b]
     const T* w;
     int64_t b;
     __device__ T operator()(int64_t p) const { return w[p - b]; }
 };
 
 // One load per lane in flight (same bits as the sweep's batched loads):
-// fewer registers in the refactorization kernels that carry it.
+// fewer registers in the refactorization kernel that carries it.
 template <typename T, class Vals>
 __device__ __forceinline__ bool fused_forward_row(int row, int64_t lo, int64_t hi, Vals vals,
                                                   const int32_t* __restrict__ Fj, const FwdArgs<T>& fw, DevScal* s,
@@ -245,21 +231,21 @@ __device__ __forceinline__ bool fused_forward_row(int row, int64_t lo, int64_t h
     return true;
 }
 
+// Every factor value and pivot reciprocal is armed with SENTINEL (the
+// refactorization gathers the caller's values itself and publishes each
+// value when it is final); Ax[e] = caller value of canonical entry e;
+// ||K||_inf from row sums.  T is the factor type: double, or float in
+// mixed precision.
 template <typename T>
-__global__ void k_gather(const double* __restrict__ vals, const int64_t* __restrict__ fsrc, int64_t nnzF,
-                         int64_t tail_begin, T* __restrict__ Fx, const int32_t* __restrict__ Arp,
-                         const int64_t* __restrict__ asrc, double* __restrict__ Ax, int n, int t0,
-                         T* __restrict__ rinv, DevScal* s, T* __restrict__ yarm) {
+__global__ void k_gather(const double* __restrict__ vals, int64_t nnzF, T* __restrict__ Fx,
+                         const int32_t* __restrict__ Arp, const int64_t* __restrict__ asrc,
+                         double* __restrict__ Ax, int n, T* __restrict__ rinv, DevScal* s, T* __restrict__ yarm) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = t0 + tid; i < n; i += stride) rinv[i] = sentinel_of<T>();   // tail rows publish 1/u_ii last
+    for (int64_t i = tid; i < n; i += stride) rinv[i] = sentinel_of<T>();
     if (yarm)   // the fused forward sweep fills y
         for (int64_t i = tid; i < n; i += stride) yarm[i] = sentinel_of<T>();
-    for (int64_t t = tid; t < nnzF; t += stride) {
-        if (t >= tail_begin) { Fx[t] = sentinel_of<T>(); continue; }
-        int64_t q = fsrc[t];
-        Fx[t] = (q >= 0) ? (T)vals[q] : T(0);
-    }
+    for (int64_t t = tid; t < nnzF; t += stride) Fx[t] = sentinel_of<T>();
     const int lane = threadIdx.x & 31;
     const int64_t warp = tid >> 5, nwarps = stride >> 5;
     bool bad = false;
@@ -288,94 +274,54 @@ __global__ void k_gather(const double* __restrict__ vals, const int64_t* __restr
 
 // ---------------------------------------------------------------- K1: refactor
 // Up-looking (row-by-row Doolittle) numeric LU on the fixed pattern: for row
-// i, in ascending k over L(i,:), l_ik = w_k / u_kk and w -= l_ik U(k,:).
-// One warp per row; lanes split the update of U(k,:) and find each target
-// column in row i by binary search.
-__device__ __forceinline__ int64_t find_col(const int32_t* __restrict__ Fj, int64_t lo, int64_t hi, int32_t c) {
-    // first position in [lo, hi) with Fj >= c
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (__ldg(&Fj[mid]) < c) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
+// i, in ascending k over L(i,:), l_ik = w_k * (1/u_kk) and w -= l_ik U(k,:),
+// every update one fused multiply-add.  ONE persistent kernel factors every
+// row; each row is placed by the room its working set needs -- its values,
+// columns and the descriptors of its elimination steps:
+//   ROW_WARP   one warp, in that warp's slice of the block's shared memory;
+//   ROW_BLOCK  the whole block, in the block's shared memory (the long
+//              rows at the dense end of the order), with a position map for
+//              the last columns;
+//   ROW_GLOBAL the whole block, its values in a global scratch area (rows
+//              that fit no block).
+// Work items (up to one warp-row per warp, or one block row) are taken from
+// an atomic ticket in the order of their rows' level in the dependency DAG
+// of L, so a row's dependencies are always dispatched before it and every
+// row a block waits on belongs to a block that is already running.  A
+// finished row publishes its U values and 1/u_ii with no fences: every
+// published datum is armed with SENTINEL by the gather and is final once it
+// is not, so a consumer spins on exactly the values it uses.
+constexpr int ROW_WARP = 0, ROW_BLOCK = 1, ROW_GLOBAL = 2;
 
-template <typename T, bool FUSED>
-__global__ void k_refactor(int n, const int32_t* __restrict__ order, const int64_t* __restrict__ Fp,
-                           const int32_t* __restrict__ Fj,
-                           const int64_t* __restrict__ Fdiag, T* Fx, T* rinv, unsigned* done, DevScal* s,
-                           double boost_eps, long long limit, FwdArgs<T> fw) {
-    // rows [0, n) of the bulk: warp per row, factor values in global memory,
-    // taken in the dispatch order order[0, n)
-    const int lane = threadIdx.x & 31;
-    const unsigned gen = *(volatile unsigned*)&s->gen_fact;
-    const T boost = (T)(boost_eps * *(volatile double*)&s->normA);
-    for (;;) {
-        int q = 0;
-        if (lane == 0) q = (int)atomicAdd(&s->ticket_fact, 1u);
-        q = __shfl_sync(0xffffffffu, q, 0);
-        if (q >= n) return;
-        if (ld_volatile_int(&s->abort)) return;
-        const int row = order[q];
-        const int64_t b = Fp[row], d = Fdiag[row], e = Fp[row + 1];
-        for (int64_t p = b; p < d; p++) {
-            const int32_t k = __ldg(&Fj[p]);
-            int ok = 1;
-            if (lane == 0) ok = wait_flag(&done[k], gen, s, limit, row);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) return;
-            __threadfence();
-            const int64_t dk = __ldg(&Fdiag[k]), ek = __ldg(&Fp[k + 1]);
-            const T lik = __ldcg(&Fx[p]) * __ldcg(&rinv[k]);   // l_ik = w_k * (1/u_kk)
-            __syncwarp();
-            if (lane == 0) __stcg(&Fx[p], lik);
-            for (int64_t q = dk + 1 + lane; q < ek; q += 32) {
-                const int32_t c = __ldg(&Fj[q]);
-                // entry q of U(k,:) lies after its predecessors and before its
-                // successors among row i's columns past k
-                const int64_t hi = e - (ek - 1 - q);
-                const int64_t pos = find_col(Fj, p + 1 + (q - dk - 1), hi, c);
-                if (pos >= hi || __ldg(&Fj[pos]) != c) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
-                __stcg(&Fx[pos], fma(-lik, __ldcg(&Fx[q]), __ldcg(&Fx[pos])));
-            }
-            __threadfence();
-            __syncwarp();
-        }
-        if (lane == 0) {
-            T u = __ldcg(&Fx[d]);
-            bool fail = false;
-            if (!isfinite(u)) { raise_error(s, KKT_ERR_NONFINITE, row); fail = true; }
-            else if (boost > 0.0) {
-                if (fabs(u) < boost) { u = (u < 0.0) ? -boost : boost; atomicAdd(&s->nboost, 1); __stcg(&Fx[d], u); }
-            } else if (u == 0.0) { raise_error(s, KKT_ERR_ZERO_PIVOT, row); fail = true; }
-            if (!fail) {
-                __stcg(&rinv[row], rcp_rn(u));
-                __threadfence();
-                st_release(&done[row], gen);
-            }
-        }
-        __syncwarp();
-        if (FUSED && !fused_forward_row<T>(row, b, d, CgVals<T>{Fx}, Fj, fw, s, limit)) return;
-    }
-}
+struct RefItem {       // rows order[first .. first + count) of one kind
+    int32_t first;
+    int32_t info;      // kind << 28 | count (ROW_WARP) or global-row index (ROW_GLOBAL)
+};
 
-// Tail rows [t0, nrows): one block per row.  The row's values live in
-// shared memory (w), and a shared map gives the position of every column
-// >= t0 of the row, so an update from a tail row costs one shared load and
-// one shared read-modify-write per entry.  Updates still go in ascending k,
-// each one fused multiply-add (the same arithmetic as the bulk kernel).  A
-// finished tail row writes its values, then its diagonal last: the diagonal
-// (armed with SENTINEL by the gather) is the row's completion flag.
-constexpr int TAIL_THREADS = 256;
+template <typename T>
+struct RefArgs {
+    const RefItem* items;
+    int nitems;
+    const int32_t* order;
+    const int64_t* Fp;
+    const int32_t* Fj;
+    const int64_t* Fdiag;
+    T* Fx;
+    T* rinv;
+    const double* vals;
+    const int64_t* fsrc;
+    int mlo, M;            // columns [mlo, mlo + M) have an O(1) position map (M may be 0)
+    int map_bytes;         // shared memory before the work area (the map, 16-byte aligned)
+    int area_bytes;        // the work area: a block row, or one slice per warp
+    // ROW_GLOBAL rows, by global-row index g: step descriptors at sd_off[g]
+    // in gdk / gcnt, values at w_off[g] in gw
+    const int64_t* gdk;
+    const int32_t* gcnt;
+    const int64_t* g_sd_off;
+    T* gw;
+    const int64_t* g_w_off;
+};
 
-__global__ void k_refactor_prep_tail(DevScal* s) {
-    s->ticket_fact = 0;
-    s->ticket_mid = 0;
-}
-
-// Publish a tail row's pivot u_ii and its reciprocal.  The reciprocal is
-// on the dependency chain, so it is formed first; the checks (non-finite,
-// zero, below the boost threshold) read the bits or run beside it.
 __device__ __forceinline__ bool finite_bits(double v) {
     return (__double_as_longlong(v) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
 }
@@ -385,8 +331,12 @@ __device__ __forceinline__ bool zero_bits(float v) { return (__float_as_uint(v) 
 __device__ __forceinline__ bool sign_bit(double v) { return __double_as_longlong(v) < 0; }
 __device__ __forceinline__ bool sign_bit(float v) { return (int)__float_as_uint(v) < 0; }
 
+// Publish a row's pivot u_ii and its reciprocal.  The reciprocal is on the
+// dependency chain, so it is formed first; the checks (non-finite, zero,
+// below the boost threshold) read the bits or run beside it.
 template <typename T>
-__device__ __forceinline__ bool tail_pivot(T u, T boost, bool use_boost, DevScal* s, int row, T* Fx_d, T* rinv_row) {
+__device__ __forceinline__ bool publish_pivot(T u, T boost, bool use_boost, DevScal* s, int row, T* Fx_d,
+                                              T* rinv_row) {
     T ri = rcp_rn(u);
     if (!finite_bits(u)) { raise_error(s, KKT_ERR_NONFINITE, row); return false; }
     if (use_boost) {
@@ -404,54 +354,9 @@ __device__ __forceinline__ bool tail_pivot(T u, T boost, bool use_boost, DevScal
     return true;
 }
 
-// One step's worth of U(k,:) for one thread: up to TAIL_E entries
-// (columns and values) and the pivot reciprocal of row k, loaded two steps
-// ahead from addresses staged in shared memory, so issuing the loads never
-// waits for an earlier load.  Tail rows publish their U values and 1/u_kk
-// with no ordering between them -- every datum is armed with SENTINEL by the
-// gather and is final once it is not -- so a consumer spins on exactly the
-// values it uses, all of them in one pass per round trip.
-constexpr int TAIL_E = 4;
-template <typename T>
-struct TailStage {
-    T rk;
-    int32_t col[TAIL_E];
-    T val[TAIL_E];
-};
-
-struct StepDesc {     // staged per L entry of the row: the step's source row
-    int64_t dk;       // position of U(k,k)
-    int32_t k, cnt;   // k, |U(k, >k)|
-};
-
-template <typename T>
-__device__ __forceinline__ void tail_load(TailStage<T>& st, int s, int nsteps, const StepDesc* sd,
-                                          const int32_t* __restrict__ Fj, const T* Fx, const T* rinv) {
-    if (s >= nsteps) return;
-    const StepDesc d = sd[s];
-    st.rk = ld_relaxed(&rinv[d.k]);
-#pragma unroll
-    for (int j = 0; j < TAIL_E; j++) {
-        const int e = threadIdx.x + j * TAIL_THREADS;
-        if (e < d.cnt) { st.col[j] = Fj[d.dk + 1 + e]; st.val[j] = ld_relaxed(&Fx[d.dk + 1 + e]); }
-    }
-}
-
-// position in the row of column c: the shared map for c >= mlo, else a
-// binary search of the row's columns (staged in shared memory) from lo
-__device__ __forceinline__ int tail_pos(int c, int mlo, const short* map, const int32_t* cols, int lo, int len) {
-    if (c >= mlo) return map[c - mlo];
-    int hi = len;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (cols[mid] < c) lo = mid + 1; else hi = mid;
-    }
-    return (lo < len && cols[lo] == c) ? lo : -1;
-}
-
 // Spin until a published datum is not SENTINEL (bounded; abort-aware).
 template <typename T>
-__device__ __forceinline__ bool tail_wait(const T* p, T* v, DevScal* s, long long limit, int row) {
+__device__ __forceinline__ bool pub_wait(const T* p, T* v, DevScal* s, long long limit, int row) {
     T x = *v;
     for (long long it = 0; is_sentinel(x); it++) {
         if ((it & 63) == 63 && ld_volatile_int(&s->abort)) return false;
@@ -475,28 +380,53 @@ __device__ __forceinline__ int slice_pos(const int32_t* cols, int lo, int hi, in
     return (lo < end && cols[lo] == c) ? lo : -1;
 }
 
-// One short tail row by one warp, its values, columns and step descriptors
-// in the warp's slice of shared memory: the same steps, the same fused
-// multiply-add per entry in ascending k, and the same publication as a
-// block row.  Returns false if a wait gave up.
+// Column c's position in the row: the shared map for c in [mlo, mlo + M),
+// else the narrowed binary search.
+__device__ __forceinline__ int row_pos(int c, int mlo, int M, const short* map, const int32_t* cols, int lo,
+                                       int hi) {
+    if ((unsigned)(c - mlo) < (unsigned)M) return map[c - mlo];
+    return slice_pos(cols, lo, hi, c);
+}
+
+// A row's working set carved from `base`: step descriptors (position of
+// U(k,k) and |U(k, >k)| for every L entry; k itself is the column), the
+// row's values and its columns -- 12 st + (sizeof(T) + 4) len bytes.
+template <typename T>
+struct RowSpace {
+    int64_t* dk;
+    T* w;
+    int32_t* cnt;
+    int32_t* cols;
+    __device__ RowSpace(unsigned char* base, int st, int len) {
+        dk = reinterpret_cast<int64_t*>(base);
+        w = reinterpret_cast<T*>(dk + st);
+        cnt = reinterpret_cast<int32_t*>(w + len);
+        cols = cnt + st;
+    }
+};
+
+// One short row by one warp in its slice: gather, steps, publication, and
+// (FUSED) the row's y.  Returns false if a wait gave up.
 template <typename T, bool FUSED>
-__device__ bool tail_warp_row(int row, int t0, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
-                              const int64_t* __restrict__ Fdiag, T* Fx, T* rinv, const double* __restrict__ vals,
-                              const int64_t* __restrict__ fsrc, DevScal* s, T boost, long long limit,
-                              unsigned long long* trace, StepDesc* sd, T* w, int32_t* cols, const FwdArgs<T>& fw) {
+__device__ bool warp_row(int row, const RefArgs<T>& a, DevScal* s, T boost, long long limit,
+                         unsigned long long* trace, unsigned char* slice, const FwdArgs<T>& fw) {
     const int lane = threadIdx.x & 31;
-    if (trace && lane == 0) trace[2 * (size_t)(row - t0)] = globaltimer_ns();
-    const int64_t b = Fp[row], d = Fdiag[row], e = Fp[row + 1];
+    if (trace && lane == 0) trace[2 * (size_t)row] = globaltimer_ns();
+    const int64_t b = a.Fp[row], d = a.Fdiag[row], e = a.Fp[row + 1];
     const int len = (int)(e - b);
     const int nsteps = (int)(d - b);
+    RowSpace<T> rs(slice, nsteps, len);
+    T* w = rs.w;
+    int32_t* cols = rs.cols;
     for (int q = lane; q < len; q += 32) {
-        const int64_t src = fsrc[b + q];
-        w[q] = src >= 0 ? (T)vals[src] : T(0);
-        const int c = Fj[b + q];
+        const int64_t src = a.fsrc[b + q];
+        w[q] = src >= 0 ? (T)a.vals[src] : T(0);
+        const int c = a.Fj[b + q];
         cols[q] = c;
         if (q < nsteps) {
-            const int64_t dk = Fdiag[c];
-            sd[q] = StepDesc{dk, c, (int32_t)(Fp[c + 1] - dk - 1)};
+            const int64_t dk = a.Fdiag[c];
+            rs.dk[q] = dk;
+            rs.cnt[q] = (int32_t)(a.Fp[c + 1] - dk - 1);
         }
     }
     __syncwarp();
@@ -506,44 +436,45 @@ __device__ bool tail_warp_row(int row, int t0, const int64_t* __restrict__ Fp, c
     int ncol = 0;
     auto prefetch = [&](int st) {
         if (st >= nsteps) return;
-        const StepDesc ds = sd[st];
-        nrk = ld_relaxed(&rinv[ds.k]);
-        if (lane < ds.cnt) {
-            ncol = Fj[ds.dk + 1 + lane];
-            nv = ld_relaxed(&Fx[ds.dk + 1 + lane]);
+        nrk = ld_relaxed(&a.rinv[cols[st]]);
+        if (lane < rs.cnt[st]) {
+            ncol = a.Fj[rs.dk[st] + 1 + lane];
+            nv = ld_relaxed(&a.Fx[rs.dk[st] + 1 + lane]);
         }
     };
     prefetch(0);
     for (int step = 0; step < nsteps; step++) {
-        const StepDesc dsc = sd[step];
+        const int k = cols[step];
+        const int64_t dk = rs.dk[step];
+        const int cnt = rs.cnt[step];
         T rk = nrk, v0 = nv;
         const int c0 = ncol;
         prefetch(step + 1);
-        int ok = tail_wait(&rinv[dsc.k], &rk, s, limit, row);
+        int ok = pub_wait(&a.rinv[k], &rk, s, limit, row);
         const T l = w[step] * rk;   // l_ik = w_k * (1/u_kk)
-        if (ok && lane < dsc.cnt) {   // the prefetched entry
-            if (!tail_wait(&Fx[dsc.dk + 1 + lane], &v0, s, limit, row)) ok = 0;
+        if (ok && lane < cnt) {   // the prefetched entry
+            if (!pub_wait(&a.Fx[dk + 1 + lane], &v0, s, limit, row)) ok = 0;
             else {
-                const int pos = slice_pos(cols, step + 1 + lane, len - (dsc.cnt - 1 - lane), c0);
+                const int pos = slice_pos(cols, step + 1 + lane, len - (cnt - 1 - lane), c0);
                 if (pos < 0) raise_error(s, KKT_ERR_PATTERN, row);
                 else w[pos] = fma(-l, v0, w[pos]);
             }
         }
         // the other entries two per lane at a time, both loads issued first
-        for (int e2 = lane + 32; e2 < dsc.cnt && ok; e2 += 64) {
-            const int64_t q = dsc.dk + 1 + e2;
-            const bool two = e2 + 32 < dsc.cnt;
-            T v = ld_relaxed(&Fx[q]), v2 = T(0);
-            const int c = Fj[q];
+        for (int e2 = lane + 32; e2 < cnt && ok; e2 += 64) {
+            const int64_t q = dk + 1 + e2;
+            const bool two = e2 + 32 < cnt;
+            T v = ld_relaxed(&a.Fx[q]), v2 = T(0);
+            const int c = a.Fj[q];
             int c2 = 0;
-            if (two) { v2 = ld_relaxed(&Fx[q + 32]); c2 = Fj[q + 32]; }
-            if (!tail_wait(&Fx[q], &v, s, limit, row)) { ok = 0; break; }
-            const int pos = slice_pos(cols, step + 1 + e2, len - (dsc.cnt - 1 - e2), c);
+            if (two) { v2 = ld_relaxed(&a.Fx[q + 32]); c2 = a.Fj[q + 32]; }
+            if (!pub_wait(&a.Fx[q], &v, s, limit, row)) { ok = 0; break; }
+            const int pos = slice_pos(cols, step + 1 + e2, len - (cnt - 1 - e2), c);
             if (pos < 0) raise_error(s, KKT_ERR_PATTERN, row);
             else w[pos] = fma(-l, v, w[pos]);
             if (!two) break;
-            if (!tail_wait(&Fx[q + 32], &v2, s, limit, row)) { ok = 0; break; }
-            const int pos2 = slice_pos(cols, step + 33 + e2, len - (dsc.cnt - 33 - e2), c2);
+            if (!pub_wait(&a.Fx[q + 32], &v2, s, limit, row)) { ok = 0; break; }
+            const int pos2 = slice_pos(cols, step + 33 + e2, len - (cnt - 33 - e2), c2);
             if (pos2 < 0) raise_error(s, KKT_ERR_PATTERN, row);
             else w[pos2] = fma(-l, v2, w[pos2]);
         }
@@ -554,161 +485,222 @@ __device__ bool tail_warp_row(int row, int t0, const int64_t* __restrict__ Fp, c
     }
     // publish: every value but the diagonal, then (lane 0) the pivot
     for (int q = lane; q < len; q += 32)
-        if (b + q != d) st_relaxed(&Fx[b + q], w[q]);
+        if (b + q != d) st_relaxed(&a.Fx[b + q], w[q]);
     if (lane == 0) {
-        if (tail_pivot<T>(w[d - b], boost, boost > T(0), s, row, &Fx[d], &rinv[row]) && trace)
-            trace[2 * (size_t)(row - t0) + 1] = globaltimer_ns();
+        if (publish_pivot<T>(w[d - b], boost, boost > T(0), s, row, &a.Fx[d], &a.rinv[row]) && trace)
+            trace[2 * (size_t)row + 1] = globaltimer_ns();
     }
     __syncwarp();
-    if (FUSED) return fused_forward_row<T>(row, b, d, SliceVals<T>{w, b}, Fj, fw, s, limit);
+    if (FUSED) return fused_forward_row<T>(row, b, d, SliceVals<T>{w, b}, a.Fj, fw, s, limit);
     return true;
 }
 
-template <typename T, bool FUSED>
-__global__ void __launch_bounds__(TAIL_THREADS)
-k_refactor_tail(int t0, int t1, int nrows, int mlo, int max_steps, int max_len, int wsteps, int wlen,
-                const int32_t* __restrict__ order, const int64_t* __restrict__ Fp, const int32_t* __restrict__ Fj,
-                const int64_t* __restrict__ Fdiag, T* Fx, T* rinv, const double* __restrict__ vals,
-                const int64_t* __restrict__ fsrc, DevScal* s, double boost_eps, long long limit,
-                unsigned long long* trace, FwdArgs<T> fw) {
-    extern __shared__ __align__(16) unsigned char tail_sh[];
-    __shared__ int s_row;
-    const int M = nrows - mlo;   // columns [mlo, nrows) have an O(1) position map
+// One elimination step's first entries for one thread of a block row:
+// PRE entries of U(k,:) (columns and values) and the pivot reciprocal of
+// row k, loaded two steps ahead so issuing them never waits on a load.
+constexpr int PRE = 4;    // entries per thread in a prefetched stage
+// entries per thread with loads in flight together past the stage: 4 in
+// 512-thread blocks (128 registers a thread), 2 in 256-thread blocks (three
+// blocks an SM, 80 registers a thread)
+template <int NT> struct BatchOf { static constexpr int value = NT >= 512 ? 4 : 2; };
+template <typename T>
+struct Stage {
+    T rk;
+    int32_t col[PRE];
+    T val[PRE];
+};
+
+template <typename T, int NT>
+__device__ __forceinline__ void stage_load(Stage<T>& st, int step, int nsteps, const int32_t* cols,
+                                           const int64_t* dk, const int32_t* cnt, const RefArgs<T>& a) {
+    if (step >= nsteps) return;
+    const int64_t base = dk[step] + 1;
+    const int c = cnt[step];
+    st.rk = ld_relaxed(&a.rinv[cols[step]]);
+#pragma unroll
+    for (int j = 0; j < PRE; j++) {
+        const int e = threadIdx.x + j * NT;
+        if (e < c) { st.col[j] = a.Fj[base + e]; st.val[j] = ld_relaxed(&a.Fx[base + e]); }
+    }
+}
+
+// One long row by the whole block.  rs: its working set, in shared memory
+// (ROW_BLOCK: staged here) or in global memory (ROW_GLOBAL: descriptors
+// precomputed at analysis, columns read from Fj, values in scratch).
+// Returns false (uniformly for the block) if a wait gave up.
+template <typename T, bool FUSED, int NT>
+__device__ bool block_row(int row, const RefArgs<T>& a, DevScal* s, T boost, long long limit,
+                          unsigned long long* trace, RowSpace<T> rs, bool staged, short* map, int M,
+                          const FwdArgs<T>& fw) {
+    const int tid = threadIdx.x;
+    if (trace && tid == 0) trace[2 * (size_t)row] = globaltimer_ns();
+    const int64_t b = a.Fp[row], d = a.Fdiag[row], e = a.Fp[row + 1];
+    const int len = (int)(e - b);
+    const int nsteps = (int)(d - b);
+    T* w = rs.w;
+    const int32_t* cols = staged ? rs.cols : a.Fj + b;
+    const int mlo = a.mlo;
+    for (int q = tid; q < len; q += NT) {
+        const int64_t src = a.fsrc[b + q];
+        w[q] = src >= 0 ? (T)a.vals[src] : T(0);
+        if (staged) {
+            const int c = a.Fj[b + q];
+            rs.cols[q] = c;
+            if ((unsigned)(c - mlo) < (unsigned)M) map[c - mlo] = (short)q;
+            if (q < nsteps) {
+                const int64_t dk = a.Fdiag[c];
+                rs.dk[q] = dk;
+                rs.cnt[q] = (int32_t)(a.Fp[c + 1] - dk - 1);
+            }
+        }
+    }
+    __syncthreads();
+    Stage<T> A, B;
+    stage_load<T, NT>(A, 0, nsteps, cols, rs.dk, rs.cnt, a);
+    stage_load<T, NT>(B, 1, nsteps, cols, rs.dk, rs.cnt, a);
+    int step = 0;
+    // One elimination step: every thread forms l_ik = w_k * (1/u_kk) itself
+    // (thread 0 also stores it), then applies its entries of U(k,:): the
+    // prefetched stage, then the rest BATCH per thread with their loads
+    // issued together.
+    auto run_step = [&](Stage<T>& st) -> bool {
+        const int k = cols[step];
+        const int64_t base = rs.dk[step] + 1;
+        const int cnt = rs.cnt[step];
+        int ok = 1;
+        // anything still SENTINEL is re-read, all of it in one pass
+        for (long long it = 0;; it++) {
+            bool pending = is_sentinel(st.rk);
+#pragma unroll
+            for (int j = 0; j < PRE; j++)
+                if (tid + j * NT < cnt && is_sentinel(st.val[j])) pending = true;
+            if (!pending) break;
+            if ((it & 63) == 63 && ld_volatile_int(&s->abort)) { ok = 0; break; }
+            if (it >= limit) { raise_error(s, KKT_ERR_TIMEOUT, row); ok = 0; break; }
+            __nanosleep(20);
+            if (is_sentinel(st.rk)) st.rk = ld_relaxed(&a.rinv[k]);
+#pragma unroll
+            for (int j = 0; j < PRE; j++) {
+                const int e2 = tid + j * NT;
+                if (e2 < cnt && is_sentinel(st.val[j])) st.val[j] = ld_relaxed(&a.Fx[base + e2]);
+            }
+        }
+        const T l = w[step] * st.rk;   // l_ik = w_k * (1/u_kk)
+        if (ok) {
+#pragma unroll
+            for (int j = 0; j < PRE; j++) {
+                const int e2 = tid + j * NT;
+                if (e2 < cnt) {
+                    const int pos = row_pos(st.col[j], mlo, M, map, cols, step + 1 + e2, len - (cnt - 1 - e2));
+                    if (pos < 0) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
+                    w[pos] = fma(-l, st.val[j], w[pos]);
+                }
+            }
+            constexpr int BATCH = BatchOf<NT>::value;
+            for (int e0 = tid + PRE * NT; e0 < cnt && ok; e0 += BATCH * NT) {
+                T v[BATCH];
+                int c[BATCH];
+#pragma unroll
+                for (int u = 0; u < BATCH; u++) {
+                    const int e2 = e0 + u * NT;
+                    if (e2 < cnt) { v[u] = ld_relaxed(&a.Fx[base + e2]); c[u] = a.Fj[base + e2]; }
+                }
+#pragma unroll
+                for (int u = 0; u < BATCH; u++) {
+                    const int e2 = e0 + u * NT;
+                    if (e2 >= cnt || !ok) continue;
+                    if (!pub_wait(&a.Fx[base + e2], &v[u], s, limit, row)) { ok = 0; continue; }
+                    const int pos = row_pos(c[u], mlo, M, map, cols, step + 1 + e2, len - (cnt - 1 - e2));
+                    if (pos < 0) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
+                    w[pos] = fma(-l, v[u], w[pos]);
+                }
+            }
+        }
+        stage_load<T, NT>(st, step + 2, nsteps, cols, rs.dk, rs.cnt, a);   // the stage's registers are free again
+        const int any_fail = __syncthreads_or(!ok);   // uniform decision for the block
+        if (tid == 0) w[step] = l;   // nobody else touches position `step` any more
+        step++;
+        return !any_fail;
+    };
+    bool ok = true;
+    while (step < nsteps && ok) {
+        ok = run_step(A);
+        if (!ok || step >= nsteps) break;
+        ok = run_step(B);
+    }
+    if (!ok) return false;
+    // publish (the row is final after the last step's barrier): every
+    // thread its share of the values but the diagonal, then thread 0 the
+    // pivot; the last step's l, which thread 0 wrote after that barrier,
+    // thread 0 stores itself
+    for (int q = tid; q < len; q += NT) {
+        if (b + q != d && q != nsteps - 1) st_relaxed(&a.Fx[b + q], w[q]);
+        if (staged) {
+            const int c = cols[q];
+            if ((unsigned)(c - mlo) < (unsigned)M) map[c - mlo] = -1;
+        }
+    }
+    if (tid == 0) {
+        if (nsteps > 0) st_relaxed(&a.Fx[b + nsteps - 1], w[nsteps - 1]);
+        if (publish_pivot<T>(w[d - b], boost, boost > T(0), s, row, &a.Fx[d], &a.rinv[row]) && trace)
+            trace[2 * (size_t)row + 1] = globaltimer_ns();
+    }
+    // the fused forward sweep's y_row, by warp 0 from the row's values; the
+    // other warps wait at the next item's first barrier
+    if (FUSED && tid < 32) {
+        __syncwarp();   // thread 0's last L value
+        fused_forward_row<T>(row, b, d, SliceVals<T>{w, b}, a.Fj, fw, s, limit);
+    }
+    return true;
+}
+
+// The refactorization: blocks of NT threads take work items from the
+// ticket until none is left.  Shared memory: the position map of the last M
+// columns (kept at -1 between rows), then the work area -- one slice per
+// warp for warp rows, or a block row's working set.
+template <typename T, bool FUSED, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1)
+k_refactor_rows(RefArgs<T> a, DevScal* s, double boost_eps, long long limit, unsigned long long* trace,
+                FwdArgs<T> fw) {
+    extern __shared__ __align__(16) unsigned char ref_sh[];
+    __shared__ RefItem s_item;
+    __shared__ int s_q;
+    short* map = reinterpret_cast<short*>(ref_sh);
+    unsigned char* area = ref_sh + a.map_bytes;
     const int tid = threadIdx.x;
     const T boost = (T)(boost_eps * *(volatile double*)&s->normA);
-    // Rows [t0, t1): short rows, one per warp (eight per block), from their
-    // own ticket, all of them dispensed before any block row below; each
-    // warp works in its own slice of shared memory.  order[] holds the rows
-    // in dispatch order: order[0, t1 - t0) this part, the rest the block rows.
-    if (t1 > t0) {
-        const int warp = tid >> 5;
-        const size_t slice = ((16 * (size_t)wsteps + (sizeof(T) + 4) * (size_t)wlen) + 15) & ~(size_t)15;
-        StepDesc* wsd = reinterpret_cast<StepDesc*>(tail_sh + warp * slice);
-        T* ww = reinterpret_cast<T*>(wsd + wsteps);
-        int32_t* wc = reinterpret_cast<int32_t*>(ww + wlen);
-        for (;;) {
-            if (tid == 0) s_row = (int)atomicAdd(&s->ticket_mid, (unsigned)(TAIL_THREADS / 32));
-            __syncthreads();
-            const int first = s_row;
-            if (__syncthreads_or(first >= t1 - t0 || ld_volatile_int(&s->abort))) break;
-            const int q = first + warp;
-            if (q < t1 - t0)
-                tail_warp_row<T, FUSED>(order[q], t0, Fp, Fj, Fdiag, Fx, rinv, vals, fsrc, s, boost, limit, trace, wsd,
-                                        ww, wc, fw);
-            __syncthreads();   // the slices and s_row are reused
-        }
-        if (__syncthreads_or(ld_volatile_int(&s->abort))) return;   // uniform for the block
-    }
-    // Rows [t1, nrows): one per block.
-    StepDesc* sd = reinterpret_cast<StepDesc*>(tail_sh);                          // max_steps
-    T* w = reinterpret_cast<T*>(sd + max_steps);                                  // row values, max_len
-    int32_t* cols = reinterpret_cast<int32_t*>(w + max_len);                      // row columns, max_len
-    short* map = reinterpret_cast<short*>(cols + max_len);                        // M entries
-    for (int c = tid; c < M; c += blockDim.x) map[c] = -1;
-    __syncthreads();
+    for (int c = tid; c < a.M; c += NT) map[c] = -1;
+    const size_t slice = ((size_t)a.area_bytes / (NT / 32)) & ~(size_t)15;
     for (;;) {
         if (tid == 0) {
             const int q = (int)atomicAdd(&s->ticket_fact, 1u);
-            s_row = q < nrows - t1 ? order[(t1 - t0) + q] : nrows;
+            s_q = q;
+            if (q < a.nitems) s_item = a.items[q];
         }
         __syncthreads();
-        const int row = s_row;
-        const int stop = __syncthreads_or(row >= nrows || ld_volatile_int(&s->abort));
-        if (stop) return;
-        if (trace && tid == 0) trace[2 * (size_t)(row - t0)] = globaltimer_ns();
-        const int64_t b = Fp[row], d = Fdiag[row], e = Fp[row + 1];
-        const int len = (int)(e - b);
-        const int nsteps = (int)(d - b);
-        for (int q = tid; q < len; q += blockDim.x) {
-            const int64_t src = fsrc[b + q];
-            w[q] = src >= 0 ? (T)vals[src] : T(0);
-            const int c = Fj[b + q];
-            cols[q] = c;
-            if (c >= mlo) map[c - mlo] = (short)q;
-            if (q < nsteps) {
-                const int64_t dk = Fdiag[c];
-                sd[q] = StepDesc{dk, c, (int32_t)(Fp[c + 1] - dk - 1)};
+        if (__syncthreads_or(s_q >= a.nitems || ld_volatile_int(&s->abort))) return;
+        const RefItem it = s_item;
+        const int kind = it.info >> 28;
+        if (kind == ROW_WARP) {
+            const int count = it.info & 0x0fffffff;
+            const int warp = tid >> 5;
+            if (warp < count)
+                warp_row<T, FUSED>(a.order[it.first + warp], a, s, boost, limit, trace, area + warp * slice, fw);
+            __syncthreads();   // the slices are reused by the next item
+        } else {
+            const int row = a.order[it.first];
+            const int64_t b = a.Fp[row];
+            const int len = (int)(a.Fp[row + 1] - b), nsteps = (int)(a.Fdiag[row] - b);
+            RowSpace<T> rs(area, nsteps, len);
+            const bool staged = kind == ROW_BLOCK;
+            if (!staged) {   // ROW_GLOBAL: descriptors and values in global memory
+                const int g = it.info & 0x0fffffff;
+                rs.dk = const_cast<int64_t*>(a.gdk) + a.g_sd_off[g];
+                rs.cnt = const_cast<int32_t*>(a.gcnt) + a.g_sd_off[g];
+                rs.w = a.gw + a.g_w_off[g];
             }
-        }
-        __syncthreads();
-        TailStage<T> A, B;
-        tail_load(A, 0, nsteps, sd, Fj, Fx, rinv);
-        tail_load(B, 1, nsteps, sd, Fj, Fx, rinv);
-        int step = 0;
-        // One elimination step: every thread forms l_ik = w_k * (1/u_kk)
-        // itself (thread 0 also stores it), then applies its entries of U(k,:).
-        auto run_step = [&](TailStage<T>& st) -> bool {
-            const StepDesc dsc = sd[step];
-            int ok = 1;
-            // anything still SENTINEL is re-read, all of it in one pass
-            for (long long it = 0;; it++) {
-                bool pending = is_sentinel(st.rk);
-#pragma unroll
-                for (int j = 0; j < TAIL_E; j++)
-                    if (tid + j * TAIL_THREADS < dsc.cnt && is_sentinel(st.val[j])) pending = true;
-                if (!pending) break;
-                if ((it & 63) == 63 && ld_volatile_int(&s->abort)) { ok = 0; break; }
-                if (it >= limit) { raise_error(s, KKT_ERR_TIMEOUT, row); ok = 0; break; }
-                __nanosleep(20);
-                if (is_sentinel(st.rk)) st.rk = ld_relaxed(&rinv[dsc.k]);
-#pragma unroll
-                for (int j = 0; j < TAIL_E; j++) {
-                    const int e2 = tid + j * TAIL_THREADS;
-                    if (e2 < dsc.cnt && is_sentinel(st.val[j])) st.val[j] = ld_relaxed(&Fx[dsc.dk + 1 + e2]);
-                }
-            }
-            const T l = w[step] * st.rk;   // l_ik = w_k * (1/u_kk)
-            if (ok) {
-#pragma unroll
-                for (int j = 0; j < TAIL_E; j++) {
-                    const int e2 = tid + j * TAIL_THREADS;
-                    if (e2 < dsc.cnt) {
-                        const int pos = tail_pos(st.col[j], mlo, map, cols, step + 1, len);
-                        if (pos < 0) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
-                        w[pos] = fma(-l, st.val[j], w[pos]);
-                    }
-                }
-                for (int e2 = tid + TAIL_E * TAIL_THREADS; e2 < dsc.cnt && ok; e2 += TAIL_THREADS) {
-                    const int64_t q = dsc.dk + 1 + e2;
-                    T v = ld_relaxed(&Fx[q]);
-                    if (!tail_wait(&Fx[q], &v, s, limit, row)) { ok = 0; break; }
-                    const int pos = tail_pos(Fj[q], mlo, map, cols, step + 1, len);
-                    if (pos < 0) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
-                    w[pos] = fma(-l, v, w[pos]);
-                }
-            }
-            tail_load(st, step + 2, nsteps, sd, Fj, Fx, rinv);   // the stage's registers are free again
-            const int any_fail = __syncthreads_or(!ok);   // uniform decision for the block
-            if (tid == 0) w[step] = l;   // nobody else touches position `step` any more
-            step++;
-            return !any_fail;
-        };
-        bool ok = true;
-        while (step < nsteps && ok) {
-            ok = run_step(A);
-            if (!ok || step >= nsteps) break;
-            ok = run_step(B);
-        }
-        if (!ok) return;
-        // publish (the row is final after the last step's barrier): every
-        // thread its share of the values but the diagonal, then thread 0 the
-        // pivot; the last step's l, which thread 0 wrote after that barrier,
-        // thread 0 stores itself
-        for (int q = tid; q < len; q += blockDim.x) {
-            if (b + q != d && q != nsteps - 1) st_relaxed(&Fx[b + q], w[q]);
-            const int c = cols[q];
-            if (c >= mlo) map[c - mlo] = -1;
-        }
-        if (tid == 0) {
-            if (nsteps > 0) st_relaxed(&Fx[b + nsteps - 1], w[nsteps - 1]);
-            if (tail_pivot<T>(w[d - b], boost, boost > T(0), s, row, &Fx[d], &rinv[row]) && trace)
-                trace[2 * (size_t)(row - t0) + 1] = globaltimer_ns();
-        }
-        // the fused forward sweep's y_row, by warp 0 from the row in shared
-        // memory; the other warps wait at the next row's first barrier
-        if (FUSED && tid < 32) {
-            __syncwarp();   // thread 0's last L value
-            fused_forward_row<T>(row, b, d, SliceVals<T>{w, b}, Fj, fw, s, limit);
+            if (!block_row<T, FUSED, NT>(row, a, s, boost, limit, trace, rs, staged, map, staged ? a.M : 0, fw))
+                return;
         }
     }
 }

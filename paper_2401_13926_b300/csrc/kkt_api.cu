@@ -61,15 +61,20 @@ struct kkt_ctx {
     int nLc = 0, nUc = 0;
     int cluster = 0;            // blocks of the cluster solve (0: use the global schedule)
     size_t cluster_smem = 0;
-    // refactorization split: rows [0, t0) warp per row with global values
-    // (k_refactor); [t0, t1) warp per row and [t1, n) block per row, both in
-    // shared memory (k_refactor_tail)
-    int t0 = 0, t1 = 0;
-    int tail_wsteps = 1, tail_wlen = 1;
-    size_t tail_smem = 0;
-    int tail_blocks = 0;
-    int tail_max_steps = 1, tail_max_len = 1, tail_mlo = 0;
-    int32_t* d_order = nullptr;   // rows in dispatch order: the [0, t0), [t0, t1) and [t1, n) parts
+    // refactorization kernel (k_refactor_rows): rows placed one per warp,
+    // one per block in shared memory, or one per block with values in
+    // global memory; work items in dispatch order
+    int ref_threads = 256, ref_blocks = 0, ref_map_cols = 0, nitems = 0, smem_optin = 0;
+    size_t ref_smem = 0, ref_map_bytes = 0, ref_area = 0;
+    int32_t rows_warp = 0, rows_block = 0, rows_global = 0;
+    int32_t* d_order = nullptr;   // rows in dispatch order
+    kkt::RefItem* d_items = nullptr;
+    // rows in global memory: step descriptors and value scratch (remade
+    // whenever the placement changes)
+    std::vector<void*> row_allocs;
+    int64_t *d_gdk = nullptr, *d_gsdoff = nullptr, *d_gwoff = nullptr;
+    int32_t* d_gcnt = nullptr;
+    void* d_gw = nullptr;
     DevScal* d_s = nullptr;
     DevScal* h_s = nullptr;   // pinned mirror
     int64_t ld = 0;
@@ -93,9 +98,9 @@ namespace {
 
 constexpr int PERSIST_THREADS = 256;
 constexpr int CHAIN_THREADS = 1024;
-constexpr int TAIL_MAX_ROWS = 32767;     // rows factored one block per row
-constexpr size_t TAIL_SMEM_MAX = 200 * 1024;
-constexpr int TAIL_MAP_COLS = 16384;     // columns with an O(1) position map in the tail kernel
+constexpr size_t TAIL_SMEM_MAX = 200 * 1024;   // shared memory of a cluster-solve block
+constexpr int REF_MAP_COLS = 16384;      // columns with an O(1) position map in block rows
+constexpr size_t REF_SMEM_WIDE = 113 * 1024;   // blocks above this run 512 threads (one block per SM)
 constexpr int CHAIN_MAX = 12288;       // rows of a chain (8 bytes of shared memory each)
 constexpr int CHAIN_WIDTH = 32;        // a level belongs to the chain if it has at most this many rows
 
@@ -192,6 +197,8 @@ void free_device(kkt_ctx* c) {
     c->ev_used = 0;
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
+    for (void* p : c->row_allocs) cudaFree(p);
+    c->row_allocs.clear();
     if (c->h_s) { cudaFreeHost(c->h_s); c->h_s = nullptr; }
     c->dev_bytes = 0;
     c->analyzed = c->factored = false;
@@ -481,8 +488,8 @@ void kkt_default_opts(kkt_opts* o) {
     o->inner_tol = 1e-6;
     o->repivot = 0;
     o->graphs = 0;
-    o->tail_warp_rows = 1;
-    o->tail_order = 1;
+    o->warp_rows = 1;
+    o->row_order = 1;
 }
 
 const char* kkt_strerror(int code) {
@@ -512,13 +519,13 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
         (c->o.precision != KKT_PRECISION_FP64 && c->o.precision != KKT_PRECISION_MIXED) ||
         (c->o.stop_mode != KKT_STOP_NRBE && c->o.stop_mode != KKT_STOP_RR) || c->o.pivot_tol <= 0 ||
         c->o.pivot_tol > 1 || c->o.boost_eps < 0 ||
-        (c->o.trisolve != KKT_TRSV_AUTO && c->o.trisolve != KKT_TRSV_GLOBAL) || c->o.tail_rows < 0 ||
+        (c->o.trisolve != KKT_TRSV_AUTO && c->o.trisolve != KKT_TRSV_GLOBAL) || c->o.block_smem < 0 ||
         (c->o.cluster_blocks != 0 && c->o.cluster_blocks != 8 && c->o.cluster_blocks != 16) ||
         c->o.method < KKT_METHOD_FGMRES || c->o.method > KKT_METHOD_FGMRES_EE ||
         c->o.ortho < KKT_ORTHO_CGS2 || c->o.ortho > KKT_ORTHO_CGS1_PYTH ||
         !(c->o.inner_tol > 0.0 && c->o.inner_tol <= 1.0) || (c->o.repivot != 0 && c->o.repivot != 1) ||
-        (c->o.graphs != 0 && c->o.graphs != 1) || (c->o.tail_warp_rows != 0 && c->o.tail_warp_rows != 1) ||
-        (c->o.tail_order != 0 && c->o.tail_order != 1)) {
+        (c->o.graphs != 0 && c->o.graphs != 1) || (c->o.warp_rows != 0 && c->o.warp_rows != 1) ||
+        (c->o.row_order != 0 && c->o.row_order != 1)) {
         delete c;
         return KKT_ERR_INVALID;
     }
@@ -534,25 +541,30 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
     }
     if (e != cudaSuccess) { delete c; return KKT_ERR_CUDA; }
     c->mixed = c->o.precision == KKT_PRECISION_MIXED;
-    int per_sm = 0, per_sm2 = 0, per_sm3 = 0, per_sm4 = 0;
+    int per_sm = 0, per_sm3 = 0;
     if (c->mixed) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kkt::k_lsolve_bulk<float>, PERSIST_THREADS, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kkt::k_refactor<float, false>, PERSIST_THREADS, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm4, kkt::k_refactor<float, true>, PERSIST_THREADS, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, kkt::k_usolve_bulk<float>, PERSIST_THREADS, 0);
     } else {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kkt::k_lsolve_bulk<double>, PERSIST_THREADS, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kkt::k_refactor<double, false>, PERSIST_THREADS, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm4, kkt::k_refactor<double, true>, PERSIST_THREADS, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, kkt::k_usolve_bulk<double>, PERSIST_THREADS, 0);
     }
     for (const void* fn : {(const void*)kkt::k_lsolve_chain<double>, (const void*)kkt::k_usolve_chain<double>,
                            (const void*)kkt::k_lsolve_chain<float>, (const void*)kkt::k_usolve_chain<float>})
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * CHAIN_MAX));
-    for (const void* fn : {(const void*)kkt::k_refactor_tail<double, false>, (const void*)kkt::k_refactor_tail<float, false>,
-                           (const void*)kkt::k_refactor_tail<double, true>, (const void*)kkt::k_refactor_tail<float, true>})
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TAIL_SMEM_MAX);
-    per_sm = std::max(1, std::min(std::min(per_sm, per_sm4), std::min(per_sm2, per_sm3)));
+    cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev);
+    c->smem_optin -= 1024;   // room for the kernel's static shared memory
+    for (const void* fn : {(const void*)kkt::k_refactor_rows<double, false, 256>,
+                           (const void*)kkt::k_refactor_rows<double, true, 256>,
+                           (const void*)kkt::k_refactor_rows<double, false, 512>,
+                           (const void*)kkt::k_refactor_rows<double, true, 512>,
+                           (const void*)kkt::k_refactor_rows<float, false, 256>,
+                           (const void*)kkt::k_refactor_rows<float, true, 256>,
+                           (const void*)kkt::k_refactor_rows<float, false, 512>,
+                           (const void*)kkt::k_refactor_rows<float, true, 512>})
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_optin);
+    cudaGetLastError();
+    per_sm = std::max(1, std::min(per_sm, per_sm3));
     c->persist_blocks = c->num_sms * per_sm;
     *out = c;
     return KKT_OK;
@@ -605,107 +617,140 @@ int kkt_pivot(int32_t n, const int32_t* rowptr, const int32_t* colind, const dou
 }
 
 namespace {
-// The rows of the shared-memory refactorization kernel: the last rows (at
-// most kkt_opts.tail_rows, default 32767), as many as fit their longest row
-// in shared memory; with tail_warp_rows, the short rows at their start and
-// the rows before them, as far as they fit a warp's slice, go one per warp.
-int setup_tail(kkt_ctx* c) {
+// Placement and dispatch order of the refactorization's rows
+// (k_refactor_rows).  A row's working set -- step descriptors (12 bytes per
+// L entry), values and columns -- decides where it runs: one per warp if it
+// fits a warp's slice of the block's work area, one per block if it fits
+// the area, else one per block with its values in global scratch.  The
+// block's shared memory is the position map of the last REF_MAP_COLS
+// columns plus the area; by default it is sized for the longest row (so no
+// row needs global scratch) up to the device's limit, dropping the map if
+// that lets every row fit.  Rows are dispatched by DAG level (ties by row)
+// or by row; consecutive warp rows form one work item per block.
+int setup_rows(kkt_ctx* c) {
     const int n = c->A.n;
-    int T = std::min<int>(n, c->o.tail_rows > 0 ? std::min(c->o.tail_rows, 32767) : TAIL_MAX_ROWS);
-    c->t0 = n;
-    c->tail_smem = 0;
-    while (T > 0) {
-        int t0 = n - T;
-        int64_t maxlen = 0, maxsteps = 0;
-        for (int32_t i = t0; i < n; i++) {
-            maxlen = std::max<int64_t>(maxlen, c->lay.Fp[i + 1] - c->lay.Fp[i]);
-            maxsteps = std::max<int64_t>(maxsteps, c->lay.Fdiag[i] - c->lay.Fp[i]);
-        }
-        // shared memory: step descriptors, row values and columns, and a
-        // position map for the last (at most TAIL_MAP_COLS) columns
-        const int mlo = std::max(t0, n - TAIL_MAP_COLS);
-        const size_t vsize = c->mixed ? sizeof(float) : sizeof(double);
-        size_t smem = 16 * (size_t)std::max<int64_t>(maxsteps, 1) + (vsize + 4) * (size_t)maxlen +
-                      2 * (size_t)(n - mlo);
-        if (smem <= TAIL_SMEM_MAX && maxlen <= 32767) {
-            c->t0 = t0;
-            c->tail_mlo = mlo;
-            c->tail_smem = smem;
-            c->tail_max_steps = (int)std::max<int64_t>(maxsteps, 1);
-            c->tail_max_len = (int)maxlen;
-            break;
-        }
-        T /= 2;
+    const auto& L = c->lay;
+    for (void* p : c->row_allocs) cudaFree(p);
+    c->row_allocs.clear();
+    c->d_gdk = c->d_gsdoff = c->d_gwoff = nullptr;
+    c->d_gcnt = nullptr;
+    c->d_gw = nullptr;
+    const size_t vsize = c->mixed ? sizeof(float) : sizeof(double);
+    auto need = [&](int32_t i) -> size_t {
+        const int64_t st = L.Fdiag[i] - L.Fp[i], len = L.Fp[i + 1] - L.Fp[i];
+        return (12 * (size_t)st + (vsize + 4) * (size_t)len + 15) & ~(size_t)15;
+    };
+    size_t maxneed = 16;
+    for (int32_t i = 0; i < n; i++) maxneed = std::max(maxneed, need(i));
+    const size_t optin = (size_t)std::max(c->smem_optin, 48 * 1024);
+    int M = std::min(REF_MAP_COLS, n);
+    size_t map_bytes = ((size_t)2 * M + 15) & ~(size_t)15;
+    size_t S;
+    if (c->o.block_smem > 0) {
+        S = std::min((size_t)c->o.block_smem, optin) & ~(size_t)15;
+        if (S < map_bytes + 4096) { M = 0; map_bytes = 0; }
+    } else if (map_bytes + maxneed <= optin) {
+        S = map_bytes + maxneed;
+    } else {
+        M = 0;   // the map would push the longest rows out of shared memory
+        map_bytes = 0;
+        S = std::min(maxneed, optin);
     }
-    // the short rows at the start of the tail go one per warp: [t0, t1), as
-    // long as every row so far fits a warp's slice (an eighth of the block's
-    // shared memory) with the running maxima of steps and length
-    c->t1 = c->t0;
-    c->tail_wsteps = 1;
-    c->tail_wlen = 1;
-    if (c->t0 < n && c->o.tail_warp_rows) {
-        const size_t vsize = c->mixed ? sizeof(float) : sizeof(double);
-        const size_t slice = (c->tail_smem / (kkt::TAIL_THREADS / 32)) & ~(size_t)15;
-        int64_t ms = 1, ml = 1;
-        int32_t i = c->t0;
-        for (; i < n; i++) {
-            const int64_t st = std::max<int64_t>(c->lay.Fdiag[i] - c->lay.Fp[i], ms);
-            const int64_t ln = std::max<int64_t>(c->lay.Fp[i + 1] - c->lay.Fp[i], ml);
-            if (((16 * (size_t)st + (vsize + 4) * (size_t)ln + 15) & ~(size_t)15) > slice) break;
-            ms = st;
-            ml = ln;
-        }
-        c->t1 = i;
-        // and the rows before the tail as far as they fit the same slice:
-        // those leave the warp-per-row kernel for the tail kernel, so they
-        // run alongside the tail's rows instead of before all of them
-        int32_t lo = c->t0;
-        for (; lo > 0; lo--) {
-            const int32_t r = lo - 1;
-            const int64_t st = std::max<int64_t>(c->lay.Fdiag[r] - c->lay.Fp[r], ms);
-            const int64_t ln = std::max<int64_t>(c->lay.Fp[r + 1] - c->lay.Fp[r], ml);
-            if (((16 * (size_t)st + (vsize + 4) * (size_t)ln + 15) & ~(size_t)15) > slice) break;
-            ms = st;
-            ml = ln;
-        }
-        c->t0 = lo;
-        c->tail_wsteps = (int)ms;
-        c->tail_wlen = (int)ml;
+    S = std::max(S, map_bytes + 4096);
+    c->ref_threads = S > REF_SMEM_WIDE ? 512 : 256;
+    c->ref_smem = S;
+    c->ref_map_cols = M;
+    c->ref_map_bytes = map_bytes;
+    c->ref_area = S - map_bytes;
+    const int nw = c->ref_threads / 32;
+    const size_t slice = (c->ref_area / nw) & ~(size_t)15;
+    std::vector<uint8_t> kind((size_t)n);
+    c->rows_warp = c->rows_block = c->rows_global = 0;
+    for (int32_t i = 0; i < n; i++) {
+        const size_t q = need(i);
+        if (c->o.warp_rows && q <= slice) { kind[i] = kkt::ROW_WARP; c->rows_warp++; }
+        else if (q <= c->ref_area) { kind[i] = kkt::ROW_BLOCK; c->rows_block++; }
+        else { kind[i] = kkt::ROW_GLOBAL; c->rows_global++; }
     }
-    {
-        // dispatch order: each part -- [0, t0) warp per row in global memory,
-        // [t0, t1) warp per row and [t1, n) block per row in shared memory --
-        // by level in the DAG of L (ties by row), so rows whose dependencies
-        // finish first start first; a row's dependencies are at lower
-        // levels, so they are dispatched before it
-        std::vector<int32_t> order((size_t)n);
-        std::iota(order.begin(), order.end(), 0);
-        if (c->o.tail_order) {
-            const std::vector<int32_t>& lev = c->lay.levL;
-            auto by_level = [&](int32_t a, int32_t b) { return lev[a] < lev[b] || (lev[a] == lev[b] && a < b); };
-            std::sort(order.begin(), order.begin() + c->t0, by_level);
-            std::sort(order.begin() + c->t0, order.begin() + c->t1, by_level);
-            std::sort(order.begin() + c->t1, order.end(), by_level);
-        }
-        CK(cudaMemcpyAsync(c->d_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice,
-                           c->stream));
-        CK(cudaStreamSynchronize(c->stream));   // `order` is a local
+    // dispatch order: by level in the DAG of L (ties by row) -- a row's
+    // dependencies are at lower levels, so they are dispatched before it
+    std::vector<int32_t> order((size_t)n);
+    std::iota(order.begin(), order.end(), 0);
+    if (c->o.row_order) {
+        const std::vector<int32_t>& lev = L.levL;
+        std::sort(order.begin(), order.end(),
+                  [&](int32_t a, int32_t b) { return lev[a] < lev[b] || (lev[a] == lev[b] && a < b); });
     }
-    if (c->t0 < n) {
-        int per_sm = 0;
-        // both instantiations (plain, and with the fused forward sweep); the
-        // grid is sized for the one with fewer resident blocks
-        per_sm = 1 << 30;
-        for (const void* fn : {c->mixed ? (const void*)kkt::k_refactor_tail<float, false>
-                                        : (const void*)kkt::k_refactor_tail<double, false>,
-                               c->mixed ? (const void*)kkt::k_refactor_tail<float, true>
-                                        : (const void*)kkt::k_refactor_tail<double, true>}) {
-            int b = 0;
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kkt::TAIL_THREADS, c->tail_smem));
-            per_sm = std::min(per_sm, b);
+    std::vector<kkt::RefItem> items;
+    items.reserve((size_t)n);
+    std::vector<int64_t> gdk, gsdoff, gwoff;
+    std::vector<int32_t> gcnt;
+    int64_t gw_total = 0;
+    for (int32_t t = 0; t < n;) {
+        const int32_t r = order[t];
+        if (kind[r] == kkt::ROW_WARP) {
+            int32_t cnt = 1;
+            while (cnt < nw && t + cnt < n && kind[order[t + cnt]] == kkt::ROW_WARP) cnt++;
+            items.push_back(kkt::RefItem{t, (kkt::ROW_WARP << 28) | cnt});
+            t += cnt;
+            continue;
         }
-        c->tail_blocks = std::max(1, per_sm) * c->num_sms;
+        if (kind[r] == kkt::ROW_BLOCK) {
+            items.push_back(kkt::RefItem{t, kkt::ROW_BLOCK << 28});
+        } else {
+            const int32_t g = (int32_t)gsdoff.size();
+            gsdoff.push_back((int64_t)gdk.size());
+            gwoff.push_back(gw_total);
+            for (int64_t q = L.Fp[r]; q < L.Fdiag[r]; q++) {
+                const int32_t k = L.Fj[q];
+                gdk.push_back(L.Fdiag[k]);
+                gcnt.push_back((int32_t)(L.Fp[k + 1] - L.Fdiag[k] - 1));
+            }
+            gw_total += L.Fp[r + 1] - L.Fp[r];
+            items.push_back(kkt::RefItem{t, (kkt::ROW_GLOBAL << 28) | g});
+        }
+        t++;
     }
+    c->nitems = (int)items.size();
+    CK(cudaMemcpyAsync(c->d_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_items, items.data(), sizeof(kkt::RefItem) * items.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+    if (!gsdoff.empty()) {
+        auto up = [&](auto** p, const auto& v) -> cudaError_t {
+            void* q = nullptr;
+            cudaError_t e = cudaMalloc(&q, std::max<size_t>(v.size(), 1) * sizeof(v[0]));
+            if (e != cudaSuccess) return e;
+            c->row_allocs.push_back(q);
+            *p = (std::remove_reference_t<decltype(**p)>*)q;
+            return v.empty() ? cudaSuccess
+                             : cudaMemcpyAsync(q, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice, c->stream);
+        };
+        CK(up(&c->d_gdk, gdk));
+        CK(up(&c->d_gcnt, gcnt));
+        CK(up(&c->d_gsdoff, gsdoff));
+        CK(up(&c->d_gwoff, gwoff));
+        void* q = nullptr;
+        CK(cudaMalloc(&q, std::max<int64_t>(gw_total, 1) * vsize));
+        c->row_allocs.push_back(q);
+        c->d_gw = q;
+    }
+    CK(cudaStreamSynchronize(c->stream));   // the host vectors are locals
+    int per_sm = 1 << 30;
+    const void* fns[2];
+    if (c->ref_threads == 512) {
+        fns[0] = c->mixed ? (const void*)kkt::k_refactor_rows<float, false, 512> : (const void*)kkt::k_refactor_rows<double, false, 512>;
+        fns[1] = c->mixed ? (const void*)kkt::k_refactor_rows<float, true, 512> : (const void*)kkt::k_refactor_rows<double, true, 512>;
+    } else {
+        fns[0] = c->mixed ? (const void*)kkt::k_refactor_rows<float, false, 256> : (const void*)kkt::k_refactor_rows<double, false, 256>;
+        fns[1] = c->mixed ? (const void*)kkt::k_refactor_rows<float, true, 256> : (const void*)kkt::k_refactor_rows<double, true, 256>;
+    }
+    for (const void* fn : fns) {   // the grid is sized for the instantiation with fewer resident blocks
+        int bl = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, fn, c->ref_threads, c->ref_smem));
+        per_sm = std::min(per_sm, bl);
+    }
+    if (per_sm < 1) { c->detail = "refactorization kernel does not fit an SM"; return KKT_ERR_INVALID; }
+    c->ref_blocks = per_sm * c->num_sms;
     return KKT_OK;
 }
 
@@ -753,12 +798,19 @@ int kkt_analyze(kkt_ctx* c, int32_t n, const int32_t* rowptr, const int32_t* col
 }
 
 namespace {
+int setup_from_layout(kkt_ctx* c, std::chrono::steady_clock::time_point t0);
+
 // Everything kkt_analyze does once P, Q and the factor structure are known:
 // the GPU layout, schedules and every device buffer.
 int setup_device(kkt_ctx* c, const kkt::ColStructure& S, std::chrono::steady_clock::time_point t0) {
-    const int32_t n = c->A.n;
     int rc = kkt::build_layout(c->A, c->P, c->Q, S, &c->lay);
     if (rc) { c->detail = "factor layout failed"; return rc; }
+    return setup_from_layout(c, t0);
+}
+
+int setup_from_layout(kkt_ctx* c, std::chrono::steady_clock::time_point t0) {
+    const int32_t n = c->A.n;
+    int rc = KKT_OK;
     // composite gather map: factor slot -> caller value index
     std::vector<int64_t> fsrc(c->lay.Fsrc.size());
     for (size_t t = 0; t < fsrc.size(); t++) fsrc[t] = c->lay.Fsrc[t] >= 0 ? c->A.src[c->lay.Fsrc[t]] : -1;
@@ -816,7 +868,8 @@ int setup_device(kkt_ctx* c, const kkt::ColStructure& S, std::chrono::steady_clo
     if (c->o.trisolve == KKT_TRSV_AUTO) pick_cluster(c);
     else c->cluster = 0;
     if ((rc = dalloc(c, &c->d_order, (size_t)n))) return rc;
-    if ((rc = setup_tail(c))) return rc;
+    if ((rc = dalloc(c, &c->d_items, (size_t)n))) return rc;
+    if ((rc = setup_rows(c))) return rc;
     if ((rc = dalloc(c, &c->d_s, 1))) return rc;
     CK(cudaMemsetAsync(c->d_s, 0, sizeof(DevScal), c->stream));
     CK(cudaMallocHost(&c->h_s, sizeof(DevScal)));
@@ -836,6 +889,96 @@ int setup_device(kkt_ctx* c, const kkt::ColStructure& S, std::chrono::steady_clo
 namespace {
 int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsigned long long* trace,
                   const double* fused_rhs = nullptr);
+}
+
+int kkt_analyze_like(kkt_ctx* c, const kkt_ctx* src) {
+    if (!c || !src || c == src) return KKT_ERR_INVALID;
+    if (!src->analyzed) { c->detail = "kkt_analyze_like: the source context is not analysed"; return KKT_ERR_STATE; }
+    auto t0 = std::chrono::steady_clock::now();
+    CK(cudaSetDevice(c->dev));
+    CK(cudaStreamSynchronize(c->stream));
+    free_device(c);
+    c->detail.clear();
+    c->A = src->A;
+    c->nnz_a = src->nnz_a;
+    c->P = src->P;
+    c->Q = src->Q;
+    c->lay = src->lay;
+    return setup_from_layout(c, t0);
+}
+
+int kkt_host_analyze(int32_t n, const int32_t* rowptr, const int32_t* colind, const double* values0,
+                     double pivot_tol, int32_t* P, int32_t* Q, kkt_host_stats* st) {
+    if (!P || !Q || !values0 || !(pivot_tol > 0) || pivot_tol > 1) return KKT_ERR_INVALID;
+    kkt::Csr A;
+    std::string why;
+    int rc = kkt::canonicalize(n, rowptr, colind, &A, &why);
+    if (rc) return rc;
+    if (n < 1) return KKT_ERR_INVALID;
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<int32_t> q;
+    if ((rc = kkt::order_colamd_like(A, &q))) return rc;
+    auto t1 = std::chrono::steady_clock::now();
+    std::vector<double> v(A.colind.size());
+    for (size_t e = 0; e < v.size(); e++) v[e] = values0[A.src[e]];
+    std::vector<int32_t> p;
+    kkt::ColStructure S;
+    int32_t bad = -1;
+    if ((rc = kkt::pivot_lu(A, v.data(), q, pivot_tol, &p, &S, &bad))) return rc;
+    auto t2 = std::chrono::steady_clock::now();
+    std::copy(p.begin(), p.end(), P);
+    std::copy(q.begin(), q.end(), Q);
+    if (st) {
+        kkt::Layout lay;
+        if ((rc = kkt::build_layout(A, p, q, S, &lay))) return rc;
+        st->nnz_l = lay.nnzL;
+        st->nnz_u = lay.nnzU;
+        st->levels_l = lay.levelsL;
+        st->levels_u = lay.levelsU;
+        st->refactor_updates = lay.updates;
+        st->order_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        st->pivot_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
+    }
+    return KKT_OK;
+}
+
+int kkt_trace_critical_path(kkt_ctx* c, const int64_t* t_start, const int64_t* t_publish, double* path_ns,
+                            int32_t* levels, double* median_link_ns, int32_t* rows) {
+    if (!c || !t_start || !t_publish) return KKT_ERR_INVALID;
+    if (!c->analyzed) return KKT_ERR_STATE;
+    const int32_t n = c->A.n;
+    const auto& L = c->lay;
+    std::vector<double> cp((size_t)n, 0.0), links;
+    links.reserve((size_t)n);
+    double best = 0.0;
+    for (int32_t i = 0; i < n; i++) {
+        double before = 0.0;
+        int64_t last = -1;
+        for (int64_t q = L.Fp[i]; q < L.Fdiag[i]; q++) {
+            const int32_t k = L.Fj[q];
+            before = std::max(before, cp[k]);
+            last = std::max<int64_t>(last, t_publish[k]);
+        }
+        double link = 0.0;
+        if (t_publish[i] > 0 && t_start[i] > 0) {
+            link = (double)(t_publish[i] - std::max<int64_t>(t_start[i], last));
+            if (link < 0) link = 0.0;
+            links.push_back(link);
+        }
+        cp[i] = before + link;
+        best = std::max(best, cp[i]);
+    }
+    if (path_ns) *path_ns = best;
+    if (levels) *levels = L.levelsL;
+    if (rows) *rows = (int32_t)links.size();
+    if (median_link_ns) {
+        if (links.empty()) *median_link_ns = 0.0;
+        else {
+            std::nth_element(links.begin(), links.begin() + links.size() / 2, links.end());
+            *median_link_ns = links[links.size() / 2];
+        }
+    }
+    return KKT_OK;
 }
 
 int kkt_repivot(kkt_ctx* c, const double* values, int values_on_device) {
@@ -881,65 +1024,68 @@ int kkt_trace_refactor(kkt_ctx* c, const double* values, int values_on_device, i
     if (rc) return rc;
     if (!t_start || !t_publish || !t0_out) return KKT_ERR_INVALID;
     const int n = c->A.n;
-    const int T = n - c->t0;
-    *t0_out = c->t0;
-    std::fill(t_start, t_start + n, (int64_t)-1);
-    std::fill(t_publish, t_publish + n, (int64_t)-1);
-    if (T <= 0) return refactor_impl(c, values, values_on_device, nullptr);
+    *t0_out = 0;
     unsigned long long* d_trace = nullptr;   // profiling only: a buffer of its own
-    CK(cudaMalloc(&d_trace, sizeof(unsigned long long) * 2 * (size_t)T));
-    CK(cudaMemsetAsync(d_trace, 0, sizeof(unsigned long long) * 2 * (size_t)T, c->stream));
+    CK(cudaMalloc(&d_trace, sizeof(unsigned long long) * 2 * (size_t)n));
+    CK(cudaMemsetAsync(d_trace, 0, sizeof(unsigned long long) * 2 * (size_t)n, c->stream));
     rc = refactor_impl(c, values, values_on_device, d_trace);
-    std::vector<unsigned long long> h(2 * (size_t)T);
+    std::vector<unsigned long long> h(2 * (size_t)n);
     cudaError_t e = cudaMemcpy(h.data(), d_trace, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost);
     cudaFree(d_trace);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy");
-    for (int r = 0; r < T; r++) {
-        t_start[c->t0 + r] = (int64_t)h[2 * (size_t)r];
-        t_publish[c->t0 + r] = (int64_t)h[2 * (size_t)r + 1];
+    for (int r = 0; r < n; r++) {
+        t_start[r] = h[2 * (size_t)r] ? (int64_t)h[2 * (size_t)r] : -1;
+        t_publish[r] = h[2 * (size_t)r + 1] ? (int64_t)h[2 * (size_t)r + 1] : -1;
     }
     return rc;
 }
 
 extern "C++" {
 namespace {
-// gather, bulk rows (warp per row), tail rows (block per row), in type T
+// gather (arms every factor value with SENTINEL), then the one
+// refactorization kernel over every row, in type T
+template <typename T, int NT>
+void refactor_rows_launch(kkt_ctx* c, const double* vals, unsigned long long* trace, const double* fused_rhs) {
+    kkt::RefArgs<T> a{};
+    a.items = c->d_items;
+    a.nitems = c->nitems;
+    a.order = c->d_order;
+    a.Fp = c->d_Fp;
+    a.Fj = c->d_Fj;
+    a.Fdiag = c->d_Fdiag;
+    a.Fx = (T*)c->d_Fx;
+    a.rinv = (T*)c->d_rinv;
+    a.vals = vals;
+    a.fsrc = c->d_fsrc;
+    a.M = c->ref_map_cols;
+    a.mlo = c->A.n - c->ref_map_cols;
+    a.map_bytes = (int)c->ref_map_bytes;
+    a.area_bytes = (int)c->ref_area;
+    a.gdk = c->d_gdk;
+    a.gcnt = c->d_gcnt;
+    a.g_sd_off = c->d_gsdoff;
+    a.gw = (T*)c->d_gw;
+    a.g_w_off = c->d_gwoff;
+    const kkt::FwdArgs<T> fw{fused_rhs, c->d_P, (T*)c->d_y, (T*)c->d_xp};
+    const int blocks = std::max(1, std::min(c->nitems, c->ref_blocks));
+    auto kern = fused_rhs ? kkt::k_refactor_rows<T, true, NT> : kkt::k_refactor_rows<T, false, NT>;
+    kern<<<blocks, NT, c->ref_smem, c->stream>>>(a, c->d_s, c->o.boost_eps, spin(c), trace, fw);
+}
+
 template <typename T>
 void refactor_launch(kkt_ctx* c, const double* vals, unsigned long long* trace, const double* fused_rhs = nullptr) {
     const int n = c->A.n;
     const int64_t nnzF = (int64_t)c->lay.Fj.size();
-    T* Fx = (T*)c->d_Fx;
-    T* rinv = (T*)c->d_rinv;
-    const kkt::FwdArgs<T> fw{fused_rhs, c->d_P, (T*)c->d_y, (T*)c->d_xp};
     int t = phase_begin(c, KKT_PHASE_GATHER);
-    const int64_t tail_begin = c->t0 < n ? c->lay.Fp[c->t0] : nnzF;
-    kkt::k_gather<T><<<2 * c->num_sms, 256, 0, c->stream>>>(vals, c->d_fsrc, nnzF, tail_begin, Fx, c->d_Arp,
-                                                            c->d_asrc, c->d_Ax, n, c->t0, rinv, c->d_s,
+    kkt::k_gather<T><<<2 * c->num_sms, 256, 0, c->stream>>>(vals, nnzF, (T*)c->d_Fx, c->d_Arp, c->d_asrc, c->d_Ax,
+                                                            n, (T*)c->d_rinv, c->d_s,
                                                             fused_rhs ? (T*)c->d_y : nullptr);
     phase_end(c, t);
     t = phase_begin(c, KKT_PHASE_REFACTOR);
-    c->launches += 2;
-    if (c->t0 > 0) {
-        auto kern = fused_rhs ? kkt::k_refactor<T, true> : kkt::k_refactor<T, false>;
-        kern<<<grid_for(c, c->t0), PERSIST_THREADS, 0, c->stream>>>(
-            c->t0, c->d_order, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, c->d_done_f, c->d_s, c->o.boost_eps, spin(c),
-            fw);
-        c->launches += 1;
-    }
+    if (c->ref_threads == 512) refactor_rows_launch<T, 512>(c, vals, trace, fused_rhs);
+    else refactor_rows_launch<T, 256>(c, vals, trace, fused_rhs);
     phase_end(c, t);
-    t = phase_begin(c, KKT_PHASE_REFACTOR_TAIL);
-    if (c->t0 < n) {
-        // the bulk kernel left ticket_fact at >= t0; restart it for the tail
-        kkt::k_refactor_prep_tail<<<1, 1, 0, c->stream>>>(c->d_s);
-        const int blocks = std::min(n - c->t0, c->tail_blocks);
-        auto kern = fused_rhs ? kkt::k_refactor_tail<T, true> : kkt::k_refactor_tail<T, false>;
-        kern<<<blocks, kkt::TAIL_THREADS, c->tail_smem, c->stream>>>(
-            c->t0, c->t1, n, c->tail_mlo, c->tail_max_steps, c->tail_max_len, c->tail_wsteps, c->tail_wlen,
-            c->d_order + c->t0, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, vals, c->d_fsrc, c->d_s, c->o.boost_eps,
-            spin(c), trace, fw);
-        c->launches += 2;
-    }
-    phase_end(c, t);
+    c->launches += 3;   // prep, gather, refactorization
 }
 }  // namespace
 }  // extern "C++"
@@ -1042,24 +1188,24 @@ int kkt_tune(kkt_ctx* c, const double* values, const double* b, int on_device, i
         hx.resize(n);
         x = hx.data();
     }
-    struct Cand { int trisolve, cluster_blocks, tail_rows, warp_rows; };
+    struct Cand { int trisolve, cluster_blocks, block_smem, warp_rows; };
     std::vector<Cand> cands;
     for (int wr : {1, 0})
-        for (int tr : {0, 16384, 8192, 4096}) {
-            for (int cb : {16, 8}) cands.push_back({KKT_TRSV_AUTO, cb, tr, wr});
-            cands.push_back({KKT_TRSV_GLOBAL, 0, tr, wr});
+        for (int bs : {0, 72 * 1024, 110 * 1024, c->smem_optin}) {
+            for (int cb : {16, 8}) cands.push_back({KKT_TRSV_AUTO, cb, bs, wr});
+            cands.push_back({KKT_TRSV_GLOBAL, 0, bs, wr});
         }
     const kkt_opts saved = c->o;
     double best = -1.0;
-    Cand pick{saved.trisolve, saved.cluster_blocks, saved.tail_rows, saved.tail_warp_rows};
+    Cand pick{saved.trisolve, saved.cluster_blocks, saved.block_smem, saved.warp_rows};
     auto apply = [&](const Cand& k) -> int {
         c->o.trisolve = k.trisolve;
         c->o.cluster_blocks = k.cluster_blocks;
-        c->o.tail_rows = k.tail_rows;
-        c->o.tail_warp_rows = k.warp_rows;
+        c->o.block_smem = k.block_smem;
+        c->o.warp_rows = k.warp_rows;
         drop_graph(&c->gx_ref, &c->g_ref);
         drop_graph(&c->gx_solve, &c->g_solve);
-        int r = setup_tail(c);
+        int r = setup_rows(c);
         if (r) return r;
         if (k.trisolve == KKT_TRSV_AUTO) {
             pick_cluster(c);
@@ -1085,7 +1231,7 @@ int kkt_tune(kkt_ctx* c, const double* values, const double* b, int on_device, i
     }
     if (best < 0) {   // nothing ran: keep the previous configuration
         c->o = saved;
-        apply(Cand{saved.trisolve, saved.cluster_blocks, saved.tail_rows, saved.tail_warp_rows});
+        apply(Cand{saved.trisolve, saved.cluster_blocks, saved.block_smem, saved.warp_rows});
         c->detail = "kkt_tune: no configuration ran";
         return KKT_ERR_STATE;
     }
@@ -1559,8 +1705,12 @@ int kkt_query(kkt_ctx* c, kkt_info* info) {
     info->h2d_bytes = c->h2d;
     info->d2h_bytes = c->d2h;
     info->repivots = c->repivots;
-    info->tail_rows = c->A.n - c->t0;
-    info->tail_warp_rows = c->t1 - c->t0;
+    info->rows_warp = c->rows_warp;
+    info->rows_block = c->rows_block;
+    info->rows_global = c->rows_global;
+    info->refactor_smem = (int32_t)c->ref_smem;
+    info->refactor_threads = c->ref_threads;
+    info->refactor_blocks = c->ref_blocks;
     return KKT_OK;
 }
 

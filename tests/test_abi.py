@@ -76,3 +76,22 @@ def test_pattern_errors(L):
     with pytest.raises(K.KKTError) as e:
         K.pivot(np.array([0, 1, 2], np.int32), np.array([0, 0], np.int32), np.array([1.0, 1.0]))
     assert e.value.code == -4                              # column 1 is empty: no pivot
+
+
+def test_host_analyze_equals_order_then_pivot(L, oracle_mod):
+    """kkt_host_analyze (no GPU) returns the order and pivots of kkt_order +
+    kkt_pivot, and its statistics describe the oracle's factorization on
+    them: the same factor sizes, and the multiply-add count of the
+    left-looking refactorization (the oracle's own count on the same P, Q)."""
+    seq = KKTSequence("kkt200", buses=60, steps=1)
+    v = seq.values(0)
+    P, Q, st = K.host_analyze(seq.rowptr, seq.colind, v)
+    Q2 = K.order(seq.rowptr, seq.colind)
+    P2, nl, nu = K.pivot(seq.rowptr, seq.colind, v, Q=Q2)
+    assert np.array_equal(Q, Q2) and np.array_equal(P, P2)
+    assert st["nnz_l"] == nl and st["nnz_u"] == nu
+    F = oracle_mod.refactor(seq.n, seq.rowptr, seq.colind, v, P, Q)
+    assert len(F.Li) == nl and len(F.Ui) == nu
+    cols, madds, _, _ = oracle_mod.refactor_sample(seq.n, seq.rowptr, seq.colind, v, P, Q, 1e9)
+    assert cols == seq.n and madds == st["refactor_updates"]
+    assert st["levels_l"] >= 1 and st["levels_u"] >= 1

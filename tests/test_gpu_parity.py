@@ -30,6 +30,17 @@ def factor_diff(gpu, ofac):
     return dl, du
 
 
+def nrbe_agrees(nr_gpu, nr_or, seq):
+    """The NRBE the GPU reports (it drives the stop decision) equals Eq.
+    (nbre) as the oracle evaluates it on the returned x, up to the rounding
+    of the two residual evaluations: each entry of b - K x carries an error
+    of at most (m + 1) eps sum_j |K_ij x_j| + eps |b_i| (m = the row's
+    entries), so with ||K||_inf >= the row sums the two NRBE values differ
+    by at most 2 (m + 2) eps besides a relative 1e-6 for the norms."""
+    m = int(np.max(np.diff(seq.rowptr)))
+    return abs(nr_gpu - nr_or) <= 1e-6 * nr_or + 2 * (m + 2) * EPS
+
+
 def csr_of(A):
     A = sp.csr_matrix(A)
     A.sum_duplicates()
@@ -68,6 +79,7 @@ def test_solve_parity_kkt200(oracle_mod, c1, sched):
         x, it, nr = s.solve(b, tol=NRBE_TOL)
         nr_or = oracle_mod.nrbe(seq.n, seq.rowptr, seq.colind, v, b, x)
         assert nr_or <= NRBE_TOL and nr <= NRBE_TOL, (k, nr_or, nr)
+        assert nrbe_agrees(nr, nr_or, seq), (k, nr, nr_or)
         F, res = oracle_mod.solve_sequence_step(seq.n, seq.rowptr, seq.colind, v, P, Q, b)
         assert res.status == 0
         info = s.info()

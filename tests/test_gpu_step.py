@@ -26,7 +26,7 @@ def _pair(rp, ci, v0=None, P=None, Q=None, **kw):
 
 
 @pytest.mark.parametrize("kw", [dict(), dict(trisolve="global"), dict(precision="mixed", max_cycles=2),
-                                dict(tail_warp_rows=False), dict(tail_rows=1024)])
+                                dict(warp_rows=False), dict(block_smem=16384)])
 def test_step_equals_refactor_then_solve_kkt200(kw):
     seq = KKTSequence("kkt200")
     a, f = _pair(seq.rowptr, seq.colind, seq.values(0), **kw)
@@ -75,27 +75,38 @@ def test_step_device_arrays_and_full_size():
     assert torch.equal(xf2, xf)
 
 
-@pytest.mark.parametrize("warp_rows", [True, False])
-def test_tail_dispatch_order_same_bits(warp_rows):
-    """The refactorization's rows dispatched by DAG level or by row give the
-    same factors, bit for bit (each row's arithmetic is fixed; only when it
-    runs changes).  Without warp rows the rows before the block rows go to
-    the warp-per-row kernel in global memory, which follows the same order."""
+@pytest.mark.parametrize("warp_rows,block_smem", [(True, 0), (False, 0), (True, 16384), (False, 16384)])
+def test_row_placement_and_order_same_bits(oracle_mod, warp_rows, block_smem):
+    """Every placement of the refactorization's rows -- one per warp in
+    shared memory, one per block in shared memory, one per block with the
+    values in global memory (a 16 KB block forces the longest kkt200 rows
+    there) -- and both dispatch orders (DAG level, row) give the same
+    factors, bit for bit, equal to the oracle's refactorization on the same
+    P and Q (each row's arithmetic is fixed; only where and when it runs
+    changes)."""
     seq = KKTSequence("kkt200", steps=2)
     out = []
     for order in ("row", "level"):
-        s = K.KKTSolver(tail_order=order, tail_warp_rows=warp_rows, tail_rows=0 if warp_rows else 1024)
+        s = K.KKTSolver(row_order=order, warp_rows=warp_rows, block_smem=block_smem)
         s.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
+        info = s.info()
+        assert info["rows_warp"] + info["rows_block"] + info["rows_global"] == seq.n
+        assert (info["rows_warp"] > 0) == warp_rows
+        if block_smem:
+            assert info["rows_global"] > 0 and info["refactor_smem"] == block_smem
+        else:
+            assert info["rows_global"] == 0
         v = seq.values(1)
         b, _ = seq.rhs(1, v)
         x, it, nr = s.step(v, b)
         f = s.factors()
         out.append((f["Lx"].copy(), f["Ux"].copy(), x.copy(), it, nr))
-        if not warp_rows:
-            assert s.info()["tail_rows"] < seq.n   # the warp-per-row kernel ran
+        P, Q = s.perm()
         s.close()
     for a, b_ in zip(out[0], out[1]):
         assert np.array_equal(a, b_)
+    of = oracle_mod.refactor(seq.n, seq.rowptr, seq.colind, seq.values(1), P, Q)
+    assert np.array_equal(out[0][0], of.Lx) and np.array_equal(out[0][1], of.Ux)
 
 
 def test_step_factors_bitwise_oracle_full_size_kkt2000(oracle_mod):
@@ -105,7 +116,7 @@ def test_step_factors_bitwise_oracle_full_size_kkt2000(oracle_mod):
     the dispatch order of the rows."""
     seq = KKTSequence("kkt2000")
     for order in ("level", "row"):
-        s = K.KKTSolver(tail_order=order)
+        s = K.KKTSolver(row_order=order)
         s.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
         P, Q = s.perm()
         for k in (0, seq.M - 1):

@@ -23,7 +23,8 @@ def test_tune_keeps_results_and_reports_choice(name):
     best = s.tune(v, b, reps=2)
     assert best > 0
     info = s.info()
-    assert 0 <= info["tail_rows"] <= seq.n and info["trisolve_cluster"] in (0, 8, 16)
+    assert info["refactor_smem"] > 0 and info["trisolve_cluster"] in (0, 8, 16)
+    assert info["rows_warp"] + info["rows_block"] + info["rows_global"] == seq.n
     with pytest.raises(K.KKTError):      # factors must be recomputed after tuning
         s.solve(b, tol=1e-12)
     s.refactor(v)
