@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--per-config", default=PER_CONFIG, help="comma-separated smaller configs ('' = none)")
+    ap.add_argument("--per-config", default=PER_CONFIG, help="comma-separated smaller configs (none = skip)")
     ap.add_argument("--per-config-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample for cpu_baseline")
     ap.add_argument("--ref-seconds", type=float, default=4.0, help="oracle sample per step of --impl reference")
@@ -59,18 +59,19 @@ def parse():
                     help="factor precision of the headline line")
     ap.add_argument("--no-mixed", action="store_true", help="skip the side-by-side other-precision run")
     ap.add_argument("--mixed-steps", type=int, default=6)
-    ap.add_argument("--mixed-cycles", type=int, default=3, help="FGMRES cycle cap of the other-precision leg")
+    ap.add_argument("--mixed-cycles", type=int, default=2,
+                    help="restart cycles the FP32 preconditioner gets before the FP64 fallback")
     ap.add_argument("--no-trace", action="store_true", help="skip the refactorization trace (critical path)")
-    ap.add_argument("--serve-instances", type=int, default=4,
+    ap.add_argument("--serve-instances", type=int, default=8,
                     help="independent kkt2000 sequences of the serving measurement (0 = skip)")
     ap.add_argument("--serve-steps", type=int, default=10)
-    ap.add_argument("--serve-workers", type=int, default=4)
-    ap.add_argument("--serve-c4", type=int, default=0,
+    ap.add_argument("--serve-batch", type=int, default=8, help="steps per batched call of the server (0 = off)")
+    ap.add_argument("--serve-c4", type=int, default=256,
                     help="mixed-size serving run: this many instances, bus counts uniform in "
                          "[200, --serve-c4-buses], Poisson arrivals, each instance's steps closed-loop (0 = skip)")
-    ap.add_argument("--serve-c4-buses", type=int, default=2000)
+    ap.add_argument("--serve-c4-buses", type=int, default=5000)
     ap.add_argument("--serve-c4-rate", type=float, default=50.0, help="instance arrivals per second")
-    ap.add_argument("--serve-c4-steps", type=int, default=10)
+    ap.add_argument("--serve-c4-steps", type=int, default=30)
     return ap.parse_args()
 
 
@@ -439,62 +440,82 @@ def measure_config(K, name, steps, warmup, flush, device, rank):
     return out
 
 
-def serve_measure(K, args, rank):
-    """Throughput and latency of several sequences of kkt2000 served
+def serve_measure(K, args, rank, N):
+    """Throughput and latency of N independent kkt2000 sequences served
     together: every instance's steps are submitted at once (closed loop, the
-    server runs one step per instance at a time), host arrays in and out."""
+    server runs one step per instance at a time, up to --serve-batch of them
+    as one batched call), host arrays in and out."""
     from paper_2401_13926_b300.workload import KKTSequence
-    N, S = args.serve_instances, args.serve_steps
-    seqs = [KKTSequence("kkt2000", instance=1000 * (rank + 1) + i, steps=S) for i in range(N)]
+    S = args.serve_steps
+    base = KKTSequence("kkt2000", instance=1000 * (rank + 1), steps=S)
+    seqs = [base.reseeded(1000 * (rank + 1) + i) for i in range(N)]
     data = [[(q.values(k), q.rhs(k, q.values(k))[0]) for k in range(S)] for q in seqs]
-    srv = K.KKTServer(workers=args.serve_workers, restart=RESTART)
+    srv = K.KKTServer(batch=args.serve_batch, restart=RESTART)
     ids = [srv.open(q.rowptr, q.colind, q.values(0)) for q in seqs]
     for i in range(N):   # warm-up: one step per instance
         srv.wait(srv.submit(ids[i], *data[i][0], tol=TOL)[0])
+    b0 = srv.info()["batches"]
     t0 = time.perf_counter()
     tickets = [srv.submit(ids[i], *data[i][k], tol=TOL)[0] for k in range(S) for i in range(N)]
     res = [srv.wait(t)[1] for t in tickets]
     dt = time.perf_counter() - t0
+    nb = srv.info()["batches"] - b0
     srv.close()
     lat = np.array([r["queue_ms"] + r["run_ms"] for r in res])
     run = np.array([r["run_ms"] for r in res])
     return {"workload": "kkt2000", "value": N * S / dt, "unit": "solves/s", "instances": N, "steps_per_instance": S,
-            "workers": args.serve_workers, "converged": int(sum(r["status"] == 0 for r in res)),
+            "batch": args.serve_batch, "batched_calls": nb, "mean_batch": N * S / max(nb, 1),
+            "converged": int(sum(r["status"] == 0 for r in res)),
             "max_nrbe": float(max(r["nrbe"] for r in res)),
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-            "step_ms": {"p50": float(np.percentile(run, 50)), "p99": float(np.percentile(run, 99))},
+            "call_ms": {"p50": float(np.percentile(run, 50)), "p99": float(np.percentile(run, 99))},
             "timing": "host wall clock, submit of all steps to the last completion; includes host<->device "
                       "copies of values, b and x"}
 
 
 def serve_c4(K, args, rank):
-    """Mixed-size serving: instances with bus counts drawn uniformly from
-    [200, serve_c4_buses] arrive at Poisson times (rate serve_c4_rate per
-    second); each runs its own sequence closed-loop (step k+1 is submitted
-    when step k returns).  Instances are analysed before the clock starts
-    (the paper, too, excludes the one-time analysis).  Latency is from a
-    step's submission to its completion."""
+    """The mixed-size serving workload: --serve-c4 instances whose bus counts
+    are uniform in [200, --serve-c4-buses] (32 grids, each shared by 1/32 of
+    the instances with values of their own), arriving at Poisson times
+    (--serve-c4-rate per second).  Each client opens its instance on arrival
+    (host analysis in its own thread, then admission by device memory) and
+    runs its sequence closed-loop (step k+1 submitted when step k returns),
+    --serve-c4-steps steps cycling over 3 generated matrices of its sequence
+    (the first, middle and last: the spread widens along it).  Step latency
+    is submission to completion; the open time is reported apart."""
     from paper_2401_13926_b300.workload import KKTSequence
     rng = np.random.default_rng(7000 + rank)
     N, S = args.serve_c4, args.serve_c4_steps
-    buses = rng.integers(200, args.serve_c4_buses + 1, size=N)
-    seqs = [KKTSequence("kkt2000", instance=5000 + 100 * rank + i, buses=int(nb), steps=S)
-            for i, nb in enumerate(buses)]
-    data = [[(q.values(k), q.rhs(k, q.values(k))[0]) for k in range(S)] for q in seqs]
-    srv = K.KKTServer(workers=args.serve_workers, restart=RESTART)
-    t_open = time.perf_counter()
-    ids = [srv.open(q.rowptr, q.colind, q.values(0)) for q in seqs]
-    t_open = time.perf_counter() - t_open
+    G = min(32, N)
+    grid_buses = rng.integers(200, args.serve_c4_buses + 1, size=G)
+    grids = [KKTSequence("kkt2000", instance=5000 + 100 * rank + g, buses=int(nb), steps=S)
+             for g, nb in enumerate(grid_buses)]
+    seqs = [grids[i % G].reseeded(6000 + 1000 * rank + i) for i in range(N)]
+    ks = [0, (S - 1) // 2, S - 1]
+    data = []
+    for q in seqs:
+        vs = [q.values(k) for k in ks]
+        data.append([(v, q.rhs(k, v)[0]) for k, v in zip(ks, vs)])
+    srv = K.KKTServer(batch=args.serve_batch, restart=RESTART)
     arrivals = np.cumsum(rng.exponential(1.0 / args.serve_c4_rate, size=N))
     results = [[] for _ in range(N)]
+    opens = [0.0] * N
+    errors = []
 
     def client(i, t_start):
-        delay = t_start + arrivals[i] - time.perf_counter()
-        if delay > 0:
-            time.sleep(delay)
-        for k in range(S):
-            t, _ = srv.submit(ids[i], *data[i][k], tol=TOL)
-            results[i].append(srv.wait(t)[1])
+        try:
+            delay = t_start + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            t = time.perf_counter()
+            inst = srv.open(seqs[i].rowptr, seqs[i].colind, seqs[i].values(0))
+            opens[i] = time.perf_counter() - t
+            for k in range(S):
+                tk, _ = srv.submit(inst, *data[i][k % 3], tol=TOL)
+                results[i].append(srv.wait(tk)[1])
+            srv.close_instance(inst)
+        except Exception as e:   # reported, not raised from the thread
+            errors.append(repr(e))
 
     t0 = time.perf_counter()
     threads = [threading.Thread(target=client, args=(i, t0)) for i in range(N)]
@@ -503,16 +524,19 @@ def serve_c4(K, args, rank):
     for th in threads:
         th.join()
     dt = time.perf_counter() - t0
+    info = srv.info()
     srv.close()
     res = [r for rr in results for r in rr]
     lat = np.array([r["queue_ms"] + r["run_ms"] for r in res])
     return {"value": len(res) / dt, "unit": "solves/s", "instances": N, "steps_per_instance": S,
-            "buses": [int(b) for b in buses], "n": [int(q.n) for q in seqs],
-            "arrival_rate_per_s": args.serve_c4_rate, "workers": args.serve_workers,
-            "converged": int(sum(r["status"] == 0 for r in res)), "max_nrbe": float(max(r["nrbe"] for r in res)),
+            "buses_range": [200, args.serve_c4_buses], "grids": G, "n": [int(g.n) for g in grids],
+            "arrival_rate_per_s": args.serve_c4_rate, "batch": args.serve_batch, "batched_calls": info["batches"],
+            "precision": "fp64", "errors": errors[:3],
+            "converged": int(sum(r["status"] == 0 for r in res)), "solves": len(res),
+            "max_nrbe": float(max(r["nrbe"] for r in res)) if res else None,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-            "analysis_s_total": t_open,
-            "timing": "host wall clock from the first arrival to the last completion"}
+            "open_s": {"p50": float(np.percentile(opens, 50)), "p99": float(np.percentile(opens, 99))},
+            "timing": "host wall clock from the first arrival to the last completion (opens included)"}
 
 
 def run_ours(args):
@@ -545,7 +569,7 @@ def run_ours(args):
     th = threading.Thread(target=analyse)
     th.start()
     per_config = {}
-    for name in [c for c in args.per_config.split(",") if c and c != args.workload]:
+    for name in [c for c in args.per_config.split(",") if c and c not in (args.workload, "none")]:
         per_config[name] = measure_config(K, name, args.per_config_steps, 3, flush, local, rank)
     th.join()
     if an_err:
@@ -623,29 +647,44 @@ def run_ours(args):
     other = None
     if not args.no_mixed:
         alt = "mixed" if args.precision == "fp64" else "fp64"
-        # FP32-preconditioned refinement stalls above 1e-12 on some of these
-        # matrices: the cycle cap keeps this leg bounded, and it reports how
-        # many solves reached the tolerance
+        # FP32 factors as the preconditioner; a solve they have not finished
+        # within --mixed-cycles restart cycles continues with the FP64
+        # refactorization (kkt_opts.mixed_fallback), counted per solve
         s2 = K.KKTSolver(restart=RESTART, device=local, stream=stream, timing=True, precision=alt,
-                         max_cycles=args.mixed_cycles)
+                         mixed_fallback=args.mixed_cycles)
         s2.analyze_like(solver)
         nm = min(args.mixed_steps, seq.M)
         idx = [int(round(i * (seq.M - 1) / max(nm - 1, 1))) for i in range(nm)]
         timed_steps(s2, [vals[idx[0]]], [rhs[idx[0]]], x, 1, 1, flush, stream, True)
         s2.phase_times(reset=True)
-        ms2, it2, nr2, st2 = timed_steps(s2, [vals[i] for i in idx], [rhs[i] for i in idx], x, nm, nm, flush,
-                                         stream, True)
+        ms2, it2, nr2, st2, fb2, fe2 = [], [], [], [], [], []
+        for i in idx:   # one step at a time: each solve's fallback and forward error are read after it
+            m_, i_, n_, s_ = timed_steps(s2, [vals[i]], [rhs[i]], x, 1, 1, flush, stream, True)
+            ms2 += m_
+            it2 += i_
+            nr2 += n_
+            st2 += s_
+            fb2.append(int(s2.info()["last_fallback"]))
+            xs = seq.rhs(i, seq.values(i))[1]
+            fe2.append(float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs)))
         ph2 = s2.phase_times(reset=True)
         other = {"precision": alt, "value": nm / (sum(ms2) / 1000.0), "unit": "solves/s", "steps": nm,
                  "matrices": idx, "latency_ms": {"p50": float(np.percentile(ms2, 50)),
                                                  "p99": float(np.percentile(ms2, 99))},
-                 "iters": it2, "nrbe": [float(f"{v:.3g}") for v in nr2], "status": st2,
+                 "fp32_cycles_before_fallback": args.mixed_cycles,
+                 "iters": it2, "nrbe": [float(f"{v:.3g}") for v in nr2], "status": st2, "fell_back": fb2,
+                 "forward_error_vs_xstar": [float(f"{v:.3g}") for v in fe2],
                  "converged": int(sum(s_ == K.OK for s_ in st2)), "max_nrbe": float(np.nanmax(nr2 + [0.0])),
                  "phase_ms_per_step": {p: round(ph2[p][0] / nm, 4) for p in ph2}}
         s2.close()
     # ---- serving: several independent sequences resident at once, their
     # steps in flight together (kkt_server_*)
-    serving = serve_measure(K, args, rank) if args.serve_instances > 0 else None
+    serving = None
+    if args.serve_instances > 0:
+        one = serve_measure(K, args, rank, 1)
+        serving = serve_measure(K, args, rank, args.serve_instances)
+        serving["one_instance"] = {k: one[k] for k in ("value", "latency_ms", "call_ms")}
+        serving["speedup_vs_one"] = serving["value"] / one["value"]
     serving_c4 = serve_c4(K, args, rank) if args.serve_c4 > 0 else None
     if rank != 0:
         return

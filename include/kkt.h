@@ -119,6 +119,20 @@ typedef struct {
                              by level in the dependency DAG of L (ties by row); 0 by
                              row.  A row's dependencies are always dispatched before
                              it.  Same arithmetic either way. */
+    int64_t warp_row_updates; /* a row is refactored one per warp only if its multiply-adds
+                             (the sum of |U(k,>k)| over its L entries) are at most this
+                             (besides fitting a warp's slice); -1 = no limit; 0 = the
+                             default limit */
+    int mixed_fallback;   /* KKT_PRECISION_MIXED only: restart cycles the FP32-factor
+                             preconditioner gets (default 2).  A solve not converged by
+                             then refactors the matrix in FP64 and continues FGMRES from
+                             its current x with the FP64 factors (up to max_cycles more
+                             cycles); an FP32 refactorization or solve that meets a zero
+                             pivot or a non-finite value falls back the same way (the
+                             solve restarting from x0).  The FP64 factors are then used
+                             until the next refactorization; kkt_info.last_fallback and
+                             fallbacks count it.  The context holds FP64 factor storage
+                             beside the FP32 one.  0 = no fallback (FP32 throughout). */
 } kkt_opts;
 
 /* Refinement methods (Section 2.1).  FGMRES: FGMRES(m) with M = LU as right
@@ -190,6 +204,9 @@ typedef struct {
     int32_t refactor_smem; /* shared memory per block of the refactorization kernel (bytes) */
     int32_t refactor_threads; /* threads per block of the refactorization kernel */
     int32_t refactor_blocks;  /* blocks of the refactorization kernel */
+    int32_t last_fallback; /* 1 if the last refactorization or solve fell back to FP64
+                              (kkt_opts.mixed_fallback) */
+    int64_t fallbacks;     /* FP64 fallbacks so far */
 } kkt_info;
 
 /* Fill *o with the defaults above. */
@@ -386,43 +403,108 @@ int kkt_lu_solve_noalloc(int32_t n, const int64_t* Fp, const int32_t* Fj, const 
                          const double* Fx, const int32_t* P, const int32_t* Q, const double* b,
                          double* x, void* stream);
 
+/* ---- one step of many instances in shared launches ----
+ *
+ * The paper solves one KKT sequence at a time; one small or mid-size
+ * instance leaves most of a B300 idle, because its refactorization and
+ * triangular solves are chains of dependent rows (Section 1.3 notes that
+ * tiny kernels underuse the GPU).  A batch runs one step -- kkt_step:
+ * gather, refactorization with the forward sweep fused, backward sweep,
+ * residual and refine-or-not decision -- of several instances together:
+ * ONE refactorization launch whose work items are taken from every
+ * instance's level-ordered queue in turn (ticket t -> instance t mod count,
+ * its item t / count, so each instance's rows keep their dispatch order),
+ * one launch of backward sweeps with one thread-block cluster per instance,
+ * and one launch each for the gathers, the residuals and the decisions.
+ * Instances whose x0 needs refinement then continue with FGMRES on their
+ * own stream.  Every instance gets the bits it would get from kkt_step
+ * alone (the same row arithmetic; the reductions keep each instance's own
+ * block count).
+ */
+typedef struct kkt_batch kkt_batch;
+
+/* Workspace for up to max_count instances per step on `device` (device
+ * memory and pinned host memory for the launch arguments, a stream). */
+int kkt_batch_create(kkt_batch** out, int max_count, int device);
+void kkt_batch_destroy(kkt_batch* bt);
+
+/*
+ * One step of each of ctxs[0..count) (distinct, analysed contexts):
+ * values[i], b[i], x[i] as in kkt_step (all host arrays when on_device == 0,
+ * else all device pointers), one tolerance.  iters, nrbe (may be NULL) and
+ * status (required) are arrays of count: status[i] is kkt_step's return
+ * code for instance i.  FP64 contexts on the batch's device with the same
+ * refactorization block size (kkt_info.refactor_threads) as the first of
+ * them share the launches; the others run as lone kkt_step calls.  Work the
+ * caller queued on a context's stream before the call is waited for; the
+ * call returns when every step is done.  Returns KKT_ERR_INVALID for bad
+ * arguments (a repeated context, count > max_count), else KKT_OK with the
+ * per-instance codes in status.  One call at a time per batch.
+ */
+int kkt_batch_step(kkt_batch* bt, kkt_ctx* const* ctxs, int count, const double* const* values,
+                   const double* const* b, double* const* x, int on_device, double tol, int* iters, double* nrbe,
+                   int* status);
+
+/* Kernels the batch has launched so far. */
+int64_t kkt_batch_launches(const kkt_batch* bt);
+
 /* ---- serving: many resident instances, steps in flight concurrently ----
  *
  * The paper solves one KKT sequence at a time and reuses the analysis,
  * factor storage and Krylov space across the sequence (Sections 2.1, 3.1.1).
- * A server holds many such sequences ("instances") resident on one GPU and
- * keeps their refactor + solve steps in flight together: each instance is a
- * context (kkt_create) with its own stream; a pool of host worker threads
- * runs steps, one step per instance at a time, in each instance's submission
- * order, so independent instances overlap on the GPU (continuous batching).
- * Admission: an instance is admitted only if the device memory the admitted
- * instances hold stays within the budget.  Results do not depend on the mix:
- * each step runs the same kernels in the same order as alone.
+ * A server holds many such sequences ("instances") resident on one or more
+ * GPUs and keeps their refactor + solve steps in flight together: each
+ * instance is a context (kkt_create) with its own stream, placed whole on
+ * one device.  Steps of one instance run one at a time in submission order.
+ *   - batch > 0 (continuous batching): one dispatcher per device takes up to
+ *     `batch` instances with a queued step and runs those steps together
+ *     (kkt_batch_step: one refactorization launch over all of them); steps
+ *     submitted meanwhile join the next batch.
+ *   - batch == 0: a pool of worker threads runs each step as its own
+ *     kkt_step, instances concurrently on their streams.
+ * Admission (kkt_server_open): the host analysis runs in the caller's
+ * thread; the instance is then placed on the device with the most budget
+ * left (kkt_place_instance) and waits, in arrival order, until its device
+ * memory fits that device's budget.  Results do not depend on the mix: each
+ * step computes the bits it would compute alone.
  */
 typedef struct kkt_server kkt_server;
 
+#define KKT_SERVER_MAX_DEVICES 16
+
 typedef struct {
-    int workers;          /* host threads = steps in flight at once (default 8, 1..256) */
-    int64_t hbm_budget;   /* device bytes the admitted instances may hold; 0 = 90% of the
-                             device memory free at kkt_server_create */
-    kkt_opts opts;        /* options of every instance's context (create_stream and
-                             stream are ignored: each instance makes its own stream) */
+    int workers;          /* host threads of the batch == 0 mode (default 8, 1..256) */
+    int64_t hbm_budget;   /* device bytes the admitted instances may hold on each device;
+                             0 = 90% of the device memory free at kkt_server_create */
+    kkt_opts opts;        /* options of every instance's context (device, create_stream
+                             and stream are ignored: each instance makes its own stream
+                             on the device it is placed on) */
+    int batch;            /* instances per batched step (continuous batching); 0 = off
+                             (default 8) */
+    int ndevices;         /* devices to place instances on: devices[0..ndevices);
+                             0 = opts.device only (default) */
+    int devices[KKT_SERVER_MAX_DEVICES];
 } kkt_server_opts;
 
 typedef struct {
     int status;           /* KKT_OK or the failing call's error (refactor or solve) */
     int32_t iters;        /* refinement iterations */
     double nrbe;          /* Eq. (nbre) of x */
-    double queue_ms;      /* submit -> a worker starts the step */
-    double run_ms;        /* refactor + solve, host wall time on the worker */
+    double queue_ms;      /* submit -> the step starts */
+    double run_ms;        /* refactor + solve (the whole batched call in batch mode), host wall time */
+    int32_t batch_size;   /* steps in the batched call that ran it (1 without batching) */
+    int32_t device;       /* device of the instance */
 } kkt_step_result;
 
 typedef struct {
     int32_t instances;      /* admitted and open */
-    int64_t device_bytes;   /* held by the admitted instances */
-    int64_t hbm_budget;
+    int64_t device_bytes;   /* held by the admitted instances (all devices) */
+    int64_t hbm_budget;     /* summed over the devices */
     int64_t submitted, completed;
     int32_t in_flight;      /* steps running now */
+    int32_t waiting;        /* opens waiting for admission */
+    int64_t batches;        /* batched calls run so far */
+    int32_t ndevices;
 } kkt_server_info;
 
 /* Fill *o with the defaults above (kkt_default_opts for o->opts). */
@@ -431,11 +513,14 @@ void kkt_server_default_opts(kkt_server_opts* o);
 int kkt_server_create(kkt_server** out, const kkt_server_opts* o);
 
 /*
- * Admit a new instance: kkt_analyze of its pattern (values0 fixes the pivots,
- * as in kkt_analyze) in a new context.  *instance gets its id.  Errors:
- * KKT_ERR_OOM when its device memory would exceed the budget (nothing is
- * kept; close an instance and retry), or kkt_create / kkt_analyze errors.
- * The arrays are host memory and are not kept.
+ * Admit a new instance: the host analysis of its pattern (values0 fixes the
+ * pivots, as in kkt_analyze) in the calling thread, placement, then -- once
+ * its device memory (kkt_estimate_device_bytes) fits the chosen device's
+ * budget, waiting behind earlier opens on that device -- its context and
+ * device buffers.  *instance gets its id.  Errors: KKT_ERR_OOM when the
+ * instance can never fit (it needs more than a whole device's budget), or
+ * kkt_create / kkt_analyze errors.  The arrays are host memory and are not
+ * kept.  Blocks while waiting for admission.
  */
 int kkt_server_open(kkt_server* s, int32_t n, const int32_t* rowptr, const int32_t* colind,
                     const double* values0, int64_t* instance);
@@ -452,7 +537,8 @@ int kkt_server_submit(kkt_server* s, int64_t instance, const double* values, con
 /* Block until the step is done; its result in *r.  Each ticket is waited once. */
 int kkt_server_wait(kkt_server* s, int64_t ticket, kkt_step_result* r);
 
-/* Wait for the instance's queued steps, then free its context and memory. */
+/* Wait for the instance's queued steps, then free its context and memory
+   (opens waiting for admission may then proceed). */
 int kkt_server_close(kkt_server* s, int64_t instance);
 
 int kkt_server_query(kkt_server* s, kkt_server_info* info);
@@ -494,6 +580,7 @@ typedef struct {
     double refactor_updates; /* multiply-adds of one refactorization */
     double order_ms;         /* host time of the column ordering */
     double pivot_ms;         /* host time of the pivoting factorization */
+    int32_t canonical_order; /* 1 if the caller's CSR rows were already sorted */
 } kkt_host_stats;
 
 /*
@@ -509,6 +596,26 @@ int kkt_host_analyze(int32_t n, const int32_t* rowptr, const int32_t* colind, co
 
 /* Column order of kkt_analyze (approximate minimum degree on K^T K). */
 int kkt_order(int32_t n, const int32_t* rowptr, const int32_t* colind, int32_t* Q);
+
+/*
+ * Device bytes kkt_analyze allocates for a pattern of n rows and nnz_a
+ * entries whose host analysis gave *st (kkt_host_analyze), under options
+ * *o (NULL = defaults); canonical_order != 0 if the caller's CSR rows are
+ * already sorted (no index map is kept).  Exactly kkt_info.device_bytes of
+ * the analysed context (the scratch of rows refactored in global memory,
+ * which only rows beyond a block's shared memory use, is not counted).
+ */
+int kkt_estimate_device_bytes(int32_t n, int64_t nnz_a, const kkt_host_stats* st, const kkt_opts* o,
+                              int canonical_order, int64_t* bytes);
+
+/*
+ * Placement of a new instance (the serving runtime's, no collective: whole
+ * instances go to one device): among ndev devices with budget[i] and
+ * held[i] bytes (held: admitted plus waiting for admission), the index of
+ * the one with the most budget left whose budget can hold `need` at all
+ * (ties to the lower index), or -1 if none can.
+ */
+int kkt_place_instance(int ndev, const int64_t* budget, const int64_t* held, int64_t need);
 
 /*
  * First factorization with threshold partial pivoting on the host, as

@@ -16,7 +16,7 @@ import os
 
 import numpy as np
 
-__all__ = ["KKTSolver", "KKTServer", "KKTError", "order", "pivot", "host_analyze", "lib", "LIB_PATH", "EXPORTS"]
+__all__ = ["KKTSolver", "KKTServer", "KKTBatch", "KKTError", "order", "pivot", "host_analyze", "lib", "LIB_PATH", "EXPORTS"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libkkt_b300.so")
 
@@ -42,6 +42,8 @@ EXPORTS = [
     "kkt_trace_solve", "kkt_repivot", "kkt_tune", "kkt_step", "kkt_server_default_opts", "kkt_server_create", "kkt_server_open",
     "kkt_server_submit", "kkt_server_wait", "kkt_server_close", "kkt_server_query", "kkt_server_destroy",
     "kkt_host_analyze", "kkt_analyze_like", "kkt_trace_critical_path",
+    "kkt_batch_create", "kkt_batch_destroy", "kkt_batch_step", "kkt_batch_launches",
+    "kkt_estimate_device_bytes", "kkt_place_instance",
 ]
 NOALLOC_MAX_N = 65536
 PHASES = ["gather", "refactor", "lsolve", "usolve", "spmv", "ortho", "update", "refactor_tail", "graph_refactor",
@@ -56,6 +58,7 @@ class _Opts(C.Structure):
         ("timing", C.c_int), ("trisolve", C.c_int), ("cluster_blocks", C.c_int), ("block_smem", C.c_int),
         ("method", C.c_int), ("ortho", C.c_int), ("inner_tol", C.c_double), ("repivot", C.c_int),
         ("graphs", C.c_int), ("warp_rows", C.c_int), ("row_order", C.c_int),
+        ("warp_row_updates", C.c_int64), ("mixed_fallback", C.c_int),
     ]
 
 
@@ -68,27 +71,34 @@ class _Info(C.Structure):
         ("norm_a_inf", C.c_double), ("analyze_ms", C.c_double), ("launches", C.c_int64),
         ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("repivots", C.c_int32), ("rows_warp", C.c_int32),
         ("rows_block", C.c_int32), ("rows_global", C.c_int32), ("refactor_smem", C.c_int32),
-        ("refactor_threads", C.c_int32), ("refactor_blocks", C.c_int32),
+        ("refactor_threads", C.c_int32), ("refactor_blocks", C.c_int32), ("last_fallback", C.c_int32),
+        ("fallbacks", C.c_int64),
     ]
 
 
+SERVER_MAX_DEVICES = 16
+
+
 class _ServerOpts(C.Structure):
-    _fields_ = [("workers", C.c_int), ("hbm_budget", C.c_int64), ("opts", _Opts)]
+    _fields_ = [("workers", C.c_int), ("hbm_budget", C.c_int64), ("opts", _Opts), ("batch", C.c_int),
+                ("ndevices", C.c_int), ("devices", C.c_int * SERVER_MAX_DEVICES)]
 
 
 class _StepResult(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int32), ("nrbe", C.c_double), ("queue_ms", C.c_double),
-                ("run_ms", C.c_double)]
+                ("run_ms", C.c_double), ("batch_size", C.c_int32), ("device", C.c_int32)]
 
 
 class _ServerInfo(C.Structure):
     _fields_ = [("instances", C.c_int32), ("device_bytes", C.c_int64), ("hbm_budget", C.c_int64),
-                ("submitted", C.c_int64), ("completed", C.c_int64), ("in_flight", C.c_int32)]
+                ("submitted", C.c_int64), ("completed", C.c_int64), ("in_flight", C.c_int32),
+                ("waiting", C.c_int32), ("batches", C.c_int64), ("ndevices", C.c_int32)]
 
 
 class _HostStats(C.Structure):
     _fields_ = [("nnz_l", C.c_int64), ("nnz_u", C.c_int64), ("levels_l", C.c_int32), ("levels_u", C.c_int32),
-                ("refactor_updates", C.c_double), ("order_ms", C.c_double), ("pivot_ms", C.c_double)]
+                ("refactor_updates", C.c_double), ("order_ms", C.c_double), ("pivot_ms", C.c_double),
+                ("canonical_order", C.c_int32)]
 
 
 class KKTError(RuntimeError):
@@ -150,10 +160,18 @@ def lib():
     L.kkt_host_analyze.argtypes = [i32, vp, vp, vp, d, vp, vp, C.POINTER(_HostStats)]
     L.kkt_analyze_like.argtypes = [vp, vp]
     L.kkt_trace_critical_path.argtypes = [vp, vp, vp, C.POINTER(d), C.POINTER(i32), C.POINTER(d), C.POINTER(i32)]
+    L.kkt_batch_create.argtypes = [C.POINTER(vp), ip, ip]
+    L.kkt_batch_destroy.argtypes = [vp]
+    L.kkt_batch_destroy.restype = None
+    L.kkt_batch_step.argtypes = [vp, vp, ip, vp, vp, vp, ip, d, vp, vp, vp]
+    L.kkt_batch_launches.argtypes = [vp]
+    L.kkt_estimate_device_bytes.argtypes = [i32, i64, C.POINTER(_HostStats), C.POINTER(_Opts), ip, C.POINTER(i64)]
+    L.kkt_place_instance.argtypes = [ip, vp, vp, i64]
     for name in EXPORTS:
         if name not in ("kkt_default_opts", "kkt_destroy", "kkt_strerror", "kkt_last_error_detail",
-                        "kkt_server_default_opts", "kkt_server_destroy"):
+                        "kkt_server_default_opts", "kkt_server_destroy", "kkt_batch_destroy"):
             getattr(L, name).restype = C.c_int
+    L.kkt_batch_launches.restype = C.c_int64
     _lib = L
     return L
 
@@ -236,6 +254,29 @@ def host_analyze(rowptr, colind, values0, pivot_tol=1e-3):
     return P, Q, {k: getattr(st, k) for k, _ in _HostStats._fields_}
 
 
+def estimate_device_bytes(n, nnz, stats, canonical_order=True, **solver_opts):
+    """kkt_estimate_device_bytes: device memory kkt_analyze will hold for a
+    pattern with these host_analyze() statistics and solver options."""
+    st = _HostStats()
+    for k, _ in _HostStats._fields_:
+        setattr(st, k, stats[k])
+    o = _solver_opts(**solver_opts)
+    out = C.c_int64()
+    rc = lib().kkt_estimate_device_bytes(int(n), int(nnz), C.byref(st), C.byref(o), int(bool(canonical_order)),
+                                         C.byref(out))
+    if rc:
+        raise KKTError(rc, "kkt_estimate_device_bytes")
+    return out.value
+
+
+def place_instance(budget, held, need):
+    """kkt_place_instance: device index for a new instance (most budget left
+    among devices whose budget can hold it), or -1."""
+    b = np.ascontiguousarray(budget, np.int64)
+    h = np.ascontiguousarray(held, np.int64)
+    return lib().kkt_place_instance(len(b), b.ctypes.data, h.ctypes.data, int(need))
+
+
 def lu_solve_noalloc(Fp, Fj, Fdiag, Fx, P, Q, b, x, stream=None):
     """kkt_lu_solve_noalloc: x = Q U^{-1} L^{-1} P b from caller-held device
     factors in the combined row layout, with no device allocation (for
@@ -255,7 +296,7 @@ def lu_solve_noalloc(Fp, Fj, Fdiag, Fx, P, Q, b, x, stream=None):
 def _solver_opts(restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3, boost_eps=0.0,
                  device=0, spin_limit=0, timing=False, trisolve="auto", block_smem=0, cluster_blocks=0,
                  precision="fp64", method="fgmres", ortho="cgs2", inner_tol=1e-6, repivot=False, graphs=False,
-                 warp_rows=True, row_order="level"):
+                 warp_rows=True, row_order="level", mixed_fallback=2, warp_row_updates=0):
     """kkt_opts from keyword arguments (defaults of kkt_default_opts)."""
     o = _Opts()
     lib().kkt_default_opts(C.byref(o))
@@ -271,6 +312,8 @@ def _solver_opts(restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, 
     o.graphs = int(bool(graphs))
     o.warp_rows = int(bool(warp_rows))
     o.row_order = ROW_ORDER[row_order]
+    o.mixed_fallback = int(mixed_fallback)
+    o.warp_row_updates = int(warp_row_updates)
     return o
 
 
@@ -281,11 +324,12 @@ class KKTSolver:
     def __init__(self, restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3,
                  boost_eps=0.0, device=0, stream=None, spin_limit=0, timing=False, trisolve="auto",
                  block_smem=0, cluster_blocks=0, precision="fp64", method="fgmres", ortho="cgs2",
-                 inner_tol=1e-6, repivot=False, graphs=False, warp_rows=True, row_order="level"):
+                 inner_tol=1e-6, repivot=False, graphs=False, warp_rows=True, row_order="level",
+                 mixed_fallback=2, warp_row_updates=0):
         L = lib()
         o = _solver_opts(restart, max_cycles, stop_mode, refine_delta, pivot_tol, boost_eps, device, spin_limit,
                          timing, trisolve, block_smem, cluster_blocks, precision, method, ortho, inner_tol, repivot,
-                         graphs, warp_rows, row_order)
+                         graphs, warp_rows, row_order, mixed_fallback, warp_row_updates)
         if stream is None:
             stream = _torch_current_stream(device)
         if stream is None:
@@ -478,18 +522,83 @@ class KKTSolver:
         return {k: getattr(inf, k) for k, _ in _Info._fields_}
 
 
-class KKTServer:
-    """Many resident KKT sequences on one GPU with their steps in flight
-    together (kkt_server_*): open() admits an instance (analysis + device
-    buffers, within the HBM budget), submit() queues a refactor + solve step
-    (host arrays; x is written when the step completes), wait() returns its
-    result.  Steps of one instance run in order; different instances overlap."""
+class KKTBatch:
+    """kkt_batch_*: one step of several KKTSolver instances in shared
+    launches (one refactorization launch over every instance's rows, one
+    cluster launch for their backward sweeps).  step() returns per-instance
+    (x, iters, nrbe, status)."""
 
-    def __init__(self, workers=8, hbm_budget=0, **solver_opts):
+    def __init__(self, max_count, device=0):
+        h = C.c_void_p()
+        rc = lib().kkt_batch_create(C.byref(h), int(max_count), int(device))
+        if rc:
+            raise KKTError(rc, "kkt_batch_create")
+        self._h = h
+        self.max_count = int(max_count)
+
+    def step(self, solvers, values, bs, xs=None, tol=1e-12):
+        """values, bs (and xs): lists of numpy arrays (host) or of CUDA
+        tensors (device), one per solver."""
+        k = len(solvers)
+        dev = _is_device(values[0])
+        if xs is None:
+            xs = [b.new_empty(s.n) if dev else np.zeros(s.n) for s, b in zip(solvers, bs)]
+        keep = []
+        def ptrs(arrs):
+            out = (C.c_void_p * k)()
+            for i, a in enumerate(arrs):
+                kk, p, d_ = _ptr(a, np.float64)
+                if d_ != dev:
+                    raise ValueError("all arrays must be host arrays or all device arrays")
+                keep.append(kk)
+                out[i] = p
+            return out
+        pv, pb, px = ptrs(values), ptrs(bs), ptrs(xs)
+        ctxs = (C.c_void_p * k)(*[s._h.value for s in solvers])
+        it = np.zeros(k, np.int32)
+        nr = np.zeros(k)
+        st = np.zeros(k, np.int32)
+        rc = lib().kkt_batch_step(self._h, ctxs, k, pv, pb, px, int(dev), float(tol), it.ctypes.data,
+                                  nr.ctypes.data, st.ctypes.data)
+        if rc:
+            raise KKTError(rc, "kkt_batch_step")
+        return xs, it, nr, st
+
+    def launches(self):
+        return lib().kkt_batch_launches(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().kkt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class KKTServer:
+    """Many resident KKT sequences on one or more GPUs with their steps in
+    flight together (kkt_server_*): open() admits an instance (host analysis
+    in the calling thread, placement on the device with the most budget
+    left, then -- waiting in arrival order until its device memory fits --
+    its device buffers), submit() queues a refactor + solve step (host
+    arrays; x is written when the step completes), wait() returns its
+    result.  batch > 0: up to `batch` queued steps of different instances
+    run as one batched call (continuous batching); batch = 0: one worker
+    thread per step.  Steps of one instance run in order."""
+
+    def __init__(self, workers=8, hbm_budget=0, batch=8, devices=None, **solver_opts):
         L = lib()
         o = _ServerOpts()
         L.kkt_server_default_opts(C.byref(o))
-        o.workers, o.hbm_budget = int(workers), int(hbm_budget)
+        o.workers, o.hbm_budget, o.batch = int(workers), int(hbm_budget), int(batch)
+        if devices:
+            o.ndevices = len(devices)
+            for i, d in enumerate(devices):
+                o.devices[i] = int(d)
         o.opts = _solver_opts(**solver_opts)
         h = C.c_void_p()
         rc = L.kkt_server_create(C.byref(h), C.byref(o))

@@ -117,13 +117,13 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // The last block to arrive (deterministic fixed-order sum of the partials)
 // returns true in every thread of that block.
-__device__ __forceinline__ bool last_block(DevScal* s) {
+__device__ __forceinline__ bool last_block(DevScal* s, unsigned nblocks) {
     __shared__ int is_last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned prev = atomicAdd(&s->red_count, 1u);
-        is_last = (prev == gridDim.x - 1);
+        is_last = (prev == nblocks - 1);
     }
     __syncthreads();
     if (is_last) {
@@ -132,12 +132,16 @@ __device__ __forceinline__ bool last_block(DevScal* s) {
     }
     return is_last;
 }
+__device__ __forceinline__ bool last_block(DevScal* s) { return last_block(s, gridDim.x); }
 
-// Sum partials part[b * RED_SLOTS + slot] over blocks b, in block order.
-__device__ __forceinline__ double reduce_partials(const double* part, int slot, double* sh) {
+// Sum partials part[b * RED_SLOTS + slot] over blocks b < nblocks, in block order.
+__device__ __forceinline__ double reduce_partials(const double* part, int slot, double* sh, int nblocks) {
     double v = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(&part[b * RED_SLOTS + slot]);
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += __ldcg(&part[b * RED_SLOTS + slot]);
     return block_sum(v, sh);
+}
+__device__ __forceinline__ double reduce_partials(const double* part, int slot, double* sh) {
+    return reduce_partials(part, slot, sh, (int)gridDim.x);
 }
 
 // Loads and stores that other blocks poll (gpu scope, not cached in L1).
@@ -162,7 +166,7 @@ __device__ __forceinline__ void st_relaxed(float* p, float v) {
 
 // ---------------------------------------------------------------- K0: gather
 // Start of a refactorization: new generation, tickets and error words.
-__global__ void k_refactor_prep(DevScal* s) {
+__device__ __forceinline__ void refactor_prep(DevScal* s) {
     s->gen_fact += 1;
     s->ticket_fact = 0;
     s->err = 0;
@@ -171,6 +175,7 @@ __global__ void k_refactor_prep(DevScal* s) {
     s->nboost = 0;
     s->normA = 0.0;
 }
+__global__ void k_refactor_prep(DevScal* s) { refactor_prep(s); }
 
 struct GiveUpGlobal {
     const int* abort;
@@ -237,9 +242,10 @@ __device__ __forceinline__ bool fused_forward_row(int row, int64_t lo, int64_t h
 // ||K||_inf from row sums.  T is the factor type: double, or float in
 // mixed precision.
 template <typename T>
-__global__ void k_gather(const double* __restrict__ vals, int64_t nnzF, T* __restrict__ Fx,
-                         const int32_t* __restrict__ Arp, const int64_t* __restrict__ asrc,
-                         double* __restrict__ Ax, int n, T* __restrict__ rinv, DevScal* s, T* __restrict__ yarm) {
+__device__ __forceinline__ void gather_body(const double* __restrict__ vals, int64_t nnzF, T* __restrict__ Fx,
+                                            const int32_t* __restrict__ Arp, const int64_t* __restrict__ asrc,
+                                            double* __restrict__ Ax, int n, T* __restrict__ rinv, DevScal* s,
+                                            T* __restrict__ yarm) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = tid; i < n; i += stride) rinv[i] = sentinel_of<T>();
@@ -270,6 +276,49 @@ __global__ void k_gather(const double* __restrict__ vals, int64_t nnzF, T* __res
     for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
     if (lane == 0 && rmax > 0.0)   // non-negative doubles order like their bit patterns
         atomicMax((unsigned long long*)&s->normA, (unsigned long long)__double_as_longlong(rmax));
+}
+
+template <typename T>
+__global__ void k_gather(const double* __restrict__ vals, int64_t nnzF, T* __restrict__ Fx,
+                         const int32_t* __restrict__ Arp, const int64_t* __restrict__ asrc,
+                         double* __restrict__ Ax, int n, T* __restrict__ rinv, DevScal* s, T* __restrict__ yarm) {
+    gather_body<T>(vals, nnzF, Fx, Arp, asrc, Ax, n, rinv, s, yarm);
+}
+
+// ---- the same first phases for a batch of instances (blockIdx.y = instance)
+struct GatherArgs {
+    const double* vals;
+    int64_t nnzF;
+    double* Fx;
+    const int32_t* Arp;
+    const int64_t* asrc;
+    double* Ax;
+    int n;
+    double* rinv;
+    DevScal* s;
+    double* yarm;
+};
+
+// every instance's refactor_prep, and the batch ticket cleared
+__global__ void k_refactor_prep_batch(const GatherArgs* ga, int count, unsigned long long* ticket) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) refactor_prep(ga[i].s);
+    if (i == 0) *ticket = 0ull;
+}
+
+__global__ void k_gather_batch(const GatherArgs* ga) {
+    const GatherArgs& g = ga[blockIdx.y];
+    gather_body<double>(g.vals, g.nnzF, g.Fx, g.Arp, g.asrc, g.Ax, g.n, g.rinv, g.s, g.yarm);
+}
+
+// The caller's values rebuilt from the canonical copy (vals[asrc[e]] =
+// Ax[e]; asrc == nullptr: the same order), for a refactorization that
+// starts from the matrix already in use.
+__global__ void k_scatter_values(int64_t nnz, const double* __restrict__ Ax, const int64_t* __restrict__ asrc,
+                                 double* __restrict__ vals) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = tid; e < nnz; e += stride) vals[asrc ? asrc[e] : e] = Ax[e];
 }
 
 // ---------------------------------------------------------------- K1: refactor
@@ -311,8 +360,9 @@ struct RefArgs {
     const double* vals;
     const int64_t* fsrc;
     int mlo, M;            // columns [mlo, mlo + M) have an O(1) position map (M may be 0)
-    int map_bytes;         // shared memory before the work area (the map, 16-byte aligned)
-    int area_bytes;        // the work area: a block row, or one slice per warp
+    int map_bytes;         // bytes of the position map (16-byte aligned), after the work area
+    int area_bytes;        // the work area of a block row, at the start of shared memory
+    int slice_bytes;       // a warp row's slice: warp w's starts at w * slice_bytes (slices span the map too)
     // ROW_GLOBAL rows, by global-row index g: step descriptors at sd_off[g]
     // in gdk / gcnt, values at w_off[g] in gw
     const int64_t* gdk;
@@ -320,6 +370,24 @@ struct RefArgs {
     const int64_t* g_sd_off;
     T* gw;
     const int64_t* g_w_off;
+    DevScal* s;            // the instance's scalars (tickets of a lone launch, errors, ||K||_inf)
+    FwdArgs<T> fw;         // the fused forward sweep (fw.rhs == nullptr: not fused)
+    double boost_eps;
+};
+
+// Several instances' refactorizations in one launch: global ticket t goes
+// to instance t mod count, its work item t / count (tickets past an
+// instance's items, or of an instance that has failed, are skipped), so
+// every instance's items are dispatched in their own order and a row's
+// dependencies are still dispatched before it.
+template <typename T>
+struct RefBatch {
+    const RefArgs<T>* args;   // device array of `count`
+    int count;
+    long long total;          // count * the most items of any instance
+    unsigned long long* ticket;   // zeroed before the launch
+    int map_cols;             // the largest position map of any instance
+    int map_off;              // where the map starts: after the largest work area of any instance
 };
 
 __device__ __forceinline__ bool finite_bits(double v) {
@@ -655,52 +723,104 @@ __device__ bool block_row(int row, const RefArgs<T>& a, DevScal* s, T boost, lon
 }
 
 // The refactorization: blocks of NT threads take work items from the
-// ticket until none is left.  Shared memory: the position map of the last M
-// columns (kept at -1 between rows), then the work area -- one slice per
-// warp for warp rows, or a block row's working set.
-template <typename T, bool FUSED, int NT>
+// ticket until none is left.  Shared memory: a block row's working set at
+// the start, the position map of the last M columns after it (-1 where the
+// row being factored has no such column); warp rows use one slice per warp
+// over all of it.  The bytes of the map that warp rows overwrote since the
+// last block row (tracked per warp) are re-armed before the next block row.
+// BATCH: the items of several instances (RefBatch); else those of `one`.
+template <typename T, bool FUSED, int NT, bool BATCH>
 __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1)
-k_refactor_rows(RefArgs<T> a, DevScal* s, double boost_eps, long long limit, unsigned long long* trace,
-                FwdArgs<T> fw) {
+k_refactor_rows(RefArgs<T> one, RefBatch<T> batch, long long limit, unsigned long long* trace) {
+    constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char ref_sh[];
     __shared__ RefItem s_item;
-    __shared__ int s_q;
-    short* map = reinterpret_cast<short*>(ref_sh);
-    unsigned char* area = ref_sh + a.map_bytes;
+    __shared__ int s_inst;
+    __shared__ int s_dlo[NW], s_dhi[NW];   // bytes of its slice each warp wrote since the map was armed
     const int tid = threadIdx.x;
-    const T boost = (T)(boost_eps * *(volatile double*)&s->normA);
-    for (int c = tid; c < a.M; c += NT) map[c] = -1;
-    const size_t slice = ((size_t)a.area_bytes / (NT / 32)) & ~(size_t)15;
+    const int map_cols = BATCH ? batch.map_cols : one.M;
+    const int map_off = BATCH ? batch.map_off : one.area_bytes;
+    short* map = reinterpret_cast<short*>(ref_sh + map_off);
+    for (int c = tid; c < map_cols; c += NT) map[c] = -1;
+    if (tid < NW) { s_dlo[tid] = 0x7fffffff; s_dhi[tid] = 0; }
+    bool map_armed = true;    // uniform for the block: no warp row since the last re-arm
+    bool map_whole = false;   // a failed block row left entries anywhere in the map
     for (;;) {
         if (tid == 0) {
-            const int q = (int)atomicAdd(&s->ticket_fact, 1u);
-            s_q = q;
-            if (q < a.nitems) s_item = a.items[q];
+            int inst = -1;
+            if (!BATCH) {
+                const int q = (int)atomicAdd(&one.s->ticket_fact, 1u);
+                if (q < one.nitems && !ld_volatile_int(&one.s->abort)) { inst = 0; s_item = one.items[q]; }
+            } else {
+                for (;;) {
+                    const long long t = (long long)atomicAdd(batch.ticket, 1ull);
+                    if (t >= batch.total) break;
+                    const int j = (int)(t % batch.count);
+                    const int q = (int)(t / batch.count);
+                    const RefArgs<T>& aj = batch.args[j];
+                    if (q < aj.nitems && !ld_volatile_int(&aj.s->abort)) { inst = j; s_item = aj.items[q]; break; }
+                }
+            }
+            s_inst = inst;
         }
         __syncthreads();
-        if (__syncthreads_or(s_q >= a.nitems || ld_volatile_int(&s->abort))) return;
+        const int inst = s_inst;
         const RefItem it = s_item;
+        __syncthreads();   // s_inst and s_item are read before thread 0 may overwrite them
+        if (inst < 0) return;
+        const RefArgs<T>& a = BATCH ? batch.args[inst] : one;
+        DevScal* s = a.s;
+        const T boost = (T)(a.boost_eps * *(volatile double*)&s->normA);
         const int kind = it.info >> 28;
         if (kind == ROW_WARP) {
             const int count = it.info & 0x0fffffff;
             const int warp = tid >> 5;
-            if (warp < count)
-                warp_row<T, FUSED>(a.order[it.first + warp], a, s, boost, limit, trace, area + warp * slice, fw);
+            if (warp < count) {
+                const int row = a.order[it.first + warp];
+                const int64_t b = a.Fp[row];
+                const int used = 12 * (int)(a.Fdiag[row] - b) + (int)(sizeof(T) + 4) * (int)(a.Fp[row + 1] - b);
+                const int lo = warp * a.slice_bytes;
+                if ((tid & 31) == 0) {
+                    s_dlo[warp] = min(s_dlo[warp], lo);
+                    s_dhi[warp] = max(s_dhi[warp], lo + used);
+                }
+                warp_row<T, FUSED>(row, a, s, boost, limit, trace, ref_sh + lo, a.fw);
+            }
+            map_armed = map_cols == 0;
             __syncthreads();   // the slices are reused by the next item
         } else {
             const int row = a.order[it.first];
             const int64_t b = a.Fp[row];
             const int len = (int)(a.Fp[row + 1] - b), nsteps = (int)(a.Fdiag[row] - b);
-            RowSpace<T> rs(area, nsteps, len);
+            RowSpace<T> rs(ref_sh, nsteps, len);
             const bool staged = kind == ROW_BLOCK;
+            if (staged && !map_armed) {
+                // re-arm the map entries warp rows overwrote (all of them
+                // after a failed block row)
+                const int mend = map_off + 2 * map_cols;
+                for (int w = 0; w < NW; w++) {
+                    int lo = map_whole ? map_off : max(s_dlo[w], map_off);
+                    int hi = map_whole ? mend : min(s_dhi[w], mend);
+                    if (lo >= hi) continue;
+                    for (int c = ((lo - map_off) >> 1) + tid; c < ((hi - map_off + 1) >> 1); c += NT) map[c] = -1;
+                    if (map_whole) break;
+                }
+                __syncthreads();
+                if (tid < NW) { s_dlo[tid] = 0x7fffffff; s_dhi[tid] = 0; }
+                map_armed = true;
+                map_whole = false;
+            }
             if (!staged) {   // ROW_GLOBAL: descriptors and values in global memory
                 const int g = it.info & 0x0fffffff;
                 rs.dk = const_cast<int64_t*>(a.gdk) + a.g_sd_off[g];
                 rs.cnt = const_cast<int32_t*>(a.gcnt) + a.g_sd_off[g];
                 rs.w = a.gw + a.g_w_off[g];
             }
-            if (!block_row<T, FUSED, NT>(row, a, s, boost, limit, trace, rs, staged, map, staged ? a.M : 0, fw))
-                return;
+            if (!block_row<T, FUSED, NT>(row, a, s, boost, limit, trace, rs, staged, map, staged ? a.M : 0, a.fw)) {
+                if (!BATCH) return;
+                map_armed = map_cols == 0;   // the failed row left its map entries behind
+                map_whole = !map_armed;
+            }
         }
     }
 }
@@ -920,11 +1040,12 @@ struct SrcCluster {   // operand in the cluster's distributed shared memory
 };
 
 template <bool LOWER, typename T, typename TIN, typename TOUT>
-__global__ void __launch_bounds__(CLUSTER_THREADS)
-k_trsv_cluster(int n, const int32_t* __restrict__ list, const int32_t* __restrict__ Fpos,
-               const int64_t* __restrict__ Fp, const int64_t* __restrict__ Fdiag, const T* __restrict__ Fx,
-               const T* __restrict__ rinv_u, const int32_t* __restrict__ perm, const TIN* __restrict__ rhs,
-               TOUT* __restrict__ out, DevScal* s, long long limit, unsigned long long* __restrict__ trace) {
+__device__ __forceinline__ void trsv_cluster_body(int n, const int32_t* __restrict__ list,
+                                                  const int32_t* __restrict__ Fpos, const int64_t* __restrict__ Fp,
+                                                  const int64_t* __restrict__ Fdiag, const T* __restrict__ Fx,
+                                                  const T* __restrict__ rinv_u, const int32_t* __restrict__ perm,
+                                                  const TIN* __restrict__ rhs, TOUT* __restrict__ out, DevScal* s,
+                                                  long long limit, unsigned long long* __restrict__ trace) {
     extern __shared__ __align__(16) unsigned char cl_sh[];
     T* xs_cl = reinterpret_cast<T*>(cl_sh);
     cgx::cluster_group cluster = cgx::this_cluster();
@@ -963,6 +1084,38 @@ k_trsv_cluster(int n, const int32_t* __restrict__ list, const int32_t* __restric
         __syncwarp();
     }
     cluster.sync();   // no block may leave while others can still read its shared memory
+}
+
+template <bool LOWER, typename T, typename TIN, typename TOUT>
+__global__ void __launch_bounds__(CLUSTER_THREADS)
+k_trsv_cluster(int n, const int32_t* __restrict__ list, const int32_t* __restrict__ Fpos,
+               const int64_t* __restrict__ Fp, const int64_t* __restrict__ Fdiag, const T* __restrict__ Fx,
+               const T* __restrict__ rinv_u, const int32_t* __restrict__ perm, const TIN* __restrict__ rhs,
+               TOUT* __restrict__ out, DevScal* s, long long limit, unsigned long long* __restrict__ trace) {
+    trsv_cluster_body<LOWER, T, TIN, TOUT>(n, list, Fpos, Fp, Fdiag, Fx, rinv_u, perm, rhs, out, s, limit, trace);
+}
+
+// The backward sweep of a batch of instances, one cluster each (cluster
+// i = blocks [i C, (i + 1) C) of the grid runs instance i).
+struct SweepArgs {
+    int n;
+    const int32_t* list;
+    const int32_t* Fpos;
+    const int64_t* Fp;
+    const int64_t* Fdiag;
+    const double* Fx;
+    const double* rinv;
+    const int32_t* perm;
+    const double* rhs;
+    double* out;
+    DevScal* s;
+};
+
+__global__ void __launch_bounds__(CLUSTER_THREADS)
+k_usolve_cluster_batch(const SweepArgs* sa, long long limit) {
+    const SweepArgs& a = sa[blockIdx.x / cgx::this_cluster().num_blocks()];
+    trsv_cluster_body<false, double, double, double>(a.n, a.list, a.Fpos, a.Fp, a.Fdiag, a.Fx, a.rinv, a.perm, a.rhs,
+                                                     a.out, a.s, limit, nullptr);
 }
 
 // ---------------------------------------------------------------- self-test of bounded waits
@@ -1008,13 +1161,16 @@ __global__ void k_spmv(int n, const int32_t* __restrict__ Arp, const int32_t* __
 // r = b - K x, with ||r||^2, ||x||^2 and ||b||^2 reduced into s (rnorm,
 // xnorm, normb).  mode 0: also sets rnorm0 and the refine decision of the
 // initial solve; mode 1: cycle end (true residual of the formed x).
-__global__ void k_residual(int n, const int32_t* __restrict__ Arp, const int32_t* __restrict__ Aci,
-                           const double* __restrict__ Ax, const double* __restrict__ b,
-                           const double* __restrict__ x, double* __restrict__ r, double* part, DevScal* s) {
+// Block bx of nb (the sums depend only on nb and the block's rows, so a
+// batched launch gives the same bits as a lone one).
+__device__ __forceinline__ void residual_body(int n, const int32_t* __restrict__ Arp,
+                                              const int32_t* __restrict__ Aci, const double* __restrict__ Ax,
+                                              const double* __restrict__ b, const double* __restrict__ x,
+                                              double* __restrict__ r, double* part, DevScal* s, int bx, int nb) {
     __shared__ double sh[33];
-    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    const int64_t g = ((int64_t)bx * blockDim.x + threadIdx.x);
     const int sub = threadIdx.x & 7;
-    const int64_t rows_per_pass = ((int64_t)gridDim.x * blockDim.x) >> 3;
+    const int64_t rows_per_pass = ((int64_t)nb * blockDim.x) >> 3;
     double rr = 0.0, xx = 0.0, bb = 0.0;
     const int64_t first = g >> 3;
     const int64_t trips = (n + rows_per_pass - 1) / rows_per_pass;
@@ -1036,19 +1192,47 @@ __global__ void k_residual(int n, const int32_t* __restrict__ Arp, const int32_t
     xx = block_sum(xx, sh);
     bb = block_sum(bb, sh);
     if (threadIdx.x == 0) {
-        part[blockIdx.x * RED_SLOTS + 0] = rr;
-        part[blockIdx.x * RED_SLOTS + 1] = xx;
-        part[blockIdx.x * RED_SLOTS + 2] = bb;
+        part[bx * RED_SLOTS + 0] = rr;
+        part[bx * RED_SLOTS + 1] = xx;
+        part[bx * RED_SLOTS + 2] = bb;
     }
-    if (!last_block(s)) return;
-    rr = reduce_partials(part, 0, sh);
-    xx = reduce_partials(part, 1, sh);
-    bb = reduce_partials(part, 2, sh);
+    if (!last_block(s, (unsigned)nb)) return;
+    rr = reduce_partials(part, 0, sh, nb);
+    xx = reduce_partials(part, 1, sh, nb);
+    bb = reduce_partials(part, 2, sh, nb);
     if (threadIdx.x == 0) {
         s->rnorm = sqrt(rr);
         s->xnorm = sqrt(xx);
         s->normb = sqrt(bb);
     }
+}
+
+__global__ void k_residual(int n, const int32_t* __restrict__ Arp, const int32_t* __restrict__ Aci,
+                           const double* __restrict__ Ax, const double* __restrict__ b,
+                           const double* __restrict__ x, double* __restrict__ r, double* part, DevScal* s) {
+    residual_body(n, Arp, Aci, Ax, b, x, r, part, s, blockIdx.x, gridDim.x);
+}
+
+// The residual of a batch of instances: blockIdx.y = instance, its first
+// nb blocks of the x dimension take part.
+struct ResidualArgs {
+    int n, nb;
+    const int32_t* Arp;
+    const int32_t* Aci;
+    const double* Ax;
+    const double* b;
+    const double* x;
+    double* r;
+    double* part;
+    DevScal* s;
+    int stop_mode;
+    double refine_delta;
+};
+
+__global__ void k_residual_batch(const ResidualArgs* ra) {
+    const ResidualArgs& a = ra[blockIdx.y];
+    if ((int)blockIdx.x >= a.nb) return;
+    residual_body(a.n, a.Arp, a.Aci, a.Ax, a.b, a.x, a.r, a.part, a.s, blockIdx.x, a.nb);
 }
 
 // ---------------------------------------------------------------- K5-K7: FGMRES
@@ -1102,6 +1286,23 @@ __device__ void decide_rule(DevScal* s, int mode, double tol, int stop_mode, dou
         else if (stop_mode == KKT_STOP_NRBE && nrbe <= tol) s->done = 1;
         else if (stop_mode == KKT_STOP_RR && rr_met) s->done = 1;
     }
+}
+
+// The initial-solve decision (mode 0) of a batch of instances, one thread each.
+__global__ void k_decide_batch(const ResidualArgs* ra, int count, double tol) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    DevScal* s = ra[i].s;
+    if (s->err) { s->done = 1; return; }   // its refactorization failed: keep that error
+    const double rn = s->rnorm, xn = s->xnorm, bn = s->normb;
+    const double nrbe = (rn == 0.0) ? 0.0 : rn / (s->normA * xn + bn);
+    s->nrbe = nrbe;
+    if (!isfinite(rn) || !isfinite(xn)) {
+        s->err = KKT_ERR_NONFINITE;
+        s->done = 1;
+        return;
+    }
+    decide_rule(s, 0, tol, ra[i].stop_mode, ra[i].refine_delta, rn, bn, nrbe);
 }
 
 // x += d (Richardson correction)

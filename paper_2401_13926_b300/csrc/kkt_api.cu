@@ -5,9 +5,11 @@
 
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <numeric>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -37,7 +39,17 @@ struct kkt_ctx {
     // factor values and pivot reciprocals in the factor type: double, or
     // float with precision = KKT_PRECISION_MIXED
     void* d_Fx = nullptr;
-    void* d_rinv = nullptr;     // 1/u_ii of every row; tail rows publish it last
+    void* d_rinv = nullptr;     // 1/u_ii of every row; each row publishes it last
+    // mixed precision with the FP64 fallback (kkt_opts.mixed_fallback): FP64
+    // factors of the same layout, used after a fallback until the next
+    // refactorization
+    void* d_Fx64 = nullptr;
+    void* d_rinv64 = nullptr;
+    bool fallback_on = false;   // mixed and mixed_fallback > 0
+    bool fp64_active = false;   // the factors in use are the FP64 ones
+    bool vec_f32 = false;       // y and xp currently hold FP32 values (their SENTINEL type)
+    int last_fallback = 0;
+    int64_t fallbacks = 0;
     double *d_Ax = nullptr, *d_vals = nullptr;
     bool mixed = false;
     unsigned long long* solve_trace = nullptr;   // kkt_trace_solve only: 2n publish stamps
@@ -96,11 +108,25 @@ struct kkt_ctx {
 
 namespace {
 
+// The factors in use: FP32 in mixed precision until a fallback, FP64
+// otherwise (the context's only factors, or the fallback's).
+bool use_f32(const kkt_ctx* c) { return c->mixed && !c->fp64_active; }
+template <typename T> T* fx_of(kkt_ctx* c);
+template <> float* fx_of<float>(kkt_ctx* c) { return (float*)c->d_Fx; }
+template <> double* fx_of<double>(kkt_ctx* c) { return (double*)(c->mixed ? c->d_Fx64 : c->d_Fx); }
+template <typename T> T* rinv_of(kkt_ctx* c);
+template <> float* rinv_of<float>(kkt_ctx* c) { return (float*)c->d_rinv; }
+template <> double* rinv_of<double>(kkt_ctx* c) { return (double*)(c->mixed ? c->d_rinv64 : c->d_rinv); }
+// bytes of a factor value as laid out for the refactorization and the
+// cluster solve (a context that may fall back to FP64 is laid out for FP64)
+size_t layout_vsize(const kkt_ctx* c) { return (c->mixed && !c->fallback_on) ? sizeof(float) : sizeof(double); }
+
 constexpr int PERSIST_THREADS = 256;
 constexpr int CHAIN_THREADS = 1024;
 constexpr size_t TAIL_SMEM_MAX = 200 * 1024;   // shared memory of a cluster-solve block
 constexpr int REF_MAP_COLS = 16384;      // columns with an O(1) position map in block rows
 constexpr size_t REF_SMEM_WIDE = 113 * 1024;   // blocks above this run 512 threads (one block per SM)
+constexpr int64_t DEFAULT_WARP_ROW_UPDATES = INT64_MAX;   // the default limit of a warp row's multiply-adds
 constexpr int CHAIN_MAX = 12288;       // rows of a chain (8 bytes of shared memory each)
 constexpr int CHAIN_WIDTH = 32;        // a level belongs to the chain if it has at most this many rows
 
@@ -136,6 +162,11 @@ int cuda_fail(kkt_ctx* c, cudaError_t e, const char* what) {
     if (c) c->detail = std::string(what) + ": " + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? KKT_ERR_OOM : KKT_ERR_CUDA;
 }
+#define CK_BT(call)                                                                  \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) return e_ == cudaErrorMemoryAllocation ? KKT_ERR_OOM : KKT_ERR_CUDA; \
+    } while (0)
 #define CK(call)                                             \
     do {                                                     \
         cudaError_t e_ = (call);                             \
@@ -300,8 +331,8 @@ cudaError_t launch_cluster(kkt_ctx* c, const int32_t* perm, const TIN* rhs, TOUT
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kkt::k_trsv_cluster<LOWER, T, TIN, TOUT>, c->A.n,
                               (const int32_t*)(LOWER ? c->d_listL : c->d_listU), (const int32_t*)c->d_Fpos,
-                              (const int64_t*)c->d_Fp, (const int64_t*)c->d_Fdiag, (const T*)c->d_Fx,
-                              (const T*)c->d_rinv, perm, rhs, out, c->d_s, spin(c),
+                              (const int64_t*)c->d_Fp, (const int64_t*)c->d_Fdiag, (const T*)fx_of<T>(c),
+                              (const T*)rinv_of<T>(c), perm, rhs, out, c->d_s, spin(c),
                               c->solve_trace ? c->solve_trace + (LOWER ? 0 : c->A.n) : nullptr);
 }
 
@@ -319,12 +350,13 @@ void cluster_attributes(int C) {
 
 int pick_cluster(kkt_ctx* c) {
     const int n = c->A.n;
-    const size_t vsize = c->mixed ? sizeof(float) : sizeof(double);
+    const size_t vsize = layout_vsize(c);
     for (int C : {16, 8}) {
         if (c->o.cluster_blocks && C != c->o.cluster_blocks) continue;
         size_t per_block = (size_t)((n + 32 * C - 1) / (32 * C)) * 32 * vsize;
         if (per_block > TAIL_SMEM_MAX) continue;
-        if (c->mixed) cluster_attributes<float>(C); else cluster_attributes<double>(C);
+        if (c->mixed) cluster_attributes<float>(C);
+        if (vsize == sizeof(double)) cluster_attributes<double>(C);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(C, 1, 1);
         cfg.blockDim = dim3(kkt::CLUSTER_THREADS, 1, 1);
@@ -337,8 +369,8 @@ int pick_cluster(kkt_ctx* c) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int active = 0;
-        const void* probe = c->mixed ? (const void*)kkt::k_trsv_cluster<true, float, double, float>
-                                     : (const void*)kkt::k_trsv_cluster<true, double, double, double>;
+        const void* probe = vsize == sizeof(float) ? (const void*)kkt::k_trsv_cluster<true, float, double, float>
+                                                   : (const void*)kkt::k_trsv_cluster<true, double, double, double>;
         if (cudaOccupancyMaxActiveClusters(&active, probe, &cfg) != cudaSuccess) {
             cudaGetLastError();
             continue;
@@ -357,7 +389,8 @@ template <typename T>
 void lu_apply_t(kkt_ctx* c, const double* rhs, double* out) {
     T* y = (T*)c->d_y;
     T* xp = (T*)c->d_xp;
-    const T* Fx = (const T*)c->d_Fx;
+    const T* Fx = fx_of<T>(c);
+    const T* rinv = rinv_of<T>(c);
     if (c->cluster) {
         int t = phase_begin(c, KKT_PHASE_LSOLVE);
         launch_cluster<true, T, double, T>(c, c->d_P, rhs, y);
@@ -388,13 +421,13 @@ void lu_apply_t(kkt_ctx* c, const double* rhs, double* out) {
     t = phase_begin(c, KKT_PHASE_USOLVE);
     if (c->nUc) {
         kkt::k_usolve_chain<T><<<1, CHAIN_THREADS, sizeof(T) * c->nUc, c->stream>>>(
-            c->nUc, c->d_listU, c->d_Fpos, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, (const T*)c->d_rinv, c->d_Q, y, xp, out,
+            c->nUc, c->d_listU, c->d_Fpos, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, c->d_Q, y, xp, out,
             c->d_s, spin(c));
         c->launches += 1;
     }
     if (nUb) {
         kkt::k_usolve_bulk<T><<<grid_for(c, nUb), PERSIST_THREADS, 0, c->stream>>>(
-            nUb, c->d_listU + c->nUc, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, (const T*)c->d_rinv, c->d_Q, y, xp, out,
+            nUb, c->d_listU + c->nUc, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, c->d_Q, y, xp, out,
             c->d_s, spin(c));
         c->launches += 1;
     }
@@ -402,7 +435,7 @@ void lu_apply_t(kkt_ctx* c, const double* rhs, double* out) {
 }
 
 void lu_apply(kkt_ctx* c, const double* rhs, double* out) {
-    if (c->mixed) lu_apply_t<float>(c, rhs, out);
+    if (use_f32(c)) lu_apply_t<float>(c, rhs, out);
     else lu_apply_t<double>(c, rhs, out);
 }
 
@@ -411,7 +444,8 @@ template <typename T>
 void u_apply_t(kkt_ctx* c, double* out) {
     T* y = (T*)c->d_y;
     T* xp = (T*)c->d_xp;
-    const T* Fx = (const T*)c->d_Fx;
+    const T* Fx = fx_of<T>(c);
+    const T* rinv = rinv_of<T>(c);
     int t = phase_begin(c, KKT_PHASE_USOLVE);
     if (c->cluster) {
         launch_cluster<false, T, T, double>(c, c->d_Q, y, out);
@@ -425,13 +459,13 @@ void u_apply_t(kkt_ctx* c, double* out) {
     c->launches += 1;
     if (c->nUc) {
         kkt::k_usolve_chain<T><<<1, CHAIN_THREADS, sizeof(T) * c->nUc, c->stream>>>(
-            c->nUc, c->d_listU, c->d_Fpos, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, (const T*)c->d_rinv, c->d_Q, y, xp, out,
+            c->nUc, c->d_listU, c->d_Fpos, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, c->d_Q, y, xp, out,
             c->d_s, spin(c));
         c->launches += 1;
     }
     if (nUb) {
         kkt::k_usolve_bulk<T><<<grid_for(c, nUb), PERSIST_THREADS, 0, c->stream>>>(
-            nUb, c->d_listU + c->nUc, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, (const T*)c->d_rinv, c->d_Q, y, xp, out,
+            nUb, c->d_listU + c->nUc, c->d_Fp, c->d_Fj, c->d_Fdiag, Fx, rinv, c->d_Q, y, xp, out,
             c->d_s, spin(c));
         c->launches += 1;
     }
@@ -439,13 +473,25 @@ void u_apply_t(kkt_ctx* c, double* out) {
 }
 
 void u_apply(kkt_ctx* c, double* out) {
-    if (c->mixed) u_apply_t<float>(c, out);
+    if (use_f32(c)) u_apply_t<float>(c, out);
     else u_apply_t<double>(c, out);
 }
 
 void fill_y_sentinel(kkt_ctx* c) {
-    if (c->mixed) kkt::k_fill_sentinel<float><<<64, 256, 0, c->stream>>>((float*)c->d_y, c->A.n);
+    if (use_f32(c)) kkt::k_fill_sentinel<float><<<64, 256, 0, c->stream>>>((float*)c->d_y, c->A.n);
     else kkt::k_fill_sentinel<double><<<64, 256, 0, c->stream>>>(c->d_y, c->A.n);
+}
+
+// y and xp hold SENTINEL of the factor type in use wherever a sweep has not
+// written them; when that type changes (FP32 <-> the FP64 fallback) both
+// are re-armed in the new type.
+void arm_vectors(kkt_ctx* c) {
+    if (c->vec_f32 == use_f32(c)) return;
+    c->vec_f32 = use_f32(c);
+    fill_y_sentinel(c);
+    if (c->vec_f32) kkt::k_fill_sentinel<float><<<64, 256, 0, c->stream>>>((float*)c->d_xp, c->A.n);
+    else kkt::k_fill_sentinel<double><<<64, 256, 0, c->stream>>>(c->d_xp, c->A.n);
+    c->launches += 2;
 }
 
 // After a failed solve some values may still be live: re-arm the L-solve's
@@ -490,6 +536,7 @@ void kkt_default_opts(kkt_opts* o) {
     o->graphs = 0;
     o->warp_rows = 1;
     o->row_order = 1;
+    o->mixed_fallback = 2;
 }
 
 const char* kkt_strerror(int code) {
@@ -525,7 +572,7 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
         c->o.ortho < KKT_ORTHO_CGS2 || c->o.ortho > KKT_ORTHO_CGS1_PYTH ||
         !(c->o.inner_tol > 0.0 && c->o.inner_tol <= 1.0) || (c->o.repivot != 0 && c->o.repivot != 1) ||
         (c->o.graphs != 0 && c->o.graphs != 1) || (c->o.warp_rows != 0 && c->o.warp_rows != 1) ||
-        (c->o.row_order != 0 && c->o.row_order != 1)) {
+        (c->o.row_order != 0 && c->o.row_order != 1) || c->o.mixed_fallback < 0 || c->o.warp_row_updates < -1) {
         delete c;
         return KKT_ERR_INVALID;
     }
@@ -541,6 +588,7 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
     }
     if (e != cudaSuccess) { delete c; return KKT_ERR_CUDA; }
     c->mixed = c->o.precision == KKT_PRECISION_MIXED;
+    c->fallback_on = c->mixed && c->o.mixed_fallback > 0;
     int per_sm = 0, per_sm3 = 0;
     if (c->mixed) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kkt::k_lsolve_bulk<float>, PERSIST_THREADS, 0);
@@ -554,14 +602,16 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * CHAIN_MAX));
     cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev);
     c->smem_optin -= 1024;   // room for the kernel's static shared memory
-    for (const void* fn : {(const void*)kkt::k_refactor_rows<double, false, 256>,
-                           (const void*)kkt::k_refactor_rows<double, true, 256>,
-                           (const void*)kkt::k_refactor_rows<double, false, 512>,
-                           (const void*)kkt::k_refactor_rows<double, true, 512>,
-                           (const void*)kkt::k_refactor_rows<float, false, 256>,
-                           (const void*)kkt::k_refactor_rows<float, true, 256>,
-                           (const void*)kkt::k_refactor_rows<float, false, 512>,
-                           (const void*)kkt::k_refactor_rows<float, true, 512>})
+    for (const void* fn : {(const void*)kkt::k_refactor_rows<double, false, 256, false>,
+                           (const void*)kkt::k_refactor_rows<double, true, 256, false>,
+                           (const void*)kkt::k_refactor_rows<double, false, 512, false>,
+                           (const void*)kkt::k_refactor_rows<double, true, 512, false>,
+                           (const void*)kkt::k_refactor_rows<float, false, 256, false>,
+                           (const void*)kkt::k_refactor_rows<float, true, 256, false>,
+                           (const void*)kkt::k_refactor_rows<float, false, 512, false>,
+                           (const void*)kkt::k_refactor_rows<float, true, 512, false>,
+                           (const void*)kkt::k_refactor_rows<double, true, 256, true>,
+                           (const void*)kkt::k_refactor_rows<double, true, 512, true>})
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_optin);
     cudaGetLastError();
     per_sm = std::max(1, std::min(per_sm, per_sm3));
@@ -620,8 +670,9 @@ namespace {
 // Placement and dispatch order of the refactorization's rows
 // (k_refactor_rows).  A row's working set -- step descriptors (12 bytes per
 // L entry), values and columns -- decides where it runs: one per warp if it
-// fits a warp's slice of the block's work area, one per block if it fits
-// the area, else one per block with its values in global scratch.  The
+// fits a warp's slice of the block's shared memory, one per block if it
+// fits the work area after the position map, else one per block with its
+// values in global scratch.  The
 // block's shared memory is the position map of the last REF_MAP_COLS
 // columns plus the area; by default it is sized for the longest row (so no
 // row needs global scratch) up to the device's limit, dropping the map if
@@ -635,7 +686,7 @@ int setup_rows(kkt_ctx* c) {
     c->d_gdk = c->d_gsdoff = c->d_gwoff = nullptr;
     c->d_gcnt = nullptr;
     c->d_gw = nullptr;
-    const size_t vsize = c->mixed ? sizeof(float) : sizeof(double);
+    const size_t vsize = layout_vsize(c);
     auto need = [&](int32_t i) -> size_t {
         const int64_t st = L.Fdiag[i] - L.Fp[i], len = L.Fp[i + 1] - L.Fp[i];
         return (12 * (size_t)st + (vsize + 4) * (size_t)len + 15) & ~(size_t)15;
@@ -663,12 +714,22 @@ int setup_rows(kkt_ctx* c) {
     c->ref_map_bytes = map_bytes;
     c->ref_area = S - map_bytes;
     const int nw = c->ref_threads / 32;
-    const size_t slice = (c->ref_area / nw) & ~(size_t)15;
+    const size_t slice = (S / nw) & ~(size_t)15;   // warp slices span the map's room too
     std::vector<uint8_t> kind((size_t)n);
     c->rows_warp = c->rows_block = c->rows_global = 0;
+    // a warp row's steps run one after another on 32 lanes: rows with much
+    // work (the dense end, on the critical path) go one per block even when
+    // they fit a slice
+    const int64_t wmax = c->o.warp_row_updates < 0 ? INT64_MAX
+                       : c->o.warp_row_updates == 0 ? DEFAULT_WARP_ROW_UPDATES : c->o.warp_row_updates;
     for (int32_t i = 0; i < n; i++) {
         const size_t q = need(i);
-        if (c->o.warp_rows && q <= slice) { kind[i] = kkt::ROW_WARP; c->rows_warp++; }
+        int64_t upd = 0;
+        for (int64_t p = L.Fp[i]; p < L.Fdiag[i] && upd <= wmax; p++) {
+            const int32_t k = L.Fj[p];
+            upd += L.Fp[k + 1] - L.Fdiag[k] - 1;
+        }
+        if (c->o.warp_rows && q <= slice && upd <= wmax) { kind[i] = kkt::ROW_WARP; c->rows_warp++; }
         else if (q <= c->ref_area) { kind[i] = kkt::ROW_BLOCK; c->rows_block++; }
         else { kind[i] = kkt::ROW_GLOBAL; c->rows_global++; }
     }
@@ -736,13 +797,18 @@ int setup_rows(kkt_ctx* c) {
     }
     CK(cudaStreamSynchronize(c->stream));   // the host vectors are locals
     int per_sm = 1 << 30;
-    const void* fns[2];
-    if (c->ref_threads == 512) {
-        fns[0] = c->mixed ? (const void*)kkt::k_refactor_rows<float, false, 512> : (const void*)kkt::k_refactor_rows<double, false, 512>;
-        fns[1] = c->mixed ? (const void*)kkt::k_refactor_rows<float, true, 512> : (const void*)kkt::k_refactor_rows<double, true, 512>;
-    } else {
-        fns[0] = c->mixed ? (const void*)kkt::k_refactor_rows<float, false, 256> : (const void*)kkt::k_refactor_rows<double, false, 256>;
-        fns[1] = c->mixed ? (const void*)kkt::k_refactor_rows<float, true, 256> : (const void*)kkt::k_refactor_rows<double, true, 256>;
+    std::vector<const void*> fns;
+    if (c->mixed) {
+        fns.push_back(c->ref_threads == 512 ? (const void*)kkt::k_refactor_rows<float, false, 512, false>
+                                            : (const void*)kkt::k_refactor_rows<float, false, 256, false>);
+        fns.push_back(c->ref_threads == 512 ? (const void*)kkt::k_refactor_rows<float, true, 512, false>
+                                            : (const void*)kkt::k_refactor_rows<float, true, 256, false>);
+    }
+    if (!c->mixed || c->fallback_on) {
+        fns.push_back(c->ref_threads == 512 ? (const void*)kkt::k_refactor_rows<double, false, 512, false>
+                                            : (const void*)kkt::k_refactor_rows<double, false, 256, false>);
+        fns.push_back(c->ref_threads == 512 ? (const void*)kkt::k_refactor_rows<double, true, 512, false>
+                                            : (const void*)kkt::k_refactor_rows<double, true, 256, false>);
     }
     for (const void* fn : fns) {   // the grid is sized for the instantiation with fewer resident blocks
         int bl = 0;
@@ -833,6 +899,14 @@ int setup_from_layout(kkt_ctx* c, std::chrono::steady_clock::time_point t0) {
         if ((rc = dalloc(c, &ri, (size_t)n))) return rc;
         c->d_Fx = fx;
         c->d_rinv = ri;
+        c->d_Fx64 = c->d_rinv64 = nullptr;
+        if (c->fallback_on) {
+            double *fx64 = nullptr, *ri64 = nullptr;
+            if ((rc = dalloc(c, &fx64, nnzF))) return rc;
+            if ((rc = dalloc(c, &ri64, (size_t)n))) return rc;
+            c->d_Fx64 = fx64;
+            c->d_rinv64 = ri64;
+        }
     } else {
         double *fx = nullptr, *ri = nullptr;
         if ((rc = dalloc(c, &fx, nnzF))) return rc;
@@ -864,6 +938,8 @@ int setup_from_layout(kkt_ctx* c, std::chrono::steady_clock::time_point t0) {
         if ((rc = upload(c, &c->d_listU, listU))) return rc;
         if ((rc = upload(c, &c->d_Fpos, fpos))) return rc;
     }
+    c->fp64_active = false;
+    c->vec_f32 = use_f32(c);
     fill_y_sentinel(c);
     if (c->o.trisolve == KKT_TRSV_AUTO) pick_cluster(c);
     else c->cluster = 0;
@@ -938,8 +1014,52 @@ int kkt_host_analyze(int32_t n, const int32_t* rowptr, const int32_t* colind, co
         st->refactor_updates = lay.updates;
         st->order_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
         st->pivot_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
+        st->canonical_order = A.identity_src ? 1 : 0;
     }
     return KKT_OK;
+}
+
+int kkt_estimate_device_bytes(int32_t n, int64_t nnz_a, const kkt_host_stats* st, const kkt_opts* o,
+                              int canonical_order, int64_t* bytes) {
+    if (!st || !bytes || n < 1 || nnz_a < 0) return KKT_ERR_INVALID;
+    kkt_opts d;
+    if (!o) { kkt_default_opts(&d); o = &d; }
+    // every dalloc / upload of setup_from_layout, in order
+    auto sz = [](int64_t count, int64_t elem) { return std::max<int64_t>(count, 1) * elem; };
+    const int64_t nnzF = st->nnz_l + st->nnz_u;
+    const int64_t ld = ((int64_t)n + 31) / 32 * 32;
+    const bool mixed = o->precision == KKT_PRECISION_MIXED;
+    int64_t b = 0;
+    b += sz(n + 1, 8) + sz(n, 8) + sz(nnzF, 4) + sz(nnzF, 8);            // Fp, Fdiag, Fj, fsrc
+    if (!canonical_order) b += sz(nnz_a, 8);                                // asrc
+    b += sz(n + 1, 4) + sz(nnz_a, 4) + sz(n, 4) + sz(n, 4);               // Arp, Aci, P, Q
+    if (mixed) {
+        b += sz(nnzF, 4) + sz(n, 4);                                        // Fx, rinv (FP32)
+        if (o->mixed_fallback > 0) b += sz(nnzF, 8) + sz(n, 8);            // the FP64 fallback's
+    } else {
+        b += sz(nnzF, 8) + sz(n, 8);
+    }
+    b += 2 * sz(nnz_a, 8);                                                  // Ax, vals
+    b += 6 * sz(ld, 8);                                                     // b, x, y, xp, r, w
+    b += sz(ld * (o->restart + 1), 8) + sz(ld * o->restart, 8);             // V, Z
+    b += sz((int64_t)kkt::RED_BLOCKS * kkt::RED_SLOTS, 8) + sz(n, 4);       // part, done flags
+    b += 2 * sz(n, 4) + sz(nnzF, 4);                                        // listL, listU, Fpos
+    b += sz(n, 4) + sz(n, (int64_t)sizeof(kkt::RefItem));                  // order, items
+    b += sz(1, (int64_t)sizeof(DevScal));
+    *bytes = b;
+    return KKT_OK;
+}
+
+int kkt_place_instance(int ndev, const int64_t* budget, const int64_t* held, int64_t need) {
+    if (ndev < 1 || !budget || !held || need < 0) return -1;
+    int best = -1;
+    int64_t best_left = 0;
+    for (int i = 0; i < ndev; i++) {
+        if (need > budget[i]) continue;   // can never fit this device
+        const int64_t left = budget[i] - held[i];
+        if (best < 0 || left > best_left) { best = i; best_left = left; }
+    }
+    return best;
 }
 
 int kkt_trace_critical_path(kkt_ctx* c, const int64_t* t_start, const int64_t* t_publish, double* path_ns,
@@ -1053,23 +1173,26 @@ void refactor_rows_launch(kkt_ctx* c, const double* vals, unsigned long long* tr
     a.Fp = c->d_Fp;
     a.Fj = c->d_Fj;
     a.Fdiag = c->d_Fdiag;
-    a.Fx = (T*)c->d_Fx;
-    a.rinv = (T*)c->d_rinv;
+    a.Fx = fx_of<T>(c);
+    a.rinv = rinv_of<T>(c);
     a.vals = vals;
     a.fsrc = c->d_fsrc;
     a.M = c->ref_map_cols;
     a.mlo = c->A.n - c->ref_map_cols;
     a.map_bytes = (int)c->ref_map_bytes;
     a.area_bytes = (int)c->ref_area;
+    a.slice_bytes = (int)((c->ref_smem / (c->ref_threads / 32)) & ~(size_t)15);
     a.gdk = c->d_gdk;
     a.gcnt = c->d_gcnt;
     a.g_sd_off = c->d_gsdoff;
     a.gw = (T*)c->d_gw;
     a.g_w_off = c->d_gwoff;
-    const kkt::FwdArgs<T> fw{fused_rhs, c->d_P, (T*)c->d_y, (T*)c->d_xp};
+    a.s = c->d_s;
+    a.fw = kkt::FwdArgs<T>{fused_rhs, c->d_P, (T*)c->d_y, (T*)c->d_xp};
+    a.boost_eps = c->o.boost_eps;
     const int blocks = std::max(1, std::min(c->nitems, c->ref_blocks));
-    auto kern = fused_rhs ? kkt::k_refactor_rows<T, true, NT> : kkt::k_refactor_rows<T, false, NT>;
-    kern<<<blocks, NT, c->ref_smem, c->stream>>>(a, c->d_s, c->o.boost_eps, spin(c), trace, fw);
+    auto kern = fused_rhs ? kkt::k_refactor_rows<T, true, NT, false> : kkt::k_refactor_rows<T, false, NT, false>;
+    kern<<<blocks, NT, c->ref_smem, c->stream>>>(a, kkt::RefBatch<T>{}, spin(c), trace);
 }
 
 template <typename T>
@@ -1077,8 +1200,8 @@ void refactor_launch(kkt_ctx* c, const double* vals, unsigned long long* trace, 
     const int n = c->A.n;
     const int64_t nnzF = (int64_t)c->lay.Fj.size();
     int t = phase_begin(c, KKT_PHASE_GATHER);
-    kkt::k_gather<T><<<2 * c->num_sms, 256, 0, c->stream>>>(vals, nnzF, (T*)c->d_Fx, c->d_Arp, c->d_asrc, c->d_Ax,
-                                                            n, (T*)c->d_rinv, c->d_s,
+    kkt::k_gather<T><<<2 * c->num_sms, 256, 0, c->stream>>>(vals, nnzF, fx_of<T>(c), c->d_Arp, c->d_asrc, c->d_Ax,
+                                                            n, rinv_of<T>(c), c->d_s,
                                                             fused_rhs ? (T*)c->d_y : nullptr);
     phase_end(c, t);
     t = phase_begin(c, KKT_PHASE_REFACTOR);
@@ -1110,6 +1233,35 @@ int build_refactor_graph(kkt_ctx* c) {
     return KKT_OK;
 }
 
+// The FP64 refactorization of a mixed-precision context (the fallback):
+// the same kernels on the same values into the FP64 factor arrays, which
+// the solves use until the next refactorization.
+int refactor_fp64(kkt_ctx* c, const double* vals, const double* fused_rhs) {
+    c->fp64_active = true;
+    arm_vectors(c);
+    kkt::k_refactor_prep<<<1, 1, 0, c->stream>>>(c->d_s);
+    refactor_launch<double>(c, vals, nullptr, fused_rhs);
+    CK(cudaGetLastError());
+    int rc = read_scalars(c);
+    if (rc) return rc;
+    c->nboost = c->h_s->nboost;
+    c->norm_a = c->h_s->normA;
+    if ((rc = device_error(c))) return rc;
+    c->last_fallback = 1;
+    c->fallbacks++;
+    return KKT_OK;
+}
+
+// Fallback during a solve: the caller's values are rebuilt from the
+// canonical copy the gather made (so kkt_solve needs no values argument),
+// then refactor_fp64.
+int fallback_from_solve(kkt_ctx* c) {
+    const int64_t nnz = c->nnz_a;
+    kkt::k_scatter_values<<<2 * c->num_sms, 256, 0, c->stream>>>(nnz, c->d_Ax, c->d_asrc, c->d_vals);
+    c->launches += 1;
+    return refactor_fp64(c, c->d_vals, nullptr);
+}
+
 int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsigned long long* trace,
                   const double* fused_rhs) {
     int rc = check_ctx(c, false);
@@ -1117,6 +1269,9 @@ int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsign
     if (!values) return KKT_ERR_INVALID;
     c->factored = false;
     c->y_fused = false;
+    c->fp64_active = false;   // a new matrix starts in the context's own precision
+    c->last_fallback = 0;
+    arm_vectors(c);
     const double* vals = values;
     const bool graphs = c->o.graphs && !trace && !fused_rhs;
     if (!values_on_device) {
@@ -1143,7 +1298,12 @@ int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsign
     if ((rc = read_scalars(c))) return rc;
     c->nboost = c->h_s->nboost;
     c->norm_a = c->h_s->normA;
-    if ((rc = device_error(c))) return rc;
+    if ((rc = device_error(c))) {
+        // an FP32 refactorization that meets a zero pivot or a non-finite
+        // value falls back to FP64 on the same values
+        if (!(c->fallback_on && (rc == KKT_ERR_ZERO_PIVOT || rc == KKT_ERR_NONFINITE))) return rc;
+        if ((rc = refactor_fp64(c, vals, fused_rhs))) return rc;
+    }
     c->factored = true;
     c->y_fused = fused_rhs != nullptr;
     return KKT_OK;
@@ -1553,7 +1713,8 @@ int solve_impl(kkt_ctx* c, const double* b, double* x, int on_device, double tol
     if (!b || !x || !(tol > 0)) return KKT_ERR_INVALID;
     const int n = c->A.n;
     const int m = c->m;
-    const bool graphs = c->o.graphs != 0;
+    // mixed precision with the FP64 fallback runs its refinement from the host
+    const bool graphs = c->o.graphs != 0 && !c->fallback_on;
     const bool y_ready = fused && c->y_fused && !graphs;
     c->y_fused = false;   // y is consumed by this solve
     const double* bd = b;
@@ -1585,10 +1746,32 @@ int solve_impl(kkt_ctx* c, const double* b, double* x, int on_device, double tol
         if ((rc = device_error(c))) { rearm(c); return rc; }
         if (c->h_s->not_converged) status = KKT_ERR_NOT_CONVERGED;
     } else {
-        seq_prologue(c, bd, xd, tol, 0, y_ready);
+        // Mixed precision with the FP64 fallback (Section 2.1's inexact
+        // factors, with a rule for when they are too inexact): the FP32
+        // preconditioner gets kkt_opts.mixed_fallback restart cycles; if the
+        // solve has not converged by then, the matrix is refactored in FP64
+        // and FGMRES continues from the current x with the FP64 factors and a
+        // budget of max_cycles more cycles; if the FP32 phase meets a zero
+        // pivot or a non-finite value, the solve restarts from x0 in FP64.
+        const bool fb = c->fallback_on && method != KKT_METHOD_RICHARDSON;
+        bool ready = y_ready;
+        int base = 0;        // cycles before the FP64 phase
+        int iters_acc = 0;   // Arnoldi steps of an abandoned FP32 attempt
+        auto fp32_failed = [&](int code) {
+            return fb && use_f32(c) && (code == KKT_ERR_NONFINITE || code == KKT_ERR_ZERO_PIVOT);
+        };
+    restart:
+        seq_prologue(c, bd, xd, tol, 0, ready);
         CK(cudaGetLastError());
         if ((rc = read_scalars(c))) return rc;
-        if ((rc = device_error(c))) { rearm(c); return rc; }
+        if ((rc = device_error(c))) {
+            rearm(c);
+            if (!fp32_failed(rc)) return rc;
+            if ((rc = fallback_from_solve(c))) return rc;
+            ready = false;
+            base = cycles;
+            goto restart;
+        }
         const int64_t max_steps = (int64_t)c->o.max_cycles * m;
         int64_t steps = 0;
         while (method == KKT_METHOD_RICHARDSON && !c->h_s->done) {
@@ -1600,7 +1783,11 @@ int solve_impl(kkt_ctx* c, const double* b, double* x, int on_device, double tol
             if ((rc = device_error(c))) return rc;
         }
         while (method != KKT_METHOD_RICHARDSON && !c->h_s->done) {
-            if (cycles >= c->o.max_cycles) { status = KKT_ERR_NOT_CONVERGED; break; }
+            if (fb && use_f32(c) && cycles - base >= std::min(c->o.mixed_fallback, c->o.max_cycles)) {
+                if ((rc = fallback_from_solve(c))) return rc;
+                base = cycles;
+            }
+            if (cycles - base >= c->o.max_cycles) { status = KKT_ERR_NOT_CONVERGED; break; }
             cycles++;
             seq_cycle_begin(c, tol, 0);
             for (int j = 0; j < m; j++) {
@@ -1613,8 +1800,17 @@ int solve_impl(kkt_ctx* c, const double* b, double* x, int on_device, double tol
             seq_cycle_end(c, bd, xd, tol, 0);
             CK(cudaGetLastError());
             if ((rc = read_scalars(c))) return rc;
-            if ((rc = device_error(c))) return rc;
+            if ((rc = device_error(c))) {
+                rearm(c);
+                if (!fp32_failed(rc)) return rc;
+                iters_acc += c->h_s->iters;
+                if ((rc = fallback_from_solve(c))) return rc;
+                ready = false;
+                base = cycles;
+                goto restart;
+            }
         }
+        c->h_s->iters += iters_acc;
     }
     if (!on_device) {
         CK(cudaMemcpyAsync(x, c->d_x, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
@@ -1657,13 +1853,14 @@ int kkt_get_factors(kkt_ctx* c, int64_t* Lp, int32_t* Li, double* Lx, int64_t* U
     const int n = c->A.n;
     const auto& L = c->lay;
     std::vector<double> fx(L.Fj.size());
-    if (c->mixed) {
+    if (use_f32(c)) {
         std::vector<float> f32(L.Fj.size());
         CK(cudaMemcpyAsync(f32.data(), c->d_Fx, sizeof(float) * f32.size(), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         for (size_t i = 0; i < f32.size(); i++) fx[i] = (double)f32[i];
     } else {
-        CK(cudaMemcpyAsync(fx.data(), c->d_Fx, sizeof(double) * fx.size(), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(fx.data(), fx_of<double>(c), sizeof(double) * fx.size(), cudaMemcpyDeviceToHost,
+                           c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
     std::fill(Lp, Lp + n + 1, 0);
@@ -1711,6 +1908,8 @@ int kkt_query(kkt_ctx* c, kkt_info* info) {
     info->refactor_smem = (int32_t)c->ref_smem;
     info->refactor_threads = c->ref_threads;
     info->refactor_blocks = c->ref_blocks;
+    info->last_fallback = c->last_fallback;
+    info->fallbacks = c->fallbacks;
     return KKT_OK;
 }
 
@@ -1747,4 +1946,334 @@ int kkt_get_phase_times(kkt_ctx* c, double* ms, int64_t* counts, int reset) {
     return KKT_OK;
 }
 
+
 }  // extern "C"
+
+// ---------------------------------------------------------------- batched steps
+struct kkt_batch {
+    int dev = 0, max_count = 0, num_sms = 0, smem_optin = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done_ev = nullptr;
+    std::vector<cudaEvent_t> ready_ev;
+    kkt::RefArgs<double>* d_ref = nullptr;
+    kkt::GatherArgs* d_gather = nullptr;
+    kkt::SweepArgs* d_sweep = nullptr;
+    kkt::ResidualArgs* d_res = nullptr;
+    unsigned long long* d_ticket = nullptr;
+    kkt::RefArgs<double>* h_ref = nullptr;   // pinned mirrors
+    kkt::GatherArgs* h_gather = nullptr;
+    kkt::SweepArgs* h_sweep = nullptr;
+    kkt::ResidualArgs* h_res = nullptr;
+    int64_t launches = 0;
+    std::mutex mu;   // one kkt_batch_step at a time
+};
+
+namespace {
+void batch_free(kkt_batch* bt) {
+    cudaSetDevice(bt->dev);
+    for (void* p : {(void*)bt->d_ref, (void*)bt->d_gather, (void*)bt->d_sweep, (void*)bt->d_res, (void*)bt->d_ticket})
+        if (p) cudaFree(p);
+    for (void* p : {(void*)bt->h_ref, (void*)bt->h_gather, (void*)bt->h_sweep, (void*)bt->h_res})
+        if (p) cudaFreeHost(p);
+    for (cudaEvent_t e : bt->ready_ev) if (e) cudaEventDestroy(e);
+    if (bt->done_ev) cudaEventDestroy(bt->done_ev);
+    if (bt->stream) cudaStreamDestroy(bt->stream);
+}
+
+// The refinement after the prologue (x0, its residual and the decision
+// are in place): the loops of solve_impl for an FP64 context, host-driven
+// on the context's stream.  Returns the status; *cycles gets the cycles.
+int refine_after_prologue(kkt_ctx* c, const double* bd, double* xd, double tol, int* cycles_out) {
+    int rc = KKT_OK, status = KKT_OK, cycles = 0;
+    const int method = c->o.method, m = c->m;
+    const int64_t max_steps = (int64_t)c->o.max_cycles * m;
+    int64_t steps = 0;
+    while (method == KKT_METHOD_RICHARDSON && !c->h_s->done) {
+        if (steps >= max_steps) { status = KKT_ERR_NOT_CONVERGED; break; }
+        steps++;
+        seq_richardson(c, bd, xd, tol, 0);
+        CK(cudaGetLastError());
+        if ((rc = read_scalars(c))) return rc;
+        if ((rc = device_error(c))) return rc;
+    }
+    while (method != KKT_METHOD_RICHARDSON && !c->h_s->done) {
+        if (cycles >= c->o.max_cycles) { status = KKT_ERR_NOT_CONVERGED; break; }
+        cycles++;
+        seq_cycle_begin(c, tol, 0);
+        for (int j = 0; j < m; j++) {
+            seq_arnoldi_step(c, j, 0);
+            CK(cudaGetLastError());
+            if ((rc = read_scalars(c))) return rc;
+            if ((rc = device_error(c))) { rearm(c); return rc; }
+            if (c->h_s->met || c->h_s->hn == 0.0) break;
+        }
+        seq_cycle_end(c, bd, xd, tol, 0);
+        CK(cudaGetLastError());
+        if ((rc = read_scalars(c))) return rc;
+        if ((rc = device_error(c))) { rearm(c); return rc; }
+    }
+    *cycles_out = cycles;
+    return status;
+}
+}  // namespace
+
+extern "C" {
+
+int kkt_batch_create(kkt_batch** out, int max_count, int device) {
+    if (!out || max_count < 1 || max_count > 4096) return KKT_ERR_INVALID;
+    *out = nullptr;
+    auto* bt = new kkt_batch();
+    bt->dev = device;
+    bt->max_count = max_count;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&bt->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&bt->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->done_ev, cudaEventDisableTiming);
+    bt->ready_ev.assign(max_count, nullptr);
+    for (int i = 0; i < max_count && e == cudaSuccess; i++)
+        e = cudaEventCreateWithFlags(&bt->ready_ev[i], cudaEventDisableTiming);
+    const size_t n = (size_t)max_count;
+    if (e == cudaSuccess) e = cudaMalloc(&bt->d_ref, n * sizeof(kkt::RefArgs<double>));
+    if (e == cudaSuccess) e = cudaMalloc(&bt->d_gather, n * sizeof(kkt::GatherArgs));
+    if (e == cudaSuccess) e = cudaMalloc(&bt->d_sweep, n * sizeof(kkt::SweepArgs));
+    if (e == cudaSuccess) e = cudaMalloc(&bt->d_res, n * sizeof(kkt::ResidualArgs));
+    if (e == cudaSuccess) e = cudaMalloc(&bt->d_ticket, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&bt->h_ref, n * sizeof(kkt::RefArgs<double>));
+    if (e == cudaSuccess) e = cudaMallocHost(&bt->h_gather, n * sizeof(kkt::GatherArgs));
+    if (e == cudaSuccess) e = cudaMallocHost(&bt->h_sweep, n * sizeof(kkt::SweepArgs));
+    if (e == cudaSuccess) e = cudaMallocHost(&bt->h_res, n * sizeof(kkt::ResidualArgs));
+    if (e == cudaSuccess) {
+        bt->smem_optin -= 1024;
+        for (const void* fn : {(const void*)kkt::k_refactor_rows<double, true, 256, true>,
+                               (const void*)kkt::k_refactor_rows<double, true, 512, true>,
+                               (const void*)kkt::k_usolve_cluster_batch}) {
+            const cudaError_t ea = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        fn == (const void*)kkt::k_usolve_cluster_batch
+                                                            ? (int)TAIL_SMEM_MAX : bt->smem_optin);
+            if (ea != cudaSuccess) e = ea;
+        }
+        const cudaError_t ec =
+            cudaFuncSetAttribute((const void*)kkt::k_usolve_cluster_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (ec != cudaSuccess) e = ec;
+    }
+    if (e != cudaSuccess) {
+        batch_free(bt);
+        delete bt;
+        return e == cudaErrorMemoryAllocation ? KKT_ERR_OOM : KKT_ERR_CUDA;
+    }
+    *out = bt;
+    return KKT_OK;
+}
+
+void kkt_batch_destroy(kkt_batch* bt) {
+    if (!bt) return;
+    cudaSetDevice(bt->dev);
+    cudaStreamSynchronize(bt->stream);
+    batch_free(bt);
+    delete bt;
+}
+
+int64_t kkt_batch_launches(const kkt_batch* bt) { return bt ? bt->launches : 0; }
+
+int kkt_batch_step(kkt_batch* bt, kkt_ctx* const* ctxs, int count, const double* const* values,
+                   const double* const* b, double* const* x, int on_device, double tol, int* iters, double* nrbe,
+                   int* status) {
+    if (!bt || !ctxs || !values || !b || !x || !status || count < 1 || count > bt->max_count || !(tol > 0))
+        return KKT_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(bt->mu);
+    CK_BT(cudaSetDevice(bt->dev));
+    // which instances share the batched launches: FP64 contexts on this
+    // device with the refactorization block size of the first of them; the
+    // others run as lone kkt_step calls afterwards
+    std::vector<int> in, alone;
+    int nt = 0;
+    for (int i = 0; i < count; i++) {
+        kkt_ctx* c = ctxs[i];
+        status[i] = KKT_ERR_INVALID;
+        if (!c || !values[i] || !b[i] || !x[i]) return KKT_ERR_INVALID;
+        for (int j = 0; j < i; j++) if (ctxs[j] == c) return KKT_ERR_INVALID;   // one step per instance
+        if (!c->analyzed) { status[i] = KKT_ERR_STATE; continue; }
+        const bool ok = c->dev == bt->dev && !c->mixed && !c->o.graphs && (nt == 0 || c->ref_threads == nt);
+        if (ok) { nt = c->ref_threads; in.push_back(i); }
+        else alone.push_back(i);
+    }
+    {   // the shared launch holds every instance's work area and the largest map
+        size_t area = 0, mapb = 0;
+        for (int i : in) {
+            area = std::max(area, ctxs[i]->ref_area);
+            mapb = std::max(mapb, ctxs[i]->ref_map_bytes);
+        }
+        if (area + mapb > (size_t)bt->smem_optin) {
+            alone.insert(alone.end(), in.begin(), in.end());
+            in.clear();
+        }
+    }
+    const int nb = (int)in.size();
+    if (nb > 0) {
+        size_t area = 0, mapb = 0;
+        int map_cols = 0, items = 0, C = -1, nbr = 1;
+        size_t cl_smem = 0;
+        for (int t = 0; t < nb; t++) {
+            const int i = in[t];
+            kkt_ctx* c = ctxs[i];
+            CK_BT(cudaEventRecord(bt->ready_ev[t], c->stream));   // work the caller queued on the instance's stream
+            CK_BT(cudaStreamWaitEvent(bt->stream, bt->ready_ev[t], 0));
+            const int n = c->A.n;
+            const double* vals = values[i];
+            const double* bd = b[i];
+            double* xd = x[i];
+            if (!on_device) {
+                CK_BT(cudaMemcpyAsync(c->d_vals, values[i], sizeof(double) * (size_t)c->nnz_a, cudaMemcpyHostToDevice,
+                                      bt->stream));
+                CK_BT(cudaMemcpyAsync(c->d_b, b[i], sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, bt->stream));
+                c->h2d += (int64_t)sizeof(double) * (c->nnz_a + n);
+                vals = c->d_vals;
+                bd = c->d_b;
+                xd = c->d_x;
+            }
+            c->factored = false;
+            c->y_fused = false;
+            c->fp64_active = false;
+            c->last_fallback = 0;
+            const int64_t nnzF = (int64_t)c->lay.Fj.size();
+            bt->h_gather[t] = kkt::GatherArgs{vals, nnzF, (double*)c->d_Fx, c->d_Arp, c->d_asrc, c->d_Ax, n,
+                                              (double*)c->d_rinv, c->d_s, c->d_y};
+            kkt::RefArgs<double>& a = bt->h_ref[t];
+            a = kkt::RefArgs<double>{};
+            a.items = c->d_items;
+            a.nitems = c->nitems;
+            a.order = c->d_order;
+            a.Fp = c->d_Fp;
+            a.Fj = c->d_Fj;
+            a.Fdiag = c->d_Fdiag;
+            a.Fx = (double*)c->d_Fx;
+            a.rinv = (double*)c->d_rinv;
+            a.vals = vals;
+            a.fsrc = c->d_fsrc;
+            a.M = c->ref_map_cols;
+            a.mlo = n - c->ref_map_cols;
+            a.map_bytes = (int)c->ref_map_bytes;
+            a.area_bytes = (int)c->ref_area;
+            a.slice_bytes = (int)((c->ref_smem / (c->ref_threads / 32)) & ~(size_t)15);
+            a.gdk = c->d_gdk;
+            a.gcnt = c->d_gcnt;
+            a.g_sd_off = c->d_gsdoff;
+            a.gw = (double*)c->d_gw;
+            a.g_w_off = c->d_gwoff;
+            a.s = c->d_s;
+            a.fw = kkt::FwdArgs<double>{bd, c->d_P, c->d_y, c->d_xp};
+            a.boost_eps = c->o.boost_eps;
+            area = std::max(area, c->ref_area);
+            mapb = std::max(mapb, c->ref_map_bytes);
+            map_cols = std::max(map_cols, c->ref_map_cols);
+            items = std::max(items, c->nitems);
+            if (C < 0) C = c->cluster;
+            if (c->cluster != C) C = 0;   // the batched sweep needs one cluster shape
+            cl_smem = std::max(cl_smem, c->cluster_smem);
+            bt->h_sweep[t] = kkt::SweepArgs{n, c->d_listU, c->d_Fpos, c->d_Fp, c->d_Fdiag, (const double*)c->d_Fx,
+                                            (const double*)c->d_rinv, c->d_Q, c->d_y, xd, c->d_s};
+            const int rb = red_blocks(c);
+            nbr = std::max(nbr, rb);
+            bt->h_res[t] = kkt::ResidualArgs{n, rb, c->d_Arp, c->d_Aci, c->d_Ax, bd, xd, c->d_r, c->d_part, c->d_s,
+                                             c->o.stop_mode, c->o.refine_delta};
+        }
+        CK_BT(cudaMemcpyAsync(bt->d_ref, bt->h_ref, nb * sizeof(kkt::RefArgs<double>), cudaMemcpyHostToDevice, bt->stream));
+        CK_BT(cudaMemcpyAsync(bt->d_gather, bt->h_gather, nb * sizeof(kkt::GatherArgs), cudaMemcpyHostToDevice, bt->stream));
+        CK_BT(cudaMemcpyAsync(bt->d_sweep, bt->h_sweep, nb * sizeof(kkt::SweepArgs), cudaMemcpyHostToDevice, bt->stream));
+        CK_BT(cudaMemcpyAsync(bt->d_res, bt->h_res, nb * sizeof(kkt::ResidualArgs), cudaMemcpyHostToDevice, bt->stream));
+        const long long limit = spin(ctxs[in[0]]);
+        const size_t smem = area + mapb;   // every instance's work area, then the largest map
+        kkt::k_refactor_prep_batch<<<(nb + 255) / 256, 256, 0, bt->stream>>>(bt->d_gather, nb, bt->d_ticket);
+        kkt::k_gather_batch<<<dim3(std::max(8, 2 * bt->num_sms / nb), nb), 256, 0, bt->stream>>>(bt->d_gather);
+        // one refactorization launch for every instance's rows
+        const void* fn = nt == 512 ? (const void*)kkt::k_refactor_rows<double, true, 512, true>
+                                   : (const void*)kkt::k_refactor_rows<double, true, 256, true>;
+        int per_sm = 0;
+        CK_BT(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
+        const int blocks = std::max(1, per_sm) * bt->num_sms;
+        const kkt::RefBatch<double> rb{bt->d_ref, nb, (long long)nb * items, bt->d_ticket, map_cols, (int)area};
+        if (nt == 512)
+            kkt::k_refactor_rows<double, true, 512, true><<<blocks, 512, smem, bt->stream>>>(kkt::RefArgs<double>{}, rb, limit, nullptr);
+        else
+            kkt::k_refactor_rows<double, true, 256, true><<<blocks, 256, smem, bt->stream>>>(kkt::RefArgs<double>{}, rb, limit, nullptr);
+        bt->launches += 3;
+        // the backward sweeps: one cluster per instance in one launch, or
+        // each instance's own schedule
+        if (C > 0) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(C * nb, 1, 1);
+            cfg.blockDim = dim3(kkt::CLUSTER_THREADS, 1, 1);
+            cfg.dynamicSmemBytes = cl_smem;
+            cfg.stream = bt->stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = C;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            CK_BT(cudaLaunchKernelEx(&cfg, kkt::k_usolve_cluster_batch, (const kkt::SweepArgs*)bt->d_sweep, limit));
+            bt->launches += 1;
+        } else {
+            for (int t = 0; t < nb; t++) {
+                kkt_ctx* c = ctxs[in[t]];
+                cudaStream_t own = c->stream;
+                c->stream = bt->stream;
+                u_apply_t<double>(c, bt->h_sweep[t].out);
+                c->stream = own;
+            }
+        }
+        kkt::k_residual_batch<<<dim3(nbr, nb), kkt::RED_THREADS, 0, bt->stream>>>(bt->d_res);
+        kkt::k_decide_batch<<<(nb + 127) / 128, 128, 0, bt->stream>>>(bt->d_res, nb, tol);
+        bt->launches += 2;
+        CK_BT(cudaGetLastError());
+        for (int t = 0; t < nb; t++) {
+            kkt_ctx* c = ctxs[in[t]];
+            CK_BT(cudaMemcpyAsync(c->h_s, c->d_s, sizeof(DevScal), cudaMemcpyDeviceToHost, bt->stream));
+            c->d2h += (int64_t)sizeof(DevScal);
+        }
+        CK_BT(cudaEventRecord(bt->done_ev, bt->stream));
+        CK_BT(cudaStreamSynchronize(bt->stream));
+        // per instance: the outcome, and the refinement where it is needed
+        for (int t = 0; t < nb; t++) {
+            const int i = in[t];
+            kkt_ctx* c = ctxs[i];
+            CK_BT(cudaStreamWaitEvent(c->stream, bt->done_ev, 0));
+            c->nboost = c->h_s->nboost;
+            c->norm_a = c->h_s->normA;
+            const double* bd = bt->h_res[t].b;
+            double* xd = bt->h_sweep[t].out;
+            int rc = device_error(c);
+            int cycles = 0;
+            if (rc) rearm(c);
+            else {
+                c->factored = true;
+                rc = refine_after_prologue(c, bd, xd, tol, &cycles);
+            }
+            if (!on_device && (rc == KKT_OK || rc == KKT_ERR_NOT_CONVERGED)) {
+                CK(cudaMemcpyAsync(x[i], c->d_x, sizeof(double) * (size_t)c->A.n, cudaMemcpyDeviceToHost, c->stream));
+                c->d2h += (int64_t)sizeof(double) * c->A.n;
+            }
+            CK(cudaStreamSynchronize(c->stream));
+            c->last_iters = c->h_s->iters;
+            c->last_cycles = cycles;
+            c->last_nrbe = c->h_s->nrbe;
+            c->last_rnorm0 = c->h_s->rnorm0;
+            if (iters) iters[i] = c->h_s->iters;
+            if (nrbe) nrbe[i] = c->h_s->nrbe;
+            status[i] = rc;
+        }
+    }
+    for (int i : alone) {
+        int it = 0;
+        double nr = 0.0;
+        status[i] = kkt_step(ctxs[i], values[i], b[i], x[i], on_device, tol, &it, &nr);
+        if (iters) iters[i] = it;
+        if (nrbe) nrbe[i] = nr;
+    }
+    return KKT_OK;
+}
+
+}  // extern "C"
+

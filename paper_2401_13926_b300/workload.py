@@ -219,6 +219,11 @@ class KKTSequence:
         self.M = cfg.steps
 
         # ---- base values, fixed per sequence
+        self._draw_base(rng)
+
+    def _draw_base(self, rng):
+        nH, nJ, nx, ny = self._nH, self._nJ, self.nx, self.ny
+
         def logu(m):
             return 10.0 ** rng.uniform(-1.0, 1.0, m) * np.where(rng.random(m) < 0.5, -1.0, 1.0)
         self._hbase = logu(nH)
@@ -228,6 +233,16 @@ class KKTSequence:
         self._hdbase = hd
         self._u = rng.uniform(-1.0, 1.0, nx)
         self._uy = rng.uniform(-1.0, 1.0, ny)
+
+    def reseeded(self, instance: int) -> "KKTSequence":
+        """Another sequence on the same grid and pattern, with its own values:
+        seed 1000 * config_id + instance for the base values and every
+        matrix (the grid is drawn once; for serving many instances cheaply)."""
+        import copy
+        other = copy.copy(self)
+        other.seed = 1000 * self.cfg.config_id + instance
+        other._draw_base(np.random.default_rng([other.seed, 0]))
+        return other
 
     # --------------------------------------------------------------------
     def spread(self, k: int) -> float:

@@ -95,3 +95,25 @@ def test_host_analyze_equals_order_then_pivot(L, oracle_mod):
     cols, madds, _, _ = oracle_mod.refactor_sample(seq.n, seq.rowptr, seq.colind, v, P, Q, 1e9)
     assert cols == seq.n and madds == st["refactor_updates"]
     assert st["levels_l"] >= 1 and st["levels_u"] >= 1
+
+
+def test_instance_placement_rule(L):
+    """kkt_place_instance (no GPU): the device with the most budget left
+    among those whose budget can hold the instance at all, ties to the
+    lower index; -1 when no device could ever hold it.  Placing a stream of
+    instances spreads them so no device's held bytes exceed another's by
+    more than the largest instance."""
+    assert K.place_instance([10, 10, 10], [5, 2, 2], 3) == 1
+    assert K.place_instance([10, 20, 10], [0, 15, 0], 3) == 0
+    assert K.place_instance([10, 4, 30], [0, 0, 29], 5) == 0   # device 1 too small, 2 fullest
+    assert K.place_instance([10, 10], [12, 11], 3) == 1        # all over budget: still the least held
+    assert K.place_instance([10, 10], [0, 0], 11) == -1
+    rng = np.random.default_rng(0)
+    budget = np.array([1000, 1000, 1000, 1000], np.int64)
+    held = np.zeros(4, np.int64)
+    sizes = rng.integers(10, 60, size=200)
+    for need in sizes:
+        d = K.place_instance(budget, held, int(need))
+        assert 0 <= d < 4
+        held[d] += need
+    assert held.max() - held.min() <= sizes.max()

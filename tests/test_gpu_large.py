@@ -79,6 +79,22 @@ def test_kkt10000_sequence_nrbe(oracle_mod, c3):
         assert nrbe_agrees(nr, nr_or, seq), (k, nr, nr_or)
 
 
+def test_kkt10000_mixed_with_fallback_sequence(oracle_mod, c3):
+    """Mixed precision (FP32 factors, FP64 fallback) on the whole 40-matrix
+    sequence: every solve ends at oracle-evaluated NRBE <= 1e-12."""
+    seq, s64 = c3
+    s = K.KKTSolver(precision="mixed")
+    s.analyze_like(s64)
+    for k in range(seq.M):
+        v = seq.values(k)
+        b, _ = seq.rhs(k, v)
+        x, it, nr = s.step(v, b, tol=NRBE_TOL)
+        nr_or = oracle_mod.nrbe(seq.n, seq.rowptr, seq.colind, v, b, x)
+        assert nr_or <= NRBE_TOL, (k, nr_or, s.info()["last_fallback"])
+        assert nrbe_agrees(nr, nr_or, seq), (k, nr, nr_or)
+    s.close()
+
+
 @pytest.fixture(scope="module")
 def c5():
     seq, s = _solver("kkt70000")

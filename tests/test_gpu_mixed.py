@@ -15,9 +15,15 @@ What is checked:
     never leaves a residual larger than that of the preconditioner solve
     it starts from (restarted GMRES minimises the 2-norm residual);
   * on a well-conditioned system mixed refinement reaches 1e-12 like the
-    oracle's FGMRES with the same FP32 factors.
-On the synthetic KKT sequences the FP32 preconditioner does not always
-reach 1e-12: with the ill-conditioned matrices, u * cond(K) is far above 1.
+    oracle's FGMRES with the same FP32 factors;
+  * the FP64 fallback (kkt_opts.mixed_fallback): on the synthetic KKT
+    sequences the FP32 preconditioner alone does not always reach 1e-12
+    (with the ill-conditioned matrices u32 * cond(K) is far above 1), so a
+    solve the FP32 factors have not finished within the allowed cycles
+    continues with the FP64 refactorization; every mixed solve then meets
+    NRBE <= 1e-12 as the oracle evaluates it, and the FP64 factors of a
+    fallback equal the oracle's refactorization bit for bit.
+The tests of the FP32-only behaviour turn the fallback off.
 """
 import numpy as np
 import pytest
@@ -89,7 +95,8 @@ def test_fp32_lu_solve_backward_error_bound(oracle_mod, c1, sched):
 
 def _check_reported(oracle_mod, s, n, rp, ci, v, b, x, it, nr, x0, tol, max_iters):
     on = oracle_mod.nrbe(n, rp, ci, v, b, x)
-    assert abs(nr - on) <= 1e-6 * on + 1e-30, (nr, on)
+    m = int(np.max(np.diff(rp)))   # two residual evaluations: 2 (m + 2) eps apart at most
+    assert abs(nr - on) <= 1e-6 * on + 2 * (m + 2) * 2.0 ** -52, (nr, on)
     if s.last_status == K.OK:
         assert on <= tol * (1 + 1e-6), on
     else:
@@ -104,7 +111,7 @@ def _check_reported(oracle_mod, s, n, rp, ci, v, b, x, it, nr, x0, tol, max_iter
 def test_mixed_solves_reported_truthfully_kkt200(oracle_mod, c1, sched):
     seq, P, Q = c1
     cycles = 3
-    s = K.KKTSolver(precision="mixed", trisolve=sched, max_cycles=cycles)
+    s = K.KKTSolver(precision="mixed", trisolve=sched, max_cycles=cycles, mixed_fallback=0)
     s.analyze(seq.rowptr, seq.colind, Q=Q, P=P)
     for k in range(seq.M):
         v = seq.values(k)
@@ -119,7 +126,7 @@ def test_mixed_solves_reported_truthfully_kkt200(oracle_mod, c1, sched):
 def test_mixed_full_size_kkt2000(oracle_mod):
     seq = KKTSequence("kkt2000")
     cycles = 2
-    s = K.KKTSolver(precision="mixed", max_cycles=cycles)
+    s = K.KKTSolver(precision="mixed", max_cycles=cycles, mixed_fallback=0)
     s.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
     P, Q = s.perm()
     converged = 0
@@ -141,7 +148,7 @@ def test_mixed_converges_on_well_conditioned_system(oracle_mod):
     n = 3000
     rp, ci, v = small_random_sparse(n, 4.0 / n, 91, diag_boost=1.0)
     P, Q, _ = oracle_mod.lu(n, rp, ci, v)
-    s = K.KKTSolver(precision="mixed")
+    s = K.KKTSolver(precision="mixed", mixed_fallback=0)
     s.analyze(rp, ci, Q=Q, P=P)
     s.refactor(v)
     b = np.random.default_rng(3).standard_normal(n)
@@ -164,3 +171,54 @@ def test_mixed_random_sparse_factor_parity(oracle_mod):
     of = oracle_mod.refactor_f32(n, rp, ci, v, P, Q)
     f = s.factors()
     assert np.array_equal(f["Lx"], of.Lx) and np.array_equal(f["Ux"], of.Ux)
+
+
+@pytest.mark.parametrize("sched", ["auto", "global"])
+def test_mixed_fallback_meets_tolerance_kkt200(oracle_mod, c1, sched):
+    """Every solve of the sequence ends at oracle-evaluated NRBE <= 1e-12;
+    a solve that fell back reports it, used the FP64 factors (equal to the
+    oracle's refactorization bit for bit), and the next refactorization
+    starts in FP32 again (its factors equal the oracle's FP32 ones)."""
+    seq, P, Q = c1
+    s = K.KKTSolver(precision="mixed", trisolve=sched, mixed_fallback=1)
+    s.analyze(seq.rowptr, seq.colind, Q=Q, P=P)
+    falls = 0
+    for k in range(seq.M):
+        v = seq.values(k)
+        b, _ = seq.rhs(k, v)
+        s.refactor(v)
+        f32 = oracle_mod.refactor_f32(seq.n, seq.rowptr, seq.colind, v, P, Q)
+        assert np.array_equal(s.factors()["Ux"], f32.Ux), k
+        x, it, nr = s.solve(b, tol=1e-12)
+        assert s.last_status == K.OK
+        on = oracle_mod.nrbe(seq.n, seq.rowptr, seq.colind, v, b, x)
+        # the two residual evaluations differ by at most 2 (m + 2) eps in NRBE
+        # (m = the longest row of K) besides 1e-6 relative
+        m = int(np.max(np.diff(seq.rowptr)))
+        assert on <= 1e-12 and abs(nr - on) <= 1e-6 * on + 2 * (m + 2) * 2.0 ** -52, (k, on, nr)
+        info = s.info()
+        if info["last_fallback"]:
+            falls += 1
+            of = oracle_mod.refactor(seq.n, seq.rowptr, seq.colind, v, P, Q)
+            f = s.factors()
+            assert np.array_equal(f["Lx"], of.Lx) and np.array_equal(f["Ux"], of.Ux), k
+    assert s.info()["fallbacks"] == falls
+    assert falls >= 1   # the s = 8 matrices of kkt200 defeat the FP32 preconditioner
+
+
+def test_mixed_step_with_fallback_equals_refactor_then_solve(oracle_mod):
+    """kkt_step in mixed precision with the fallback gives the same x,
+    iterations and NRBE as kkt_refactor then kkt_solve."""
+    seq = KKTSequence("kkt200", steps=4)
+    a = K.KKTSolver(precision="mixed", mixed_fallback=1)
+    f = K.KKTSolver(precision="mixed", mixed_fallback=1)
+    a.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
+    f.analyze_like(a)
+    for k in range(seq.M):
+        v = seq.values(k)
+        b, _ = seq.rhs(k, v)
+        a.refactor(v)
+        xa, ia, na = a.solve(b, tol=1e-12)
+        xf, i_f, nf = f.step(v, b, tol=1e-12)
+        assert np.array_equal(xa, xf) and ia == i_f and na == nf, k
+        assert a.info()["last_fallback"] == f.info()["last_fallback"]

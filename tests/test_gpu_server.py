@@ -1,9 +1,14 @@
 """Serving runtime (kkt_server_*): many resident KKT sequences with their
-steps in flight together.  Each result must equal, bit for bit, the same
-step run alone on a solver of its own (the sequences are independent and
-every step runs the same kernels in the same order); steps of one instance
-run in submission order; admission keeps the device memory within budget;
-a failing step reports its error without disturbing the others."""
+steps in flight together, either as batched calls (continuous batching:
+one refactorization launch over several instances' rows) or one worker per
+step.  Each result must equal, bit for bit, the same step run alone on a
+solver of its own; steps of one instance run in submission order;
+admission keeps each device's memory within its budget, an open that does
+not fit yet waits (first come, first served) until memory is freed; a
+failing step reports its error without disturbing the others."""
+import threading
+import time
+
 import numpy as np
 import pytest
 
@@ -25,7 +30,8 @@ def _alone(rp, ci, v0, steps, tol=1e-12):
     return out
 
 
-def test_mix_equals_alone():
+@pytest.mark.parametrize("batch", [0, 4])
+def test_mix_equals_alone(batch):
     cases = []
     for inst in range(3):
         seq = KKTSequence("kkt200", instance=inst, steps=4)
@@ -35,7 +41,7 @@ def test_mix_equals_alone():
     rng = np.random.default_rng(0)
     steps = [(v * (1 + 0.01 * rng.standard_normal(len(v))), rng.standard_normal(1500)) for _ in range(4)]
     cases.append((rp, ci, v, steps))
-    srv = K.KKTServer(workers=4)
+    srv = K.KKTServer(workers=4, batch=batch)
     ids = [srv.open(rp_, ci_, v0) for rp_, ci_, v0, _ in cases]
     tickets = []
     for k in range(4):                  # interleaved submission across instances
@@ -48,6 +54,8 @@ def test_mix_equals_alone():
         got[(i, k)] = (x, r)
     info = srv.info()
     assert info["submitted"] == info["completed"] == 16 and info["in_flight"] == 0
+    if batch:
+        assert 0 < info["batches"] <= 16
     for i, (rp_, ci_, v0, st) in enumerate(cases):
         ref = _alone(rp_, ci_, v0, st)
         for k in range(4):
@@ -57,29 +65,64 @@ def test_mix_equals_alone():
     srv.close()
 
 
-def test_admission_by_device_memory():
+def test_device_bytes_estimate_is_exact():
+    """kkt_estimate_device_bytes (what admission reserves) equals the device
+    memory kkt_analyze then holds, in each precision."""
+    seq = KKTSequence("kkt200", steps=1)
+    P, Q, st = K.host_analyze(seq.rowptr, seq.colind, seq.values(0))
+    for kw in (dict(), dict(precision="mixed"), dict(precision="mixed", mixed_fallback=0), dict(restart=10)):
+        s = K.KKTSolver(**kw)
+        s.analyze(seq.rowptr, seq.colind, Q=Q, P=P)
+        est = K.estimate_device_bytes(seq.n, seq.nnz, st, canonical_order=bool(st["canonical_order"]), **kw)
+        assert s.info()["device_bytes"] == est, kw
+        s.close()
+
+
+def test_admission_waits_for_memory_in_order():
+    """A budget for one instance: the second and third opens wait, and are
+    admitted in arrival order as the earlier instances close; an instance
+    larger than the whole budget is refused at once."""
     seq = KKTSequence("kkt200", steps=2)
-    probe = K.KKTSolver()
-    probe.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
-    one = probe.info()["device_bytes"]
-    probe.close()
-    srv = K.KKTServer(workers=2, hbm_budget=int(1.5 * one))
-    a = srv.open(seq.rowptr, seq.colind, seq.values(0))
+    _, _, st = K.host_analyze(seq.rowptr, seq.colind, seq.values(0))
+    one = K.estimate_device_bytes(seq.n, seq.nnz, st, canonical_order=bool(st["canonical_order"]))
+    srv = K.KKTServer(batch=2, hbm_budget=int(1.5 * one))
+    big = KKTSequence("kkt2000", steps=1)
     with pytest.raises(K.KKTError) as e:
-        srv.open(seq.rowptr, seq.colind, seq.values(0))
+        srv.open(big.rowptr, big.colind, big.values(0))
     assert e.value.code == -3
-    assert srv.info()["instances"] == 1 and srv.info()["device_bytes"] == one
+    a = srv.open(seq.rowptr, seq.colind, seq.values(0))
+    admitted = []
+
+    def opener(tag):
+        inst = srv.open(seq.rowptr, seq.colind, seq.values(0))
+        admitted.append((tag, inst))
+
+    tb = threading.Thread(target=opener, args=("b",))
+    tb.start()
+    while srv.info()["waiting"] < 1:
+        time.sleep(0.01)
+    tc = threading.Thread(target=opener, args=("c",))
+    tc.start()
+    while srv.info()["waiting"] < 2:
+        time.sleep(0.01)
+    assert srv.info()["instances"] == 1 and not admitted
     srv.close_instance(a)
-    b = srv.open(seq.rowptr, seq.colind, seq.values(0))
-    t, _ = srv.submit(b, seq.values(1), seq.rhs(1, seq.values(1))[0])
-    x, r = srv.wait(t)
-    assert r["status"] == 0
+    tb.join(timeout=60)
+    assert [t for t, _ in admitted] == ["b"] and srv.info()["waiting"] == 1
+    assert srv.info()["device_bytes"] <= srv.info()["hbm_budget"]
+    bid = admitted[0][1]
+    t, _ = srv.submit(bid, seq.values(1), seq.rhs(1, seq.values(1))[0])
+    assert srv.wait(t)[1]["status"] == 0
+    srv.close_instance(bid)
+    tc.join(timeout=60)
+    assert [t for t, _ in admitted] == ["b", "c"] and srv.info()["waiting"] == 0
     srv.close()
 
 
-def test_failing_step_is_reported_and_isolated():
+@pytest.mark.parametrize("batch", [0, 4])
+def test_failing_step_is_reported_and_isolated(batch):
     seq = KKTSequence("kkt200", steps=3)
-    srv = K.KKTServer(workers=3)
+    srv = K.KKTServer(workers=3, batch=batch)
     a = srv.open(seq.rowptr, seq.colind, seq.values(0))
     b = srv.open(seq.rowptr, seq.colind, seq.values(0))
     bad = seq.values(1).copy()
