@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--mixed-cycles", type=int, default=2,
                     help="restart cycles the FP32 preconditioner gets before the FP64 fallback")
     ap.add_argument("--no-trace", action="store_true", help="skip the refactorization trace (critical path)")
+    ap.add_argument("--trisolve", default="auto", choices=["auto", "global"],
+                    help="triangular-solve schedule of the headline solver (global: the whole-GPU kernels)")
     ap.add_argument("--serve-instances", type=int, default=8,
                     help="independent kkt2000 sequences of the serving measurement (0 = skip)")
     ap.add_argument("--serve-steps", type=int, default=10)
@@ -552,7 +554,8 @@ def run_ours(args):
     t_job = time.perf_counter()
     seq = KKTSequence(args.workload, instance=rank)
     stream = torch.cuda.Stream()
-    solver = K.KKTSolver(restart=RESTART, device=local, stream=stream, timing=True, precision=args.precision)
+    solver = K.KKTSolver(restart=RESTART, device=local, stream=stream, timing=True, precision=args.precision,
+                         trisolve=args.trisolve)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     # the headline's host analysis (ordering + pivoting factorization, one

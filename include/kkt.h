@@ -119,10 +119,15 @@ typedef struct {
                              by level in the dependency DAG of L (ties by row); 0 by
                              row.  A row's dependencies are always dispatched before
                              it.  Same arithmetic either way. */
+    int map_cols;         /* columns (the last ones) with an O(1) position map in block rows:
+                             0 = default (16384 when it fits beside the longest row),
+                             -1 = none, > 0 = at most that many */
     int64_t warp_row_updates; /* a row is refactored one per warp only if its multiply-adds
                              (the sum of |U(k,>k)| over its L entries) are at most this
                              (besides fitting a warp's slice); -1 = no limit; 0 = the
-                             default limit */
+                             default: 2048 with 256-thread blocks, 65536 with 512-thread
+                             blocks (the long rows at the dense end, on the critical
+                             path, then go one per block) */
     int mixed_fallback;   /* KKT_PRECISION_MIXED only: restart cycles the FP32-factor
                              preconditioner gets (default 2).  A solve not converged by
                              then refactors the matrix in FP64 and continues FGMRES from

@@ -365,8 +365,8 @@ struct RefArgs {
     int slice_bytes;       // a warp row's slice: warp w's starts at w * slice_bytes (slices span the map too)
     // ROW_GLOBAL rows, by global-row index g: step descriptors at sd_off[g]
     // in gdk / gcnt, values at w_off[g] in gw
-    const int64_t* gdk;
-    const int32_t* gcnt;
+    const uint32_t* gdk;
+    const uint32_t* gcnt;
     const int64_t* g_sd_off;
     T* gw;
     const int64_t* g_w_off;
@@ -457,19 +457,20 @@ __device__ __forceinline__ int row_pos(int c, int mlo, int M, const short* map, 
 }
 
 // A row's working set carved from `base`: step descriptors (position of
-// U(k,k) and |U(k, >k)| for every L entry; k itself is the column), the
-// row's values and its columns -- 12 st + (sizeof(T) + 4) len bytes.
+// U(k,k) and |U(k, >k)| for every L entry, 4 bytes each -- the analysis
+// keeps every factor position below 2^32; k itself is the column), the
+// row's values and its columns -- 8 st + (sizeof(T) + 4) len bytes.
 template <typename T>
 struct RowSpace {
-    int64_t* dk;
+    uint32_t* dk;
+    uint32_t* cnt;
     T* w;
-    int32_t* cnt;
     int32_t* cols;
     __device__ RowSpace(unsigned char* base, int st, int len) {
-        dk = reinterpret_cast<int64_t*>(base);
-        w = reinterpret_cast<T*>(dk + st);
-        cnt = reinterpret_cast<int32_t*>(w + len);
-        cols = cnt + st;
+        dk = reinterpret_cast<uint32_t*>(base);
+        cnt = dk + st;
+        w = reinterpret_cast<T*>(cnt + st);   // 8 st bytes in: aligned for double
+        cols = reinterpret_cast<int32_t*>(w + len);
     }
 };
 
@@ -493,8 +494,8 @@ __device__ bool warp_row(int row, const RefArgs<T>& a, DevScal* s, T boost, long
         cols[q] = c;
         if (q < nsteps) {
             const int64_t dk = a.Fdiag[c];
-            rs.dk[q] = dk;
-            rs.cnt[q] = (int32_t)(a.Fp[c + 1] - dk - 1);
+            rs.dk[q] = (uint32_t)dk;
+            rs.cnt[q] = (uint32_t)(a.Fp[c + 1] - dk - 1);
         }
     }
     __syncwarp();
@@ -505,16 +506,16 @@ __device__ bool warp_row(int row, const RefArgs<T>& a, DevScal* s, T boost, long
     auto prefetch = [&](int st) {
         if (st >= nsteps) return;
         nrk = ld_relaxed(&a.rinv[cols[st]]);
-        if (lane < rs.cnt[st]) {
-            ncol = a.Fj[rs.dk[st] + 1 + lane];
-            nv = ld_relaxed(&a.Fx[rs.dk[st] + 1 + lane]);
+        if (lane < (int)rs.cnt[st]) {
+            ncol = a.Fj[(int64_t)rs.dk[st] + 1 + lane];
+            nv = ld_relaxed(&a.Fx[(int64_t)rs.dk[st] + 1 + lane]);
         }
     };
     prefetch(0);
     for (int step = 0; step < nsteps; step++) {
         const int k = cols[step];
         const int64_t dk = rs.dk[step];
-        const int cnt = rs.cnt[step];
+        const int cnt = (int)rs.cnt[step];
         T rk = nrk, v0 = nv;
         const int c0 = ncol;
         prefetch(step + 1);
@@ -563,27 +564,35 @@ __device__ bool warp_row(int row, const RefArgs<T>& a, DevScal* s, T boost, long
     return true;
 }
 
+// Block shapes of the refactorization kernel, picked by its shared memory
+// per block: NT threads, at least MINB blocks an SM (which caps the
+// registers: 80 a thread for three 256-thread blocks, 128 otherwise), PRE
+// entries of each step a thread prefetches two steps ahead, BATCH entries a
+// thread loads together past those.  Measured on kkt2000 (three blocks an
+// SM): PRE 3 under the 80-register cap 5.11 ms against 5.42 with PRE 4;
+// on kkt10000 (two blocks an SM by shared memory) no cap 39.2 ms against
+// 43.0 with it.
+template <int SHAPE> struct RefShape;
+template <> struct RefShape<0> { static constexpr int NT = 256, MINB = 3, PRE = 3, BATCH = 2; };
+template <> struct RefShape<1> { static constexpr int NT = 256, MINB = 2, PRE = 4, BATCH = 4; };
+template <> struct RefShape<2> { static constexpr int NT = 512, MINB = 1, PRE = 4, BATCH = 4; };
+
 // One elimination step's first entries for one thread of a block row:
 // PRE entries of U(k,:) (columns and values) and the pivot reciprocal of
 // row k, loaded two steps ahead so issuing them never waits on a load.
-constexpr int PRE = 4;    // entries per thread in a prefetched stage
-// entries per thread with loads in flight together past the stage: 4 in
-// 512-thread blocks (128 registers a thread), 2 in 256-thread blocks (three
-// blocks an SM, 80 registers a thread)
-template <int NT> struct BatchOf { static constexpr int value = NT >= 512 ? 4 : 2; };
-template <typename T>
+template <typename T, int PRE>
 struct Stage {
     T rk;
     int32_t col[PRE];
     T val[PRE];
 };
 
-template <typename T, int NT>
-__device__ __forceinline__ void stage_load(Stage<T>& st, int step, int nsteps, const int32_t* cols,
-                                           const int64_t* dk, const int32_t* cnt, const RefArgs<T>& a) {
+template <typename T, int NT, int PRE>
+__device__ __forceinline__ void stage_load(Stage<T, PRE>& st, int step, int nsteps, const int32_t* cols,
+                                           const uint32_t* dk, const uint32_t* cnt, const RefArgs<T>& a) {
     if (step >= nsteps) return;
-    const int64_t base = dk[step] + 1;
-    const int c = cnt[step];
+    const int64_t base = (int64_t)dk[step] + 1;
+    const int c = (int)cnt[step];
     st.rk = ld_relaxed(&a.rinv[cols[step]]);
 #pragma unroll
     for (int j = 0; j < PRE; j++) {
@@ -596,10 +605,11 @@ __device__ __forceinline__ void stage_load(Stage<T>& st, int step, int nsteps, c
 // (ROW_BLOCK: staged here) or in global memory (ROW_GLOBAL: descriptors
 // precomputed at analysis, columns read from Fj, values in scratch).
 // Returns false (uniformly for the block) if a wait gave up.
-template <typename T, bool FUSED, int NT>
+template <typename T, bool FUSED, int SHAPE>
 __device__ bool block_row(int row, const RefArgs<T>& a, DevScal* s, T boost, long long limit,
                           unsigned long long* trace, RowSpace<T> rs, bool staged, short* map, int M,
                           const FwdArgs<T>& fw) {
+    constexpr int NT = RefShape<SHAPE>::NT, PRE = RefShape<SHAPE>::PRE;
     const int tid = threadIdx.x;
     if (trace && tid == 0) trace[2 * (size_t)row] = globaltimer_ns();
     const int64_t b = a.Fp[row], d = a.Fdiag[row], e = a.Fp[row + 1];
@@ -617,24 +627,24 @@ __device__ bool block_row(int row, const RefArgs<T>& a, DevScal* s, T boost, lon
             if ((unsigned)(c - mlo) < (unsigned)M) map[c - mlo] = (short)q;
             if (q < nsteps) {
                 const int64_t dk = a.Fdiag[c];
-                rs.dk[q] = dk;
-                rs.cnt[q] = (int32_t)(a.Fp[c + 1] - dk - 1);
+                rs.dk[q] = (uint32_t)dk;
+                rs.cnt[q] = (uint32_t)(a.Fp[c + 1] - dk - 1);
             }
         }
     }
     __syncthreads();
-    Stage<T> A, B;
-    stage_load<T, NT>(A, 0, nsteps, cols, rs.dk, rs.cnt, a);
-    stage_load<T, NT>(B, 1, nsteps, cols, rs.dk, rs.cnt, a);
+    Stage<T, PRE> A, B;
+    stage_load<T, NT, PRE>(A, 0, nsteps, cols, rs.dk, rs.cnt, a);
+    stage_load<T, NT, PRE>(B, 1, nsteps, cols, rs.dk, rs.cnt, a);
     int step = 0;
     // One elimination step: every thread forms l_ik = w_k * (1/u_kk) itself
     // (thread 0 also stores it), then applies its entries of U(k,:): the
     // prefetched stage, then the rest BATCH per thread with their loads
     // issued together.
-    auto run_step = [&](Stage<T>& st) -> bool {
+    auto run_step = [&](Stage<T, PRE>& st) -> bool {
         const int k = cols[step];
-        const int64_t base = rs.dk[step] + 1;
-        const int cnt = rs.cnt[step];
+        const int64_t base = (int64_t)rs.dk[step] + 1;
+        const int cnt = (int)rs.cnt[step];
         int ok = 1;
         // anything still SENTINEL is re-read, all of it in one pass
         for (long long it = 0;; it++) {
@@ -664,7 +674,7 @@ __device__ bool block_row(int row, const RefArgs<T>& a, DevScal* s, T boost, lon
                     w[pos] = fma(-l, st.val[j], w[pos]);
                 }
             }
-            constexpr int BATCH = BatchOf<NT>::value;
+            constexpr int BATCH = RefShape<SHAPE>::BATCH;
             for (int e0 = tid + PRE * NT; e0 < cnt && ok; e0 += BATCH * NT) {
                 T v[BATCH];
                 int c[BATCH];
@@ -684,7 +694,7 @@ __device__ bool block_row(int row, const RefArgs<T>& a, DevScal* s, T boost, lon
                 }
             }
         }
-        stage_load<T, NT>(st, step + 2, nsteps, cols, rs.dk, rs.cnt, a);   // the stage's registers are free again
+        stage_load<T, NT, PRE>(st, step + 2, nsteps, cols, rs.dk, rs.cnt, a);   // the stage's registers are free again
         const int any_fail = __syncthreads_or(!ok);   // uniform decision for the block
         if (tid == 0) w[step] = l;   // nobody else touches position `step` any more
         step++;
@@ -729,9 +739,10 @@ __device__ bool block_row(int row, const RefArgs<T>& a, DevScal* s, T boost, lon
 // over all of it.  The bytes of the map that warp rows overwrote since the
 // last block row (tracked per warp) are re-armed before the next block row.
 // BATCH: the items of several instances (RefBatch); else those of `one`.
-template <typename T, bool FUSED, int NT, bool BATCH>
-__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1)
+template <typename T, bool FUSED, int SHAPE, bool BATCH>
+__global__ void __launch_bounds__(RefShape<SHAPE>::NT, RefShape<SHAPE>::MINB)
 k_refactor_rows(RefArgs<T> one, RefBatch<T> batch, long long limit, unsigned long long* trace) {
+    constexpr int NT = RefShape<SHAPE>::NT;
     constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char ref_sh[];
     __shared__ RefItem s_item;
@@ -778,7 +789,7 @@ k_refactor_rows(RefArgs<T> one, RefBatch<T> batch, long long limit, unsigned lon
             if (warp < count) {
                 const int row = a.order[it.first + warp];
                 const int64_t b = a.Fp[row];
-                const int used = 12 * (int)(a.Fdiag[row] - b) + (int)(sizeof(T) + 4) * (int)(a.Fp[row + 1] - b);
+                const int used = 8 * (int)(a.Fdiag[row] - b) + (int)(sizeof(T) + 4) * (int)(a.Fp[row + 1] - b);
                 const int lo = warp * a.slice_bytes;
                 if ((tid & 31) == 0) {
                     s_dlo[warp] = min(s_dlo[warp], lo);
@@ -812,11 +823,11 @@ k_refactor_rows(RefArgs<T> one, RefBatch<T> batch, long long limit, unsigned lon
             }
             if (!staged) {   // ROW_GLOBAL: descriptors and values in global memory
                 const int g = it.info & 0x0fffffff;
-                rs.dk = const_cast<int64_t*>(a.gdk) + a.g_sd_off[g];
-                rs.cnt = const_cast<int32_t*>(a.gcnt) + a.g_sd_off[g];
+                rs.dk = const_cast<uint32_t*>(a.gdk) + a.g_sd_off[g];
+                rs.cnt = const_cast<uint32_t*>(a.gcnt) + a.g_sd_off[g];
                 rs.w = a.gw + a.g_w_off[g];
             }
-            if (!block_row<T, FUSED, NT>(row, a, s, boost, limit, trace, rs, staged, map, staged ? a.M : 0, a.fw)) {
+            if (!block_row<T, FUSED, SHAPE>(row, a, s, boost, limit, trace, rs, staged, map, staged ? a.M : 0, a.fw)) {
                 if (!BATCH) return;
                 map_armed = map_cols == 0;   // the failed row left its map entries behind
                 map_whole = !map_armed;

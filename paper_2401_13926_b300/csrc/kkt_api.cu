@@ -76,7 +76,7 @@ struct kkt_ctx {
     // refactorization kernel (k_refactor_rows): rows placed one per warp,
     // one per block in shared memory, or one per block with values in
     // global memory; work items in dispatch order
-    int ref_threads = 256, ref_blocks = 0, ref_map_cols = 0, nitems = 0, smem_optin = 0;
+    int ref_threads = 256, ref_shape = 0, ref_blocks = 0, ref_map_cols = 0, nitems = 0, smem_optin = 0;
     size_t ref_smem = 0, ref_map_bytes = 0, ref_area = 0;
     int32_t rows_warp = 0, rows_block = 0, rows_global = 0;
     int32_t* d_order = nullptr;   // rows in dispatch order
@@ -84,8 +84,8 @@ struct kkt_ctx {
     // rows in global memory: step descriptors and value scratch (remade
     // whenever the placement changes)
     std::vector<void*> row_allocs;
-    int64_t *d_gdk = nullptr, *d_gsdoff = nullptr, *d_gwoff = nullptr;
-    int32_t* d_gcnt = nullptr;
+    uint32_t *d_gdk = nullptr, *d_gcnt = nullptr;
+    int64_t *d_gsdoff = nullptr, *d_gwoff = nullptr;
     void* d_gw = nullptr;
     DevScal* d_s = nullptr;
     DevScal* h_s = nullptr;   // pinned mirror
@@ -126,7 +126,13 @@ constexpr int CHAIN_THREADS = 1024;
 constexpr size_t TAIL_SMEM_MAX = 200 * 1024;   // shared memory of a cluster-solve block
 constexpr int REF_MAP_COLS = 16384;      // columns with an O(1) position map in block rows
 constexpr size_t REF_SMEM_WIDE = 113 * 1024;   // blocks above this run 512 threads (one block per SM)
-constexpr int64_t DEFAULT_WARP_ROW_UPDATES = INT64_MAX;   // the default limit of a warp row's multiply-adds
+constexpr size_t REF_SMEM_THREE = 74 * 1024;   // blocks up to this fit three an SM
+// The default limit of a warp row's multiply-adds (measured: kkt2000's
+// refactorization 8.7 ms with no limit, 5.3 ms with 1,024, 5.6 with 4,096;
+// kkt10000 41-43 ms between 1k and 16k; kkt70000, one 512-thread block per
+// SM, 1.38 s with 65,536 against 1.39-1.42 s with lower limits)
+constexpr int64_t DEFAULT_WARP_ROW_UPDATES = 2048;         // 256-thread blocks
+constexpr int64_t DEFAULT_WARP_ROW_UPDATES_WIDE = 65536;   // 512-thread blocks
 constexpr int CHAIN_MAX = 12288;       // rows of a chain (8 bytes of shared memory each)
 constexpr int CHAIN_WIDTH = 32;        // a level belongs to the chain if it has at most this many rows
 
@@ -572,7 +578,8 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
         c->o.ortho < KKT_ORTHO_CGS2 || c->o.ortho > KKT_ORTHO_CGS1_PYTH ||
         !(c->o.inner_tol > 0.0 && c->o.inner_tol <= 1.0) || (c->o.repivot != 0 && c->o.repivot != 1) ||
         (c->o.graphs != 0 && c->o.graphs != 1) || (c->o.warp_rows != 0 && c->o.warp_rows != 1) ||
-        (c->o.row_order != 0 && c->o.row_order != 1) || c->o.mixed_fallback < 0 || c->o.warp_row_updates < -1) {
+        (c->o.row_order != 0 && c->o.row_order != 1) || c->o.mixed_fallback < 0 || c->o.warp_row_updates < -1 ||
+        c->o.map_cols < -1 || c->o.map_cols > 16384) {
         delete c;
         return KKT_ERR_INVALID;
     }
@@ -602,16 +609,21 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * CHAIN_MAX));
     cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev);
     c->smem_optin -= 1024;   // room for the kernel's static shared memory
-    for (const void* fn : {(const void*)kkt::k_refactor_rows<double, false, 256, false>,
-                           (const void*)kkt::k_refactor_rows<double, true, 256, false>,
-                           (const void*)kkt::k_refactor_rows<double, false, 512, false>,
-                           (const void*)kkt::k_refactor_rows<double, true, 512, false>,
-                           (const void*)kkt::k_refactor_rows<float, false, 256, false>,
-                           (const void*)kkt::k_refactor_rows<float, true, 256, false>,
-                           (const void*)kkt::k_refactor_rows<float, false, 512, false>,
-                           (const void*)kkt::k_refactor_rows<float, true, 512, false>,
-                           (const void*)kkt::k_refactor_rows<double, true, 256, true>,
-                           (const void*)kkt::k_refactor_rows<double, true, 512, true>})
+    for (const void* fn : {(const void*)kkt::k_refactor_rows<double, false, 0, false>,
+                           (const void*)kkt::k_refactor_rows<double, true, 0, false>,
+                           (const void*)kkt::k_refactor_rows<double, false, 1, false>,
+                           (const void*)kkt::k_refactor_rows<double, true, 1, false>,
+                           (const void*)kkt::k_refactor_rows<double, false, 2, false>,
+                           (const void*)kkt::k_refactor_rows<double, true, 2, false>,
+                           (const void*)kkt::k_refactor_rows<float, false, 0, false>,
+                           (const void*)kkt::k_refactor_rows<float, true, 0, false>,
+                           (const void*)kkt::k_refactor_rows<float, false, 1, false>,
+                           (const void*)kkt::k_refactor_rows<float, true, 1, false>,
+                           (const void*)kkt::k_refactor_rows<float, false, 2, false>,
+                           (const void*)kkt::k_refactor_rows<float, true, 2, false>,
+                           (const void*)kkt::k_refactor_rows<double, true, 0, true>,
+                           (const void*)kkt::k_refactor_rows<double, true, 1, true>,
+                           (const void*)kkt::k_refactor_rows<double, true, 2, true>})
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_optin);
     cudaGetLastError();
     per_sm = std::max(1, std::min(per_sm, per_sm3));
@@ -668,7 +680,7 @@ int kkt_pivot(int32_t n, const int32_t* rowptr, const int32_t* colind, const dou
 
 namespace {
 // Placement and dispatch order of the refactorization's rows
-// (k_refactor_rows).  A row's working set -- step descriptors (12 bytes per
+// (k_refactor_rows).  A row's working set -- step descriptors (8 bytes per
 // L entry), values and columns -- decides where it runs: one per warp if it
 // fits a warp's slice of the block's shared memory, one per block if it
 // fits the work area after the position map, else one per block with its
@@ -683,18 +695,22 @@ int setup_rows(kkt_ctx* c) {
     const auto& L = c->lay;
     for (void* p : c->row_allocs) cudaFree(p);
     c->row_allocs.clear();
-    c->d_gdk = c->d_gsdoff = c->d_gwoff = nullptr;
-    c->d_gcnt = nullptr;
+    c->d_gdk = c->d_gcnt = nullptr;
+    c->d_gsdoff = c->d_gwoff = nullptr;
     c->d_gw = nullptr;
     const size_t vsize = layout_vsize(c);
+    if ((uint64_t)L.Fj.size() >= ((uint64_t)1 << 32)) {   // step descriptors hold 32-bit factor positions
+        c->detail = "the factors have 2^32 entries or more";
+        return KKT_ERR_INVALID;
+    }
     auto need = [&](int32_t i) -> size_t {
         const int64_t st = L.Fdiag[i] - L.Fp[i], len = L.Fp[i + 1] - L.Fp[i];
-        return (12 * (size_t)st + (vsize + 4) * (size_t)len + 15) & ~(size_t)15;
+        return (8 * (size_t)st + (vsize + 4) * (size_t)len + 15) & ~(size_t)15;
     };
     size_t maxneed = 16;
     for (int32_t i = 0; i < n; i++) maxneed = std::max(maxneed, need(i));
     const size_t optin = (size_t)std::max(c->smem_optin, 48 * 1024);
-    int M = std::min(REF_MAP_COLS, n);
+    int M = std::min(c->o.map_cols > 0 ? c->o.map_cols : c->o.map_cols < 0 ? 0 : REF_MAP_COLS, n);
     size_t map_bytes = ((size_t)2 * M + 15) & ~(size_t)15;
     size_t S;
     if (c->o.block_smem > 0) {
@@ -708,7 +724,10 @@ int setup_rows(kkt_ctx* c) {
         S = std::min(maxneed, optin);
     }
     S = std::max(S, map_bytes + 4096);
-    c->ref_threads = S > REF_SMEM_WIDE ? 512 : 256;
+    // block shape: three 256-thread blocks an SM when they fit its shared
+    // memory, else two, else one of 512 threads
+    c->ref_shape = S <= REF_SMEM_THREE ? 0 : S <= REF_SMEM_WIDE ? 1 : 2;
+    c->ref_threads = c->ref_shape == 2 ? 512 : 256;
     c->ref_smem = S;
     c->ref_map_cols = M;
     c->ref_map_bytes = map_bytes;
@@ -721,7 +740,8 @@ int setup_rows(kkt_ctx* c) {
     // work (the dense end, on the critical path) go one per block even when
     // they fit a slice
     const int64_t wmax = c->o.warp_row_updates < 0 ? INT64_MAX
-                       : c->o.warp_row_updates == 0 ? DEFAULT_WARP_ROW_UPDATES : c->o.warp_row_updates;
+                       : c->o.warp_row_updates > 0 ? c->o.warp_row_updates
+                       : c->ref_threads == 512 ? DEFAULT_WARP_ROW_UPDATES_WIDE : DEFAULT_WARP_ROW_UPDATES;
     for (int32_t i = 0; i < n; i++) {
         const size_t q = need(i);
         int64_t upd = 0;
@@ -744,8 +764,8 @@ int setup_rows(kkt_ctx* c) {
     }
     std::vector<kkt::RefItem> items;
     items.reserve((size_t)n);
-    std::vector<int64_t> gdk, gsdoff, gwoff;
-    std::vector<int32_t> gcnt;
+    std::vector<uint32_t> gdk, gcnt;
+    std::vector<int64_t> gsdoff, gwoff;
     int64_t gw_total = 0;
     for (int32_t t = 0; t < n;) {
         const int32_t r = order[t];
@@ -764,8 +784,8 @@ int setup_rows(kkt_ctx* c) {
             gwoff.push_back(gw_total);
             for (int64_t q = L.Fp[r]; q < L.Fdiag[r]; q++) {
                 const int32_t k = L.Fj[q];
-                gdk.push_back(L.Fdiag[k]);
-                gcnt.push_back((int32_t)(L.Fp[k + 1] - L.Fdiag[k] - 1));
+                gdk.push_back((uint32_t)L.Fdiag[k]);
+                gcnt.push_back((uint32_t)(L.Fp[k + 1] - L.Fdiag[k] - 1));
             }
             gw_total += L.Fp[r + 1] - L.Fp[r];
             items.push_back(kkt::RefItem{t, (kkt::ROW_GLOBAL << 28) | g});
@@ -798,17 +818,16 @@ int setup_rows(kkt_ctx* c) {
     CK(cudaStreamSynchronize(c->stream));   // the host vectors are locals
     int per_sm = 1 << 30;
     std::vector<const void*> fns;
+    auto both = [&](auto f_plain, auto f_fused) { fns.push_back((const void*)f_plain); fns.push_back((const void*)f_fused); };
     if (c->mixed) {
-        fns.push_back(c->ref_threads == 512 ? (const void*)kkt::k_refactor_rows<float, false, 512, false>
-                                            : (const void*)kkt::k_refactor_rows<float, false, 256, false>);
-        fns.push_back(c->ref_threads == 512 ? (const void*)kkt::k_refactor_rows<float, true, 512, false>
-                                            : (const void*)kkt::k_refactor_rows<float, true, 256, false>);
+        if (c->ref_shape == 0) both(kkt::k_refactor_rows<float, false, 0, false>, kkt::k_refactor_rows<float, true, 0, false>);
+        if (c->ref_shape == 1) both(kkt::k_refactor_rows<float, false, 1, false>, kkt::k_refactor_rows<float, true, 1, false>);
+        if (c->ref_shape == 2) both(kkt::k_refactor_rows<float, false, 2, false>, kkt::k_refactor_rows<float, true, 2, false>);
     }
     if (!c->mixed || c->fallback_on) {
-        fns.push_back(c->ref_threads == 512 ? (const void*)kkt::k_refactor_rows<double, false, 512, false>
-                                            : (const void*)kkt::k_refactor_rows<double, false, 256, false>);
-        fns.push_back(c->ref_threads == 512 ? (const void*)kkt::k_refactor_rows<double, true, 512, false>
-                                            : (const void*)kkt::k_refactor_rows<double, true, 256, false>);
+        if (c->ref_shape == 0) both(kkt::k_refactor_rows<double, false, 0, false>, kkt::k_refactor_rows<double, true, 0, false>);
+        if (c->ref_shape == 1) both(kkt::k_refactor_rows<double, false, 1, false>, kkt::k_refactor_rows<double, true, 1, false>);
+        if (c->ref_shape == 2) both(kkt::k_refactor_rows<double, false, 2, false>, kkt::k_refactor_rows<double, true, 2, false>);
     }
     for (const void* fn : fns) {   // the grid is sized for the instantiation with fewer resident blocks
         int bl = 0;
@@ -1164,8 +1183,9 @@ extern "C++" {
 namespace {
 // gather (arms every factor value with SENTINEL), then the one
 // refactorization kernel over every row, in type T
-template <typename T, int NT>
+template <typename T, int SHAPE>
 void refactor_rows_launch(kkt_ctx* c, const double* vals, unsigned long long* trace, const double* fused_rhs) {
+    constexpr int NT = kkt::RefShape<SHAPE>::NT;
     kkt::RefArgs<T> a{};
     a.items = c->d_items;
     a.nitems = c->nitems;
@@ -1191,7 +1211,7 @@ void refactor_rows_launch(kkt_ctx* c, const double* vals, unsigned long long* tr
     a.fw = kkt::FwdArgs<T>{fused_rhs, c->d_P, (T*)c->d_y, (T*)c->d_xp};
     a.boost_eps = c->o.boost_eps;
     const int blocks = std::max(1, std::min(c->nitems, c->ref_blocks));
-    auto kern = fused_rhs ? kkt::k_refactor_rows<T, true, NT, false> : kkt::k_refactor_rows<T, false, NT, false>;
+    auto kern = fused_rhs ? kkt::k_refactor_rows<T, true, SHAPE, false> : kkt::k_refactor_rows<T, false, SHAPE, false>;
     kern<<<blocks, NT, c->ref_smem, c->stream>>>(a, kkt::RefBatch<T>{}, spin(c), trace);
 }
 
@@ -1205,8 +1225,9 @@ void refactor_launch(kkt_ctx* c, const double* vals, unsigned long long* trace, 
                                                             fused_rhs ? (T*)c->d_y : nullptr);
     phase_end(c, t);
     t = phase_begin(c, KKT_PHASE_REFACTOR);
-    if (c->ref_threads == 512) refactor_rows_launch<T, 512>(c, vals, trace, fused_rhs);
-    else refactor_rows_launch<T, 256>(c, vals, trace, fused_rhs);
+    if (c->ref_shape == 2) refactor_rows_launch<T, 2>(c, vals, trace, fused_rhs);
+    else if (c->ref_shape == 1) refactor_rows_launch<T, 1>(c, vals, trace, fused_rhs);
+    else refactor_rows_launch<T, 0>(c, vals, trace, fused_rhs);
     phase_end(c, t);
     c->launches += 3;   // prep, gather, refactorization
 }
@@ -2045,8 +2066,9 @@ int kkt_batch_create(kkt_batch** out, int max_count, int device) {
     if (e == cudaSuccess) e = cudaMallocHost(&bt->h_res, n * sizeof(kkt::ResidualArgs));
     if (e == cudaSuccess) {
         bt->smem_optin -= 1024;
-        for (const void* fn : {(const void*)kkt::k_refactor_rows<double, true, 256, true>,
-                               (const void*)kkt::k_refactor_rows<double, true, 512, true>,
+        for (const void* fn : {(const void*)kkt::k_refactor_rows<double, true, 0, true>,
+                               (const void*)kkt::k_refactor_rows<double, true, 1, true>,
+                               (const void*)kkt::k_refactor_rows<double, true, 2, true>,
                                (const void*)kkt::k_usolve_cluster_batch}) {
             const cudaError_t ea = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                         fn == (const void*)kkt::k_usolve_cluster_batch
@@ -2087,15 +2109,15 @@ int kkt_batch_step(kkt_batch* bt, kkt_ctx* const* ctxs, int count, const double*
     // device with the refactorization block size of the first of them; the
     // others run as lone kkt_step calls afterwards
     std::vector<int> in, alone;
-    int nt = 0;
+    int shape = -1;
     for (int i = 0; i < count; i++) {
         kkt_ctx* c = ctxs[i];
         status[i] = KKT_ERR_INVALID;
         if (!c || !values[i] || !b[i] || !x[i]) return KKT_ERR_INVALID;
         for (int j = 0; j < i; j++) if (ctxs[j] == c) return KKT_ERR_INVALID;   // one step per instance
         if (!c->analyzed) { status[i] = KKT_ERR_STATE; continue; }
-        const bool ok = c->dev == bt->dev && !c->mixed && !c->o.graphs && (nt == 0 || c->ref_threads == nt);
-        if (ok) { nt = c->ref_threads; in.push_back(i); }
+        const bool ok = c->dev == bt->dev && !c->mixed && !c->o.graphs && (shape < 0 || c->ref_shape == shape);
+        if (ok) { shape = c->ref_shape; in.push_back(i); }
         else alone.push_back(i);
     }
     {   // the shared launch holds every instance's work area and the largest map
@@ -2187,16 +2209,23 @@ int kkt_batch_step(kkt_batch* bt, kkt_ctx* const* ctxs, int count, const double*
         kkt::k_refactor_prep_batch<<<(nb + 255) / 256, 256, 0, bt->stream>>>(bt->d_gather, nb, bt->d_ticket);
         kkt::k_gather_batch<<<dim3(std::max(8, 2 * bt->num_sms / nb), nb), 256, 0, bt->stream>>>(bt->d_gather);
         // one refactorization launch for every instance's rows
-        const void* fn = nt == 512 ? (const void*)kkt::k_refactor_rows<double, true, 512, true>
-                                   : (const void*)kkt::k_refactor_rows<double, true, 256, true>;
+        // the shared launch's shared memory may exceed every instance's own,
+        // so its shape is taken from that size
+        const int sh = smem <= REF_SMEM_THREE ? 0 : smem <= REF_SMEM_WIDE ? 1 : 2;
+        const int nt = sh == 2 ? 512 : 256;
+        const void* fn = sh == 2 ? (const void*)kkt::k_refactor_rows<double, true, 2, true>
+                       : sh == 1 ? (const void*)kkt::k_refactor_rows<double, true, 1, true>
+                                 : (const void*)kkt::k_refactor_rows<double, true, 0, true>;
         int per_sm = 0;
         CK_BT(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
         const int blocks = std::max(1, per_sm) * bt->num_sms;
         const kkt::RefBatch<double> rb{bt->d_ref, nb, (long long)nb * items, bt->d_ticket, map_cols, (int)area};
-        if (nt == 512)
-            kkt::k_refactor_rows<double, true, 512, true><<<blocks, 512, smem, bt->stream>>>(kkt::RefArgs<double>{}, rb, limit, nullptr);
+        if (sh == 2)
+            kkt::k_refactor_rows<double, true, 2, true><<<blocks, 512, smem, bt->stream>>>(kkt::RefArgs<double>{}, rb, limit, nullptr);
+        else if (sh == 1)
+            kkt::k_refactor_rows<double, true, 1, true><<<blocks, 256, smem, bt->stream>>>(kkt::RefArgs<double>{}, rb, limit, nullptr);
         else
-            kkt::k_refactor_rows<double, true, 256, true><<<blocks, 256, smem, bt->stream>>>(kkt::RefArgs<double>{}, rb, limit, nullptr);
+            kkt::k_refactor_rows<double, true, 0, true><<<blocks, 256, smem, bt->stream>>>(kkt::RefArgs<double>{}, rb, limit, nullptr);
         bt->launches += 3;
         // the backward sweeps: one cluster per instance in one launch, or
         // each instance's own schedule
