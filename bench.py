@@ -733,7 +733,7 @@ def run_ours(args):
         "gpu_launches": launches, "clocks": clk, "wall_s": t_wall, "job_s": time.perf_counter() - t_job,
         "precision": args.precision, "other_precision": other, "per_config": per_config,
         "serving": serving, "serving_mixed": serving_c4,
-        "schedule": {k: info0[k] for k in ("rows_warp", "rows_block", "rows_global", "refactor_smem",
+        "schedule": {k: info0[k] for k in ("rows_warp", "rows_team", "rows_block", "rows_global", "refactor_smem",
                                            "refactor_threads", "refactor_blocks", "trisolve_cluster")},
         "analysis": {"analyze_ms": info0["analyze_ms"], "nnz_l": info0["nnz_l"], "nnz_u": info0["nnz_u"],
                      "levels_l": info0["levels_l"], "levels_u": info0["levels_u"],

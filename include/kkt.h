@@ -89,12 +89,14 @@ typedef struct {
     int cluster_blocks;   /* blocks of the cluster solve: 0 = 16 if it fits and can be
                              scheduled, else 8; 8 or 16 to force one */
     int block_smem;       /* shared memory (bytes) of each block of the refactorization
-                             kernel: 0 (default) = sized by the longest row of the
-                             factors, up to the device's limit; rows whose working set
-                             fits a warp's slice of it go one per warp, longer rows
-                             that fit it one per block, the rest one per block with
-                             their values in global memory.  Blocks of more than
-                             ~113 KB run 512 threads, else 256. */
+                             kernel: 0 (default) = the most of the bracket (74 KB: three
+                             blocks an SM; 112 KB: two; the device's limit: one) that
+                             holds the row needing the most (its working set and
+                             position table); rows whose working set fits a warp's
+                             slice of it go one per warp, longer rows that fit it one
+                             per block (or per half block, kkt_opts.team_rows), the
+                             rest one per block with their values in global memory.
+                             Blocks of more than 112 KB run 512 threads, else 256. */
     int method;           /* refinement after x0 = (LU)^{-1} b: KKT_METHOD_FGMRES (default),
                              KKT_METHOD_RICHARDSON, KKT_METHOD_FGMRES_EE */
     int ortho;            /* Arnoldi orthogonalisation: KKT_ORTHO_CGS2 (default),
@@ -119,9 +121,6 @@ typedef struct {
                              by level in the dependency DAG of L (ties by row); 0 by
                              row.  A row's dependencies are always dispatched before
                              it.  Same arithmetic either way. */
-    int map_cols;         /* columns (the last ones) with an O(1) position map in block rows:
-                             0 = default (16384 when it fits beside the longest row),
-                             -1 = none, > 0 = at most that many */
     int64_t warp_row_updates; /* a row is refactored one per warp only if its multiply-adds
                              (the sum of |U(k,>k)| over its L entries) are at most this
                              (besides fitting a warp's slice); -1 = no limit; 0 = the
@@ -138,6 +137,15 @@ typedef struct {
                              until the next refactorization; kkt_info.last_fallback and
                              fallbacks count it.  The context holds FP64 factor storage
                              beside the FP32 one.  0 = no fallback (FP32 throughout). */
+    int stream_last;      /* 1 (default): a row refactored by a whole block stores each value
+                             of its last elimination step as soon as that value is final
+                             (the pivot by the thread that updates it), so rows that wait
+                             on it start while it finishes; 0: all values after the last
+                             step's barrier.  Same values and bits either way. */
+    int team_rows;        /* 1 (default): with 512-thread blocks, rows that fit half the
+                             block's shared memory are refactored one per half block
+                             (two such rows at a time, 256 threads each); 0: one per
+                             block.  Same arithmetic either way. */
 } kkt_opts;
 
 /* Refinement methods (Section 2.1).  FGMRES: FGMRES(m) with M = LU as right
@@ -204,7 +212,7 @@ typedef struct {
     int64_t d2h_bytes;     /* device->host bytes copied by refactor/solve calls so far */
     int32_t repivots;      /* pivoting refactorizations run by kkt_repivot so far */
     int32_t rows_warp;     /* rows refactored one per warp in shared memory */
-    int32_t rows_block;    /* rows refactored one per block in shared memory */
+    int32_t rows_block;    /* rows refactored one per block in shared memory (whole block) */
     int32_t rows_global;   /* rows refactored one per block with values in global memory */
     int32_t refactor_smem; /* shared memory per block of the refactorization kernel (bytes) */
     int32_t refactor_threads; /* threads per block of the refactorization kernel */
@@ -212,6 +220,7 @@ typedef struct {
     int32_t last_fallback; /* 1 if the last refactorization or solve fell back to FP64
                               (kkt_opts.mixed_fallback) */
     int64_t fallbacks;     /* FP64 fallbacks so far */
+    int32_t rows_team;     /* rows refactored one per half block (512-thread blocks) */
 } kkt_info;
 
 /* Fill *o with the defaults above. */

@@ -58,7 +58,8 @@ class _Opts(C.Structure):
         ("timing", C.c_int), ("trisolve", C.c_int), ("cluster_blocks", C.c_int), ("block_smem", C.c_int),
         ("method", C.c_int), ("ortho", C.c_int), ("inner_tol", C.c_double), ("repivot", C.c_int),
         ("graphs", C.c_int), ("warp_rows", C.c_int), ("row_order", C.c_int),
-        ("map_cols", C.c_int), ("warp_row_updates", C.c_int64), ("mixed_fallback", C.c_int),
+        ("warp_row_updates", C.c_int64), ("mixed_fallback", C.c_int),
+        ("stream_last", C.c_int), ("team_rows", C.c_int),
     ]
 
 
@@ -72,7 +73,7 @@ class _Info(C.Structure):
         ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("repivots", C.c_int32), ("rows_warp", C.c_int32),
         ("rows_block", C.c_int32), ("rows_global", C.c_int32), ("refactor_smem", C.c_int32),
         ("refactor_threads", C.c_int32), ("refactor_blocks", C.c_int32), ("last_fallback", C.c_int32),
-        ("fallbacks", C.c_int64),
+        ("fallbacks", C.c_int64), ("rows_team", C.c_int32),
     ]
 
 
@@ -296,7 +297,8 @@ def lu_solve_noalloc(Fp, Fj, Fdiag, Fx, P, Q, b, x, stream=None):
 def _solver_opts(restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, pivot_tol=1e-3, boost_eps=0.0,
                  device=0, spin_limit=0, timing=False, trisolve="auto", block_smem=0, cluster_blocks=0,
                  precision="fp64", method="fgmres", ortho="cgs2", inner_tol=1e-6, repivot=False, graphs=False,
-                 warp_rows=True, row_order="level", mixed_fallback=2, warp_row_updates=0, map_cols=0):
+                 warp_rows=True, row_order="level", mixed_fallback=2, warp_row_updates=0, stream_last=True,
+                 team_rows=True):
     """kkt_opts from keyword arguments (defaults of kkt_default_opts)."""
     o = _Opts()
     lib().kkt_default_opts(C.byref(o))
@@ -314,7 +316,8 @@ def _solver_opts(restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, 
     o.row_order = ROW_ORDER[row_order]
     o.mixed_fallback = int(mixed_fallback)
     o.warp_row_updates = int(warp_row_updates)
-    o.map_cols = int(map_cols)
+    o.stream_last = int(bool(stream_last))
+    o.team_rows = int(bool(team_rows))
     return o
 
 
@@ -326,11 +329,11 @@ class KKTSolver:
                  boost_eps=0.0, device=0, stream=None, spin_limit=0, timing=False, trisolve="auto",
                  block_smem=0, cluster_blocks=0, precision="fp64", method="fgmres", ortho="cgs2",
                  inner_tol=1e-6, repivot=False, graphs=False, warp_rows=True, row_order="level",
-                 mixed_fallback=2, warp_row_updates=0, map_cols=0):
+                 mixed_fallback=2, warp_row_updates=0, stream_last=True, team_rows=True):
         L = lib()
         o = _solver_opts(restart, max_cycles, stop_mode, refine_delta, pivot_tol, boost_eps, device, spin_limit,
                          timing, trisolve, block_smem, cluster_blocks, precision, method, ortho, inner_tol, repivot,
-                         graphs, warp_rows, row_order, mixed_fallback, warp_row_updates, map_cols)
+                         graphs, warp_rows, row_order, mixed_fallback, warp_row_updates, stream_last, team_rows)
         if stream is None:
             stream = _torch_current_stream(device)
         if stream is None:

@@ -21,6 +21,7 @@
 #define SPIN_SLEEP_NS 20
 #endif
 #include <cooperative_groups.h>
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -329,22 +330,25 @@ __global__ void k_scatter_values(int64_t nnz, const double* __restrict__ Ax, con
 // columns and the descriptors of its elimination steps:
 //   ROW_WARP   one warp, in that warp's slice of the block's shared memory;
 //   ROW_BLOCK  the whole block, in the block's shared memory (the long
-//              rows at the dense end of the order), with a position map for
-//              the last columns;
+//              rows at the dense end of the order), with a table of its
+//              columns' positions;
+//   ROW_TEAM   one team of the block's threads (RefShape::TEAMS > 1), in
+//              that team's share of the shared memory, with a table;
 //   ROW_GLOBAL the whole block, its values in a global scratch area (rows
 //              that fit no block).
-// Work items (up to one warp-row per warp, or one block row) are taken from
+// Work items (up to one warp row per warp, one team row per team, or one
+// block row) are taken from
 // an atomic ticket in the order of their rows' level in the dependency DAG
 // of L, so a row's dependencies are always dispatched before it and every
 // row a block waits on belongs to a block that is already running.  A
 // finished row publishes its U values and 1/u_ii with no fences: every
 // published datum is armed with SENTINEL by the gather and is final once it
 // is not, so a consumer spins on exactly the values it uses.
-constexpr int ROW_WARP = 0, ROW_BLOCK = 1, ROW_GLOBAL = 2;
+constexpr int ROW_WARP = 0, ROW_BLOCK = 1, ROW_GLOBAL = 2, ROW_TEAM = 3;
 
 struct RefItem {       // rows order[first .. first + count) of one kind
     int32_t first;
-    int32_t info;      // kind << 28 | count (ROW_WARP) or global-row index (ROW_GLOBAL)
+    int32_t info;      // kind << 28 | count (ROW_WARP, ROW_TEAM) or global-row index (ROW_GLOBAL)
 };
 
 template <typename T>
@@ -359,10 +363,8 @@ struct RefArgs {
     T* rinv;
     const double* vals;
     const int64_t* fsrc;
-    int mlo, M;            // columns [mlo, mlo + M) have an O(1) position map (M may be 0)
-    int map_bytes;         // bytes of the position map (16-byte aligned), after the work area
-    int area_bytes;        // the work area of a block row, at the start of shared memory
-    int slice_bytes;       // a warp row's slice: warp w's starts at w * slice_bytes (slices span the map too)
+    int area_bytes;        // a block row's room in shared memory (working set and position table)
+    int slice_bytes;       // a warp row's slice: warp w's starts at w * slice_bytes
     // ROW_GLOBAL rows, by global-row index g: step descriptors at sd_off[g]
     // in gdk / gcnt, values at w_off[g] in gw
     const uint32_t* gdk;
@@ -373,6 +375,7 @@ struct RefArgs {
     DevScal* s;            // the instance's scalars (tickets of a lone launch, errors, ||K||_inf)
     FwdArgs<T> fw;         // the fused forward sweep (fw.rhs == nullptr: not fused)
     double boost_eps;
+    int stream_last;       // block rows publish their last step's values as they are formed
 };
 
 // Several instances' refactorizations in one launch: global ticket t goes
@@ -386,8 +389,6 @@ struct RefBatch {
     int count;
     long long total;          // count * the most items of any instance
     unsigned long long* ticket;   // zeroed before the launch
-    int map_cols;             // the largest position map of any instance
-    int map_off;              // where the map starts: after the largest work area of any instance
 };
 
 __device__ __forceinline__ bool finite_bits(double v) {
@@ -448,29 +449,77 @@ __device__ __forceinline__ int slice_pos(const int32_t* cols, int lo, int hi, in
     return (lo < end && cols[lo] == c) ? lo : -1;
 }
 
-// Column c's position in the row: the shared map for c in [mlo, mlo + M),
-// else the narrowed binary search.
-__device__ __forceinline__ int row_pos(int c, int mlo, int M, const short* map, const int32_t* cols, int lo,
-                                       int hi) {
-    if ((unsigned)(c - mlo) < (unsigned)M) return map[c - mlo];
-    return slice_pos(cols, lo, hi, c);
+// A block row in shared memory finds the position of a column through a
+// table of its own columns: 2^bits entries of 16-bit positions (0xFFFF
+// empty), linear probing.  A row whose columns span fewer than 2^bits
+// indices is mapped directly (slot c - c_0 for column c, c_0 its first:
+// no collisions, and consecutive columns in consecutive slots); other rows
+// by Fibonacci hashing.  Its bits: the most
+// that fit `room` bytes beside the row's working set (8 st + (vsize + 4)
+// len bytes), at most ceil(log2(4 len)) (load factor above 1/8) and at
+// least ceil(log2(len + len/4 + 1)) (load factor below 0.8, so a probe
+// sequence always meets an empty entry); -1 if even that does not fit
+// (the row then runs with its values in global memory).  The host's
+// placement and the kernel evaluate the same function.
+constexpr int REF_TAB_EMPTY = 0xFFFF;
+// windows of at most this many entries are searched rather than hashed
+constexpr int REF_WINDOW_MAX = 16;
+__host__ __device__ inline int ceil_log2_i64(int64_t x) {
+    int b = 0;
+    while (((int64_t)1 << b) < x) b++;
+    return b;
+}
+__host__ __device__ inline int64_t row_set_bytes(int64_t st, int64_t len, int64_t vsize) {
+    return 8 * st + (vsize + 4) * len;
+}
+__host__ __device__ inline int row_table_bits(int64_t st, int64_t len, int64_t vsize, int64_t room) {
+    if (len >= REF_TAB_EMPTY) return -1;
+    const int lo0 = ceil_log2_i64(len + len / 4 + 1), hi0 = ceil_log2_i64(4 * len);
+    const int lo = lo0 < 4 ? 4 : lo0, hi = hi0 < 4 ? 4 : hi0;
+    const int64_t base = row_set_bytes(st, len, vsize);
+    for (int b = hi; b >= lo; b--)
+        if (base + ((int64_t)2 << b) <= room) return b;
+    return -1;
+}
+// c0 >= 0: the direct map of a row starting at column c0; else hashing
+__device__ __forceinline__ uint32_t col_slot(int c, int bits, int c0) {
+    return c0 >= 0 ? (uint32_t)(c - c0) & ((1u << bits) - 1) : ((uint32_t)c * 0x9E3779B1u) >> (32 - bits);
+}
+
+// Position of column c in a block row through its table, or -1.  A
+// direct map holds every column of the row in its own slot, so its one
+// probe decides.
+__device__ __forceinline__ int tab_pos(const uint16_t* tab, int bits, int c0, const int32_t* cols, int c) {
+    if (c0 >= 0) {
+        const int p = tab[(uint32_t)(c - c0) & ((1u << bits) - 1)];
+        return p == REF_TAB_EMPTY ? -1 : p;
+    }
+    const uint32_t mask = (1u << bits) - 1;
+    for (uint32_t h = col_slot(c, bits, c0);; h = (h + 1) & mask) {
+        const int p = tab[h];
+        if (p == REF_TAB_EMPTY) return -1;
+        if (cols[p] == c) return p;
+    }
 }
 
 // A row's working set carved from `base`: step descriptors (position of
 // U(k,k) and |U(k, >k)| for every L entry, 4 bytes each -- the analysis
 // keeps every factor position below 2^32; k itself is the column), the
-// row's values and its columns -- 8 st + (sizeof(T) + 4) len bytes.
+// row's values and its columns -- 8 st + (sizeof(T) + 4) len bytes -- and,
+// for a block row in shared memory, its position table after them.
 template <typename T>
 struct RowSpace {
     uint32_t* dk;
     uint32_t* cnt;
     T* w;
     int32_t* cols;
+    uint16_t* tab;
     __device__ RowSpace(unsigned char* base, int st, int len) {
         dk = reinterpret_cast<uint32_t*>(base);
         cnt = dk + st;
         w = reinterpret_cast<T*>(cnt + st);   // 8 st bytes in: aligned for double
         cols = reinterpret_cast<int32_t*>(w + len);
+        tab = reinterpret_cast<uint16_t*>(cols + len);
     }
 };
 
@@ -568,14 +617,35 @@ __device__ bool warp_row(int row, const RefArgs<T>& a, DevScal* s, T boost, long
 // per block: NT threads, at least MINB blocks an SM (which caps the
 // registers: 80 a thread for three 256-thread blocks, 128 otherwise), PRE
 // entries of each step a thread prefetches two steps ahead, BATCH entries a
-// thread loads together past those.  Measured on kkt2000 (three blocks an
-// SM): PRE 3 under the 80-register cap 5.11 ms against 5.42 with PRE 4;
-// on kkt10000 (two blocks an SM by shared memory) no cap 39.2 ms against
-// 43.0 with it.
+// thread loads together past those, TEAMS teams of NT / TEAMS threads that
+// each refactor a row of their own (ROW_TEAM items: rows that fit 1/TEAMS
+// of the shared memory) when the block is not working on one row whole.
+// Measured on kkt2000 (three blocks an SM, the fused step's refactor):
+// PRE 2 under the 80-register cap 5.05 ms against 5.31 with PRE 3 (which
+// spills); on kkt10000 (two blocks an SM by shared memory) no cap 39.2 ms
+// against 43.0 with it.
 template <int SHAPE> struct RefShape;
-template <> struct RefShape<0> { static constexpr int NT = 256, MINB = 3, PRE = 3, BATCH = 2; };
-template <> struct RefShape<1> { static constexpr int NT = 256, MINB = 2, PRE = 4, BATCH = 4; };
-template <> struct RefShape<2> { static constexpr int NT = 512, MINB = 1, PRE = 4, BATCH = 4; };
+template <> struct RefShape<0> { static constexpr int NT = 256, MINB = 3, PRE = 2, BATCH = 2, TEAMS = 1; };
+template <> struct RefShape<1> { static constexpr int NT = 256, MINB = 2, PRE = 4, BATCH = 4, TEAMS = 1; };
+template <> struct RefShape<2> { static constexpr int NT = 512, MINB = 1, PRE = 4, BATCH = 4, TEAMS = 2; };
+
+// The barrier of a team of tt threads working on one row: named barrier
+// `id` (1 + the team's index for a team of a block, REF_BAR_BLOCK for the
+// whole block), so the teams of a block never wait on each other.
+constexpr int REF_BAR_BLOCK = 3;
+__device__ __forceinline__ void team_sync(int id, int tt) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(tt) : "memory");
+}
+__device__ __forceinline__ int team_sync_or(int id, int tt, int pred) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(pred), "r"(id), "r"(tt)
+        : "memory");
+    return r;
+}
 
 // One elimination step's first entries for one thread of a block row:
 // PRE entries of U(k,:) (columns and values) and the pivot reciprocal of
@@ -587,8 +657,8 @@ struct Stage {
     T val[PRE];
 };
 
-template <typename T, int NT, int PRE>
-__device__ __forceinline__ void stage_load(Stage<T, PRE>& st, int step, int nsteps, const int32_t* cols,
+template <typename T, int PRE>
+__device__ __forceinline__ void stage_load(Stage<T, PRE>& st, int tid, int NT, int step, int nsteps, const int32_t* cols,
                                            const uint32_t* dk, const uint32_t* cnt, const RefArgs<T>& a) {
     if (step >= nsteps) return;
     const int64_t base = (int64_t)dk[step] + 1;
@@ -596,35 +666,44 @@ __device__ __forceinline__ void stage_load(Stage<T, PRE>& st, int step, int nste
     st.rk = ld_relaxed(&a.rinv[cols[step]]);
 #pragma unroll
     for (int j = 0; j < PRE; j++) {
-        const int e = threadIdx.x + j * NT;
+        const int e = tid + j * NT;
         if (e < c) { st.col[j] = a.Fj[base + e]; st.val[j] = ld_relaxed(&a.Fx[base + e]); }
     }
 }
 
-// One long row by the whole block.  rs: its working set, in shared memory
-// (ROW_BLOCK: staged here) or in global memory (ROW_GLOBAL: descriptors
-// precomputed at analysis, columns read from Fj, values in scratch).
-// Returns false (uniformly for the block) if a wait gave up.
+// One long row by a team of NT threads: the whole block (team 0, NT the
+// block's threads), or one of its RefShape::TEAMS teams (team t: threads
+// [t NT, (t + 1) NT)).  rs: its working set, in shared memory (ROW_BLOCK /
+// ROW_TEAM: staged here, with its position table, in `room` bytes) or in
+// global memory (ROW_GLOBAL: descriptors precomputed at analysis, columns
+// read from Fj, values in scratch, positions by binary search).  Returns
+// false (uniformly for the team) if a wait gave up.
 template <typename T, bool FUSED, int SHAPE>
 __device__ bool block_row(int row, const RefArgs<T>& a, DevScal* s, T boost, long long limit,
-                          unsigned long long* trace, RowSpace<T> rs, bool staged, short* map, int M,
+                          unsigned long long* trace, RowSpace<T> rs, bool staged, int room, int team, int NT,
                           const FwdArgs<T>& fw) {
-    constexpr int NT = RefShape<SHAPE>::NT, PRE = RefShape<SHAPE>::PRE;
-    const int tid = threadIdx.x;
+    constexpr int NB = RefShape<SHAPE>::NT, PRE = RefShape<SHAPE>::PRE;
+    const int tid = threadIdx.x - team * NT;
+    const int bar = NT == NB ? REF_BAR_BLOCK : 1 + team;
     if (trace && tid == 0) trace[2 * (size_t)row] = globaltimer_ns();
     const int64_t b = a.Fp[row], d = a.Fdiag[row], e = a.Fp[row + 1];
     const int len = (int)(e - b);
     const int nsteps = (int)(d - b);
     T* w = rs.w;
     const int32_t* cols = staged ? rs.cols : a.Fj + b;
-    const int mlo = a.mlo;
+    const int tbits = staged ? row_table_bits(nsteps, len, sizeof(T), room) : 0;
+    const int dpos = (int)(d - b);
+    __shared__ int s_pivot_done_t[RefShape<SHAPE>::TEAMS];   // the last step's updater of the diagonal published the pivot
+    int& s_pivot_done = s_pivot_done_t[team];
+    if (tid == 0) s_pivot_done = 0;
+    if (staged)
+        for (int h = tid; h < (1 << tbits); h += NT) rs.tab[h] = (uint16_t)REF_TAB_EMPTY;
     for (int q = tid; q < len; q += NT) {
         const int64_t src = a.fsrc[b + q];
         w[q] = src >= 0 ? (T)a.vals[src] : T(0);
         if (staged) {
             const int c = a.Fj[b + q];
             rs.cols[q] = c;
-            if ((unsigned)(c - mlo) < (unsigned)M) map[c - mlo] = (short)q;
             if (q < nsteps) {
                 const int64_t dk = a.Fdiag[c];
                 rs.dk[q] = (uint32_t)dk;
@@ -632,10 +711,23 @@ __device__ bool block_row(int row, const RefArgs<T>& a, DevScal* s, T boost, lon
             }
         }
     }
-    __syncthreads();
+    team_sync(bar, NT);
+    // the position table (every column inserted by the thread that staged
+    // it): direct when the row's columns span fewer than 2^tbits indices
+    const int tc0 = staged && len > 0 && rs.cols[len - 1] - rs.cols[0] < (1 << tbits) ? rs.cols[0] : -1;
+    if (staged) {
+        const uint32_t mask = (1u << tbits) - 1;
+        for (int q = tid; q < len; q += NT) {
+            if (tc0 >= 0) { rs.tab[rs.cols[q] - tc0] = (uint16_t)q; continue; }
+            for (uint32_t h = col_slot(rs.cols[q], tbits, -1);; h = (h + 1) & mask)
+                if (atomicCAS(&rs.tab[h], (unsigned short)REF_TAB_EMPTY, (unsigned short)q) == REF_TAB_EMPTY) break;
+        }
+        team_sync(bar, NT);
+    }
+
     Stage<T, PRE> A, B;
-    stage_load<T, NT, PRE>(A, 0, nsteps, cols, rs.dk, rs.cnt, a);
-    stage_load<T, NT, PRE>(B, 1, nsteps, cols, rs.dk, rs.cnt, a);
+    stage_load<T, PRE>(A, tid, NT, 0, nsteps, cols, rs.dk, rs.cnt, a);
+    stage_load<T, PRE>(B, tid, NT, 1, nsteps, cols, rs.dk, rs.cnt, a);
     int step = 0;
     // One elimination step: every thread forms l_ik = w_k * (1/u_kk) itself
     // (thread 0 also stores it), then applies its entries of U(k,:): the
@@ -664,14 +756,39 @@ __device__ bool block_row(int row, const RefArgs<T>& a, DevScal* s, T boost, lon
             }
         }
         const T l = w[step] * st.rk;   // l_ik = w_k * (1/u_kk)
+        // the last step leaves every value it updates final: with stream_last
+        // it is published at once (U values, and the pivot by its updater),
+        // so rows waiting on this one start their step while this one ends
+        const bool stream = a.stream_last && step == nsteps - 1;
+        auto update = [&](int pos, T v) {
+            const T nw = fma(-l, v, w[pos]);
+            w[pos] = nw;
+            if (stream) {
+                if (pos > dpos) st_relaxed(&a.Fx[b + pos], nw);
+                else if (pos == dpos) {
+                    if (publish_pivot<T>(nw, boost, boost > T(0), s, row, &a.Fx[d], &a.rinv[row]) && trace)
+                        trace[2 * (size_t)row + 1] = globaltimer_ns();
+                    s_pivot_done = 1;
+                }
+            }
+        };
+        // position of entry e2 of U(k,:), column c, in the row: a search
+        // of the window entry e2 must lie in (W entries, the same width for
+        // every entry of the step) when it is narrow or the row has no
+        // table, else the row's table
+        const int W = len - cnt - step;
+        const bool by_table = staged && W > REF_WINDOW_MAX;
+        auto find = [&](int c, int e2) -> int {
+            return by_table ? tab_pos(rs.tab, tbits, tc0, cols, c) : slice_pos(cols, step + 1 + e2, step + 1 + e2 + W, c);
+        };
         if (ok) {
 #pragma unroll
             for (int j = 0; j < PRE; j++) {
                 const int e2 = tid + j * NT;
                 if (e2 < cnt) {
-                    const int pos = row_pos(st.col[j], mlo, M, map, cols, step + 1 + e2, len - (cnt - 1 - e2));
+                    const int pos = find(st.col[j], e2);
                     if (pos < 0) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
-                    w[pos] = fma(-l, st.val[j], w[pos]);
+                    update(pos, st.val[j]);
                 }
             }
             constexpr int BATCH = RefShape<SHAPE>::BATCH;
@@ -688,14 +805,14 @@ __device__ bool block_row(int row, const RefArgs<T>& a, DevScal* s, T boost, lon
                     const int e2 = e0 + u * NT;
                     if (e2 >= cnt || !ok) continue;
                     if (!pub_wait(&a.Fx[base + e2], &v[u], s, limit, row)) { ok = 0; continue; }
-                    const int pos = row_pos(c[u], mlo, M, map, cols, step + 1 + e2, len - (cnt - 1 - e2));
+                    const int pos = find(c[u], e2);
                     if (pos < 0) { raise_error(s, KKT_ERR_PATTERN, row); continue; }
-                    w[pos] = fma(-l, v[u], w[pos]);
+                    update(pos, v[u]);
                 }
             }
         }
-        stage_load<T, NT, PRE>(st, step + 2, nsteps, cols, rs.dk, rs.cnt, a);   // the stage's registers are free again
-        const int any_fail = __syncthreads_or(!ok);   // uniform decision for the block
+        stage_load<T, PRE>(st, tid, NT, step + 2, nsteps, cols, rs.dk, rs.cnt, a);   // the stage's registers are free again
+        const int any_fail = team_sync_or(bar, NT, !ok);   // uniform decision for the team
         if (tid == 0) w[step] = l;   // nobody else touches position `step` any more
         step++;
         return !any_fail;
@@ -711,16 +828,12 @@ __device__ bool block_row(int row, const RefArgs<T>& a, DevScal* s, T boost, lon
     // thread its share of the values but the diagonal, then thread 0 the
     // pivot; the last step's l, which thread 0 wrote after that barrier,
     // thread 0 stores itself
-    for (int q = tid; q < len; q += NT) {
+    for (int q = tid; q < len; q += NT)
         if (b + q != d && q != nsteps - 1) st_relaxed(&a.Fx[b + q], w[q]);
-        if (staged) {
-            const int c = cols[q];
-            if ((unsigned)(c - mlo) < (unsigned)M) map[c - mlo] = -1;
-        }
-    }
     if (tid == 0) {
         if (nsteps > 0) st_relaxed(&a.Fx[b + nsteps - 1], w[nsteps - 1]);
-        if (publish_pivot<T>(w[d - b], boost, boost > T(0), s, row, &a.Fx[d], &a.rinv[row]) && trace)
+        if (!s_pivot_done &&
+            publish_pivot<T>(w[d - b], boost, boost > T(0), s, row, &a.Fx[d], &a.rinv[row]) && trace)
             trace[2 * (size_t)row + 1] = globaltimer_ns();
     }
     // the fused forward sweep's y_row, by warp 0 from the row's values; the
@@ -733,29 +846,18 @@ __device__ bool block_row(int row, const RefArgs<T>& a, DevScal* s, T boost, lon
 }
 
 // The refactorization: blocks of NT threads take work items from the
-// ticket until none is left.  Shared memory: a block row's working set at
-// the start, the position map of the last M columns after it (-1 where the
-// row being factored has no such column); warp rows use one slice per warp
-// over all of it.  The bytes of the map that warp rows overwrote since the
-// last block row (tracked per warp) are re-armed before the next block row.
-// BATCH: the items of several instances (RefBatch); else those of `one`.
+// ticket until none is left.  Shared memory: a block row's working set and
+// position table, or one slice per warp for warp rows.  BATCH: the items
+// of several instances (RefBatch); else those of `one`.
 template <typename T, bool FUSED, int SHAPE, bool BATCH>
 __global__ void __launch_bounds__(RefShape<SHAPE>::NT, RefShape<SHAPE>::MINB)
 k_refactor_rows(RefArgs<T> one, RefBatch<T> batch, long long limit, unsigned long long* trace) {
     constexpr int NT = RefShape<SHAPE>::NT;
-    constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char ref_sh[];
     __shared__ RefItem s_item;
     __shared__ int s_inst;
-    __shared__ int s_dlo[NW], s_dhi[NW];   // bytes of its slice each warp wrote since the map was armed
+    __shared__ RefArgs<T> s_args;   // BATCH: the current item's instance, read from shared memory
     const int tid = threadIdx.x;
-    const int map_cols = BATCH ? batch.map_cols : one.M;
-    const int map_off = BATCH ? batch.map_off : one.area_bytes;
-    short* map = reinterpret_cast<short*>(ref_sh + map_off);
-    for (int c = tid; c < map_cols; c += NT) map[c] = -1;
-    if (tid < NW) { s_dlo[tid] = 0x7fffffff; s_dhi[tid] = 0; }
-    bool map_armed = true;    // uniform for the block: no warp row since the last re-arm
-    bool map_whole = false;   // a failed block row left entries anywhere in the map
     for (;;) {
         if (tid == 0) {
             int inst = -1;
@@ -769,7 +871,12 @@ k_refactor_rows(RefArgs<T> one, RefBatch<T> batch, long long limit, unsigned lon
                     const int j = (int)(t % batch.count);
                     const int q = (int)(t / batch.count);
                     const RefArgs<T>& aj = batch.args[j];
-                    if (q < aj.nitems && !ld_volatile_int(&aj.s->abort)) { inst = j; s_item = aj.items[q]; break; }
+                    if (q < aj.nitems && !ld_volatile_int(&aj.s->abort)) {
+                        inst = j;
+                        s_item = aj.items[q];
+                        s_args = aj;
+                        break;
+                    }
                 }
             }
             s_inst = inst;
@@ -779,7 +886,7 @@ k_refactor_rows(RefArgs<T> one, RefBatch<T> batch, long long limit, unsigned lon
         const RefItem it = s_item;
         __syncthreads();   // s_inst and s_item are read before thread 0 may overwrite them
         if (inst < 0) return;
-        const RefArgs<T>& a = BATCH ? batch.args[inst] : one;
+        const RefArgs<T>& a = BATCH ? s_args : one;
         DevScal* s = a.s;
         const T boost = (T)(a.boost_eps * *(volatile double*)&s->normA);
         const int kind = it.info >> 28;
@@ -788,50 +895,35 @@ k_refactor_rows(RefArgs<T> one, RefBatch<T> batch, long long limit, unsigned lon
             const int warp = tid >> 5;
             if (warp < count) {
                 const int row = a.order[it.first + warp];
-                const int64_t b = a.Fp[row];
-                const int used = 8 * (int)(a.Fdiag[row] - b) + (int)(sizeof(T) + 4) * (int)(a.Fp[row + 1] - b);
-                const int lo = warp * a.slice_bytes;
-                if ((tid & 31) == 0) {
-                    s_dlo[warp] = min(s_dlo[warp], lo);
-                    s_dhi[warp] = max(s_dhi[warp], lo + used);
-                }
-                warp_row<T, FUSED>(row, a, s, boost, limit, trace, ref_sh + lo, a.fw);
+                warp_row<T, FUSED>(row, a, s, boost, limit, trace, ref_sh + warp * a.slice_bytes, a.fw);
             }
-            map_armed = map_cols == 0;
             __syncthreads();   // the slices are reused by the next item
         } else {
-            const int row = a.order[it.first];
-            const int64_t b = a.Fp[row];
-            const int len = (int)(a.Fp[row + 1] - b), nsteps = (int)(a.Fdiag[row] - b);
-            RowSpace<T> rs(ref_sh, nsteps, len);
-            const bool staged = kind == ROW_BLOCK;
-            if (staged && !map_armed) {
-                // re-arm the map entries warp rows overwrote (all of them
-                // after a failed block row)
-                const int mend = map_off + 2 * map_cols;
-                for (int w = 0; w < NW; w++) {
-                    int lo = map_whole ? map_off : max(s_dlo[w], map_off);
-                    int hi = map_whole ? mend : min(s_dhi[w], mend);
-                    if (lo >= hi) continue;
-                    for (int c = ((lo - map_off) >> 1) + tid; c < ((hi - map_off + 1) >> 1); c += NT) map[c] = -1;
-                    if (map_whole) break;
+            // ROW_BLOCK / ROW_GLOBAL: the whole block on one row; ROW_TEAM:
+            // each team on a row of its own in its share of the memory
+            constexpr int TEAMS = RefShape<SHAPE>::TEAMS;
+            const bool teams = TEAMS > 1 && kind == ROW_TEAM;
+            const int nt = teams ? NT / TEAMS : NT;
+            const int team = teams ? tid / nt : 0;
+            const int room = teams ? (a.area_bytes / TEAMS) & ~15 : a.area_bytes;
+            const int count = teams ? it.info & 0x0fffffff : 1;
+            int ok = 1;
+            if (team < count) {
+                const int row = a.order[it.first + team];
+                const int64_t b = a.Fp[row];
+                const int len = (int)(a.Fp[row + 1] - b), nsteps = (int)(a.Fdiag[row] - b);
+                RowSpace<T> rs(ref_sh + team * room, nsteps, len);
+                const bool staged = kind != ROW_GLOBAL;
+                if (!staged) {   // ROW_GLOBAL: descriptors and values in global memory
+                    const int g = it.info & 0x0fffffff;
+                    rs.dk = const_cast<uint32_t*>(a.gdk) + a.g_sd_off[g];
+                    rs.cnt = const_cast<uint32_t*>(a.gcnt) + a.g_sd_off[g];
+                    rs.w = a.gw + a.g_w_off[g];
                 }
-                __syncthreads();
-                if (tid < NW) { s_dlo[tid] = 0x7fffffff; s_dhi[tid] = 0; }
-                map_armed = true;
-                map_whole = false;
+                ok = block_row<T, FUSED, SHAPE>(row, a, s, boost, limit, trace, rs, staged, room, team, nt, a.fw);
             }
-            if (!staged) {   // ROW_GLOBAL: descriptors and values in global memory
-                const int g = it.info & 0x0fffffff;
-                rs.dk = const_cast<uint32_t*>(a.gdk) + a.g_sd_off[g];
-                rs.cnt = const_cast<uint32_t*>(a.gcnt) + a.g_sd_off[g];
-                rs.w = a.gw + a.g_w_off[g];
-            }
-            if (!block_row<T, FUSED, SHAPE>(row, a, s, boost, limit, trace, rs, staged, map, staged ? a.M : 0, a.fw)) {
-                if (!BATCH) return;
-                map_armed = map_cols == 0;   // the failed row left its map entries behind
-                map_whole = !map_armed;
-            }
+            if (teams) ok = !__syncthreads_or(!ok);   // the teams' rooms are reused by the next item
+            if (!ok && !BATCH) return;
         }
     }
 }

@@ -76,9 +76,9 @@ struct kkt_ctx {
     // refactorization kernel (k_refactor_rows): rows placed one per warp,
     // one per block in shared memory, or one per block with values in
     // global memory; work items in dispatch order
-    int ref_threads = 256, ref_shape = 0, ref_blocks = 0, ref_map_cols = 0, nitems = 0, smem_optin = 0;
-    size_t ref_smem = 0, ref_map_bytes = 0, ref_area = 0;
-    int32_t rows_warp = 0, rows_block = 0, rows_global = 0;
+    int ref_threads = 256, ref_shape = 0, ref_blocks = 0, nitems = 0, smem_optin = 0;
+    size_t ref_smem = 0;
+    int32_t rows_warp = 0, rows_block = 0, rows_global = 0, rows_team = 0;
     int32_t* d_order = nullptr;   // rows in dispatch order
     kkt::RefItem* d_items = nullptr;
     // rows in global memory: step descriptors and value scratch (remade
@@ -124,9 +124,11 @@ size_t layout_vsize(const kkt_ctx* c) { return (c->mixed && !c->fallback_on) ? s
 constexpr int PERSIST_THREADS = 256;
 constexpr int CHAIN_THREADS = 1024;
 constexpr size_t TAIL_SMEM_MAX = 200 * 1024;   // shared memory of a cluster-solve block
-constexpr int REF_MAP_COLS = 16384;      // columns with an O(1) position map in block rows
-constexpr size_t REF_SMEM_WIDE = 113 * 1024;   // blocks above this run 512 threads (one block per SM)
-constexpr size_t REF_SMEM_THREE = 74 * 1024;   // blocks up to this fit three an SM
+// blocks up to REF_SMEM_THREE fit three an SM, up to REF_SMEM_WIDE two (each
+// block also holds 1 KB reserved and its static shared memory, and an SM
+// 228 KB); larger blocks run 512 threads, one an SM
+constexpr size_t REF_SMEM_WIDE = 112 * 1024;
+constexpr size_t REF_SMEM_THREE = 74 * 1024;
 // The default limit of a warp row's multiply-adds (measured: kkt2000's
 // refactorization 8.7 ms with no limit, 5.3 ms with 1,024, 5.6 with 4,096;
 // kkt10000 41-43 ms between 1k and 16k; kkt70000, one 512-thread block per
@@ -543,6 +545,8 @@ void kkt_default_opts(kkt_opts* o) {
     o->warp_rows = 1;
     o->row_order = 1;
     o->mixed_fallback = 2;
+    o->stream_last = 1;
+    o->team_rows = 1;
 }
 
 const char* kkt_strerror(int code) {
@@ -578,8 +582,9 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
         c->o.ortho < KKT_ORTHO_CGS2 || c->o.ortho > KKT_ORTHO_CGS1_PYTH ||
         !(c->o.inner_tol > 0.0 && c->o.inner_tol <= 1.0) || (c->o.repivot != 0 && c->o.repivot != 1) ||
         (c->o.graphs != 0 && c->o.graphs != 1) || (c->o.warp_rows != 0 && c->o.warp_rows != 1) ||
-        (c->o.row_order != 0 && c->o.row_order != 1) || c->o.mixed_fallback < 0 || c->o.warp_row_updates < -1 ||
-        c->o.map_cols < -1 || c->o.map_cols > 16384) {
+        (c->o.row_order != 0 && c->o.row_order != 1) || c->o.mixed_fallback < 0 ||
+        (c->o.stream_last != 0 && c->o.stream_last != 1) || (c->o.team_rows != 0 && c->o.team_rows != 1) ||
+        c->o.warp_row_updates < -1) {
         delete c;
         return KKT_ERR_INVALID;
     }
@@ -683,13 +688,12 @@ namespace {
 // (k_refactor_rows).  A row's working set -- step descriptors (8 bytes per
 // L entry), values and columns -- decides where it runs: one per warp if it
 // fits a warp's slice of the block's shared memory, one per block if it
-// fits the work area after the position map, else one per block with its
-// values in global scratch.  The
-// block's shared memory is the position map of the last REF_MAP_COLS
-// columns plus the area; by default it is sized for the longest row (so no
-// row needs global scratch) up to the device's limit, dropping the map if
-// that lets every row fit.  Rows are dispatched by DAG level (ties by row)
-// or by row; consecutive warp rows form one work item per block.
+// fits the block's shared memory with a position table of its columns
+// (kkt::row_table_bits), else one per block with its values in global
+// scratch.  By default the block's shared memory is sized for the row that
+// needs the most (so no row needs global scratch) up to the device's
+// limit.  Rows are dispatched by DAG level (ties by row) or by row;
+// consecutive warp rows form one work item per block.
 int setup_rows(kkt_ctx* c) {
     const int n = c->A.n;
     const auto& L = c->lay;
@@ -703,39 +707,38 @@ int setup_rows(kkt_ctx* c) {
         c->detail = "the factors have 2^32 entries or more";
         return KKT_ERR_INVALID;
     }
+    // a warp row's working set; a block row's also holds its position table
+    // (the smallest that kkt::row_table_bits allows)
     auto need = [&](int32_t i) -> size_t {
         const int64_t st = L.Fdiag[i] - L.Fp[i], len = L.Fp[i + 1] - L.Fp[i];
-        return (8 * (size_t)st + (vsize + 4) * (size_t)len + 15) & ~(size_t)15;
+        return ((size_t)kkt::row_set_bytes(st, len, (int64_t)vsize) + 15) & ~(size_t)15;
+    };
+    auto need_block = [&](int32_t i) -> size_t {
+        const int64_t st = L.Fdiag[i] - L.Fp[i], len = L.Fp[i + 1] - L.Fp[i];
+        const int bits = std::max(kkt::ceil_log2_i64(len + len / 4 + 1), 4);
+        return ((size_t)kkt::row_set_bytes(st, len, (int64_t)vsize) + ((size_t)2 << bits) + 15) & ~(size_t)15;
     };
     size_t maxneed = 16;
-    for (int32_t i = 0; i < n; i++) maxneed = std::max(maxneed, need(i));
+    for (int32_t i = 0; i < n; i++) maxneed = std::max(maxneed, need_block(i));
     const size_t optin = (size_t)std::max(c->smem_optin, 48 * 1024);
-    int M = std::min(c->o.map_cols > 0 ? c->o.map_cols : c->o.map_cols < 0 ? 0 : REF_MAP_COLS, n);
-    size_t map_bytes = ((size_t)2 * M + 15) & ~(size_t)15;
-    size_t S;
-    if (c->o.block_smem > 0) {
-        S = std::min((size_t)c->o.block_smem, optin) & ~(size_t)15;
-        if (S < map_bytes + 4096) { M = 0; map_bytes = 0; }
-    } else if (map_bytes + maxneed <= optin) {
-        S = map_bytes + maxneed;
-    } else {
-        M = 0;   // the map would push the longest rows out of shared memory
-        map_bytes = 0;
-        S = std::min(maxneed, optin);
-    }
-    S = std::max(S, map_bytes + 4096);
+    size_t S = c->o.block_smem > 0 ? std::min((size_t)c->o.block_smem, optin) & ~(size_t)15 : std::min(maxneed, optin);
+    S = std::max(S, (size_t)4096);
+    // by default a block takes all the room of its shape's blocks per SM:
+    // the blocks an SM holds are the same, the warp rows' slices larger
+    if (c->o.block_smem <= 0) S = std::min(S <= REF_SMEM_THREE ? REF_SMEM_THREE : S <= REF_SMEM_WIDE ? REF_SMEM_WIDE : optin, optin);
     // block shape: three 256-thread blocks an SM when they fit its shared
     // memory, else two, else one of 512 threads
     c->ref_shape = S <= REF_SMEM_THREE ? 0 : S <= REF_SMEM_WIDE ? 1 : 2;
     c->ref_threads = c->ref_shape == 2 ? 512 : 256;
     c->ref_smem = S;
-    c->ref_map_cols = M;
-    c->ref_map_bytes = map_bytes;
-    c->ref_area = S - map_bytes;
     const int nw = c->ref_threads / 32;
-    const size_t slice = (S / nw) & ~(size_t)15;   // warp slices span the map's room too
+    const size_t slice = (S / nw) & ~(size_t)15;
     std::vector<uint8_t> kind((size_t)n);
-    c->rows_warp = c->rows_block = c->rows_global = 0;
+    c->rows_warp = c->rows_block = c->rows_global = c->rows_team = 0;
+    // with 512-thread blocks, rows that fit half the shared memory go one
+    // per half block (the kernel's team room: (S / 2) rounded down to 16)
+    const int teams = c->ref_shape == 2 && c->o.team_rows ? 2 : 1;
+    const int64_t team_room = (int64_t)((S / 2) & ~(size_t)15);
     // a warp row's steps run one after another on 32 lanes: rows with much
     // work (the dense end, on the critical path) go one per block even when
     // they fit a slice
@@ -750,7 +753,14 @@ int setup_rows(kkt_ctx* c) {
             upd += L.Fp[k + 1] - L.Fdiag[k] - 1;
         }
         if (c->o.warp_rows && q <= slice && upd <= wmax) { kind[i] = kkt::ROW_WARP; c->rows_warp++; }
-        else if (q <= c->ref_area) { kind[i] = kkt::ROW_BLOCK; c->rows_block++; }
+        else if (teams > 1 && kkt::row_table_bits(L.Fdiag[i] - L.Fp[i], L.Fp[i + 1] - L.Fp[i], (int64_t)vsize,
+                                                   team_room) >= 0) {
+            kind[i] = kkt::ROW_TEAM;
+            c->rows_team++;
+        } else if (kkt::row_table_bits(L.Fdiag[i] - L.Fp[i], L.Fp[i + 1] - L.Fp[i], (int64_t)vsize, (int64_t)S) >= 0) {
+            kind[i] = kkt::ROW_BLOCK;
+            c->rows_block++;
+        }
         else { kind[i] = kkt::ROW_GLOBAL; c->rows_global++; }
     }
     // dispatch order: by level in the DAG of L (ties by row) -- a row's
@@ -773,6 +783,13 @@ int setup_rows(kkt_ctx* c) {
             int32_t cnt = 1;
             while (cnt < nw && t + cnt < n && kind[order[t + cnt]] == kkt::ROW_WARP) cnt++;
             items.push_back(kkt::RefItem{t, (kkt::ROW_WARP << 28) | cnt});
+            t += cnt;
+            continue;
+        }
+        if (kind[r] == kkt::ROW_TEAM) {
+            int32_t cnt = 1;
+            while (cnt < teams && t + cnt < n && kind[order[t + cnt]] == kkt::ROW_TEAM) cnt++;
+            items.push_back(kkt::RefItem{t, (kkt::ROW_TEAM << 28) | cnt});
             t += cnt;
             continue;
         }
@@ -1197,10 +1214,7 @@ void refactor_rows_launch(kkt_ctx* c, const double* vals, unsigned long long* tr
     a.rinv = rinv_of<T>(c);
     a.vals = vals;
     a.fsrc = c->d_fsrc;
-    a.M = c->ref_map_cols;
-    a.mlo = c->A.n - c->ref_map_cols;
-    a.map_bytes = (int)c->ref_map_bytes;
-    a.area_bytes = (int)c->ref_area;
+    a.area_bytes = (int)c->ref_smem;
     a.slice_bytes = (int)((c->ref_smem / (c->ref_threads / 32)) & ~(size_t)15);
     a.gdk = c->d_gdk;
     a.gcnt = c->d_gcnt;
@@ -1210,6 +1224,7 @@ void refactor_rows_launch(kkt_ctx* c, const double* vals, unsigned long long* tr
     a.s = c->d_s;
     a.fw = kkt::FwdArgs<T>{fused_rhs, c->d_P, (T*)c->d_y, (T*)c->d_xp};
     a.boost_eps = c->o.boost_eps;
+    a.stream_last = c->o.stream_last;
     const int blocks = std::max(1, std::min(c->nitems, c->ref_blocks));
     auto kern = fused_rhs ? kkt::k_refactor_rows<T, true, SHAPE, false> : kkt::k_refactor_rows<T, false, SHAPE, false>;
     kern<<<blocks, NT, c->ref_smem, c->stream>>>(a, kkt::RefBatch<T>{}, spin(c), trace);
@@ -1926,6 +1941,7 @@ int kkt_query(kkt_ctx* c, kkt_info* info) {
     info->rows_warp = c->rows_warp;
     info->rows_block = c->rows_block;
     info->rows_global = c->rows_global;
+    info->rows_team = c->rows_team;
     info->refactor_smem = (int32_t)c->ref_smem;
     info->refactor_threads = c->ref_threads;
     info->refactor_blocks = c->ref_blocks;
@@ -2120,21 +2136,18 @@ int kkt_batch_step(kkt_batch* bt, kkt_ctx* const* ctxs, int count, const double*
         if (ok) { shape = c->ref_shape; in.push_back(i); }
         else alone.push_back(i);
     }
-    {   // the shared launch holds every instance's work area and the largest map
-        size_t area = 0, mapb = 0;
-        for (int i : in) {
-            area = std::max(area, ctxs[i]->ref_area);
-            mapb = std::max(mapb, ctxs[i]->ref_map_bytes);
-        }
-        if (area + mapb > (size_t)bt->smem_optin) {
+    {   // the shared launch's shared memory holds every instance's block rows
+        size_t area = 0;
+        for (int i : in) area = std::max(area, ctxs[i]->ref_smem);
+        if (area > (size_t)bt->smem_optin) {
             alone.insert(alone.end(), in.begin(), in.end());
             in.clear();
         }
     }
     const int nb = (int)in.size();
     if (nb > 0) {
-        size_t area = 0, mapb = 0;
-        int map_cols = 0, items = 0, C = -1, nbr = 1;
+        size_t area = 0;
+        int items = 0, C = -1, nbr = 1;
         size_t cl_smem = 0;
         for (int t = 0; t < nb; t++) {
             const int i = in[t];
@@ -2173,10 +2186,7 @@ int kkt_batch_step(kkt_batch* bt, kkt_ctx* const* ctxs, int count, const double*
             a.rinv = (double*)c->d_rinv;
             a.vals = vals;
             a.fsrc = c->d_fsrc;
-            a.M = c->ref_map_cols;
-            a.mlo = n - c->ref_map_cols;
-            a.map_bytes = (int)c->ref_map_bytes;
-            a.area_bytes = (int)c->ref_area;
+            a.area_bytes = (int)c->ref_smem;
             a.slice_bytes = (int)((c->ref_smem / (c->ref_threads / 32)) & ~(size_t)15);
             a.gdk = c->d_gdk;
             a.gcnt = c->d_gcnt;
@@ -2186,9 +2196,8 @@ int kkt_batch_step(kkt_batch* bt, kkt_ctx* const* ctxs, int count, const double*
             a.s = c->d_s;
             a.fw = kkt::FwdArgs<double>{bd, c->d_P, c->d_y, c->d_xp};
             a.boost_eps = c->o.boost_eps;
-            area = std::max(area, c->ref_area);
-            mapb = std::max(mapb, c->ref_map_bytes);
-            map_cols = std::max(map_cols, c->ref_map_cols);
+            a.stream_last = c->o.stream_last;
+            area = std::max(area, c->ref_smem);
             items = std::max(items, c->nitems);
             if (C < 0) C = c->cluster;
             if (c->cluster != C) C = 0;   // the batched sweep needs one cluster shape
@@ -2205,7 +2214,7 @@ int kkt_batch_step(kkt_batch* bt, kkt_ctx* const* ctxs, int count, const double*
         CK_BT(cudaMemcpyAsync(bt->d_sweep, bt->h_sweep, nb * sizeof(kkt::SweepArgs), cudaMemcpyHostToDevice, bt->stream));
         CK_BT(cudaMemcpyAsync(bt->d_res, bt->h_res, nb * sizeof(kkt::ResidualArgs), cudaMemcpyHostToDevice, bt->stream));
         const long long limit = spin(ctxs[in[0]]);
-        const size_t smem = area + mapb;   // every instance's work area, then the largest map
+        const size_t smem = area;
         kkt::k_refactor_prep_batch<<<(nb + 255) / 256, 256, 0, bt->stream>>>(bt->d_gather, nb, bt->d_ticket);
         kkt::k_gather_batch<<<dim3(std::max(8, 2 * bt->num_sms / nb), nb), 256, 0, bt->stream>>>(bt->d_gather);
         // one refactorization launch for every instance's rows
@@ -2219,7 +2228,7 @@ int kkt_batch_step(kkt_batch* bt, kkt_ctx* const* ctxs, int count, const double*
         int per_sm = 0;
         CK_BT(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
         const int blocks = std::max(1, per_sm) * bt->num_sms;
-        const kkt::RefBatch<double> rb{bt->d_ref, nb, (long long)nb * items, bt->d_ticket, map_cols, (int)area};
+        const kkt::RefBatch<double> rb{bt->d_ref, nb, (long long)nb * items, bt->d_ticket};
         if (sh == 2)
             kkt::k_refactor_rows<double, true, 2, true><<<blocks, 512, smem, bt->stream>>>(kkt::RefArgs<double>{}, rb, limit, nullptr);
         else if (sh == 1)

@@ -26,7 +26,7 @@ def _pair(rp, ci, v0=None, P=None, Q=None, **kw):
 
 
 @pytest.mark.parametrize("kw", [dict(), dict(trisolve="global"), dict(precision="mixed", max_cycles=2),
-                                dict(warp_rows=False), dict(block_smem=16384)])
+                                dict(warp_rows=False), dict(block_smem=8192)])
 def test_step_equals_refactor_then_solve_kkt200(kw):
     seq = KKTSequence("kkt200")
     a, f = _pair(seq.rowptr, seq.colind, seq.values(0), **kw)
@@ -75,27 +75,38 @@ def test_step_device_arrays_and_full_size():
     assert torch.equal(xf2, xf)
 
 
-@pytest.mark.parametrize("warp_rows,block_smem", [(True, 0), (False, 0), (True, 16384), (False, 16384)])
+@pytest.mark.parametrize("warp_rows,block_smem", [(True, 0), (False, 0), (True, 8192), (False, 8192),
+                                                  (False, 150000), (True, 150000)])
 def test_row_placement_and_order_same_bits(oracle_mod, warp_rows, block_smem):
     """Every placement of the refactorization's rows -- one per warp in
-    shared memory, one per block in shared memory, one per block with the
-    values in global memory (a 16 KB block forces the longest kkt200 rows
-    there) -- and both dispatch orders (DAG level, row) give the same
-    factors, bit for bit, equal to the oracle's refactorization on the same
-    P and Q (each row's arithmetic is fixed; only where and when it runs
-    changes)."""
+    shared memory, one per block in shared memory, one per half of a
+    512-thread block (a 150 KB block makes the blocks 512 threads wide),
+    one per block with the values in global memory (an 8 KB block forces
+    the longest kkt200 rows there) -- both dispatch orders (DAG level,
+    row) and both times a block row may store its last step's values (as
+    each is formed, or after the step) give the same factors, bit for bit,
+    equal to the oracle's refactorization on the same P and Q (each row's
+    arithmetic is fixed; only where and when it runs changes)."""
     seq = KKTSequence("kkt200", steps=2)
     out = []
-    for order in ("row", "level"):
-        s = K.KKTSolver(row_order=order, warp_rows=warp_rows, block_smem=block_smem)
+    runs = [("row", True, True), ("level", True, True), ("level", False, True)]
+    if block_smem == 150000:
+        runs.append(("level", True, False))   # the same rows one per whole block
+    for order, stream_last, team_rows in runs:
+        s = K.KKTSolver(row_order=order, warp_rows=warp_rows, block_smem=block_smem, stream_last=stream_last,
+                        team_rows=team_rows)
         s.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
         info = s.info()
-        assert info["rows_warp"] + info["rows_block"] + info["rows_global"] == seq.n
+        assert info["rows_warp"] + info["rows_block"] + info["rows_global"] + info["rows_team"] == seq.n
         assert (info["rows_warp"] > 0) == warp_rows
         if block_smem:
-            assert info["rows_global"] > 0 and info["refactor_smem"] == block_smem
+            assert info["refactor_smem"] == block_smem
+        assert (info["rows_global"] > 0) == (block_smem == 8192)
+        if block_smem == 150000:
+            assert info["refactor_threads"] == 512
+            assert (info["rows_team"] > 0) == (team_rows and not warp_rows)
         else:
-            assert info["rows_global"] == 0
+            assert info["rows_team"] == 0
         v = seq.values(1)
         b, _ = seq.rhs(1, v)
         x, it, nr = s.step(v, b)
@@ -103,8 +114,9 @@ def test_row_placement_and_order_same_bits(oracle_mod, warp_rows, block_smem):
         out.append((f["Lx"].copy(), f["Ux"].copy(), x.copy(), it, nr))
         P, Q = s.perm()
         s.close()
-    for a, b_ in zip(out[0], out[1]):
-        assert np.array_equal(a, b_)
+    for o in out[1:]:
+        for a, b_ in zip(out[0], o):
+            assert np.array_equal(a, b_)
     of = oracle_mod.refactor(seq.n, seq.rowptr, seq.colind, seq.values(1), P, Q)
     assert np.array_equal(out[0][0], of.Lx) and np.array_equal(out[0][1], of.Ux)
 
@@ -113,10 +125,11 @@ def test_step_factors_bitwise_oracle_full_size_kkt2000(oracle_mod):
     """The benchmark's timed call at its size: kkt_step on the library's own
     ordering and pivots gives factors equal, bit for bit, to the oracle's
     refactorization on the same P and Q (first and last matrix), whatever
-    the dispatch order of the rows."""
+    the dispatch order of the rows and the time block rows store their last
+    step's values."""
     seq = KKTSequence("kkt2000")
-    for order in ("level", "row"):
-        s = K.KKTSolver(row_order=order)
+    for order, stream_last in (("level", True), ("row", False)):
+        s = K.KKTSolver(row_order=order, stream_last=stream_last)
         s.analyze(seq.rowptr, seq.colind, values0=seq.values(0))
         P, Q = s.perm()
         for k in (0, seq.M - 1):

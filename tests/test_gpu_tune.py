@@ -24,7 +24,7 @@ def test_tune_keeps_results_and_reports_choice(name):
     assert best > 0
     info = s.info()
     assert info["refactor_smem"] > 0 and info["trisolve_cluster"] in (0, 8, 16)
-    assert info["rows_warp"] + info["rows_block"] + info["rows_global"] == seq.n
+    assert info["rows_warp"] + info["rows_block"] + info["rows_global"] + info["rows_team"] == seq.n
     with pytest.raises(K.KKTError):      # factors must be recomputed after tuning
         s.solve(b, tol=1e-12)
     s.refactor(v)
