@@ -462,6 +462,17 @@ int kkt_batch_step(kkt_batch* bt, kkt_ctx* const* ctxs, int count, const double*
 /* Kernels the batch has launched so far. */
 int64_t kkt_batch_launches(const kkt_batch* bt);
 
+/* Time spent by kkt_batch_step's shared part since creation or the last
+ * reset, in ms, per phase (CUDA events on the batch's stream, except the
+ * last): [0] argument and value copies, [1] the batched gather, [2] the
+ * batched refactorization with the fused forward sweeps, [3] the backward
+ * sweeps, [4] the batched residual and decision, [5] host wall time of the
+ * per-instance rest (outcomes, the refinement where needed, copies of x).
+ * steps (may be NULL): instance-steps run in shared launches.  reset != 0
+ * zeroes the sums.  Errors: KKT_ERR_INVALID (NULL bt or ms). */
+#define KKT_BATCH_PHASES 6
+int kkt_batch_phase_times(kkt_batch* bt, double* ms, int64_t* steps, int reset);
+
 /* ---- serving: many resident instances, steps in flight concurrently ----
  *
  * The paper solves one KKT sequence at a time and reuses the analysis,

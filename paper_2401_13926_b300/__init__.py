@@ -42,7 +42,7 @@ EXPORTS = [
     "kkt_trace_solve", "kkt_repivot", "kkt_tune", "kkt_step", "kkt_server_default_opts", "kkt_server_create", "kkt_server_open",
     "kkt_server_submit", "kkt_server_wait", "kkt_server_close", "kkt_server_query", "kkt_server_destroy",
     "kkt_host_analyze", "kkt_analyze_like", "kkt_trace_critical_path",
-    "kkt_batch_create", "kkt_batch_destroy", "kkt_batch_step", "kkt_batch_launches",
+    "kkt_batch_create", "kkt_batch_destroy", "kkt_batch_step", "kkt_batch_launches", "kkt_batch_phase_times",
     "kkt_estimate_device_bytes", "kkt_place_instance",
 ]
 NOALLOC_MAX_N = 65536
@@ -166,6 +166,7 @@ def lib():
     L.kkt_batch_destroy.restype = None
     L.kkt_batch_step.argtypes = [vp, vp, ip, vp, vp, vp, ip, d, vp, vp, vp]
     L.kkt_batch_launches.argtypes = [vp]
+    L.kkt_batch_phase_times.argtypes = [vp, vp, vp, C.c_int]
     L.kkt_estimate_device_bytes.argtypes = [i32, i64, C.POINTER(_HostStats), C.POINTER(_Opts), ip, C.POINTER(i64)]
     L.kkt_place_instance.argtypes = [ip, vp, vp, i64]
     for name in EXPORTS:
@@ -570,6 +571,17 @@ class KKTBatch:
 
     def launches(self):
         return lib().kkt_batch_launches(self._h)
+
+    def phase_times(self, reset=False):
+        """kkt_batch_phase_times: ({phase: ms}, instance-steps) of the shared
+        launches since creation or the last reset."""
+        ms = np.zeros(6)
+        steps = C.c_int64()
+        rc = lib().kkt_batch_phase_times(self._h, ms.ctypes.data, C.byref(steps), int(bool(reset)))
+        if rc:
+            raise KKTError(rc, "kkt_batch_phase_times")
+        names = ("copies", "gather", "refactor", "usolve", "residual", "refine_host")
+        return {k: float(v) for k, v in zip(names, ms)}, steps.value
 
     def close(self):
         if getattr(self, "_h", None):

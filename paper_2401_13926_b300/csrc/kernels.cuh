@@ -628,6 +628,10 @@ template <int SHAPE> struct RefShape;
 template <> struct RefShape<0> { static constexpr int NT = 256, MINB = 3, PRE = 2, BATCH = 2, TEAMS = 1; };
 template <> struct RefShape<1> { static constexpr int NT = 256, MINB = 2, PRE = 4, BATCH = 4, TEAMS = 1; };
 template <> struct RefShape<2> { static constexpr int NT = 512, MINB = 1, PRE = 4, BATCH = 4, TEAMS = 2; };
+// the teams of a shape's blocks, for the host's placement of rows
+inline constexpr int ref_teams(int shape) {
+    return shape == 0 ? RefShape<0>::TEAMS : shape == 1 ? RefShape<1>::TEAMS : RefShape<2>::TEAMS;
+}
 
 // The barrier of a team of tt threads working on one row: named barrier
 // `id` (1 + the team's index for a team of a block, REF_BAR_BLOCK for the

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "analysis.h"
@@ -735,10 +736,11 @@ int setup_rows(kkt_ctx* c) {
     const size_t slice = (S / nw) & ~(size_t)15;
     std::vector<uint8_t> kind((size_t)n);
     c->rows_warp = c->rows_block = c->rows_global = c->rows_team = 0;
-    // with 512-thread blocks, rows that fit half the shared memory go one
-    // per half block (the kernel's team room: (S / 2) rounded down to 16)
-    const int teams = c->ref_shape == 2 && c->o.team_rows ? 2 : 1;
-    const int64_t team_room = (int64_t)((S / 2) & ~(size_t)15);
+    // with teams (kkt::RefShape::TEAMS), rows that fit a team's share of the
+    // shared memory go one per team (the kernel's team room: S / teams
+    // rounded down to 16)
+    const int teams = c->o.team_rows ? kkt::ref_teams(c->ref_shape) : 1;
+    const int64_t team_room = (int64_t)((S / (size_t)teams) & ~(size_t)15);
     // a warp row's steps run one after another on 32 lanes: rows with much
     // work (the dense end, on the critical path) go one per block even when
     // they fit a slice
@@ -2002,6 +2004,12 @@ struct kkt_batch {
     kkt::SweepArgs* h_sweep = nullptr;
     kkt::ResidualArgs* h_res = nullptr;
     int64_t launches = 0;
+    // phase timing (kkt_batch_phase_times): events around the shared
+    // launches, host time for the per-instance refinement
+    cudaEvent_t ph_ev[KKT_BATCH_PHASES + 1] = {};
+    std::vector<cudaStream_t> slot_streams;   // one per instance of a step, for its refinement
+    double ph_ms[KKT_BATCH_PHASES] = {};
+    int64_t ph_steps = 0;
     std::mutex mu;   // one kkt_batch_step at a time
 };
 
@@ -2013,8 +2021,48 @@ void batch_free(kkt_batch* bt) {
     for (void* p : {(void*)bt->h_ref, (void*)bt->h_gather, (void*)bt->h_sweep, (void*)bt->h_res})
         if (p) cudaFreeHost(p);
     for (cudaEvent_t e : bt->ready_ev) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : bt->ph_ev) if (e) cudaEventDestroy(e);
+    for (cudaStream_t st : bt->slot_streams) if (st) cudaStreamDestroy(st);
     if (bt->done_ev) cudaEventDestroy(bt->done_ev);
     if (bt->stream) cudaStreamDestroy(bt->stream);
+}
+
+int refine_after_prologue(kkt_ctx* c, const double* bd, double* xd, double tol, int* cycles_out);
+
+// The per-instance rest of a batched step, on stream `st` (after the
+// shared launches, event `shared`): the outcome, the refinement where it is
+// needed and the copy of x to the host (x_host != NULL).  The context's
+// stream is st meanwhile and waits for it afterwards.  Returns the status.
+int batch_finish(kkt_ctx* c, cudaStream_t st, cudaEvent_t shared, const double* bd, double* xd, double* x_host,
+                 double tol, int32_t* iters, double* nrbe) {
+    CK(cudaSetDevice(c->dev));
+    CK(cudaStreamWaitEvent(st, shared, 0));
+    cudaStream_t own = c->stream;
+    c->stream = st;
+    c->nboost = c->h_s->nboost;
+    c->norm_a = c->h_s->normA;
+    int rc = device_error(c);
+    int cycles = 0;
+    if (rc) rearm(c);
+    else {
+        c->factored = true;
+        rc = refine_after_prologue(c, bd, xd, tol, &cycles);
+    }
+    cudaError_t e = cudaSuccess;
+    if (x_host && (rc == KKT_OK || rc == KKT_ERR_NOT_CONVERGED)) {
+        e = cudaMemcpyAsync(x_host, c->d_x, sizeof(double) * (size_t)c->A.n, cudaMemcpyDeviceToHost, st);
+        c->d2h += (int64_t)sizeof(double) * c->A.n;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    c->stream = own;
+    if (e != cudaSuccess) return cuda_fail(c, e, "batch_finish");
+    c->last_iters = c->h_s->iters;
+    c->last_cycles = cycles;
+    c->last_nrbe = c->h_s->nrbe;
+    c->last_rnorm0 = c->h_s->rnorm0;
+    if (iters) *iters = c->h_s->iters;
+    if (nrbe) *nrbe = c->h_s->nrbe;
+    return rc;
 }
 
 // The refinement after the prologue (x0, its residual and the decision
@@ -2070,6 +2118,7 @@ int kkt_batch_create(kkt_batch** out, int max_count, int device) {
     bt->ready_ev.assign(max_count, nullptr);
     for (int i = 0; i < max_count && e == cudaSuccess; i++)
         e = cudaEventCreateWithFlags(&bt->ready_ev[i], cudaEventDisableTiming);
+    for (int i = 0; i <= KKT_BATCH_PHASES && e == cudaSuccess; i++) e = cudaEventCreate(&bt->ph_ev[i]);
     const size_t n = (size_t)max_count;
     if (e == cudaSuccess) e = cudaMalloc(&bt->d_ref, n * sizeof(kkt::RefArgs<double>));
     if (e == cudaSuccess) e = cudaMalloc(&bt->d_gather, n * sizeof(kkt::GatherArgs));
@@ -2114,6 +2163,18 @@ void kkt_batch_destroy(kkt_batch* bt) {
 
 int64_t kkt_batch_launches(const kkt_batch* bt) { return bt ? bt->launches : 0; }
 
+int kkt_batch_phase_times(kkt_batch* bt, double* ms, int64_t* steps, int reset) {
+    if (!bt || !ms) return KKT_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(bt->mu);
+    for (int p = 0; p < KKT_BATCH_PHASES; p++) ms[p] = bt->ph_ms[p];
+    if (steps) *steps = bt->ph_steps;
+    if (reset) {
+        for (double& v : bt->ph_ms) v = 0.0;
+        bt->ph_steps = 0;
+    }
+    return KKT_OK;
+}
+
 int kkt_batch_step(kkt_batch* bt, kkt_ctx* const* ctxs, int count, const double* const* values,
                    const double* const* b, double* const* x, int on_device, double tol, int* iters, double* nrbe,
                    int* status) {
@@ -2146,6 +2207,8 @@ int kkt_batch_step(kkt_batch* bt, kkt_ctx* const* ctxs, int count, const double*
     }
     const int nb = (int)in.size();
     if (nb > 0) {
+        const auto host_t0 = std::chrono::steady_clock::now();
+        CK_BT(cudaEventRecord(bt->ph_ev[0], bt->stream));
         size_t area = 0;
         int items = 0, C = -1, nbr = 1;
         size_t cl_smem = 0;
@@ -2215,8 +2278,10 @@ int kkt_batch_step(kkt_batch* bt, kkt_ctx* const* ctxs, int count, const double*
         CK_BT(cudaMemcpyAsync(bt->d_res, bt->h_res, nb * sizeof(kkt::ResidualArgs), cudaMemcpyHostToDevice, bt->stream));
         const long long limit = spin(ctxs[in[0]]);
         const size_t smem = area;
+        CK_BT(cudaEventRecord(bt->ph_ev[1], bt->stream));
         kkt::k_refactor_prep_batch<<<(nb + 255) / 256, 256, 0, bt->stream>>>(bt->d_gather, nb, bt->d_ticket);
         kkt::k_gather_batch<<<dim3(std::max(8, 2 * bt->num_sms / nb), nb), 256, 0, bt->stream>>>(bt->d_gather);
+        CK_BT(cudaEventRecord(bt->ph_ev[2], bt->stream));
         // one refactorization launch for every instance's rows
         // the shared launch's shared memory may exceed every instance's own,
         // so its shape is taken from that size
@@ -2236,6 +2301,7 @@ int kkt_batch_step(kkt_batch* bt, kkt_ctx* const* ctxs, int count, const double*
         else
             kkt::k_refactor_rows<double, true, 0, true><<<blocks, 256, smem, bt->stream>>>(kkt::RefArgs<double>{}, rb, limit, nullptr);
         bt->launches += 3;
+        CK_BT(cudaEventRecord(bt->ph_ev[3], bt->stream));
         // the backward sweeps: one cluster per instance in one launch, or
         // each instance's own schedule
         if (C > 0) {
@@ -2262,9 +2328,11 @@ int kkt_batch_step(kkt_batch* bt, kkt_ctx* const* ctxs, int count, const double*
                 c->stream = own;
             }
         }
+        CK_BT(cudaEventRecord(bt->ph_ev[4], bt->stream));
         kkt::k_residual_batch<<<dim3(nbr, nb), kkt::RED_THREADS, 0, bt->stream>>>(bt->d_res);
         kkt::k_decide_batch<<<(nb + 127) / 128, 128, 0, bt->stream>>>(bt->d_res, nb, tol);
         bt->launches += 2;
+        CK_BT(cudaEventRecord(bt->ph_ev[5], bt->stream));
         CK_BT(cudaGetLastError());
         for (int t = 0; t < nb; t++) {
             kkt_ctx* c = ctxs[in[t]];
@@ -2273,35 +2341,39 @@ int kkt_batch_step(kkt_batch* bt, kkt_ctx* const* ctxs, int count, const double*
         }
         CK_BT(cudaEventRecord(bt->done_ev, bt->stream));
         CK_BT(cudaStreamSynchronize(bt->stream));
-        // per instance: the outcome, and the refinement where it is needed
+        for (int p = 0; p < KKT_BATCH_PHASES - 1; p++) {
+            float f = 0.f;
+            if (cudaEventElapsedTime(&f, bt->ph_ev[p], bt->ph_ev[p + 1]) == cudaSuccess) bt->ph_ms[p] += f;
+        }
+        bt->ph_steps += nb;
+        const auto host_t1 = std::chrono::steady_clock::now();
+        // per instance: the outcome, and the refinement where it is
+        // needed -- each instance that still has work on its own host
+        // thread and its own stream of the batch, so the instances'
+        // refinements (host-driven loops of short launches, and the
+        // triangular sweeps of one cluster each) overlap on the device
+        while ((int)bt->slot_streams.size() < nb) {
+            cudaStream_t st = nullptr;
+            CK_BT(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            bt->slot_streams.push_back(st);
+        }
+        std::vector<std::thread> workers;
         for (int t = 0; t < nb; t++) {
             const int i = in[t];
             kkt_ctx* c = ctxs[i];
-            CK_BT(cudaStreamWaitEvent(c->stream, bt->done_ev, 0));
-            c->nboost = c->h_s->nboost;
-            c->norm_a = c->h_s->normA;
-            const double* bd = bt->h_res[t].b;
-            double* xd = bt->h_sweep[t].out;
-            int rc = device_error(c);
-            int cycles = 0;
-            if (rc) rearm(c);
-            else {
-                c->factored = true;
-                rc = refine_after_prologue(c, bd, xd, tol, &cycles);
-            }
-            if (!on_device && (rc == KKT_OK || rc == KKT_ERR_NOT_CONVERGED)) {
-                CK(cudaMemcpyAsync(x[i], c->d_x, sizeof(double) * (size_t)c->A.n, cudaMemcpyDeviceToHost, c->stream));
-                c->d2h += (int64_t)sizeof(double) * c->A.n;
-            }
-            CK(cudaStreamSynchronize(c->stream));
-            c->last_iters = c->h_s->iters;
-            c->last_cycles = cycles;
-            c->last_nrbe = c->h_s->nrbe;
-            c->last_rnorm0 = c->h_s->rnorm0;
-            if (iters) iters[i] = c->h_s->iters;
-            if (nrbe) nrbe[i] = c->h_s->nrbe;
-            status[i] = rc;
+            auto finish = [=, &status]() {
+                const int rc = batch_finish(c, bt->slot_streams[t], bt->done_ev, bt->h_res[t].b, bt->h_sweep[t].out,
+                                            on_device ? nullptr : x[i], tol, iters ? &iters[i] : nullptr,
+                                            nrbe ? &nrbe[i] : nullptr);
+                status[i] = rc;
+            };
+            if (c->h_s->done && on_device) finish();   // nothing left but the bookkeeping
+            else workers.emplace_back(finish);
         }
+        for (std::thread& w : workers) w.join();
+        (void)host_t0;
+        bt->ph_ms[KKT_BATCH_PHASES - 1] +=
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - host_t1).count();
     }
     for (int i : alone) {
         int it = 0;
