@@ -124,9 +124,9 @@ typedef struct {
     int64_t warp_row_updates; /* a row is refactored one per warp only if its multiply-adds
                              (the sum of |U(k,>k)| over its L entries) are at most this
                              (besides fitting a warp's slice); -1 = no limit; 0 = the
-                             default: 2048 with 256-thread blocks, 65536 with 512-thread
+                             default: 2048 with 256-thread blocks, 4096 with 512-thread
                              blocks (the long rows at the dense end, on the critical
-                             path, then go one per block) */
+                             path, then go one per block or half block) */
     int mixed_fallback;   /* KKT_PRECISION_MIXED only: restart cycles the FP32-factor
                              preconditioner gets (default 2).  A solve not converged by
                              then refactors the matrix in FP64 and continues FGMRES from

@@ -616,7 +616,7 @@ __device__ bool warp_row(int row, const RefArgs<T>& a, DevScal* s, T boost, long
 // Block shapes of the refactorization kernel, picked by its shared memory
 // per block: NT threads, at least MINB blocks an SM (which caps the
 // registers: 80 a thread for three 256-thread blocks, 128 otherwise), PRE
-// entries of each step a thread prefetches two steps ahead, BATCH entries a
+// entries of each step a thread prefetches STAGES steps ahead, BATCH entries a
 // thread loads together past those, TEAMS teams of NT / TEAMS threads that
 // each refactor a row of their own (ROW_TEAM items: rows that fit 1/TEAMS
 // of the shared memory) when the block is not working on one row whole.
@@ -625,9 +625,9 @@ __device__ bool warp_row(int row, const RefArgs<T>& a, DevScal* s, T boost, long
 // spills); on kkt10000 (two blocks an SM by shared memory) no cap 39.2 ms
 // against 43.0 with it.
 template <int SHAPE> struct RefShape;
-template <> struct RefShape<0> { static constexpr int NT = 256, MINB = 3, PRE = 2, BATCH = 2, TEAMS = 1; };
-template <> struct RefShape<1> { static constexpr int NT = 256, MINB = 2, PRE = 4, BATCH = 4, TEAMS = 1; };
-template <> struct RefShape<2> { static constexpr int NT = 512, MINB = 1, PRE = 4, BATCH = 4, TEAMS = 2; };
+template <> struct RefShape<0> { static constexpr int NT = 256, MINB = 3, PRE = 2, BATCH = 2, TEAMS = 1, STAGES = 2; };
+template <> struct RefShape<1> { static constexpr int NT = 256, MINB = 2, PRE = 4, BATCH = 4, TEAMS = 1, STAGES = 2; };
+template <> struct RefShape<2> { static constexpr int NT = 512, MINB = 1, PRE = 4, BATCH = 4, TEAMS = 2, STAGES = 2; };
 // the teams of a shape's blocks, for the host's placement of rows
 inline constexpr int ref_teams(int shape) {
     return shape == 0 ? RefShape<0>::TEAMS : shape == 1 ? RefShape<1>::TEAMS : RefShape<2>::TEAMS;
@@ -653,7 +653,7 @@ __device__ __forceinline__ int team_sync_or(int id, int tt, int pred) {
 
 // One elimination step's first entries for one thread of a block row:
 // PRE entries of U(k,:) (columns and values) and the pivot reciprocal of
-// row k, loaded two steps ahead so issuing them never waits on a load.
+// row k, loaded STAGES steps ahead so issuing them never waits on a load.
 template <typename T, int PRE>
 struct Stage {
     T rk;
@@ -729,9 +729,10 @@ __device__ bool block_row(int row, const RefArgs<T>& a, DevScal* s, T boost, lon
         team_sync(bar, NT);
     }
 
-    Stage<T, PRE> A, B;
-    stage_load<T, PRE>(A, tid, NT, 0, nsteps, cols, rs.dk, rs.cnt, a);
-    stage_load<T, PRE>(B, tid, NT, 1, nsteps, cols, rs.dk, rs.cnt, a);
+    constexpr int STAGES = RefShape<SHAPE>::STAGES;
+    Stage<T, PRE> stg[STAGES];   // indexed by constants only: registers
+#pragma unroll
+    for (int q = 0; q < STAGES; q++) stage_load<T, PRE>(stg[q], tid, NT, q, nsteps, cols, rs.dk, rs.cnt, a);
     int step = 0;
     // One elimination step: every thread forms l_ik = w_k * (1/u_kk) itself
     // (thread 0 also stores it), then applies its entries of U(k,:): the
@@ -815,7 +816,7 @@ __device__ bool block_row(int row, const RefArgs<T>& a, DevScal* s, T boost, lon
                 }
             }
         }
-        stage_load<T, PRE>(st, tid, NT, step + 2, nsteps, cols, rs.dk, rs.cnt, a);   // the stage's registers are free again
+        stage_load<T, PRE>(st, tid, NT, step + STAGES, nsteps, cols, rs.dk, rs.cnt, a);   // the stage's registers are free again
         const int any_fail = team_sync_or(bar, NT, !ok);   // uniform decision for the team
         if (tid == 0) w[step] = l;   // nobody else touches position `step` any more
         step++;
@@ -823,9 +824,11 @@ __device__ bool block_row(int row, const RefArgs<T>& a, DevScal* s, T boost, lon
     };
     bool ok = true;
     while (step < nsteps && ok) {
-        ok = run_step(A);
-        if (!ok || step >= nsteps) break;
-        ok = run_step(B);
+#pragma unroll
+        for (int q = 0; q < STAGES; q++) {
+            if (!ok || step >= nsteps) break;
+            ok = run_step(stg[q]);
+        }
     }
     if (!ok) return false;
     // publish (the row is final after the last step's barrier): every

@@ -132,10 +132,11 @@ constexpr size_t REF_SMEM_WIDE = 112 * 1024;
 constexpr size_t REF_SMEM_THREE = 74 * 1024;
 // The default limit of a warp row's multiply-adds (measured: kkt2000's
 // refactorization 8.7 ms with no limit, 5.3 ms with 1,024, 5.6 with 4,096;
-// kkt10000 41-43 ms between 1k and 16k; kkt70000, one 512-thread block per
-// SM, 1.38 s with 65,536 against 1.39-1.42 s with lower limits)
-constexpr int64_t DEFAULT_WARP_ROW_UPDATES = 2048;         // 256-thread blocks
-constexpr int64_t DEFAULT_WARP_ROW_UPDATES_WIDE = 65536;   // 512-thread blocks
+// kkt10000 41-43 ms between 1k and 16k; kkt70000, 512-thread blocks whose
+// halves take the rows warps do not, 684 ms with 4,096, 689 with 16,384,
+// 727 with 65,536, 771 with 262,144)
+constexpr int64_t DEFAULT_WARP_ROW_UPDATES = 2048;        // 256-thread blocks
+constexpr int64_t DEFAULT_WARP_ROW_UPDATES_WIDE = 4096;   // 512-thread blocks
 constexpr int CHAIN_MAX = 12288;       // rows of a chain (8 bytes of shared memory each)
 constexpr int CHAIN_WIDTH = 32;        // a level belongs to the chain if it has at most this many rows
 
