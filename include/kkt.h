@@ -119,8 +119,10 @@ typedef struct {
                              block.  Same arithmetic either way. */
     int row_order;        /* dispatch order of the refactorization's rows: 1 (default)
                              by level in the dependency DAG of L (ties by row); 0 by
-                             row.  A row's dependencies are always dispatched before
-                             it.  Same arithmetic either way. */
+                             row; 2 by critical-path priority (descending longest path
+                             of estimated row costs to the end of the DAG).  A row's
+                             dependencies are always dispatched before it.  Same
+                             arithmetic either way. */
     int64_t warp_row_updates; /* a row is refactored one per warp only if its multiply-adds
                              (the sum of |U(k,>k)| over its L entries) are at most this
                              (besides fitting a warp's slice); -1 = no limit; 0 = the

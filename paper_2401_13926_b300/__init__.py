@@ -31,7 +31,7 @@ TRSV = {"auto": 0, "global": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 METHOD = {"fgmres": 0, "richardson": 1, "fgmres_ee": 2}
 ORTHO = {"cgs2": 0, "cgs2_pythagoras": 1, "cgs1_pythagoras": 2}
-ROW_ORDER = {"row": 0, "level": 1}
+ROW_ORDER = {"row": 0, "level": 1, "critical": 2}
 
 # every entry point declared in include/kkt.h
 EXPORTS = [

@@ -636,7 +636,7 @@ inline constexpr int ref_teams(int shape) {
 // The barrier of a team of tt threads working on one row: named barrier
 // `id` (1 + the team's index for a team of a block, REF_BAR_BLOCK for the
 // whole block), so the teams of a block never wait on each other.
-constexpr int REF_BAR_BLOCK = 3;
+constexpr int REF_BAR_BLOCK = 15;
 __device__ __forceinline__ void team_sync(int id, int tt) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(tt) : "memory");
 }

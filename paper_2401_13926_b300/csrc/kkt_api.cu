@@ -584,7 +584,7 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
         c->o.ortho < KKT_ORTHO_CGS2 || c->o.ortho > KKT_ORTHO_CGS1_PYTH ||
         !(c->o.inner_tol > 0.0 && c->o.inner_tol <= 1.0) || (c->o.repivot != 0 && c->o.repivot != 1) ||
         (c->o.graphs != 0 && c->o.graphs != 1) || (c->o.warp_rows != 0 && c->o.warp_rows != 1) ||
-        (c->o.row_order != 0 && c->o.row_order != 1) || c->o.mixed_fallback < 0 ||
+        (c->o.row_order < 0 || c->o.row_order > 2) || c->o.mixed_fallback < 0 ||
         (c->o.stream_last != 0 && c->o.stream_last != 1) || (c->o.team_rows != 0 && c->o.team_rows != 1) ||
         c->o.warp_row_updates < -1) {
         delete c;
@@ -767,13 +767,37 @@ int setup_rows(kkt_ctx* c) {
         else { kind[i] = kkt::ROW_GLOBAL; c->rows_global++; }
     }
     // dispatch order: by level in the DAG of L (ties by row) -- a row's
-    // dependencies are at lower levels, so they are dispatched before it
+    // dependencies are at lower levels, so they are dispatched before it;
+    // or by critical-path priority: descending bottom level, the longest
+    // path of estimated row costs from the row to the end of the DAG (a
+    // dependency's is larger than its dependents', so it still comes
+    // first), so rows on long chains get slots before rows with slack
     std::vector<int32_t> order((size_t)n);
     std::iota(order.begin(), order.end(), 0);
-    if (c->o.row_order) {
+    if (c->o.row_order == 1) {
         const std::vector<int32_t>& lev = L.levL;
         std::sort(order.begin(), order.end(),
                   [&](int32_t a, int32_t b) { return lev[a] < lev[b] || (lev[a] == lev[b] && a < b); });
+    } else if (c->o.row_order == 2) {
+        // cost of a row: its steps plus its multiply-adds / 1024 (a heavy
+        // block row's step is ~1 us with ~1,000 updates)
+        std::vector<double> w((size_t)n), bl((size_t)n);
+        for (int32_t i = 0; i < n; i++) {
+            double upd = 0.0;
+            for (int64_t p = L.Fp[i]; p < L.Fdiag[i]; p++) {
+                const int32_t k = L.Fj[p];
+                upd += (double)(L.Fp[k + 1] - L.Fdiag[k] - 1);
+            }
+            w[i] = 2.0 + (double)(L.Fdiag[i] - L.Fp[i]) + upd / 1024.0;
+            bl[i] = w[i];
+        }
+        for (int32_t r = n - 1; r >= 0; r--)   // a row's dependencies are rows before it
+            for (int64_t p = L.Fp[r]; p < L.Fdiag[r]; p++) {
+                const int32_t k = L.Fj[p];
+                bl[k] = std::max(bl[k], w[k] + bl[r]);
+            }
+        std::sort(order.begin(), order.end(),
+                  [&](int32_t a, int32_t b) { return bl[a] > bl[b] || (bl[a] == bl[b] && a < b); });
     }
     std::vector<kkt::RefItem> items;
     items.reserve((size_t)n);
