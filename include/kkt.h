@@ -404,7 +404,8 @@ int kkt_selftest_wait(kkt_ctx* c, int64_t limit);
  * call makes no cudaMalloc or cudaFree.  The first call on a device looks up
  * that array's device address (cudaGetSymbolAddress) with the device current
  * and caches it.  Every call reads its error status back and synchronises
- * the stream before it returns.  All calls on a device share the array, so
+ * the stream before it returns, so it cannot be captured into a CUDA
+ * graph.  All calls on a device share the array, so
  * calls that overlap on the GPU (other streams, other threads) race and give
  * wrong results: serialise them.  Each call re-arms the parts of the array
  * it uses (the vectors' first n entries, the tickets, the error words).

@@ -82,14 +82,15 @@ def test_row_placement_and_order_same_bits(oracle_mod, warp_rows, block_smem):
     shared memory, one per block in shared memory, one per half of a
     512-thread block (a 150 KB block makes the blocks 512 threads wide),
     one per block with the values in global memory (an 8 KB block forces
-    the longest kkt200 rows there) -- both dispatch orders (DAG level,
-    row) and both times a block row may store its last step's values (as
-    each is formed, or after the step) give the same factors, bit for bit,
-    equal to the oracle's refactorization on the same P and Q (each row's
-    arithmetic is fixed; only where and when it runs changes)."""
+    the longest kkt200 rows there) -- every dispatch order (DAG level, row,
+    critical-path priority) and both times a block row may store its last
+    step's values (as each is formed, or after the step) give the same
+    factors, bit for bit, equal to the oracle's refactorization on the same
+    P and Q (each row's arithmetic is fixed; only where and when it runs
+    changes)."""
     seq = KKTSequence("kkt200", steps=2)
     out = []
-    runs = [("row", True, True), ("level", True, True), ("level", False, True)]
+    runs = [("row", True, True), ("level", True, True), ("level", False, True), ("critical", True, True)]
     if block_smem == 150000:
         runs.append(("level", True, False))   # the same rows one per whole block
     for order, stream_last, team_rows in runs:
