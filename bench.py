@@ -650,46 +650,53 @@ def run_ours(args):
     other = None
     if not args.no_mixed:
         alt = "mixed" if args.precision == "fp64" else "fp64"
-        # FP32 factors as the preconditioner; a solve they have not finished
-        # within --mixed-cycles restart cycles continues with the FP64
-        # refactorization (kkt_opts.mixed_fallback), counted per solve
-        s2 = K.KKTSolver(restart=RESTART, device=local, stream=stream, timing=True, precision=alt,
-                         mixed_fallback=args.mixed_cycles)
-        s2.analyze_like(solver)
         nm = min(args.mixed_steps, seq.M)
         idx = [int(round(i * (seq.M - 1) / max(nm - 1, 1))) for i in range(nm)]
-        timed_steps(s2, [vals[idx[0]]], [rhs[idx[0]]], x, 1, 1, flush, stream, True)
-        s2.phase_times(reset=True)
-        ms2, it2, nr2, st2, fb2, fe2, f64 = [], [], [], [], [], [], []
         x64 = torch.empty_like(x)
-        for i in idx:   # one step at a time: each solve's fallback and forward error are read after it
-            m_, i_, n_, s_ = timed_steps(s2, [vals[i]], [rhs[i]], x, 1, 1, flush, stream, True)
-            ms2 += m_
-            it2 += i_
-            nr2 += n_
-            st2 += s_
-            fb2.append(int(s2.info()["last_fallback"]))
-            xs = seq.rhs(i, seq.values(i))[1]
-            xm = x.cpu().numpy()
-            fe2.append(float(np.linalg.norm(xm - xs) / np.linalg.norm(xs)))
-            # the FP64 path's solution of the same system (factors equal to
-            # the oracle's refactorization bit for bit), outside any timing
-            with torch.cuda.stream(stream):
-                solver.step(vals[i], rhs[i], x=x64, allow_not_converged=True)
-            stream.synchronize()
-            xf = x64.cpu().numpy()
-            f64.append(float(np.linalg.norm(xm - xf) / np.linalg.norm(xf)))
-        ph2 = s2.phase_times(reset=True)
-        other = {"precision": alt, "value": nm / (sum(ms2) / 1000.0), "unit": "solves/s", "steps": nm,
-                 "matrices": idx, "latency_ms": {"p50": float(np.percentile(ms2, 50)),
-                                                 "p99": float(np.percentile(ms2, 99))},
-                 "fp32_cycles_before_fallback": args.mixed_cycles,
-                 "iters": it2, "nrbe": [float(f"{v:.3g}") for v in nr2], "status": st2, "fell_back": fb2,
-                 "forward_error_vs_xstar": [float(f"{v:.3g}") for v in fe2],
-                 "rel_diff_vs_fp64_solution": [float(f"{v:.3g}") for v in f64],
-                 "converged": int(sum(s_ == K.OK for s_ in st2)), "max_nrbe": float(np.nanmax(nr2 + [0.0])),
-                 "phase_ms_per_step": {p: round(ph2[p][0] / nm, 4) for p in ph2}}
-        s2.close()
+        ref64 = {}   # the FP64 path's solution per matrix (factors equal to the oracle's bit for bit)
+
+        def precision_leg(equilibrate):
+            # FP32 factors as the preconditioner; a solve they have not
+            # finished within --mixed-cycles restart cycles continues with the
+            # FP64 refactorization (kkt_opts.mixed_fallback), counted per solve
+            s2 = K.KKTSolver(restart=RESTART, device=local, stream=stream, timing=True, precision=alt,
+                             mixed_fallback=args.mixed_cycles, equilibrate=equilibrate)
+            s2.analyze_like(solver)
+            timed_steps(s2, [vals[idx[0]]], [rhs[idx[0]]], x, 1, 1, flush, stream, True)
+            s2.phase_times(reset=True)
+            ms2, it2, nr2, st2, fb2, fe2, f64 = [], [], [], [], [], [], []
+            for i in idx:   # one step at a time: each solve's fallback and errors are read after it
+                m_, i_, n_, s_ = timed_steps(s2, [vals[i]], [rhs[i]], x, 1, 1, flush, stream, True)
+                ms2 += m_
+                it2 += i_
+                nr2 += n_
+                st2 += s_
+                fb2.append(int(s2.info()["last_fallback"]))
+                xs = seq.rhs(i, seq.values(i))[1]
+                xm = x.cpu().numpy()
+                fe2.append(float(np.linalg.norm(xm - xs) / np.linalg.norm(xs)))
+                if i not in ref64:   # outside any timing
+                    with torch.cuda.stream(stream):
+                        solver.step(vals[i], rhs[i], x=x64, allow_not_converged=True)
+                    stream.synchronize()
+                    ref64[i] = x64.cpu().numpy()
+                xf = ref64[i]
+                f64.append(float(np.linalg.norm(xm - xf) / np.linalg.norm(xf)))
+            ph2 = s2.phase_times(reset=True)
+            s2.close()
+            return {"precision": alt, "equilibrate": bool(equilibrate), "value": nm / (sum(ms2) / 1000.0),
+                    "unit": "solves/s", "steps": nm, "matrices": idx,
+                    "latency_ms": {"p50": float(np.percentile(ms2, 50)), "p99": float(np.percentile(ms2, 99))},
+                    "fp32_cycles_before_fallback": args.mixed_cycles,
+                    "iters": it2, "nrbe": [float(f"{v:.3g}") for v in nr2], "status": st2, "fell_back": fb2,
+                    "forward_error_vs_xstar": [float(f"{v:.3g}") for v in fe2],
+                    "rel_diff_vs_fp64_solution": [float(f"{v:.3g}") for v in f64],
+                    "converged": int(sum(s_ == K.OK for s_ in st2)), "max_nrbe": float(np.nanmax(nr2 + [0.0])),
+                    "phase_ms_per_step": {p: round(ph2[p][0] / nm, 4) for p in ph2}}
+
+        other = precision_leg(False)
+        if alt == "mixed":   # the same solves with the FP32 factors of the equilibrated matrix
+            other["equilibrated"] = precision_leg(True)
     # ---- serving: several independent sequences resident at once, their
     # steps in flight together (kkt_server_*)
     serving = None

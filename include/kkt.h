@@ -148,6 +148,14 @@ typedef struct {
                              block's shared memory are refactored one per half block
                              (two such rows at a time, 256 threads each); 0: one per
                              block.  Same arithmetic either way. */
+    int equilibrate;      /* KKT_PRECISION_MIXED only: 1 = the FP32 factors are of R K C,
+                             R and C diagonal powers of two (r_i = 2^(1-E) with max_j
+                             |a_ij| = f 2^E, f in [0.5,1); c_j the same for the columns
+                             of R K), computed on the device from each matrix, so every
+                             scaled value is exact; the preconditioner applies
+                             C (R K C)^{-1} R and kkt_get_factors returns the factors of
+                             R K C.  The FP64 fallback factors K unscaled.  0 (default)
+                             = no scaling. */
 } kkt_opts;
 
 /* Refinement methods (Section 2.1).  FGMRES: FGMRES(m) with M = LU as right

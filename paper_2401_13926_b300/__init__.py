@@ -59,7 +59,7 @@ class _Opts(C.Structure):
         ("method", C.c_int), ("ortho", C.c_int), ("inner_tol", C.c_double), ("repivot", C.c_int),
         ("graphs", C.c_int), ("warp_rows", C.c_int), ("row_order", C.c_int),
         ("warp_row_updates", C.c_int64), ("mixed_fallback", C.c_int),
-        ("stream_last", C.c_int), ("team_rows", C.c_int),
+        ("stream_last", C.c_int), ("team_rows", C.c_int), ("equilibrate", C.c_int),
     ]
 
 
@@ -299,7 +299,7 @@ def _solver_opts(restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, 
                  device=0, spin_limit=0, timing=False, trisolve="auto", block_smem=0, cluster_blocks=0,
                  precision="fp64", method="fgmres", ortho="cgs2", inner_tol=1e-6, repivot=False, graphs=False,
                  warp_rows=True, row_order="level", mixed_fallback=2, warp_row_updates=0, stream_last=True,
-                 team_rows=True):
+                 team_rows=True, equilibrate=False):
     """kkt_opts from keyword arguments (defaults of kkt_default_opts)."""
     o = _Opts()
     lib().kkt_default_opts(C.byref(o))
@@ -319,6 +319,7 @@ def _solver_opts(restart=20, max_cycles=50, stop_mode="nrbe", refine_delta=0.0, 
     o.warp_row_updates = int(warp_row_updates)
     o.stream_last = int(bool(stream_last))
     o.team_rows = int(bool(team_rows))
+    o.equilibrate = int(bool(equilibrate))
     return o
 
 
@@ -330,11 +331,12 @@ class KKTSolver:
                  boost_eps=0.0, device=0, stream=None, spin_limit=0, timing=False, trisolve="auto",
                  block_smem=0, cluster_blocks=0, precision="fp64", method="fgmres", ortho="cgs2",
                  inner_tol=1e-6, repivot=False, graphs=False, warp_rows=True, row_order="level",
-                 mixed_fallback=2, warp_row_updates=0, stream_last=True, team_rows=True):
+                 mixed_fallback=2, warp_row_updates=0, stream_last=True, team_rows=True, equilibrate=False):
         L = lib()
         o = _solver_opts(restart, max_cycles, stop_mode, refine_delta, pivot_tol, boost_eps, device, spin_limit,
                          timing, trisolve, block_smem, cluster_blocks, precision, method, ortho, inner_tol, repivot,
-                         graphs, warp_rows, row_order, mixed_fallback, warp_row_updates, stream_last, team_rows)
+                         graphs, warp_rows, row_order, mixed_fallback, warp_row_updates, stream_last, team_rows,
+                         equilibrate)
         if stream is None:
             stream = _torch_current_stream(device)
         if stream is None:

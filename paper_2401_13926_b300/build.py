@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libkkt_b300.so")
 SOURCES = [os.path.join(CSRC, f) for f in ("analysis.cpp", "kkt_api.cu", "noalloc.cu", "server.cpp")]
-DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("analysis.h", "kernels.cuh", "trsv_row.cuh")] + [os.path.join(INCLUDE, "kkt.h")]
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("analysis.h", "kernels.cuh", "trsv_row.cuh", "equilibrate.cuh")] + [os.path.join(INCLUDE, "kkt.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -12,10 +12,12 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "analysis.h"
 #include "kernels.cuh"
+#include "equilibrate.cuh"
 #include "kkt.h"
 
 using kkt::DevScal;
@@ -47,6 +49,14 @@ struct kkt_ctx {
     void* d_Fx64 = nullptr;
     void* d_rinv64 = nullptr;
     bool fallback_on = false;   // mixed and mixed_fallback > 0
+    // mixed precision with kkt_opts.equilibrate: the FP32 factors are of
+    // R K C (powers of two); the preconditioner applies C (RKC)^{-1} R
+    bool eq_on = false;
+    double* d_eq_r = nullptr;               // R (by original row)
+    double* d_eq_c = nullptr;               // C (by original column)
+    unsigned long long* d_eq_colmax = nullptr;
+    double* d_eq_vals = nullptr;            // R K C in the caller's value order
+    double* d_eq_tmp = nullptr;             // R times the right-hand side of a sweep pair
     bool fp64_active = false;   // the factors in use are the FP64 ones
     bool vec_f32 = false;       // y and xp currently hold FP32 values (their SENTINEL type)
     int last_fallback = 0;
@@ -445,8 +455,17 @@ void lu_apply_t(kkt_ctx* c, const double* rhs, double* out) {
 }
 
 void lu_apply(kkt_ctx* c, const double* rhs, double* out) {
-    if (use_f32(c)) lu_apply_t<float>(c, rhs, out);
-    else lu_apply_t<double>(c, rhs, out);
+    if (use_f32(c) && c->eq_on) {   // K^{-1} ~ C (R K C)^{-1} R
+        const int n = c->A.n, g = 2 * c->num_sms;
+        kkt::k_scale_vec<<<g, 256, 0, c->stream>>>(n, c->d_eq_r, rhs, c->d_eq_tmp);
+        lu_apply_t<float>(c, c->d_eq_tmp, out);
+        kkt::k_scale_vec<<<g, 256, 0, c->stream>>>(n, c->d_eq_c, out, out);
+        c->launches += 2;
+    } else if (use_f32(c)) {
+        lu_apply_t<float>(c, rhs, out);
+    } else {
+        lu_apply_t<double>(c, rhs, out);
+    }
 }
 
 // x = Q U^{-1} y with y already in the context (the fused forward sweep)
@@ -549,6 +568,7 @@ void kkt_default_opts(kkt_opts* o) {
     o->mixed_fallback = 2;
     o->stream_last = 1;
     o->team_rows = 1;
+    o->equilibrate = 0;
 }
 
 const char* kkt_strerror(int code) {
@@ -586,6 +606,7 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
         (c->o.graphs != 0 && c->o.graphs != 1) || (c->o.warp_rows != 0 && c->o.warp_rows != 1) ||
         (c->o.row_order < 0 || c->o.row_order > 2) || c->o.mixed_fallback < 0 ||
         (c->o.stream_last != 0 && c->o.stream_last != 1) || (c->o.team_rows != 0 && c->o.team_rows != 1) ||
+        (c->o.equilibrate != 0 && c->o.equilibrate != 1) ||
         c->o.warp_row_updates < -1) {
         delete c;
         return KKT_ERR_INVALID;
@@ -603,6 +624,7 @@ int kkt_create(kkt_ctx** out, const kkt_opts* o) {
     if (e != cudaSuccess) { delete c; return KKT_ERR_CUDA; }
     c->mixed = c->o.precision == KKT_PRECISION_MIXED;
     c->fallback_on = c->mixed && c->o.mixed_fallback > 0;
+    c->eq_on = c->mixed && c->o.equilibrate;
     int per_sm = 0, per_sm3 = 0;
     if (c->mixed) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kkt::k_lsolve_bulk<float>, PERSIST_THREADS, 0);
@@ -979,6 +1001,15 @@ int setup_from_layout(kkt_ctx* c, std::chrono::steady_clock::time_point t0) {
     }
     if ((rc = dalloc(c, &c->d_Ax, c->nnz_a))) return rc;
     if ((rc = dalloc(c, &c->d_vals, c->nnz_a))) return rc;
+    c->d_eq_r = c->d_eq_c = c->d_eq_vals = c->d_eq_tmp = nullptr;
+    c->d_eq_colmax = nullptr;
+    if (c->eq_on) {
+        if ((rc = dalloc(c, &c->d_eq_r, (size_t)n))) return rc;
+        if ((rc = dalloc(c, &c->d_eq_c, (size_t)n))) return rc;
+        if ((rc = dalloc(c, &c->d_eq_colmax, (size_t)n))) return rc;
+        if ((rc = dalloc(c, &c->d_eq_tmp, (size_t)n))) return rc;
+        if ((rc = dalloc(c, &c->d_eq_vals, c->nnz_a))) return rc;
+    }
     for (double** p : {&c->d_b, &c->d_x, &c->d_y, &c->d_xp, &c->d_r, &c->d_w})
         if ((rc = dalloc(c, p, c->ld))) return rc;
     if ((rc = dalloc(c, &c->d_V, (size_t)c->ld * (c->m + 1)))) return rc;
@@ -1099,6 +1130,7 @@ int kkt_estimate_device_bytes(int32_t n, int64_t nnz_a, const kkt_host_stats* st
     if (mixed) {
         b += sz(nnzF, 4) + sz(n, 4);                                        // Fx, rinv (FP32)
         if (o->mixed_fallback > 0) b += sz(nnzF, 8) + sz(n, 8);            // the FP64 fallback's
+        if (o->equilibrate) b += 4 * sz(n, 8) + sz(nnz_a, 8);               // R, C, column maxima, R b, R K C
     } else {
         b += sz(nnzF, 8) + sz(n, 8);
     }
@@ -1265,6 +1297,18 @@ void refactor_launch(kkt_ctx* c, const double* vals, unsigned long long* trace, 
     kkt::k_gather<T><<<2 * c->num_sms, 256, 0, c->stream>>>(vals, nnzF, fx_of<T>(c), c->d_Arp, c->d_asrc, c->d_Ax,
                                                             n, rinv_of<T>(c), c->d_s,
                                                             fused_rhs ? (T*)c->d_y : nullptr);
+    if (std::is_same<T, float>::value && c->eq_on) {
+        // R K C from the canonical copy the gather just wrote; the FP32
+        // factors are of it (the gather's ||K||_inf stays that of K)
+        const int g = 2 * c->num_sms;
+        kkt::k_eq_rows<<<g, 256, 0, c->stream>>>(n, c->d_Arp, c->d_Ax, c->d_eq_r, c->d_eq_colmax);
+        kkt::k_eq_cols<<<g, 256, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, c->d_eq_r, c->d_eq_colmax);
+        kkt::k_eq_values<<<g, 256, 0, c->stream>>>(n, c->d_Arp, c->d_Aci, c->d_Ax, c->d_asrc, c->d_eq_r,
+                                                   c->d_eq_colmax, c->d_eq_c, c->d_eq_vals);
+        c->launches += 3;
+        vals = c->d_eq_vals;
+        fused_rhs = nullptr;   // the fused sweep would need R b
+    }
     phase_end(c, t);
     t = phase_begin(c, KKT_PHASE_REFACTOR);
     if (c->ref_shape == 2) refactor_rows_launch<T, 2>(c, vals, trace, fused_rhs);
@@ -1357,6 +1401,8 @@ int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsign
         if (c->mixed) refactor_launch<float>(c, vals, trace, fused_rhs);
         else refactor_launch<double>(c, vals, trace, fused_rhs);
     }
+    // an equilibrated FP32 refactorization does not fuse the forward sweep
+    bool fused = fused_rhs != nullptr && !c->eq_on;
     CK(cudaGetLastError());
     if ((rc = read_scalars(c))) return rc;
     c->nboost = c->h_s->nboost;
@@ -1366,9 +1412,10 @@ int refactor_impl(kkt_ctx* c, const double* values, int values_on_device, unsign
         // value falls back to FP64 on the same values
         if (!(c->fallback_on && (rc == KKT_ERR_ZERO_PIVOT || rc == KKT_ERR_NONFINITE))) return rc;
         if ((rc = refactor_fp64(c, vals, fused_rhs))) return rc;
+        fused = fused_rhs != nullptr;
     }
     c->factored = true;
-    c->y_fused = fused_rhs != nullptr;
+    c->y_fused = fused;
     return KKT_OK;
 }
 }  // namespace

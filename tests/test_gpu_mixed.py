@@ -222,3 +222,59 @@ def test_mixed_step_with_fallback_equals_refactor_then_solve(oracle_mod):
         xf, i_f, nf = f.step(v, b, tol=1e-12)
         assert np.array_equal(xa, xf) and ia == i_f and na == nf, k
         assert a.info()["last_fallback"] == f.info()["last_fallback"]
+
+
+def _equilibrated(n, rowptr, colind, v):
+    """R K C as the equilibration option defines it, written out here from
+    its definition: r_i = 2^(1-E) with max_j |a_ij| = f 2^E, f in [0.5, 1)
+    (1 for an empty row), c_j the same for max_i |a_ij r_i|; returns the
+    scaled values (exact: powers of two), r and c."""
+    rows = np.repeat(np.arange(n), np.diff(np.asarray(rowptr)))
+    cols = np.asarray(colind)
+    a = np.abs(np.asarray(v, dtype=np.float64))
+    rmax = np.zeros(n)
+    np.maximum.at(rmax, rows, a)
+    r = np.where(rmax > 0, np.ldexp(1.0, 1 - np.frexp(rmax)[1]), 1.0)
+    cmax = np.zeros(n)
+    np.maximum.at(cmax, cols, a * r[rows])
+    c = np.where(cmax > 0, np.ldexp(1.0, 1 - np.frexp(cmax)[1]), 1.0)
+    assert np.all(np.abs(a * r[rows] * c[cols]) < 2.0)
+    return np.asarray(v) * r[rows] * c[cols], r, c
+
+
+@pytest.mark.parametrize("sched", ["auto", "global"])
+def test_equilibrated_fp32_factors_and_solve(oracle_mod, c1, sched):
+    """With kkt_opts.equilibrate the FP32 factors are those of R K C: equal,
+    bit for bit, to the oracle's FP32 refactorization of the scaled values
+    on the same P and Q; and kkt_lu_solve returns x = C z with z the FP32
+    triangular solve of (R K C) z = R b, within that solve's componentwise
+    backward-error bound."""
+    seq, P, Q = c1
+    s = K.KKTSolver(precision="mixed", trisolve=sched, equilibrate=True, mixed_fallback=0)
+    s.analyze(seq.rowptr, seq.colind, Q=Q, P=P)
+    rng = np.random.default_rng(11)
+    for k in (0, seq.M // 2, seq.M - 1):
+        v = seq.values(k)
+        s.refactor(v)
+        vs, r, c = _equilibrated(seq.n, seq.rowptr, seq.colind, v)
+        of = oracle_mod.refactor_f32(seq.n, seq.rowptr, seq.colind, vs, P, Q)
+        f = s.factors()
+        assert np.array_equal(f["Lx"], of.Lx), k
+        assert np.array_equal(f["Ux"], of.Ux), k
+        for b in (seq.rhs(k, v)[0], rng.standard_normal(seq.n)):
+            x = s.lu_solve(b)
+            _check_fp32_solve_bound(seq.n, f, P, Q, r * b, np.asarray(x) / c)
+
+
+def test_equilibrated_mixed_solves_meet_tolerance_kkt200(oracle_mod, c1):
+    """Every mixed solve of the kkt200 sequence with equilibration (and the
+    FP64 fallback rule) ends at NRBE <= 1e-12 as the oracle evaluates it."""
+    seq, P, Q = c1
+    s = K.KKTSolver(precision="mixed", equilibrate=True)
+    s.analyze(seq.rowptr, seq.colind, Q=Q, P=P)
+    for k in range(seq.M):
+        v = seq.values(k)
+        b, _ = seq.rhs(k, v)
+        x, it, nr = s.step(v, b, tol=1e-12)
+        on = oracle_mod.nrbe(seq.n, seq.rowptr, seq.colind, v, b, x)
+        assert on <= 1e-12 * (1 + 1e-6), (k, on, it)
