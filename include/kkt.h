@@ -195,7 +195,7 @@ typedef struct {
 #define KKT_PHASE_SPMV 4      /* products with K and residuals */
 #define KKT_PHASE_ORTHO 5     /* CGS2 passes, normalisation, Givens */
 #define KKT_PHASE_UPDATE 6    /* cycle start and end (v_0, y = R^{-1} g, x += Z y) */
-#define KKT_PHASE_REFACTOR_TAIL 7  /* reserved (the refactorization is one kernel: KKT_PHASE_REFACTOR) */
+#define KKT_PHASE_RESERVED 7  /* unused (the refactorization is one kernel: KKT_PHASE_REFACTOR) */
 #define KKT_PHASE_GRAPH_REFACTOR 8 /* a whole refactorization replayed as a graph (kkt_opts.graphs) */
 #define KKT_PHASE_GRAPH_SOLVE 9    /* a whole solve replayed as a graph (kkt_opts.graphs) */
 #define KKT_NUM_PHASES 10

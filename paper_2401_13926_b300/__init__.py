@@ -46,7 +46,7 @@ EXPORTS = [
     "kkt_estimate_device_bytes", "kkt_place_instance",
 ]
 NOALLOC_MAX_N = 65536
-PHASES = ["gather", "refactor", "lsolve", "usolve", "spmv", "ortho", "update", "refactor_tail", "graph_refactor",
+PHASES = ["gather", "refactor", "lsolve", "usolve", "spmv", "ortho", "update", "reserved", "graph_refactor",
           "graph_solve"]
 
 
