@@ -70,7 +70,8 @@ def test_device_bytes_estimate_is_exact():
     memory kkt_analyze then holds, in each precision."""
     seq = KKTSequence("kkt200", steps=1)
     P, Q, st = K.host_analyze(seq.rowptr, seq.colind, seq.values(0))
-    for kw in (dict(), dict(precision="mixed"), dict(precision="mixed", mixed_fallback=0), dict(restart=10)):
+    for kw in (dict(), dict(precision="mixed"), dict(precision="mixed", mixed_fallback=0), dict(restart=10),
+               dict(precision="mixed", equilibrate=True)):
         s = K.KKTSolver(**kw)
         s.analyze(seq.rowptr, seq.colind, Q=Q, P=P)
         est = K.estimate_device_bytes(seq.n, seq.nnz, st, canonical_order=bool(st["canonical_order"]), **kw)
